@@ -1,0 +1,296 @@
+/*
+ * warpspeed.h -- C ABI of libwarpspeed, a GB300 (sm_103a) implementation of the
+ * data-volume hot path of the Warpspeed metric estimator (Ernst et al., "Analytical
+ * Performance Estimation during Code Generation on Modern GPUs").
+ *
+ * For every code-generation candidate the library evaluates the address expression
+ * of every thread of a representative thread block and of a wave of co-resident
+ * blocks (Sec. 3.2-3.4), collapses the addresses to unique 32 B sectors and 128 B
+ * lines, derives bank-conflict cycles (Sec. 3.2), L1/L2/DRAM volumes per lattice
+ * update with layer-condition reuse (Sec. 3.4.2) and capacity misses (Sec. 3.5), and
+ * combines them in the four-limiter performance model (Sec. 2) into a predicted time
+ * and a ranking (Sec. 5.7).
+ *
+ * Conventions
+ *   - All structs are plain C with natural alignment; sizes are fixed (see the
+ *     static asserts in the implementation).
+ *   - Unless stated otherwise pointers are HOST pointers owned by the caller; the
+ *     library copies what it needs before returning and never keeps them.
+ *   - Every call returns a status: WS_OK (0) or a negative WS_E* code.  Per-candidate
+ *     problems are reported in ws_result.status and do not fail the call.
+ *   - A ws_ctx binds one CUDA device.  It is not thread safe, except that one
+ *     ws_server may run on it while the owner thread makes no other call.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     context's own stream).
+ *   - Address expressions are affine (Sec. 1.2): for a thread whose grid point is p,
+ *     access (o, dc) of field f touches the byte
+ *         align + elem_bytes * (stride . (p + o) + const_off + dc)
+ *     i.e. the unknown base pointer is replaced by the field alignment (Sec. 3.3).
+ */
+#ifndef WARPSPEED_H
+#define WARPSPEED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WS_VERSION 1
+
+/* ---- status codes --------------------------------------------------------------- */
+#define WS_OK 0
+#define WS_EINVAL (-1)     /* malformed argument or descriptor                           */
+#define WS_ENOMEM (-2)     /* does not fit the context's device-memory budget            */
+#define WS_EAGAIN (-3)     /* server: request not finished yet                           */
+#define WS_ETIMEDOUT (-4)  /* a bounded wait (host or device) ran out                    */
+#define WS_EOVERFLOW (-5)  /* a counting structure overflowed (never silent)             */
+#define WS_ECUDA (-6)      /* a CUDA runtime call failed                                 */
+#define WS_ENOTFOUND (-7)  /* unknown request id                                         */
+#define WS_ECANCELED (-8)  /* server shut down before the request ran                    */
+
+/* ---- modes of ws_plan_execute / ws_estimate_batch ---------------------------------- */
+#define WS_MODE_PLAIN 0    /* one synchronous launch sequence per candidate               */
+#define WS_MODE_BATCHED 1  /* one persistent launch over all candidates, CUDA graph replay */
+#define WS_MODE_DIRECT 2   /* the batched kernels launched directly (no graph)            */
+
+/* ---- limiters (ws_result.limiter, Sec. 2) ------------------------------------------ */
+#define WS_LIMITER_L1 0    /* L1 <-> register cycles (bank conflicts)                     */
+#define WS_LIMITER_L2 1    /* L2 <-> L1 bandwidth                                         */
+#define WS_LIMITER_DRAM 2  /* DRAM <-> L2 bandwidth                                       */
+#define WS_LIMITER_FP 3    /* floating-point throughput                                   */
+
+/* One relative access of a field (Sec. 1.2, 3.3): grid offset (dx, dy, dz) from the
+ * updated point, plus an extra element offset dc (components of AoS layouts).
+ * is_store: 0 = load, 1 = store.  |dx|,|dy|,|dz| <= 65535, |dc| < 2^40. */
+typedef struct ws_access {
+  int32_t dx, dy, dz;
+  int32_t is_store;
+  int64_t dc;
+} ws_access; /* 24 bytes */
+
+/* One array.  Fields never alias (Sec. 3.3): sectors are counted per field and then
+ * summed.  elem_bytes in 1..64; stride[d] in elements (|stride| < 2^40, any sign);
+ * align_bytes replaces the base pointer (|align| < 2^50, any value, negative allowed);
+ * the field's accesses are acc[access_off .. access_off + n_access). */
+typedef struct ws_field {
+  int32_t elem_bytes;
+  int32_t n_access;
+  int64_t align_bytes;
+  int64_t stride[3];
+  int64_t const_off;
+  int64_t access_off;
+} ws_field; /* 56 bytes */
+
+/* One candidate (Sec. 5.1): domain N (points), thread-block shape B, thread folding
+ * (fold_axis 0 = none, 1 = y, 2 = z; each thread updates `fold` consecutive points
+ * along that axis, fold in 1..16, fold == 1 when fold_axis == 0), its fields
+ * fld[field_off .. field_off + n_field), flops per lattice update (0 = no FP limiter),
+ * registers per thread (0 = not limiting; Sec. 5.1 LBM remark), and an optional wave
+ * size in blocks (0 = SMs x resident blocks per SM).  Limits: 1 <= N[d] <= 2^20,
+ * B[0]*B[1]*B[2] <= 1024, B[2] <= 64, grid blocks < 2^31. */
+typedef struct ws_config {
+  int32_t N[3];
+  int32_t B[3];
+  int32_t fold_axis;
+  int32_t fold;
+  int32_t n_field;
+  int32_t regs_per_thread;
+  int64_t field_off;
+  double flops_per_lup;
+  int32_t wave_blocks_override;
+  int32_t reserved; /* must be 0 */
+} ws_config; /* 64 bytes */
+
+/* Modelled GPU (Table 1 of the paper; the A100-SXM4-40G column with a 20 MB effective
+ * L2 is the reference setting).  Rates in bytes/s, flop/s and Hz; sizes in bytes.
+ * hit[i] = (a, b, c) of the capacity hit-rate fit R(O) = a*exp(-b*exp(-c*O))
+ * (Sec. 3.5) for i = 0 L1 redundant loads, 1 L2 y-layer overlap, 2 L2 z-layer
+ * overlap, 3 L2 redundant stores.  capacity_model = 0 sets every R to 1. */
+typedef struct ws_hw {
+  int32_t sms, max_threads_sm, max_blocks_sm, regs_sm;
+  double clock_hz, l1_bytes, l2_bytes, bw_l2, bw_dram, fp_peak;
+  int32_t banks, bank_bytes, pair_dist_bytes, capacity_model;
+  double hit[4][3];
+} ws_hw; /* 176 bytes */
+
+/* Result of one candidate.  The int64 part is exact (it is what the parity tests
+ * compare bit for bit); volumes are bytes per lattice update (LUP), o_* are
+ * oversubscription factors, t_* are seconds per LUP for the whole GPU. */
+typedef struct ws_result {
+  int64_t lups_block, lups_wave;              /* valid lattice updates of block / wave   */
+  int64_t l1_req_sectors;                     /* sum over warp x load instr of unique sectors */
+  int64_t l1_bank_cycles;                     /* sum over half-warp x instr of wavefronts */
+  int64_t l1_store_sectors;                   /* sum over warp x store instr of unique sectors */
+  int64_t blk_load_sectors, blk_load_lines;   /* unique in the representative block     */
+  int64_t blk_store_sectors, blk_store_lines;
+  int64_t wave_load_sectors, wave_load_lines; /* unique in the representative wave      */
+  int64_t wave_store_sectors, wave_store_lines;
+  int64_t wave_store_req_sectors;             /* sum over wave warps x store instr       */
+  int64_t ov_y, ov_z;                         /* wave footprint shared with the y / z sets */
+  int64_t y_lines, z_lines;                   /* footprint lines of the y / z sets        */
+  int64_t wave_blocks, wave_first_block;      /* representative wave [first, first+blocks) */
+  int64_t y_dist_blocks, z_dist_blocks;       /* blocks scheduled since the y / z set start */
+  int64_t blocks_per_sm;
+  double v_l1, v_l2_load, v_l2_store, v_dram_load, v_dram_store;
+  double o_l1, o_y, o_z, o_st;
+  double t_l1, t_l2, t_dram, t_fp, t_pred, glups;
+  int32_t limiter;                            /* WS_LIMITER_*                            */
+  int32_t status;                             /* WS_OK or WS_E*                          */
+} ws_result; /* 312 bytes */
+
+/* Tuning of the batched kernels (picked by ws_autotune; zeros = defaults). */
+typedef struct ws_tuning {
+  int32_t chunk_warps;     /* modelled warps per enumeration work item                   */
+  int32_t enum_threads;    /* threads per CTA of the enumeration kernel (128..1024)      */
+  int32_t count_words;     /* bitmap words per counting work item                        */
+  int32_t ctas_per_sm;     /* persistent CTAs per SM (0 = occupancy limit)               */
+} ws_tuning;
+
+/* Per-kernel device time of one profiled step (CUDA events on the launch stream). */
+typedef struct ws_profile {
+  float ms_total, ms_enum, ms_count, ms_model, ms_rank;
+  int32_t launches;          /* kernels launched by the step                             */
+  int64_t enum_items, count_items;
+  int64_t warp_instr;        /* modelled (warp, access) pairs evaluated                  */
+  int64_t addresses;         /* valid (thread, access) address evaluations               */
+  int64_t bitmap_bytes;      /* bitmap bytes read + cleared by the counting kernel        */
+  int64_t passes;            /* scratch passes the plan needed                            */
+  int64_t upload_bytes;      /* descriptor bytes the plan copied host -> device           */
+} ws_profile;
+
+typedef struct ws_ctx ws_ctx;
+typedef struct ws_plan ws_plan;
+typedef struct ws_server ws_server;
+
+int ws_version(void);
+const char *ws_status_string(int status);
+/* Text of the last CUDA or allocation failure seen by the calling thread. */
+const char *ws_last_error(void);
+
+/* Default modelled hardware: A100-SXM4-40G (Table 1, 20 MB effective L2, Sec. 4),
+ * illustrative hit-rate coefficients (the paper prints none). */
+void ws_hw_a100(ws_hw *hw);
+
+/* Binds `device`.  arena / arena_bytes: a caller-owned DEVICE buffer used for all
+ * device memory of the context (descriptors, bitmaps, results); arena == NULL makes
+ * the library allocate arena_bytes itself.  The arena is the memory budget. */
+int ws_create(ws_ctx **ctx, int device, void *arena, size_t arena_bytes);
+int ws_destroy(ws_ctx *ctx);
+
+/* Compiles n_cfg candidates into device-resident descriptors (host descriptor
+ * compiler: grid, representative block and wave, y/z sets, folded access lists,
+ * bitmap ranges; Sec. 3.2-3.4) and reserves their scratch.  cfgs[i].field_off indexes
+ * fld[0..n_fld), fld[j].access_off indexes acc[0..n_acc).  seg_begin (n_seg + 1
+ * entries, ascending, seg_begin[0] = 0, seg_begin[n_seg] = n_cfg) splits the
+ * candidates into independently ranked lists; NULL = one list.  tuning may be NULL.
+ * Malformed candidates get status WS_EINVAL in their result; the call still
+ * succeeds.  WS_ENOMEM if one field's scratch alone exceeds the arena. */
+int ws_plan_create(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                   const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin,
+                   int n_seg, const ws_tuning *tuning, ws_plan **plan);
+/* Runs one full estimation step on the device (enumeration, counting, model,
+ * ranking) in `mode`; results stay on the device.  Asynchronous except in
+ * WS_MODE_PLAIN, which synchronises after every candidate. */
+int ws_plan_execute(ws_plan *plan, int mode, void *stream);
+/* Copies results (n_cfg) and ranking (n_cfg indices; per segment, ascending predicted
+ * time, ties by index) to host arrays and synchronises `stream`.  Either may be NULL. */
+int ws_plan_results(ws_plan *plan, ws_result *out, int32_t *order, void *stream);
+/* Device pointers of the plan's result and order arrays (valid until destroy). */
+int ws_plan_device_results(ws_plan *plan, ws_result **results, int32_t **order);
+/* Runs one direct step with CUDA events around each kernel and synchronises. */
+int ws_plan_profile(ws_plan *plan, void *stream, ws_profile *out);
+/* Tries a small grid of tunings on this plan, keeps the fastest (also returned). */
+int ws_autotune(ws_plan *plan, void *stream, ws_tuning *best);
+int ws_plan_destroy(ws_plan *plan);
+
+/* ---- host-only introspection of the descriptor compiler (no GPU needed) ------------ */
+typedef struct ws_cfg_info {
+  int32_t status;                 /* WS_OK or the candidate's WS_E* status               */
+  int32_t grid[3];                /* thread-block grid (after folding)                   */
+  int32_t threads, warps_per_block, blocks_per_sm, n_field;
+  int64_t total_blocks, rep_block;            /* representative block: grid middle      */
+  int64_t wave_first, wave_blocks;            /* representative wave (Sec. 3.4)         */
+  int64_t y_lo, y_hi, z_lo, z_hi;             /* y / z layer-set candidate block ranges */
+  int64_t y_dist, z_dist;                     /* blocks since the first y / z set block */
+  int64_t modelled_warps;                     /* warps enumerated per loaded field      */
+  int64_t folded_loads, folded_stores;        /* folded instructions, summed over fields */
+  int64_t scratch_bytes;                      /* bitmap bytes of the candidate          */
+} ws_cfg_info; /* 144 bytes */
+
+typedef struct ws_field_info {
+  int64_t lo_sector[2];     /* first sector of the block [0] and wave/y/z [1] bitmaps    */
+  int64_t words[2];         /* 32-bit words of each of those bitmaps                     */
+  int32_t n_load, n_store;  /* folded load / store instructions                          */
+} ws_field_info; /* 40 bytes */
+
+/* Compiles candidates on the host only and reports what the device would run
+ * (Sec. 3.3-3.4 thread groups).  out: n_cfg entries.  Returns WS_EINVAL on a bad
+ * argument; per-candidate problems go to out[i].status. */
+int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
+                const ws_hw *hw, ws_cfg_info *out);
+/* Per-field bitmap ranges of one candidate; out holds cfg->n_field entries. */
+int ws_describe_fields(const ws_config *cfg, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
+                       const ws_hw *hw, ws_field_info *out);
+
+/* One-shot estimate from host buffers: plan_create + execute + results + destroy.
+ * out: n_cfg results; order_out (may be NULL): ranking of the whole batch. */
+int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                      const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
+                      int32_t *order_out, int mode, void *stream);
+
+/* Stable ranking on the device (Sec. 5.7): ascending t_pred rounded to 40
+ * significant bits, ties by index; NaN ranks as +inf.  res: n host results. */
+int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_out, void *stream);
+/* The rank key: t rounded to 40 significant mantissa bits, half to even. */
+double ws_rank_key(double t);
+
+/* Measures, on the context's GPU, the two rates that bound the enumeration kernel:
+ * 32-bit integer adds per second (8 independent add chains per thread, all SMs) and
+ * L2 red.or operations per second on distinct words of a 64 MiB buffer.  Used as the
+ * roofline denominators of the benchmark. */
+int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_red_per_s);
+
+/* ---- continuous-batching server ---------------------------------------------------- */
+typedef struct ws_server_opts {
+  size_t mem_budget;        /* bytes of the arena the server may hold (0 = whole arena)  */
+  int32_t max_inflight;     /* concurrent device steps (streams), 1..8                   */
+  int32_t max_step_cfgs;    /* candidates admitted into one step (and per request)       */
+  int32_t max_queue;        /* pending requests before submit fails with WS_EAGAIN       */
+  int32_t reserved;
+} ws_server_opts;
+
+/* One estimation request: a candidate list of one stencil (same layout rules as
+ * ws_plan_create); the whole list is ranked as one segment. */
+typedef struct ws_request {
+  const ws_config *cfgs;
+  int32_t n_cfg;
+  int32_t n_fld;
+  const ws_field *fld;
+  const ws_access *acc;
+  int32_t n_acc;
+  int32_t reserved;
+} ws_request;
+
+typedef struct ws_server_stats {
+  int64_t submitted, completed, rejected, steps, configs_done;
+  int64_t bytes_in_use, peak_bytes;
+  int32_t inflight_steps, queued;
+} ws_server_stats;
+
+int ws_server_create(ws_ctx *ctx, const ws_server_opts *opts, const ws_hw *hw, ws_server **srv);
+/* Copies the request and queues it; returns at once.  WS_ENOMEM if the request can
+ * never fit the budget, WS_EAGAIN if the queue is full. */
+int ws_server_submit(ws_server *srv, const ws_request *req, uint64_t *req_id);
+/* Waits up to timeout_us (0 = just test) for the request; on WS_OK copies its n_cfg
+ * results (and ranking, may be NULL) and forgets it.  WS_EAGAIN if not finished. */
+int ws_server_poll(ws_server *srv, uint64_t req_id, ws_result *out, int32_t *order, int64_t timeout_us);
+int ws_server_stats_get(ws_server *srv, ws_server_stats *out);
+/* Finishes every admitted step, cancels queued requests, joins the worker. */
+int ws_server_destroy(ws_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WARPSPEED_H */

@@ -1,0 +1,88 @@
+// Host-side objects of libwarpspeed (context, arena, plan), shared by ws_plan.cpp
+// and ws_server.cpp.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "warpspeed.h"
+#include "ws_internal.h"
+
+namespace ws {
+
+// First-fit allocator over one device buffer; offsets are 256-byte aligned.
+struct Arena {
+  char *base;
+  size_t size;
+  size_t in_use = 0, peak = 0;
+  std::map<size_t, size_t> free_, used_;
+  std::mutex mu;
+  Arena(char *b, size_t n);
+  int64_t alloc(size_t bytes);  // offset, or -1
+  void release(int64_t off);
+  size_t largest_free();
+  size_t used();
+};
+
+void set_error(const std::string &s);
+const char *last_error();
+
+}  // namespace ws
+
+struct ws_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int l2_bytes = 0;
+  bool owns_arena = false;
+  ws::Arena *arena = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+};
+
+struct ws_plan {
+  ws_ctx *ctx = nullptr;
+  int n_cfg = 0, n_seg = 1;
+  ws_hw hw;
+  ws::DHw dhw;
+  ws_tuning tune;
+  std::vector<ws::DField> hfld;
+  std::vector<int64_t> need_words;
+  std::vector<int32_t> cfg_cf_begin;
+  std::vector<ws::DPass> passes;
+  int64_t scratch_words = 0;
+  size_t scratch_bytes = 0;
+  int64_t item_begin_end = 0, citem_begin_end = 0;
+  size_t grab_bytes = 0, counters_bytes = 0;
+  int64_t upload_bytes = 0;
+  int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
+          d_order = -1, d_scratch = -1;
+  std::vector<int64_t> allocs;
+  bool ext_scratch = false;  // scratch lent by a server pool (kept zeroed by the counting kernel)
+  cudaGraphExec_t graph_exec = nullptr;
+
+  void *dev(int64_t off) const;
+  int64_t take(size_t bytes);
+  void release_all();
+  void layout();
+  int upload_fields(cudaStream_t st);
+  int grid_for(int threads, int64_t items, bool counting) const;
+  int enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof);
+  int run_plain(cudaStream_t st);
+  int execute(int mode, cudaStream_t st);
+};
+
+namespace ws {
+using Plan = ::ws_plan;
+
+int plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                      int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes);
+int plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                     const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
+                     const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,
+                     int64_t ext_scratch, size_t ext_scratch_bytes);
+void tuning_cache_lookup(ws_ctx *ctx, int n_cfg, ws_tuning *t);
+void tuning_cache_store(ws_ctx *ctx, int n_cfg, const ws_tuning &t);
+}  // namespace ws

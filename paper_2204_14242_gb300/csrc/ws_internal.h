@@ -1,0 +1,90 @@
+// Internal layouts shared by the host descriptor compiler (ws_plan.cpp) and the
+// kernels (ws_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+
+#include "warpspeed.h"
+
+namespace ws {
+
+// Exact integer counters accumulated per candidate by the kernels (int64 atomics).
+enum Counter {
+  C_LUPS_BLOCK, C_LUPS_WAVE, C_L1_REQ, C_BANK, C_L1_STORE,
+  C_BLK_LS, C_BLK_LL, C_BLK_SS, C_BLK_SL,
+  C_W_LS, C_W_LL, C_W_SS, C_W_SL, C_W_SREQ,
+  C_OV_Y, C_OV_Z, C_Y_LINES, C_Z_LINES,
+  C_ADDR,      // valid address evaluations (diagnostic, for the roofline)
+  C_WINSTR,    // modelled (warp, access) pairs (diagnostic)
+  C_OVERFLOW,  // bitmap indices outside the bitmap (skipped; the candidate fails)
+  N_COUNTERS
+};
+
+// Bitmaps of one field, in order: block loads, block stores, wave loads, y-set loads,
+// z-set loads, wave stores.  Bit i of a bitmap stands for sector (lo + i).
+enum Bitmap { BM_BL, BM_BS, BM_W, BM_Y, BM_Z, BM_WS, N_BITMAPS };
+
+// Thread groups of one candidate, flattened into one index space of "modelled warps":
+//   level 0: the representative block      [0, lev_end[0])
+//   level 1: the representative wave       [lev_end[0], lev_end[1])
+//   level 2: y-set candidate blocks        [lev_end[1], lev_end[2])
+//   level 3: z-set candidate blocks        [lev_end[2], lev_end[3])
+struct DCfg {
+  int32_t N[3];
+  int32_t B[3];
+  int32_t fold_axis, fold;
+  int32_t g[3];           // grid in blocks
+  int32_t T, wpb;         // threads per block, warps per block
+  int32_t n_field, field_begin;
+  int32_t bpsm, status;
+  int64_t rep;            // representative block id (X-Y-Z order)
+  int64_t s, weff;        // wave = [s, s + weff)
+  int64_t y_lo, y_hi;     // y-set candidates [y_lo, y_hi): kept iff by != g[1]-1
+  int64_t z_lo, z_hi;     // z-set candidates: kept iff not in the y set
+  int64_t y_dist, z_dist; // s - first block of the y / z set (0 if empty)
+  int64_t lev_end[4];
+  double flops;
+  int64_t pad[1];
+};
+
+struct DField {
+  int64_t base;           // align + elem_bytes * const_off  (bytes)
+  int64_t stride[3];      // elements
+  int64_t lo[2];          // first sector of the block bitmaps [0] / wave bitmaps [1]
+  int64_t words[2];       // 32-bit words per block bitmap [0] / wave bitmap [1]
+  int64_t bm[N_BITMAPS];  // word offset of each bitmap in the pass scratch, -1 = absent
+  int64_t item_begin;     // first enumeration work item (global numbering)
+  int64_t citem_begin;    // first counting work item
+  int64_t mw_end;         // modelled warps this field visits (loads: all levels, stores: block + wave)
+  int32_t esize;
+  int32_t n_load, n_store;// folded access counts (loads first, then stores)
+  int32_t acc_begin;      // index into the DAcc array
+  int32_t cfg;            // owning candidate
+  int32_t first_of_cfg;   // 1 if this is the candidate's first field (counts LUPs)
+};
+
+// One folded access: byte offset from the thread's first point, and the smallest
+// folded point index k that needs it (issued iff k < number of valid points).
+struct DAcc {
+  int64_t boff;
+  int32_t kmin;
+  int32_t pad;
+};
+
+struct DHw {
+  double clock_hz, l1_bytes, l2_bytes, bw_l2, bw_dram, fp_peak;
+  double hit[4][3];
+  int32_t sms, banks, bank_bytes, pair_dist_bytes, capacity_model, pad;
+};
+
+// One pass = a contiguous range of (candidate, field) pairs whose bitmaps fit the
+// scratch together.  Passes run one after the other and reuse the same scratch.
+struct DPass {
+  int64_t item_lo, item_hi;    // enumeration items of the pass
+  int64_t citem_lo, citem_hi;  // counting items of the pass
+  int32_t cf_lo, cf_hi;        // (candidate, field) index range
+};
+
+constexpr int kMaxFoldedAccesses = 2048;   // per field, staged in shared memory
+constexpr int64_t kMaxBitmapWords = (int64_t)1 << 31;
+
+}  // namespace ws

@@ -1,0 +1,56 @@
+// Kernel argument blocks and launchers (implemented in ws_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ws_internal.h"
+
+namespace ws {
+
+struct EnumArgs {
+  const DCfg *cfg;
+  const DField *fld;
+  const DAcc *acc;
+  uint32_t *scratch;               // bitmaps of the pass
+  int64_t *counters;               // [n_cfg][N_COUNTERS]
+  unsigned long long *grab;        // work-stealing counter (zeroed before the launch)
+  int64_t item_lo, item_hi;        // enumeration items of the pass
+  int32_t cf_lo, cf_hi;            // (candidate, field) range of the pass
+  int32_t chunk;                   // modelled warps per item
+  int32_t banks, bank_bytes, pair_dist;
+};
+
+struct CountArgs {
+  const DField *fld;
+  uint32_t *scratch;
+  int64_t *counters;
+  unsigned long long *grab;
+  int64_t citem_lo, citem_hi;
+  int32_t cf_lo, cf_hi;
+  int32_t chunk_words;             // multiple of 4
+};
+
+struct ModelArgs {
+  const DCfg *cfg;
+  const int64_t *counters;
+  ws_result *results;
+  double *keys;                    // rank keys (t_pred rounded to 40 bits)
+  int32_t n;
+  DHw hw;
+};
+
+struct RankArgs {
+  const double *keys;
+  const int32_t *seg;              // n_seg + 1 segment starts
+  int32_t *order;
+  int32_t n, n_seg;
+};
+
+cudaError_t launch_enum(const EnumArgs &args, int grid, int threads, cudaStream_t st);
+cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st);
+cudaError_t launch_model(const ModelArgs &args, cudaStream_t st);
+cudaError_t launch_rank(const RankArgs &args, cudaStream_t st);
+cudaError_t launch_keys(const ws_result *res, int n, double *keys, cudaStream_t st);
+cudaError_t enum_occupancy(int threads, int *blocks_per_sm);
+cudaError_t count_occupancy(int *blocks_per_sm);
+
+}  // namespace ws

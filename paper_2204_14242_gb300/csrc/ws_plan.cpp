@@ -1,0 +1,1174 @@
+// Host side of libwarpspeed: context and device arena, descriptor compiler, plans
+// (passes, CUDA-graph capture, plain / batched execution), profiling, autotuning,
+// ranking.  See warpspeed.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <set>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ws_host.h"
+#include "ws_internal.h"
+#include "ws_kernels.h"
+
+static_assert(sizeof(ws_access) == 24, "ws_access layout");
+static_assert(sizeof(ws_field) == 56, "ws_field layout");
+static_assert(sizeof(ws_config) == 64, "ws_config layout");
+static_assert(sizeof(ws_hw) == 176, "ws_hw layout");
+static_assert(sizeof(ws_result) == 312, "ws_result layout");
+static_assert(sizeof(ws_cfg_info) == 144, "ws_cfg_info layout");
+static_assert(sizeof(ws_field_info) == 40, "ws_field_info layout");
+
+namespace ws {
+
+// ---------------------------------------------------------------------------------
+// device arena: first-fit allocator over one device buffer (the memory budget)
+// ---------------------------------------------------------------------------------
+Arena::Arena(char *b, size_t n) : base(b), size(n) { free_[0] = n; }
+
+int64_t Arena::alloc(size_t bytes) {
+  std::lock_guard<std::mutex> g(mu);
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second >= bytes) {
+      size_t off = it->first, rem = it->second - bytes;
+      free_.erase(it);
+      if (rem) free_[off + bytes] = rem;
+      used_[off] = bytes;
+      in_use += bytes;
+      peak = std::max(peak, in_use);
+      return (int64_t)off;
+    }
+  }
+  return -1;
+}
+
+void Arena::release(int64_t off) {
+  if (off < 0) return;
+  std::lock_guard<std::mutex> g(mu);
+  auto u = used_.find((size_t)off);
+  if (u == used_.end()) return;
+  size_t o = u->first, n = u->second;
+  used_.erase(u);
+  in_use -= n;
+  auto nx = free_.lower_bound(o);
+  if (nx != free_.end() && o + n == nx->first) {
+    n += nx->second;
+    nx = free_.erase(nx);
+  }
+  if (nx != free_.begin()) {
+    auto pv = std::prev(nx);
+    if (pv->first + pv->second == o) {
+      pv->second += n;
+      return;
+    }
+  }
+  free_[o] = n;
+}
+
+size_t Arena::largest_free() {
+  std::lock_guard<std::mutex> g(mu);
+  size_t m = 0;
+  for (auto &kv : free_) m = std::max(m, kv.second);
+  return m;
+}
+
+size_t Arena::used() {
+  std::lock_guard<std::mutex> g(mu);
+  return in_use;
+}
+
+// ---------------------------------------------------------------------------------
+// descriptor compiler
+// ---------------------------------------------------------------------------------
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static int64_t floor_div128(__int128 a, int64_t b) {
+  __int128 q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+  return (int64_t)q;
+}
+
+// Inclusive block-coordinate box of the contiguous block-id range [a, b), b > a.
+static void block_box(int64_t a, int64_t b, const int64_t g[3], int64_t lo[3], int64_t hi[3]) {
+  int64_t last = b - 1;
+  int64_t za = a / (g[0] * g[1]), zb = last / (g[0] * g[1]);
+  lo[2] = za;
+  hi[2] = zb;
+  if (za == zb) {
+    lo[1] = (a / g[0]) % g[1];
+    hi[1] = (last / g[0]) % g[1];
+  } else {
+    lo[1] = 0;
+    hi[1] = g[1] - 1;
+  }
+  if (a / g[0] == last / g[0]) {
+    lo[0] = a % g[0];
+    hi[0] = last % g[0];
+  } else {
+    lo[0] = 0;
+    hi[0] = g[0] - 1;
+  }
+}
+
+struct Compiled {
+  DCfg d{};
+  std::vector<DField> f;
+  std::vector<std::vector<DAcc>> acc;
+  std::vector<int64_t> need_words;  // bitmap words per field
+};
+
+typedef std::tuple<int64_t, int64_t, int64_t, int64_t> Off4;
+
+// Returns WS_OK or a per-candidate error status.
+static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
+                          const ws_hw &hw, Compiled &out) {
+  DCfg &d = out.d;
+  memset(&d, 0, sizeof(d));
+  for (int k = 0; k < 3; ++k) {
+    if (c.N[k] < 1 || c.N[k] > (1 << 20) || c.B[k] < 1) return WS_EINVAL;
+    d.N[k] = c.N[k];
+    d.B[k] = c.B[k];
+  }
+  const int64_t T = (int64_t)c.B[0] * c.B[1] * c.B[2];
+  if (T > 1024 || c.B[2] > 64) return WS_EINVAL;
+  if (c.fold_axis < 0 || c.fold_axis > 2 || c.fold < 1 || c.fold > 16) return WS_EINVAL;
+  if (c.fold_axis == 0 && c.fold != 1) return WS_EINVAL;
+  if (c.n_field < 1 || c.field_off < 0 || c.field_off + c.n_field > n_fld) return WS_EINVAL;
+  if (c.regs_per_thread < 0 || c.wave_blocks_override < 0) return WS_EINVAL;
+  if (!(c.flops_per_lup >= 0.0) || std::isinf(c.flops_per_lup)) return WS_EINVAL;
+  d.fold_axis = c.fold_axis;
+  d.fold = c.fold;
+  const int64_t fy = c.fold_axis == 1 ? c.fold : 1, fz = c.fold_axis == 2 ? c.fold : 1;
+  const int64_t g[3] = {ceil_div(c.N[0], c.B[0]), ceil_div(c.N[1], c.B[1] * fy), ceil_div(c.N[2], c.B[2] * fz)};
+  const int64_t total = g[0] * g[1] * g[2];
+  if (total >= ((int64_t)1 << 31)) return WS_EINVAL;
+  for (int k = 0; k < 3; ++k) d.g[k] = (int32_t)g[k];
+  d.T = (int32_t)T;
+  d.wpb = (int32_t)ceil_div(T, 32);
+  // resident blocks per SM: thread slots are allocated per warp
+  int64_t bpsm = std::min<int64_t>(hw.max_blocks_sm, hw.max_threads_sm / (32 * (int64_t)d.wpb));
+  if (c.regs_per_thread > 0)
+    bpsm = std::min<int64_t>(bpsm, hw.regs_sm / ((int64_t)c.regs_per_thread * 32 * d.wpb));
+  if (bpsm < 1) return WS_EINVAL;
+  d.bpsm = (int32_t)bpsm;
+  d.flops = c.flops_per_lup;
+
+  // representative block (middle of the grid) and wave (X-Y-Z scheduling order)
+  const int64_t W = c.wave_blocks_override > 0 ? c.wave_blocks_override : (int64_t)hw.sms * bpsm;
+  const int64_t weff = std::min(W, total);
+  const int64_t rep = g[0] / 2 + g[0] * (g[1] / 2 + g[1] * (g[2] / 2));
+  int64_t s = W * (rep / W);
+  s = std::min(s, total - weff);
+  d.rep = rep;
+  d.s = s;
+  d.weff = weff;
+  // y set: wave shifted back one block row, minus the wave: [y_lo, y_hi) with by != gy-1
+  int64_t y_lo = std::max<int64_t>(0, s - g[0]), y_hi = std::min(s, s + weff - g[0]);
+  if (y_hi <= y_lo || g[1] == 1) y_lo = y_hi = 0;
+  // z set: wave shifted back one block slab, minus the wave and the y set
+  int64_t z_lo = std::max<int64_t>(0, s - g[0] * g[1]), z_hi = std::min(s, s + weff - g[0] * g[1]);
+  if (z_hi <= z_lo) z_lo = z_hi = 0;
+  d.y_lo = y_lo; d.y_hi = y_hi; d.z_lo = z_lo; d.z_hi = z_hi;
+  auto in_y = [&](int64_t b) { return b >= y_lo && b < y_hi && (b / g[0]) % g[1] != g[1] - 1; };
+  // first block of the y set
+  int64_t y_first = -1;
+  if (y_hi > y_lo) {
+    if ((y_lo / g[0]) % g[1] != g[1] - 1) y_first = y_lo;
+    else if ((y_lo / g[0] + 1) * g[0] < y_hi) y_first = (y_lo / g[0] + 1) * g[0];
+  }
+  // first block of the z set: z_lo itself, the first block of a row gy-1 at or after
+  // z_lo, or the first block after the y range
+  int64_t z_first = -1;
+  if (z_hi > z_lo) {
+    if (!in_y(z_lo)) {
+      z_first = z_lo;
+    } else {
+      int64_t q0 = z_lo / g[0];
+      int64_t q = q0 + ((g[1] - 1 - q0 % g[1]) % g[1] + g[1]) % g[1];
+      int64_t cand1 = std::max(z_lo, q * g[0]);
+      int64_t cand2 = y_hi;
+      int64_t best = -1;
+      if (cand1 < z_hi) best = cand1;
+      if (cand2 < z_hi && (best < 0 || cand2 < best)) best = cand2;
+      z_first = best;
+    }
+  }
+  d.y_dist = y_first >= 0 ? s - y_first : 0;
+  d.z_dist = z_first >= 0 ? s - z_first : 0;
+  const int64_t wpb = d.wpb;
+  d.lev_end[0] = wpb;
+  d.lev_end[1] = d.lev_end[0] + weff * wpb;
+  d.lev_end[2] = d.lev_end[1] + (y_hi - y_lo) * wpb;
+  d.lev_end[3] = d.lev_end[2] + (z_hi - z_lo) * wpb;
+
+  // point boxes (valid points only) of the block level and of wave + y + z
+  int64_t pb_lo[2][3], pb_hi[2][3];
+  {
+    int64_t bl[3] = {rep % g[0], (rep / g[0]) % g[1], rep / (g[0] * g[1])};
+    for (int k = 0; k < 3; ++k) {
+      int64_t f = (k == 1 ? fy : k == 2 ? fz : 1) * c.B[k];
+      pb_lo[0][k] = bl[k] * f;
+      pb_hi[0][k] = std::min<int64_t>(c.N[k] - 1, (bl[k] + 1) * f - 1);
+    }
+    int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1};
+    const int64_t ranges[3][2] = {{s, s + weff}, {y_lo, y_hi}, {z_lo, z_hi}};
+    for (auto &r : ranges) {
+      if (r[1] <= r[0]) continue;
+      int64_t bl2[3], bh2[3];
+      block_box(r[0], r[1], g, bl2, bh2);
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], bl2[k]);
+        hi[k] = std::max(hi[k], bh2[k]);
+      }
+    }
+    for (int k = 0; k < 3; ++k) {
+      int64_t f = (k == 1 ? fy : k == 2 ? fz : 1) * c.B[k];
+      pb_lo[1][k] = lo[k] * f;
+      pb_hi[1][k] = std::min<int64_t>(c.N[k] - 1, (hi[k] + 1) * f - 1);
+    }
+  }
+
+  // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps
+  out.f.clear();
+  out.acc.clear();
+  out.need_words.clear();
+  for (int fi = 0; fi < c.n_field; ++fi) {
+    const ws_field &F = fld[c.field_off + fi];
+    if (F.elem_bytes < 1 || F.elem_bytes > 64 || F.n_access < 1 || F.access_off < 0 ||
+        F.access_off + F.n_access > n_acc)
+      return WS_EINVAL;
+    for (int k = 0; k < 3; ++k)
+      if (std::llabs(F.stride[k]) >= ((int64_t)1 << 40)) return WS_EINVAL;
+    if (std::llabs(F.align_bytes) >= ((int64_t)1 << 50) || std::llabs(F.const_off) >= ((int64_t)1 << 40))
+      return WS_EINVAL;
+    std::set<Off4> L, S;
+    for (int a = 0; a < F.n_access; ++a) {
+      const ws_access &A = acc[F.access_off + a];
+      if (std::abs(A.dx) > 65535 || std::abs(A.dy) > 65535 || std::abs(A.dz) > 65535 ||
+          std::llabs(A.dc) >= ((int64_t)1 << 40) || (A.is_store != 0 && A.is_store != 1))
+        return WS_EINVAL;
+      (A.is_store ? S : L).insert(Off4(A.dx, A.dy, A.dz, A.dc));
+    }
+    auto fold_list = [&](const std::set<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
+      std::map<Off4, int> kmin;
+      for (const Off4 &o : src)
+        for (int k = 0; k < c.fold; ++k) {
+          Off4 q = o;
+          if (c.fold_axis == 1) std::get<1>(q) += k;
+          if (c.fold_axis == 2) std::get<2>(q) += k;
+          auto it = kmin.find(q);
+          if (it == kmin.end() || k < it->second) kmin[q] = k;
+        }
+      for (auto &kv : kmin) dst.push_back(kv);
+    };
+    std::vector<std::pair<Off4, int>> fl, fs;
+    fold_list(L, fl);
+    fold_list(S, fs);
+    if ((int64_t)(fl.size() + fs.size()) > kMaxFoldedAccesses) return WS_EINVAL;
+
+    DField df;
+    memset(&df, 0, sizeof(df));
+    df.esize = F.elem_bytes;
+    for (int k = 0; k < 3; ++k) df.stride[k] = F.stride[k];
+    df.base = F.align_bytes + (int64_t)F.elem_bytes * F.const_off;
+    df.n_load = (int32_t)fl.size();
+    df.n_store = (int32_t)fs.size();
+    std::vector<DAcc> da;
+    auto off_elems = [&](const Off4 &o) -> __int128 {
+      return (__int128)F.stride[0] * std::get<0>(o) + (__int128)F.stride[1] * std::get<1>(o) +
+             (__int128)F.stride[2] * std::get<2>(o) + std::get<3>(o);
+    };
+    for (auto *lst : {&fl, &fs})
+      for (auto &kv : *lst) {
+        DAcc x;
+        x.boff = (int64_t)(off_elems(kv.first) * F.elem_bytes);
+        x.kmin = kv.second;
+        x.pad = 0;
+        da.push_back(x);
+      }
+    // An issued folded access o' of a thread whose first point is p0 touches the same
+    // address as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e,
+    // so valid points x raw offsets bound every address of the field.
+    __int128 omin = 0, omax = 0;
+    bool first = true;
+    for (auto *src : {&L, &S})
+      for (const Off4 &o : *src) {
+        __int128 e = off_elems(o);
+        if (first || e < omin) omin = e;
+        if (first || e > omax) omax = e;
+        first = false;
+      }
+    // address range of each level: valid point box x raw offsets
+    for (int lv = 0; lv < 2; ++lv) {
+      __int128 pmin = 0, pmax = 0;
+      for (int k = 0; k < 3; ++k) {
+        __int128 a0 = (__int128)F.stride[k] * pb_lo[lv][k], a1 = (__int128)F.stride[k] * pb_hi[lv][k];
+        pmin += std::min(a0, a1);
+        pmax += std::max(a0, a1);
+      }
+      __int128 amin = (__int128)df.base + (__int128)F.elem_bytes * (pmin + omin);
+      __int128 amax = (__int128)df.base + (__int128)F.elem_bytes * (pmax + omax);
+      if (amin < -((__int128)1 << 60) || amax > ((__int128)1 << 60)) return WS_EINVAL;
+      int64_t lo = floor_div128(amin, 1024) * 32;
+      int64_t hi = floor_div128(amax, 32);
+      int64_t words = ceil_div(hi - lo + 1, 32);
+      words = (words + 3) & ~(int64_t)3;
+      if (words > kMaxBitmapWords) return WS_ENOMEM;
+      df.lo[lv] = lo;
+      df.words[lv] = words;
+    }
+    const bool has_l = df.n_load > 0, has_s = df.n_store > 0;
+    df.mw_end = has_l ? d.lev_end[3] : d.lev_end[1];
+    df.first_of_cfg = fi == 0;
+    for (int k = 0; k < N_BITMAPS; ++k) df.bm[k] = -1;
+    int64_t need = 0;
+    if (has_l) need += df.words[0] + 3 * df.words[1];
+    if (has_s) need += df.words[0] + df.words[1];
+    out.f.push_back(df);
+    out.acc.push_back(da);
+    out.need_words.push_back(need);
+  }
+  d.n_field = c.n_field;
+  return WS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// last-error text
+// ---------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void set_error(const std::string &s) { g_last_error = s; }
+const char *last_error() { return g_last_error.c_str(); }
+
+#define CU(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+      return WS_ECUDA;                                                                 \
+    }                                                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------------
+static DHw to_dhw(const ws_hw &h) {
+  DHw d;
+  memset(&d, 0, sizeof(d));
+  d.clock_hz = h.clock_hz;
+  d.l1_bytes = h.l1_bytes;
+  d.l2_bytes = h.l2_bytes;
+  d.bw_l2 = h.bw_l2;
+  d.bw_dram = h.bw_dram;
+  d.fp_peak = h.fp_peak;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 3; ++j) d.hit[i][j] = h.hit[i][j];
+  d.sms = h.sms;
+  d.banks = h.banks;
+  d.bank_bytes = h.bank_bytes;
+  d.pair_dist_bytes = h.pair_dist_bytes;
+  d.capacity_model = h.capacity_model;
+  return d;
+}
+
+static bool hw_valid(const ws_hw &h) {
+  return h.sms >= 1 && h.max_threads_sm >= 32 && h.max_blocks_sm >= 1 && h.regs_sm >= 1 && h.banks >= 1 &&
+         h.bank_bytes >= 1 && h.pair_dist_bytes >= 1 && h.clock_hz > 0 && h.l1_bytes > 0 && h.l2_bytes > 0 &&
+         h.bw_l2 > 0 && h.bw_dram > 0 && h.fp_peak >= 0 && std::isfinite(h.clock_hz) && std::isfinite(h.bw_l2) &&
+         std::isfinite(h.bw_dram);
+}
+
+}  // namespace ws
+
+using namespace ws;
+
+void *ws_plan::dev(int64_t off) const { return ctx->arena->base + off; }
+
+void ws_plan::release_all() {
+  for (int64_t o : allocs) ctx->arena->release(o);
+  allocs.clear();
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  graph_exec = nullptr;
+}
+
+int64_t ws_plan::take(size_t bytes) {
+  int64_t o = ctx->arena->alloc(bytes);
+  if (o >= 0) allocs.push_back(o);
+  return o;
+}
+
+static void default_tuning(ws_tuning &t) {
+  if (t.chunk_warps <= 0) t.chunk_warps = 64;
+  if (t.enum_threads <= 0) t.enum_threads = 256;
+  if (t.count_words <= 0) t.count_words = 16384;
+  t.enum_threads = std::max(64, std::min(1024, t.enum_threads / 32 * 32));
+  t.count_words = std::max(256, t.count_words / 4 * 4);
+  t.chunk_warps = std::max(1, t.chunk_warps);
+}
+
+// Numbers work items and cuts passes for the current tuning.
+void ws_plan::layout() {
+  passes.clear();
+  int64_t items = 0, citems = 0, used = 0;
+  DPass cur{0, 0, 0, 0, 0, 0};
+  const int ncf = (int)hfld.size();
+  for (int cf = 0; cf < ncf; ++cf) {
+    DField &f = hfld[cf];
+    int64_t need = need_words[cf];
+    if (used + need > scratch_words && cf > cur.cf_lo) {
+      cur.cf_hi = cf;
+      cur.item_hi = items;
+      cur.citem_hi = citems;
+      passes.push_back(cur);
+      cur = DPass{items, 0, citems, 0, cf, 0};
+      used = 0;
+    }
+    int64_t o = used;
+    const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
+    for (int k = 0; k < N_BITMAPS; ++k) f.bm[k] = -1;
+    if (has_l) {
+      f.bm[BM_BL] = o; o += f.words[0];
+      f.bm[BM_W] = o; o += f.words[1];
+      f.bm[BM_Y] = o; o += f.words[1];
+      f.bm[BM_Z] = o; o += f.words[1];
+    }
+    if (has_s) {
+      f.bm[BM_BS] = o; o += f.words[0];
+      f.bm[BM_WS] = o; o += f.words[1];
+    }
+    used = o;
+    f.item_begin = items;
+    f.citem_begin = citems;
+    items += ceil_div(f.mw_end, tune.chunk_warps);
+    citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
+  }
+  cur.cf_hi = ncf;
+  cur.item_hi = items;
+  cur.citem_hi = citems;
+  if (ncf > 0) passes.push_back(cur);
+  item_begin_end = items;
+  citem_begin_end = citems;
+}
+
+int ws_plan::upload_fields(cudaStream_t st) {
+  if (!hfld.empty()) CU(cudaMemcpyAsync(dev(d_fld), hfld.data(), hfld.size() * sizeof(DField), cudaMemcpyHostToDevice, st));
+  if (graph_exec) {
+    cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+  }
+  return WS_OK;
+}
+
+int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
+  int occ = 1;
+  if (counting) count_occupancy(&occ);
+  else enum_occupancy(threads, &occ);
+  if (tune.ctas_per_sm > 0) occ = std::min(occ, tune.ctas_per_sm);
+  occ = std::max(occ, 1);
+  int64_t g = (int64_t)ctx->sm_count * occ;
+  g = std::min<int64_t>(g, std::max<int64_t>(items, 1));
+  return (int)g;
+}
+
+// Enqueues one batched step (all passes, model, rank) on `st`; `ev` (may be null)
+// receives events [start, after enum_k, after count_k ..., after model, after rank].
+int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof) {
+  auto mark = [&](int k) -> int {
+    if (ev) CU(cudaEventRecord((*ev)[k], st));
+    return WS_OK;
+  };
+  int rc;
+  if ((rc = mark(0)) != WS_OK) return rc;
+  CU(cudaMemsetAsync(dev(d_counters), 0, counters_bytes, st));
+  int launches = 0;
+  for (size_t p = 0; p < passes.size(); ++p) {
+    const DPass &P = passes[p];
+    EnumArgs ea;
+    ea.cfg = (const DCfg *)dev(d_cfg);
+    ea.fld = (const DField *)dev(d_fld);
+    ea.acc = (const DAcc *)dev(d_acc);
+    ea.scratch = (uint32_t *)dev(d_scratch);
+    ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
+    ea.grab = (unsigned long long *)dev(d_counters) + 2 * p;
+    ea.item_lo = P.item_lo;
+    ea.item_hi = P.item_hi;
+    ea.cf_lo = P.cf_lo;
+    ea.cf_hi = P.cf_hi;
+    ea.chunk = tune.chunk_warps;
+    ea.banks = hw.banks;
+    ea.bank_bytes = hw.bank_bytes;
+    ea.pair_dist = hw.pair_dist_bytes;
+    if (P.item_hi > P.item_lo) {
+      CU(launch_enum(ea, grid_for(tune.enum_threads, P.item_hi - P.item_lo, false), tune.enum_threads, st));
+      ++launches;
+    }
+    if ((rc = mark(1 + 2 * (int)p)) != WS_OK) return rc;
+    CountArgs ca;
+    ca.fld = ea.fld;
+    ca.scratch = ea.scratch;
+    ca.counters = ea.counters;
+    ca.grab = ea.grab + 1;
+    ca.citem_lo = P.citem_lo;
+    ca.citem_hi = P.citem_hi;
+    ca.cf_lo = P.cf_lo;
+    ca.cf_hi = P.cf_hi;
+    ca.chunk_words = tune.count_words;
+    if (P.citem_hi > P.citem_lo) {
+      CU(launch_count(ca, grid_for(256, P.citem_hi - P.citem_lo, true), st));
+      ++launches;
+    }
+    if ((rc = mark(2 + 2 * (int)p)) != WS_OK) return rc;
+  }
+  ModelArgs ma;
+  ma.cfg = (const DCfg *)dev(d_cfg);
+  ma.counters = (const int64_t *)((char *)dev(d_counters) + grab_bytes);
+  ma.results = (ws_result *)dev(d_results);
+  ma.keys = (double *)dev(d_keys);
+  ma.n = n_cfg;
+  ma.hw = dhw;
+  CU(launch_model(ma, st));
+  launches += n_cfg > 0;
+  if ((rc = mark(1 + 2 * (int)passes.size())) != WS_OK) return rc;
+  RankArgs ra;
+  ra.keys = (const double *)dev(d_keys);
+  ra.seg = (const int32_t *)dev(d_seg);
+  ra.order = (int32_t *)dev(d_order);
+  ra.n = n_cfg;
+  ra.n_seg = n_seg;
+  CU(launch_rank(ra, st));
+  launches += n_cfg > 0;
+  if ((rc = mark(2 + 2 * (int)passes.size())) != WS_OK) return rc;
+  if (prof) prof->launches = launches;
+  return WS_OK;
+}
+
+// Plain form: for every candidate, its own enumeration / counting / model launches,
+// then a synchronisation; the ranking runs once at the end.
+int ws_plan::run_plain(cudaStream_t st) {
+  CU(cudaMemsetAsync(dev(d_counters), 0, counters_bytes, st));
+  int64_t *counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
+  unsigned long long *grab = (unsigned long long *)dev(d_counters);
+  for (int i = 0; i < n_cfg; ++i) {
+    const int cf_a = cfg_cf_begin[i], cf_b = cfg_cf_begin[i + 1];
+    for (size_t p = 0; p < passes.size() && cf_a < cf_b; ++p) {
+      const DPass &P = passes[p];
+      const int lo = std::max(cf_a, P.cf_lo), hi = std::min(cf_b, P.cf_hi);
+      if (lo >= hi) continue;
+      const int64_t it_lo = hfld[lo].item_begin, it_hi = hi < (int)hfld.size() ? hfld[hi].item_begin : item_begin_end;
+      const int64_t ct_lo = hfld[lo].citem_begin, ct_hi = hi < (int)hfld.size() ? hfld[hi].citem_begin : citem_begin_end;
+      CU(cudaMemsetAsync(grab, 0, 2 * sizeof(unsigned long long), st));
+      EnumArgs ea;
+      ea.cfg = (const DCfg *)dev(d_cfg);
+      ea.fld = (const DField *)dev(d_fld);
+      ea.acc = (const DAcc *)dev(d_acc);
+      ea.scratch = (uint32_t *)dev(d_scratch);
+      ea.counters = counters;
+      ea.grab = grab;
+      ea.item_lo = it_lo;
+      ea.item_hi = it_hi;
+      ea.cf_lo = lo;
+      ea.cf_hi = hi;
+      ea.chunk = tune.chunk_warps;
+      ea.banks = hw.banks;
+      ea.bank_bytes = hw.bank_bytes;
+      ea.pair_dist = hw.pair_dist_bytes;
+      if (it_hi > it_lo) CU(launch_enum(ea, grid_for(tune.enum_threads, it_hi - it_lo, false), tune.enum_threads, st));
+      CountArgs ca;
+      ca.fld = ea.fld;
+      ca.scratch = ea.scratch;
+      ca.counters = counters;
+      ca.grab = grab + 1;
+      ca.citem_lo = ct_lo;
+      ca.citem_hi = ct_hi;
+      ca.cf_lo = lo;
+      ca.cf_hi = hi;
+      ca.chunk_words = tune.count_words;
+      if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(256, ct_hi - ct_lo, true), st));
+    }
+    ModelArgs ma;
+    ma.cfg = (const DCfg *)dev(d_cfg) + i;
+    ma.counters = counters + (int64_t)i * N_COUNTERS;
+    ma.results = (ws_result *)dev(d_results) + i;
+    ma.keys = (double *)dev(d_keys) + i;
+    ma.n = 1;
+    ma.hw = dhw;
+    CU(launch_model(ma, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  RankArgs ra;
+  ra.keys = (const double *)dev(d_keys);
+  ra.seg = (const int32_t *)dev(d_seg);
+  ra.order = (int32_t *)dev(d_order);
+  ra.n = n_cfg;
+  ra.n_seg = n_seg;
+  CU(launch_rank(ra, st));
+  return WS_OK;
+}
+
+int ws_plan::execute(int mode, cudaStream_t st) {
+  if (mode == WS_MODE_PLAIN) return run_plain(st);
+  if (mode == WS_MODE_DIRECT) return enqueue(st, nullptr, nullptr);
+  if (mode != WS_MODE_BATCHED) {
+    set_error("unknown mode");
+    return WS_EINVAL;
+  }
+  if (!graph_exec) {
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue(ctx->capture_stream, nullptr, nullptr);
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (rc != WS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CU(e);
+    e = cudaGraphInstantiate(&graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CU(e);
+  }
+  CU(cudaGraphLaunch(graph_exec, st));
+  return WS_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------
+extern "C" int ws_version(void) { return WS_VERSION; }
+
+extern "C" const char *ws_status_string(int s) {
+  switch (s) {
+    case WS_OK: return "ok";
+    case WS_EINVAL: return "invalid argument or descriptor";
+    case WS_ENOMEM: return "does not fit the device-memory budget";
+    case WS_EAGAIN: return "not finished yet";
+    case WS_ETIMEDOUT: return "bounded wait ran out";
+    case WS_EOVERFLOW: return "counting structure overflow";
+    case WS_ECUDA: return "CUDA runtime error";
+    case WS_ENOTFOUND: return "unknown request";
+    case WS_ECANCELED: return "canceled";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char *ws_last_error(void) { return last_error(); }
+
+extern "C" void ws_hw_a100(ws_hw *h) {
+  if (!h) return;
+  memset(h, 0, sizeof(*h));
+  h->sms = 108;
+  h->max_threads_sm = 2048;
+  h->max_blocks_sm = 32;
+  h->regs_sm = 65536;
+  h->clock_hz = 1.41e9;
+  h->l1_bytes = 192.0 * 1024;
+  h->l2_bytes = 20.0 * 1024 * 1024;
+  h->bw_l2 = 5000e9;
+  h->bw_dram = 1400e9;
+  h->fp_peak = 4.9e12;
+  h->banks = 16;
+  h->bank_bytes = 8;
+  h->pair_dist_bytes = 1024;
+  h->capacity_model = 1;
+  const double hit[4][3] = {{1.0, 0.01, -3.07}, {1.0, 0.05, -2.0}, {1.0, 0.01, -3.07}, {1.0, 0.01, -3.07}};
+  memcpy(h->hit, hit, sizeof(hit));
+}
+
+extern "C" int ws_create(ws_ctx **out, int device, void *arena, size_t arena_bytes) {
+  if (!out || arena_bytes < (1 << 20)) return WS_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return WS_EINVAL;
+  CU(cudaSetDevice(device));
+  ws_ctx *c = new ws_ctx();
+  c->device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete c;
+    return WS_ECUDA;
+  }
+  c->sm_count = prop.multiProcessorCount;
+  c->l2_bytes = prop.l2CacheSize;
+  char *base = (char *)arena;
+  if (!base) {
+    if (cudaMalloc((void **)&base, arena_bytes) != cudaSuccess) {
+      delete c;
+      set_error("cudaMalloc of the arena failed");
+      return WS_ENOMEM;
+    }
+    c->owns_arena = true;
+  }
+  c->arena = new Arena(base, arena_bytes);
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (c->owns_arena) cudaFree(base);
+    delete c->arena;
+    delete c;
+    return WS_ECUDA;
+  }
+  *out = c;
+  return WS_OK;
+}
+
+extern "C" int ws_destroy(ws_ctx *c) {
+  if (!c) return WS_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaStreamDestroy(c->stream);
+  cudaStreamDestroy(c->capture_stream);
+  if (c->owns_arena) cudaFree(c->arena->base);
+  delete c->arena;
+  delete c;
+  return WS_OK;
+}
+
+static cudaStream_t pick_stream(ws_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
+
+// Bytes of device memory a plan of these candidates needs with one pass.
+int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                          int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes) {
+  size_t dsc = 0, scr = 0;
+  for (int i = 0; i < n_cfg; ++i) {
+    Compiled cc;
+    if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc) != WS_OK) continue;
+    for (size_t k = 0; k < cc.f.size(); ++k) {
+      dsc += sizeof(DField) + cc.acc[k].size() * sizeof(DAcc);
+      scr += (size_t)cc.need_words[k] * 4;
+    }
+  }
+  dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4) + 64 * 1024;
+  *desc_bytes = dsc;
+  *scratch_bytes = scr;
+  return WS_OK;
+}
+
+int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                         const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
+                         const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,
+                         int64_t ext_scratch, size_t ext_scratch_bytes) {
+  if (!ctx || !out || !hw || n_cfg < 0 || n_fld < 0 || n_acc < 0) return WS_EINVAL;
+  if (n_cfg > 0 && (!cfgs || (n_fld > 0 && !fld) || (n_acc > 0 && !acc))) return WS_EINVAL;
+  if (!hw_valid(*hw)) return WS_EINVAL;
+  *out = nullptr;
+  CU(cudaSetDevice(ctx->device));
+  std::vector<int32_t> seg;
+  if (seg_begin && n_seg > 0) {
+    if (seg_begin[0] != 0 || seg_begin[n_seg] != n_cfg) return WS_EINVAL;
+    for (int k = 0; k < n_seg; ++k)
+      if (seg_begin[k + 1] < seg_begin[k]) return WS_EINVAL;
+    seg.assign(seg_begin, seg_begin + n_seg + 1);
+  } else {
+    seg = {0, n_cfg};
+    n_seg = 1;
+  }
+  Plan *p = new Plan();
+  p->ctx = ctx;
+  p->n_cfg = n_cfg;
+  p->n_seg = n_seg;
+  p->hw = *hw;
+  p->dhw = to_dhw(*hw);
+  memset(&p->tune, 0, sizeof(p->tune));
+  if (tuning) p->tune = *tuning;
+  else ws::tuning_cache_lookup(ctx, n_cfg, &p->tune);
+  default_tuning(p->tune);
+
+  std::vector<DCfg> hcfg(n_cfg);
+  std::vector<DAcc> hacc;
+  p->cfg_cf_begin.assign(n_cfg + 1, 0);
+  std::vector<Compiled> comp(n_cfg);
+  std::vector<int> status(n_cfg, WS_OK);
+  for (int i = 0; i < n_cfg; ++i) status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, comp[i]);
+  // scratch capacity: what the arena can give after the descriptors
+  size_t dsc = 64 * 1024, total_need = 0, max_field = 0;
+  for (int i = 0; i < n_cfg; ++i) {
+    if (status[i] != WS_OK) continue;
+    for (size_t k = 0; k < comp[i].f.size(); ++k) {
+      dsc += sizeof(DField) + comp[i].acc[k].size() * sizeof(DAcc);
+      total_need += (size_t)comp[i].need_words[k] * 4;
+      max_field = std::max(max_field, (size_t)comp[i].need_words[k] * 4);
+    }
+  }
+  dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4);
+  size_t avail = ctx->arena->largest_free();
+  avail = avail > dsc + (8 << 20) ? avail - dsc - (8 << 20) : 0;
+  if (ext_scratch >= 0) avail = ext_scratch_bytes;
+  if (scratch_cap) avail = std::min(avail, scratch_cap);
+  size_t scratch = std::min(total_need, avail);
+  scratch = std::max<size_t>(scratch, 16);
+  for (int i = 0; i < n_cfg; ++i) {
+    if (status[i] != WS_OK) continue;
+    for (int64_t w : comp[i].need_words)
+      if ((size_t)w * 4 > scratch) status[i] = WS_ENOMEM;
+  }
+  for (int i = 0; i < n_cfg; ++i) {
+    DCfg &d = hcfg[i];
+    if (status[i] == WS_OK) {
+      d = comp[i].d;
+    } else {
+      memset(&d, 0, sizeof(d));
+    }
+    d.status = status[i];
+    d.field_begin = (int32_t)p->hfld.size();
+    p->cfg_cf_begin[i] = (int32_t)p->hfld.size();
+    if (status[i] == WS_OK) {
+      for (size_t k = 0; k < comp[i].f.size(); ++k) {
+        DField f = comp[i].f[k];
+        f.cfg = i;
+        f.acc_begin = (int32_t)hacc.size();
+        hacc.insert(hacc.end(), comp[i].acc[k].begin(), comp[i].acc[k].end());
+        p->hfld.push_back(f);
+        p->need_words.push_back(comp[i].need_words[k]);
+      }
+    } else {
+      d.n_field = 0;
+    }
+  }
+  p->cfg_cf_begin[n_cfg] = (int32_t)p->hfld.size();
+  p->scratch_words = (int64_t)(scratch / 4);
+  p->layout();
+
+  // device buffers
+  p->grab_bytes = 16 * std::max<size_t>(p->passes.size(), 1);
+  p->counters_bytes = p->grab_bytes + (size_t)n_cfg * N_COUNTERS * 8;
+  p->d_cfg = p->take(std::max<size_t>(hcfg.size() * sizeof(DCfg), 256));
+  p->d_fld = p->take(std::max<size_t>(p->hfld.size() * sizeof(DField), 256));
+  p->d_acc = p->take(std::max<size_t>(hacc.size() * sizeof(DAcc), 256));
+  p->d_seg = p->take((seg.size()) * sizeof(int32_t));
+  p->d_counters = p->take(p->counters_bytes);
+  p->d_results = p->take(std::max<size_t>((size_t)n_cfg * sizeof(ws_result), 256));
+  p->d_keys = p->take(std::max<size_t>((size_t)n_cfg * sizeof(double), 256));
+  p->d_order = p->take(std::max<size_t>((size_t)n_cfg * sizeof(int32_t), 256));
+  if (ext_scratch >= 0) {
+    p->d_scratch = ext_scratch;
+    p->ext_scratch = true;
+  } else {
+    p->d_scratch = p->take(scratch);
+  }
+  for (int64_t o : {p->d_cfg, p->d_fld, p->d_acc, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
+                    p->d_scratch}) {
+    if (o < 0) {
+      p->release_all();
+      delete p;
+      set_error("arena exhausted while creating a plan");
+      return WS_ENOMEM;
+    }
+  }
+  cudaStream_t st = upload ? upload : ctx->stream;
+  int rc = WS_OK;
+  auto fail = [&](cudaError_t e) {
+    set_error(std::string("plan upload: ") + cudaGetErrorString(e));
+    p->release_all();
+    delete p;
+    return WS_ECUDA;
+  };
+  cudaError_t e;
+  if (n_cfg && (e = cudaMemcpyAsync(p->dev(p->d_cfg), hcfg.data(), hcfg.size() * sizeof(DCfg), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if (!hacc.empty() && (e = cudaMemcpyAsync(p->dev(p->d_acc), hacc.data(), hacc.size() * sizeof(DAcc), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(p->dev(p->d_seg), seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if (!p->ext_scratch && (e = cudaMemsetAsync(p->dev(p->d_scratch), 0, scratch, st)) != cudaSuccess) return fail(e);
+  if ((rc = p->upload_fields(st)) != WS_OK) {
+    p->release_all();
+    delete p;
+    return rc;
+  }
+  if (!upload && (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+  p->scratch_bytes = scratch;
+  p->upload_bytes = (int64_t)(hcfg.size() * sizeof(DCfg) + p->hfld.size() * sizeof(DField) +
+                              hacc.size() * sizeof(DAcc) + seg.size() * sizeof(int32_t));
+  *out = p;
+  return WS_OK;
+}
+
+extern "C" int ws_plan_create(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                              const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
+                              const ws_tuning *tuning, ws_plan **plan) {
+  return plan_create_impl(ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, seg_begin, n_seg, tuning, 0, plan, nullptr,
+                          -1, 0);
+}
+
+extern "C" int ws_plan_execute(ws_plan *p, int mode, void *stream) {
+  if (!p) return WS_EINVAL;
+  CU(cudaSetDevice(p->ctx->device));
+  return p->execute(mode, pick_stream(p->ctx, stream));
+}
+
+extern "C" int ws_plan_results(ws_plan *p, ws_result *out, int32_t *order, void *stream) {
+  if (!p) return WS_EINVAL;
+  CU(cudaSetDevice(p->ctx->device));
+  cudaStream_t st = pick_stream(p->ctx, stream);
+  if (out && p->n_cfg) CU(cudaMemcpyAsync(out, p->dev(p->d_results), (size_t)p->n_cfg * sizeof(ws_result), cudaMemcpyDeviceToHost, st));
+  if (order && p->n_cfg) CU(cudaMemcpyAsync(order, p->dev(p->d_order), (size_t)p->n_cfg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return WS_OK;
+}
+
+extern "C" int ws_plan_device_results(ws_plan *p, ws_result **res, int32_t **order) {
+  if (!p) return WS_EINVAL;
+  if (res) *res = (ws_result *)p->dev(p->d_results);
+  if (order) *order = (int32_t *)p->dev(p->d_order);
+  return WS_OK;
+}
+
+extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
+  if (!p || !out) return WS_EINVAL;
+  CU(cudaSetDevice(p->ctx->device));
+  cudaStream_t st = pick_stream(p->ctx, stream);
+  memset(out, 0, sizeof(*out));
+  const int nev = 3 + 2 * (int)p->passes.size();
+  std::vector<cudaEvent_t> ev(nev);
+  for (auto &e : ev) CU(cudaEventCreate(&e));
+  int rc = p->enqueue(st, &ev, out);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == WS_OK && e == cudaSuccess) {
+    float ms = 0;
+    const int np = (int)p->passes.size();
+    for (int k = 0; k < np; ++k) {
+      cudaEventElapsedTime(&ms, ev[k == 0 ? 0 : 2 * k], ev[1 + 2 * k]);
+      out->ms_enum += ms;
+      cudaEventElapsedTime(&ms, ev[1 + 2 * k], ev[2 + 2 * k]);
+      out->ms_count += ms;
+    }
+    cudaEventElapsedTime(&ms, ev[2 * np], ev[1 + 2 * np]);
+    out->ms_model = ms;
+    cudaEventElapsedTime(&ms, ev[1 + 2 * np], ev[2 + 2 * np]);
+    out->ms_rank = ms;
+    cudaEventElapsedTime(&ms, ev[0], ev[2 + 2 * np]);
+    out->ms_total = ms;
+    out->enum_items = p->item_begin_end;
+    out->count_items = p->citem_begin_end;
+    out->passes = (int64_t)p->passes.size();
+    out->upload_bytes = p->upload_bytes;
+    std::vector<int64_t> cnt((size_t)p->n_cfg * N_COUNTERS);
+    if (p->n_cfg)
+      e = cudaMemcpy(cnt.data(), (char *)p->dev(p->d_counters) + p->grab_bytes, cnt.size() * 8, cudaMemcpyDeviceToHost);
+    for (int i = 0; i < p->n_cfg; ++i) {
+      out->addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR];
+      out->warp_instr += cnt[(size_t)i * N_COUNTERS + C_WINSTR];
+    }
+    int64_t bm = 0;
+    for (size_t k = 0; k < p->hfld.size(); ++k) bm += p->need_words[k] * 4;
+    out->bitmap_bytes = 2 * bm;
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (rc != WS_OK) return rc;
+  CU(e);
+  return WS_OK;
+}
+
+extern "C" int ws_plan_destroy(ws_plan *p) {
+  if (!p) return WS_EINVAL;
+  cudaSetDevice(p->ctx->device);
+  cudaStreamSynchronize(p->ctx->stream);
+  p->release_all();
+  delete p;
+  return WS_OK;
+}
+
+extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
+  if (!p) return WS_EINVAL;
+  CU(cudaSetDevice(p->ctx->device));
+  cudaStream_t st = pick_stream(p->ctx, stream);
+  const ws_tuning orig = p->tune;
+  ws_tuning win = orig;
+  float win_ms = -1.f;
+  const int chunks[] = {16, 64, 256, 1024};
+  const int threads[] = {256, 512};
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int rc = WS_OK;
+  for (int ch : chunks) {
+    for (int th : threads) {
+      p->tune = orig;
+      p->tune.chunk_warps = ch;
+      p->tune.enum_threads = th;
+      p->layout();
+      if ((rc = p->upload_fields(st)) != WS_OK) break;
+      if ((rc = p->enqueue(st, nullptr, nullptr)) != WS_OK) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && rc == WS_OK; ++r) rc = p->enqueue(st, nullptr, nullptr);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = WS_ECUDA;
+      if (rc != WS_OK) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (win_ms < 0 || ms < win_ms) {
+        win_ms = ms;
+        win = p->tune;
+      }
+    }
+    if (rc != WS_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->tune = rc == WS_OK ? win : orig;
+  p->layout();
+  int rc2 = p->upload_fields(st);
+  cudaStreamSynchronize(st);
+  if (rc != WS_OK) return rc;
+  if (rc2 != WS_OK) return rc2;
+  if (best) *best = p->tune;
+  ws::tuning_cache_store(p->ctx, p->n_cfg, p->tune);
+  return WS_OK;
+}
+
+extern "C" int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                                 const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
+                                 int32_t *order_out, int mode, void *stream) {
+  if (!ctx || (n_cfg > 0 && !out)) return WS_EINVAL;
+  ws_plan *p = nullptr;
+  int rc = ws_plan_create(ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, &p);
+  if (rc != WS_OK) return rc;
+  rc = ws_plan_execute(p, mode, stream);
+  if (rc == WS_OK) rc = ws_plan_results(p, out, order_out, stream);
+  ws_plan_destroy(p);
+  return rc;
+}
+
+extern "C" int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                           int n_acc, const ws_hw *hw, ws_cfg_info *out) {
+  if (n_cfg < 0 || !hw || (n_cfg > 0 && (!cfgs || !out))) return WS_EINVAL;
+  if (!hw_valid(*hw)) return WS_EINVAL;
+  for (int i = 0; i < n_cfg; ++i) {
+    Compiled cc;
+    ws_cfg_info &o = out[i];
+    memset(&o, 0, sizeof(o));
+    o.status = compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc);
+    if (o.status != WS_OK) continue;
+    const DCfg &d = cc.d;
+    for (int k = 0; k < 3; ++k) o.grid[k] = d.g[k];
+    o.threads = d.T;
+    o.warps_per_block = d.wpb;
+    o.blocks_per_sm = d.bpsm;
+    o.n_field = d.n_field;
+    o.total_blocks = (int64_t)d.g[0] * d.g[1] * d.g[2];
+    o.rep_block = d.rep;
+    o.wave_first = d.s;
+    o.wave_blocks = d.weff;
+    o.y_lo = d.y_lo;
+    o.y_hi = d.y_hi;
+    o.z_lo = d.z_lo;
+    o.z_hi = d.z_hi;
+    o.y_dist = d.y_dist;
+    o.z_dist = d.z_dist;
+    o.modelled_warps = d.lev_end[3];
+    for (size_t k = 0; k < cc.f.size(); ++k) {
+      o.folded_loads += cc.f[k].n_load;
+      o.folded_stores += cc.f[k].n_store;
+      o.scratch_bytes += cc.need_words[k] * 4;
+    }
+  }
+  return WS_OK;
+}
+
+extern "C" int ws_describe_fields(const ws_config *cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                                  int n_acc, const ws_hw *hw, ws_field_info *out) {
+  if (!cfg || !hw || !out || !hw_valid(*hw)) return WS_EINVAL;
+  Compiled cc;
+  int rc = compile_config(*cfg, fld, n_fld, acc, n_acc, *hw, cc);
+  if (rc != WS_OK) return rc;
+  for (size_t k = 0; k < cc.f.size(); ++k) {
+    ws_field_info &o = out[k];
+    memset(&o, 0, sizeof(o));
+    for (int j = 0; j < 2; ++j) {
+      o.lo_sector[j] = cc.f[k].lo[j];
+      o.words[j] = cc.f[k].words[j];
+    }
+    o.n_load = cc.f[k].n_load;
+    o.n_store = cc.f[k].n_store;
+  }
+  return WS_OK;
+}
+
+extern "C" double ws_rank_key(double t) {
+  if (!(t > 0.0) || std::isinf(t)) return t;
+  int e = 0;
+  double m = std::frexp(t, &e);
+  return std::ldexp(std::nearbyint(std::ldexp(m, 40)), e - 40);
+}
+
+extern "C" int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_out, void *stream) {
+  if (!ctx || n < 0 || (n > 0 && (!res || !order_out))) return WS_EINVAL;
+  if (n == 0) return WS_OK;
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, stream);
+  const size_t rb = (size_t)n * sizeof(ws_result);
+  int64_t o_res = ctx->arena->alloc(rb), o_keys = ctx->arena->alloc((size_t)n * 8),
+          o_ord = ctx->arena->alloc((size_t)n * 4), o_seg = ctx->arena->alloc(8);
+  int rc = WS_OK;
+  if (o_res < 0 || o_keys < 0 || o_ord < 0 || o_seg < 0) rc = WS_ENOMEM;
+  char *b = ctx->arena->base;
+  if (rc == WS_OK) {
+    int32_t seg[2] = {0, n};
+    cudaError_t e = cudaMemcpyAsync(b + o_res, res, rb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_seg, seg, sizeof(seg), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_keys((const ws_result *)(b + o_res), n, (double *)(b + o_keys), st);
+    if (e == cudaSuccess) {
+      RankArgs ra;
+      ra.keys = (const double *)(b + o_keys);
+      ra.seg = (const int32_t *)(b + o_seg);
+      ra.order = (int32_t *)(b + o_ord);
+      ra.n = n;
+      ra.n_seg = 1;
+      e = launch_rank(ra, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(order_out, b + o_ord, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(std::string("ws_rank: ") + cudaGetErrorString(e));
+      rc = WS_ECUDA;
+    }
+  }
+  for (int64_t o : {o_res, o_keys, o_ord, o_seg}) ctx->arena->release(o);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------
+// autotuner cache: one line per workload class, "n_cfg_bucket chunk threads words"
+// ---------------------------------------------------------------------------------
+static int bucket(int n) {
+  int b = 0;
+  while (n > 1) {
+    n >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+void ws::tuning_cache_lookup(ws_ctx *ctx, int n_cfg, ws_tuning *t) {
+  const char *path = getenv("WS_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ifstream f(path);
+  int b, ch, th, cw, cs;
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    if (is >> b >> ch >> th >> cw >> cs && b == bucket(n_cfg)) {
+      t->chunk_warps = ch;
+      t->enum_threads = th;
+      t->count_words = cw;
+      t->ctas_per_sm = cs;
+    }
+  }
+  (void)ctx;
+}
+
+void ws::tuning_cache_store(ws_ctx *ctx, int n_cfg, const ws_tuning &t) {
+  const char *path = getenv("WS_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream f(path, std::ios::app);
+  f << bucket(n_cfg) << " " << t.chunk_warps << " " << t.enum_threads << " " << t.count_words << " "
+    << t.ctas_per_sm << "\n";
+  (void)ctx;
+}

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer counts must match bit for bit; fp64 volumes and times within 1e-12 relative
+(the only differences allowed are exp() rounding between CUDA and the host libm);
+rankings must be identical.  Small cases are checked in full; the full-size sweeps
+run exactly as the benchmark launches them and are checked on sampled candidates
+the oracle computes one by one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_14242_gb300 import binding as B
+from paper_2204_14242_gb300 import workloads as W
+from test_oracle_pins import random_tiny
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+THREADS = max(1, len(os.sched_getaffinity(0)))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    B.load()
+    c = B.Context(0, 24 << 30)
+    yield c
+    c.close()
+
+
+def assert_match(res, want, idx=None, what=""):
+    got = B.results_to_dicts(res)
+    idx = range(len(want)) if idx is None else idx
+    for j, i in enumerate(idx):
+        g, w = got[i], want[j]
+        assert g["status"] == w["status"], (what, i, g["status"], w["status"])
+        if w["status"] != 0:
+            continue
+        for k in B.RESULT_INT:
+            assert g[k] == w[k], (what, i, k, g[k], w[k])
+        assert g["limiter"] == w["limiter"], (what, i)
+        for k in B.RESULT_DBL:
+            assert np.isclose(g[k], w[k], rtol=RTOL, atol=0.0), (what, i, k, g[k], w[k])
+
+
+def test_7pt_all_modes(ctx):
+    c = [W.stencil_7pt_128()]
+    want = oracle.estimate(c, W.a100())
+    for mode in (B.WS_MODE_PLAIN, B.WS_MODE_BATCHED, B.WS_MODE_DIRECT):
+        res, order = B.ws_estimate_batch(ctx, c, W.a100(), mode=mode)
+        assert_match(res, want, what=f"mode {mode}")
+    assert res[0]["wave_load_sectors"] == 832 and res[0]["ov_z"] == 480
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_tiny_candidates(ctx, seed):
+    rng = W.SplitMix64(100 + seed)
+    hw = W.Hardware(sms=3, max_blocks_sm=2)
+    cfgs = [random_tiny(rng) for _ in range(300)]
+    want = oracle.estimate(cfgs, hw, threads=THREADS)
+    res, order = B.ws_estimate_batch(ctx, cfgs, hw, mode=B.WS_MODE_BATCHED)
+    assert_match(res, want, what="tiny")
+    assert list(order) == list(oracle.rank([w["t_pred"] for w in want]))
+
+
+def test_modes_are_bit_identical(ctx):
+    rng = W.SplitMix64(55)
+    hw = W.Hardware(sms=5)
+    cfgs = [random_tiny(rng) for _ in range(60)] + W.stencil_25pt_sweep(N=(128, 96, 80))[::29]
+    outs = []
+    for mode in (B.WS_MODE_PLAIN, B.WS_MODE_BATCHED, B.WS_MODE_DIRECT):
+        res, order = B.ws_estimate_batch(ctx, cfgs, hw, mode=mode)
+        outs.append((res.tobytes(), order.tobytes()))
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_graph_replay_is_repeatable(ctx):
+    cfgs = W.stencil_25pt_sweep(N=(160, 128, 96))[::7]
+    with B.Plan(ctx, cfgs, W.a100()) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        r1, o1 = p.results()
+        for _ in range(3):
+            p.execute(B.WS_MODE_BATCHED)
+        r2, o2 = p.results()
+    assert r1.tobytes() == r2.tobytes() and o1.tobytes() == o2.tobytes()
+
+
+def sample(n_total, k, seed):
+    rng = W.SplitMix64(seed)
+    idx = {0, n_total - 1}
+    while len(idx) < k:
+        idx.add(rng.randint(0, n_total - 1))
+    return sorted(idx)
+
+
+def test_25pt_sweep_full_size(ctx):
+    """640x512x512 (x = 640), 755 candidates in one batched launch; 16 sampled against the oracle."""
+    cfgs = W.stencil_25pt_sweep()
+    hw = W.a100()
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        res, order = p.results()
+    assert (res["status"] == 0).all()
+    idx = sample(len(cfgs), 16, 3)
+    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
+    assert_match(res, want, idx, "25pt")
+    # ranking: the GPU's order sorts its own keys exactly like the oracle's rule
+    keys = [B.ws_rank_key(t) for t in res["t_pred"]]
+    assert list(order) == sorted(range(len(cfgs)), key=lambda i: (keys[i], i))
+
+
+def test_lbm_sweep_full_size(ctx):
+    """256^3, 42 arrays, 755 candidates; 4 sampled against the oracle."""
+    cfgs = W.lbm_sweep()
+    hw = W.a100()
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        res, order = p.results()
+    assert (res["status"] == 0).all()
+    idx = sample(len(cfgs), 4, 4)
+    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
+    assert_match(res, want, idx, "lbm")
+
+
+def test_mixed_set_full_size(ctx):
+    """20,000 seeded mixed candidates in one plan (several scratch passes); the 12 with
+    the least enumeration work plus 4 random ones checked against the oracle."""
+    cfgs = W.mixed_set()
+    hw = W.a100()
+    info = B.ws_describe(cfgs, hw)
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        res, order = p.results()
+    assert (res["status"] == 0).all()
+    work = info["modelled_warps"] * (info["folded_loads"] + info["folded_stores"])
+    idx = sorted(set(np.argsort(work)[:12].tolist()) | set(sample(len(cfgs), 4, 5)))
+    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
+    assert_match(res, want, idx, "mixed")
+
+
+def test_edge_cases(ctx):
+    hw = W.a100()
+    N = (70, 33, 19)
+    st = W.dense_strides(N)
+    cfgs = [
+        W.Config(N=(5, 3, 2), B=(32, 4, 2), fields=W.copy_fields((5, 3, 2), W.star_offsets(1))),   # domain < block
+        W.Config(N=N, B=(32, 4, 2), fields=W.copy_fields(N, W.box_offsets(2))),                   # ragged
+        W.Config(N=N, B=(8, 4, 1), fields=W.copy_fields(N, W.star_offsets(3)), fold_axis=1, fold=16),
+        W.Config(N=N, B=(1024, 1, 1), fields=W.copy_fields(N, W.star_offsets(1))),
+        W.Config(N=N, B=(1, 1, 64), fields=W.copy_fields(N, W.star_offsets(1)), fold_axis=2, fold=4),
+        W.Config(N=N, B=(16, 2, 2), fields=[W.Field(4, [W.Access(0, 0, 0, 0, k) for k in range(3)] +
+                                                    [W.Access(0, 0, 0, 1, 1)], align=-20, strides=(3, 3 * 70, 3 * 70 * 33))]),
+        W.Config(N=N, B=(32, 2, 1), fields=[W.Field(2, [W.Access(1, -1, 0), W.Access(0, 0, 0, 1)], align=6,
+                                                    strides=st, const_off=-7)]),
+        W.Config(N=((1 << 20), 3, 2), B=(256, 1, 1), fields=W.copy_fields(((1 << 20), 3, 2), W.star_offsets(2))),
+        W.Config(N=N, B=(64, 32, 1), fields=W.copy_fields(N, [(0, 0, 0)])),                         # invalid
+        W.Config(N=N, B=(32, 1, 1), fields=[W.Field(8, [W.Access(0, 0, 0)], strides=(-1, -70, -70 * 33))]),
+    ]
+    want = oracle.estimate(cfgs, hw, threads=THREADS)
+    res, order = B.ws_estimate_batch(ctx, cfgs, hw)
+    assert res[8]["status"] == B.WS_EINVAL
+    want[8]["status"] = B.WS_EINVAL
+    assert_match(res, want, what="edge")
+    assert list(order) == list(oracle.rank([w["t_pred"] for w in want]))
+    # empty batch
+    r0, o0 = B.ws_estimate_batch(ctx, [], hw)
+    assert len(r0) == 0
+
+
+def test_multi_pass_equals_single_pass(ctx):
+    cfgs = W.lbm_sweep(N=(128, 96, 64))[::5]
+    hw = W.a100()
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        ref, ref_o = p.results()
+        assert p.profile()["passes"] == 1
+    small = B.Context(0, 96 << 20)
+    try:
+        with B.Plan(small, cfgs, hw) as p:
+            prof = p.profile()
+            assert prof["passes"] > 1
+            p.execute(B.WS_MODE_BATCHED)
+            res, order = p.results()
+    finally:
+        small.close()
+    assert res.tobytes() == ref.tobytes() and order.tobytes() == ref_o.tobytes()
+
+
+def test_segmented_and_standalone_ranking(ctx):
+    cfgs = W.stencil_25pt_sweep(N=(96, 64, 64))[::3]
+    hw = W.a100()
+    seg = [0, 40, 41, 120, len(cfgs)]
+    with B.Plan(ctx, cfgs, hw, segments=seg) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        res, order = p.results()
+    for a, b in zip(seg[:-1], seg[1:]):
+        want = a + oracle.rank(res["t_pred"][a:b])
+        assert list(order[a:b]) == list(want)
+    o2 = B.ws_rank(ctx, res)
+    assert list(o2) == list(oracle.rank(res["t_pred"]))
+
+
+def test_autotune_keeps_results(ctx):
+    cfgs = W.stencil_25pt_sweep(N=(160, 128, 96))[::11]
+    hw = W.a100()
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        r1, o1 = p.results()
+        best = p.autotune()
+        assert best["chunk_warps"] in (16, 64, 256, 1024)
+        p.execute(B.WS_MODE_BATCHED)
+        r2, o2 = p.results()
+        prof = p.profile()
+    assert r1.tobytes() == r2.tobytes() and o1.tobytes() == o2.tobytes()
+    assert prof["launches"] == 4 and prof["addresses"] > 0 and prof["ms_enum"] > 0
+
+
+def test_server_results_same_alone_and_in_the_mix(ctx):
+    hw = W.a100()
+    reqs = W.request_stream(n_requests=24, seed=77, kmin=4, kmax=40)
+    alone = []
+    for r in reqs:
+        res, order = B.ws_estimate_batch(ctx, r.configs, hw)
+        alone.append((res, order))
+    with B.Server(ctx, hw, mem_budget=8 << 30, max_inflight=3) as srv:
+        ids = [srv.submit(r.configs) for r in reqs]
+        got = {}
+        pending = set(ids)
+        for _ in range(2000):
+            for rid in list(pending):
+                rc, res, order = srv.poll(rid, timeout_us=10000)
+                if rc == B.WS_OK:
+                    got[rid] = (res, order)
+                    pending.discard(rid)
+                else:
+                    assert rc == B.WS_EAGAIN
+            if not pending:
+                break
+        assert not pending
+        stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["steps"] >= 1
+    for rid, (res_a, ord_a) in zip(ids, alone):
+        res, order = got[rid]
+        assert res.tobytes() == res_a.tobytes()
+        assert order.tobytes() == ord_a.tobytes()
+    # and the mix agrees with the oracle on one request
+    want = oracle.estimate(reqs[0].configs[:3], hw, threads=THREADS)
+    assert_match(got[ids[0]][0], want, [0, 1, 2], "server")

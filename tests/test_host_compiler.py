@@ -1,0 +1,94 @@
+"""Host descriptor compiler (CPU): thread groups agree with the oracle, every address
+the kernels can produce lies inside the bitmap the compiler sized for it, and the
+validation rules reject what they should."""
+import numpy as np
+import pytest
+
+import brute_force
+import oracle
+from paper_2204_14242_gb300 import binding as B
+from paper_2204_14242_gb300 import workloads as W
+from test_oracle_pins import random_tiny
+
+
+def sample_configs():
+    rng = W.SplitMix64(21)
+    out = [(random_tiny(rng), W.Hardware(sms=rng.randint(1, 4), max_blocks_sm=2)) for _ in range(150)]
+    out += [(c, W.a100()) for c in W.stencil_25pt_sweep(N=(96, 64, 48))[::37]]
+    out += [(W.stencil_7pt_128(), W.a100())]
+    return out
+
+
+def test_thread_groups_match_the_oracle():
+    for c, hw in sample_configs():
+        info = B.ws_describe([c], hw)[0]
+        o = oracle.estimate([c], hw)[0]
+        assert info["status"] == o["status"] == 0
+        assert info["wave_first"] == o["wave_first_block"]
+        assert info["wave_blocks"] == o["wave_blocks"]
+        assert info["y_dist"] == o["y_dist_blocks"]
+        assert info["z_dist"] == o["z_dist_blocks"]
+        assert info["blocks_per_sm"] == o["blocks_per_sm"]
+        # y / z candidate ranges + predicates reproduce the brute-force block sets
+        grp = brute_force.thread_groups(c, hw)
+        g = info["grid"]
+        ys = [b for b in range(info["y_lo"], info["y_hi"]) if (b // g[0]) % g[1] != g[1] - 1]
+        assert ys == list(grp["y"])
+        zs = [b for b in range(info["z_lo"], info["z_hi"]) if b not in set(ys)]
+        assert zs == list(grp["z"])
+
+
+def test_bitmaps_contain_every_sector():
+    for c, hw in sample_configs():
+        finfo = B.ws_describe_fields(c, hw)
+        grp = brute_force.thread_groups(c, hw)
+        g = grp["grid"]
+        for fi, f in enumerate(c.fields):
+            loads = {(a.dx, a.dy, a.dz, a.dc) for a in f.accesses if not a.is_store}
+            stores = {(a.dx, a.dy, a.dz, a.dc) for a in f.accesses if a.is_store}
+            for lv, groups in ((0, ("rep",)), (1, ("wave", "y", "z"))):
+                lo = finfo[fi]["lo_sector"][lv]
+                hi = lo + 32 * finfo[fi]["words"][lv]
+                assert lo % 32 == 0 and finfo[fi]["words"][lv] % 4 == 0
+                for name in groups:
+                    p, kv, warp, lane = brute_force.threads(c, g, grp[name])
+                    for offs in (loads, stores):
+                        for o in brute_force.folded(c, offs):
+                            m = brute_force.needed(c, offs, o, kv)
+                            sec = np.floor_divide(brute_force.addresses(f, p, o)[m], 32)
+                            if sec.size:
+                                assert sec.min() >= lo and sec.max() < hi, (c, fi, lv, name)
+
+
+def test_validation_rules():
+    N = (64, 64, 64)
+    ok = W.Config(N=N, B=(32, 4, 1), fields=W.copy_fields(N, W.star_offsets(1)))
+    bad = [
+        W.Config(N=N, B=(64, 32, 1), fields=ok.fields),                            # 2048 threads
+        W.Config(N=N, B=(1, 1, 128), fields=ok.fields),                            # bz > 64
+        W.Config(N=(0, 4, 4), B=(32, 1, 1), fields=ok.fields),                     # empty domain
+        W.Config(N=(1 << 21, 4, 4), B=(32, 1, 1), fields=ok.fields),               # N > 2^20
+        W.Config(N=N, B=(32, 1, 1), fields=ok.fields, fold_axis=0, fold=2),        # fold without axis
+        W.Config(N=N, B=(32, 1, 1), fields=ok.fields, fold_axis=1, fold=17),       # fold > 16
+        W.Config(N=N, B=(1024, 1, 1), fields=ok.fields, regs_per_thread=255),      # no block fits
+        W.Config(N=N, B=(32, 1, 1), fields=[W.Field(8, [W.Access(0, 0, 0)], strides=(1 << 41, 1, 1))]),
+        W.Config(N=N, B=(32, 1, 1), fields=[W.Field(0, [W.Access(0, 0, 0)], strides=(1, 64, 4096))]),
+    ]
+    info = B.ws_describe([ok] + bad, W.a100())
+    assert info[0]["status"] == 0
+    assert all(s == B.WS_EINVAL for s in info["status"][1:]), list(info["status"])
+    # the oracle rejects the first five (its own, looser, rules) as well
+    for o in oracle.estimate(bad[:3] + bad[4:5] + bad[6:7], W.a100()):
+        assert o["status"] == -1
+
+
+def test_folded_instruction_counts():
+    N = (64, 64, 64)
+    for r in (1, 2, 4):
+        for axis, f in W.FOLD_VARIANTS:
+            c = W.Config(N=N, B=(32, 2, 2), fields=W.copy_fields(N, W.star_offsets(r)), fold_axis=axis, fold=f)
+            info = B.ws_describe([c], W.a100())[0]
+            # a star of radius r folded f times along y or z: the fold-axis line grows to
+            # 2r + f points, the 4r points off that axis are repeated f times
+            assert info["folded_loads"] == 2 * r + f + 4 * r * f
+            assert info["folded_stores"] == f
