@@ -184,6 +184,13 @@ def serve(B, W, ctx, hw, seconds, seed=20222):
     reqs = W.request_stream(n_requests=n_req, seed=seed)
     arrays = [B.marshal(r.configs) for r in reqs]
     srv = B.Server(ctx, hw, mem_budget=int(24 << 30), max_inflight=4, max_step_cfgs=4096)
+    try:
+        return _serve(B, srv, reqs, arrays)
+    finally:
+        srv.close()
+
+
+def _serve(B, srv, reqs, arrays):
     lat = {}
     done = threading.Event()
     submitted = {}
@@ -222,7 +229,6 @@ def serve(B, W, ctx, hw, seconds, seed=20222):
     th.join()
     t1 = time.perf_counter()
     stats = srv.stats()
-    srv.close()
     ls = sorted(v[0] for v in lat.values())
     ok = sum(1 for v in lat.values() if v[1] == 0)
     cfg_done = sum(v[2] for v in lat.values())

@@ -280,8 +280,9 @@ typedef struct ws_server_stats {
 } ws_server_stats;
 
 int ws_server_create(ws_ctx *ctx, const ws_server_opts *opts, const ws_hw *hw, ws_server **srv);
-/* Copies the request and queues it; returns at once.  WS_ENOMEM if the request can
- * never fit the budget, WS_EAGAIN if the queue is full. */
+/* Copies the request and queues it; returns at once.  A request whose scratch exceeds
+ * the free budget runs in several scratch passes; WS_ENOMEM only if one of its fields
+ * alone can never fit the budget.  WS_EAGAIN if the queue is full. */
 int ws_server_submit(ws_server *srv, const ws_request *req, uint64_t *req_id);
 /* Waits up to timeout_us (0 = just test) for the request; on WS_OK copies its n_cfg
  * results (and ranking, may be NULL) and forgets it.  WS_EAGAIN if not finished. */

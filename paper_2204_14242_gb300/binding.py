@@ -9,9 +9,11 @@ absent, calls raise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
+import weakref
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -81,6 +83,20 @@ class WsError(RuntimeError):
 
 _lib = None
 _lock = threading.Lock()
+
+# Live handles, closed at exit in dependency order (servers, then plans, then contexts)
+# so that no worker thread or plan outlives the context it runs on.
+_live = {"server": weakref.WeakSet(), "plan": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("server", "plan", "ctx"):
+        for obj in list(_live[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
 
 
 def library_path() -> str:
@@ -238,9 +254,14 @@ class Context:
         self.handle = h
         self.device = device
         self.arena_bytes = arena_bytes
+        _live["ctx"].add(self)
 
     def close(self):
         if self.handle:
+            for kind in ("server", "plan"):
+                for obj in list(_live[kind]):
+                    if getattr(obj, "ctx", None) is self:
+                        obj.close()
             load().ws_destroy(self.handle)
             self.handle = None
         self._arena_tensor = None
@@ -298,6 +319,7 @@ class Plan:
                                   tun.ctypes.data if tun is not None else None, ctypes.byref(h)), "ws_plan_create")
         self.handle = h
         self.ctx = ctx
+        _live["plan"].add(self)
 
     def execute(self, mode: int = WS_MODE_BATCHED, stream=None):
         _check(load().ws_plan_execute(self.handle, mode, _stream_handle(stream)), "ws_plan_execute")
@@ -404,6 +426,7 @@ class Server:
         self.handle = h
         self.ctx = ctx
         self.sizes = {}
+        _live["server"].add(self)
 
     def submit(self, configs=None, arrays=None) -> int:
         cfg, fld, acc = arrays if arrays is not None else marshal(configs)

@@ -78,7 +78,8 @@ namespace ws {
 using Plan = ::ws_plan;
 
 int plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
-                      int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes);
+                      int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes,
+                      size_t *max_field_bytes);
 int plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                      const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
                      const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,

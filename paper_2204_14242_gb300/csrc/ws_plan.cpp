@@ -737,16 +737,19 @@ static cudaStream_t pick_stream(ws_ctx *c, void *s) { return s ? (cudaStream_t)s
 
 // Bytes of device memory a plan of these candidates needs with one pass.
 int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
-                          int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes) {
-  size_t dsc = 0, scr = 0;
+                          int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes,
+                          size_t *max_field_bytes) {
+  size_t dsc = 0, scr = 0, mf = 0;
   for (int i = 0; i < n_cfg; ++i) {
     Compiled cc;
     if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc) != WS_OK) continue;
     for (size_t k = 0; k < cc.f.size(); ++k) {
       dsc += sizeof(DField) + cc.acc[k].size() * sizeof(DAcc);
       scr += (size_t)cc.need_words[k] * 4;
+      mf = std::max(mf, (size_t)cc.need_words[k] * 4);
     }
   }
+  *max_field_bytes = mf;
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4) + 64 * 1024;
   *desc_bytes = dsc;
   *scratch_bytes = scr;

@@ -32,7 +32,8 @@ struct Request {
   std::vector<ws_config> cfgs;
   std::vector<ws_field> fld;
   std::vector<ws_access> acc;
-  size_t scratch_bytes = 0;
+  size_t scratch_bytes = 0;    // one-pass scratch of the whole request
+  size_t max_field_bytes = 0;  // the least scratch it can run with (several passes)
   int status = WS_EAGAIN;  // WS_EAGAIN until finished
   bool done = false;
   std::vector<ws_result> results;
@@ -115,15 +116,25 @@ bool admit(ws_server *s, std::unique_lock<std::mutex> &lk) {
       break;
     }
   if (slot < 0) return false;
-  // take requests from the head while they fit the pool and the step size
+  // take requests from the head while they fit the pool (one pass each) and the step
+  // size; a head request larger than the free scratch runs alone in several passes
+  // once enough of the pool is free (or nothing else is running)
   std::vector<Request *> take;
   size_t bytes = 0;
   int ncfg = 0;
-  size_t room = s->pool->largest_free();
+  size_t room = s->pool->largest_free() & ~(size_t)255;
   for (Request *r : s->queue) {
     if (!take.empty() && ncfg + (int)r->cfgs.size() > s->opts.max_step_cfgs) break;
     size_t b = (r->scratch_bytes + 255) & ~(size_t)255;
-    if (bytes + b > room) break;
+    if (bytes + b > room) {
+      if (take.empty() && room >= r->max_field_bytes &&
+          (s->inflight.empty() || room >= std::min(b, s->pool->size / 2))) {
+        take.push_back(r);
+        bytes = room;
+        ncfg += (int)r->cfgs.size();
+      }
+      break;
+    }
     take.push_back(r);
     bytes += b;
     ncfg += (int)r->cfgs.size();
@@ -313,16 +324,17 @@ extern "C" int ws_server_submit(ws_server *s, const ws_request *req, uint64_t *r
   r->cfgs.assign(req->cfgs, req->cfgs + req->n_cfg);
   r->fld.assign(req->fld, req->fld + req->n_fld);
   r->acc.assign(req->acc, req->acc + req->n_acc);
-  size_t dsc = 0, scr = 0;
+  size_t dsc = 0, scr = 0, mf = 0;
   ws::plan_requirements(r->cfgs.data(), req->n_cfg, r->fld.data(), req->n_fld, r->acc.data(), req->n_acc, &s->hw,
-                        &dsc, &scr);
+                        &dsc, &scr, &mf);
   r->scratch_bytes = scr;
+  r->max_field_bytes = mf;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->stop) {
     delete r;
     return WS_ECANCELED;
   }
-  if (((scr + 255) & ~(size_t)255) > s->pool->size) {
+  if (((mf + 255) & ~(size_t)255) > s->pool->size) {
     s->stats.rejected += 1;
     delete r;
     return WS_ENOMEM;
