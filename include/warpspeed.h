@@ -146,6 +146,8 @@ typedef struct ws_tuning {
   int32_t enum_threads;    /* threads per CTA of the enumeration kernel (128..1024)      */
   int32_t count_words;     /* bitmap words per counting work item                        */
   int32_t ctas_per_sm;     /* persistent CTAs per SM (0 = occupancy limit)               */
+  int32_t pass_mb;         /* bitmap scratch per pass in MiB, sized to stay in L2 (0 = 96,
+                              < 0 = as large as the arena allows); never below one field   */
 } ws_tuning;
 
 /* Per-kernel device time of one profiled step (CUDA events on the launch stream). */
@@ -201,7 +203,9 @@ int ws_plan_results(ws_plan *plan, ws_result *out, int32_t *order, void *stream)
 int ws_plan_device_results(ws_plan *plan, ws_result **results, int32_t **order);
 /* Runs one direct step with CUDA events around each kernel and synchronises. */
 int ws_plan_profile(ws_plan *plan, void *stream, ws_profile *out);
-/* Tries a small grid of tunings on this plan, keeps the fastest (also returned). */
+/* Tries a small grid of tunings (chunk, CTA size, pass size) on this plan and keeps the
+ * fastest (also returned); with WS_TUNE_CACHE set, the choice is appended to that file
+ * and later plans of the same size class start from it. */
 int ws_autotune(ws_plan *plan, void *stream, ws_tuning *best);
 int ws_plan_destroy(ws_plan *plan);
 

@@ -41,7 +41,7 @@ RESULT_DBL = ["v_l1", "v_l2_load", "v_l2_store", "v_dram_load", "v_dram_store", 
 RESULT = np.dtype([(k, "<i8") for k in RESULT_INT] + [(k, "<f8") for k in RESULT_DBL] +
                   [("limiter", "<i4"), ("status", "<i4")], align=True)
 TUNING = np.dtype([("chunk_warps", "<i4"), ("enum_threads", "<i4"), ("count_words", "<i4"),
-                   ("ctas_per_sm", "<i4")], align=True)
+                   ("ctas_per_sm", "<i4"), ("pass_mb", "<i4")], align=True)
 PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4"), ("ms_model", "<f4"),
                     ("ms_rank", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),

@@ -23,6 +23,13 @@ enum Counter {
 // z-set loads, wave stores.  Bit i of a bitmap stands for sector (lo + i).
 enum Bitmap { BM_BL, BM_BS, BM_W, BM_Y, BM_Z, BM_WS, N_BITMAPS };
 
+// Division by an invariant 32-bit divisor d >= 1 by multiply and shift (Granlund and
+// Montgomery 1994): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> s for every n < 2^31.
+struct FastDiv {
+  uint32_t d, m, s, pad;
+};
+
 // Thread groups of one candidate, flattened into one index space of "modelled warps":
 //   level 0: the representative block      [0, lev_end[0])
 //   level 1: the representative wave       [lev_end[0], lev_end[1])
@@ -41,9 +48,9 @@ struct DCfg {
   int64_t y_lo, y_hi;     // y-set candidates [y_lo, y_hi): kept iff by != g[1]-1
   int64_t z_lo, z_hi;     // z-set candidates: kept iff not in the y set
   int64_t y_dist, z_dist; // s - first block of the y / z set (0 if empty)
-  int64_t lev_end[4];
+  int64_t lev_end[4];      // all < 2^31 (checked by the descriptor compiler)
   double flops;
-  int64_t pad[1];
+  FastDiv fd_gx, fd_gy, fd_wpb;
 };
 
 struct DField {
@@ -60,6 +67,10 @@ struct DField {
   int32_t acc_begin;      // index into the DAcc array
   int32_t cfg;            // owning candidate
   int32_t first_of_cfg;   // 1 if this is the candidate's first field (counts LUPs)
+  int32_t wide;           // a bitmap spans >= 2^32 bytes: 64-bit address path
+  int32_t pad;
+  int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
+  int16_t cnt_store[17];  // folded stores likewise
 };
 
 // One folded access: byte offset from the thread's first point, and the smallest

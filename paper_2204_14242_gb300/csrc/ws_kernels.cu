@@ -100,15 +100,69 @@ __device__ __forceinline__ int find_cf(const DField *__restrict__ fld, int lo, i
   return lo;
 }
 
-__global__ void __launch_bounds__(1024) enum_kernel(EnumArgs a) {
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+  return (__umulhi(n, f.m) + n) >> f.s;
+}
+
+// Run-head insertion of one access instruction (32-bit addresses).  Consecutive
+// active lanes whose sectors step by 0 or 1 inside one bitmap word form a run; the
+// first lane of each run sets the run's bit range [head sector, tail sector] with one
+// red.or.  Every sector between head and tail is touched by some lane of the run, so
+// the bitmap receives exactly the union of the lanes' sectors whatever the layout
+// (a scattered layout just makes more, shorter runs).  r: byte address relative to
+// the bitmap origin; lanes with r >= limit are skipped and counted in `bad`.
+// With want_count the number of distinct sectors of the instruction is returned
+// (warp-uniform): the sum of run lengths when runs increase strictly across the
+// warp, else the exact per-word count.
+__device__ __forceinline__ uint32_t runs_insert(uint32_t *__restrict__ bm, uint32_t r, bool act, uint32_t limit,
+                                                uint32_t lane, uint32_t &bad, bool want_count) {
+  const bool inside = r < limit;
+  bad += act && !inside;
+  act = act && inside;
+  const uint32_t sec = r >> 5;
+  const uint32_t prev = __shfl_up_sync(FULL, sec, 1);
+  const uint32_t actm = __ballot_sync(FULL, act);
+  const uint32_t below = actm & ((1u << lane) - 1u);
+  const bool prev_act = ((actm << 1) >> lane) & 1u;
+  const bool cont = prev_act && (sec - prev) <= 1u && ((sec ^ prev) >> 5) == 0u;
+  const bool head = act && !cont;
+  const uint32_t heads = __ballot_sync(FULL, head);
+  const uint32_t ends = actm & ~((actm & ~heads) >> 1);
+  const uint32_t t = __ffs(ends & (0xffffffffu << lane)) - 1u;
+  const uint32_t tail = __shfl_sync(FULL, sec, t);
+  if (head) {
+    const uint32_t hb = sec & 31u, tb = tail & 31u;
+    atomicOr(bm + (sec >> 5), (0xffffffffu >> (31u - tb)) & (0xffffffffu << hb));
+  }
+  if (!want_count) return 0;
+  const uint32_t pl = below ? 31u - __clz(below) : 0u;
+  const uint32_t psec = __shfl_sync(FULL, sec, pl);
+  if (__all_sync(FULL, !head || below == 0u || sec > psec))
+    return __reduce_add_sync(FULL, head ? tail - sec + 1u : 0u);
+  uint32_t cnt = 0;   // overlapping runs: count distinct sectors word by word
+  const uint32_t word = sec >> 5, bit = 1u << (sec & 31u);
+  uint32_t pending = actm;
+  while (pending) {
+    const uint32_t lw = __shfl_sync(FULL, word, __ffs(pending) - 1);
+    const bool mine = act && word == lw;
+    cnt += __popc(__reduce_or_sync(FULL, mine ? bit : 0u));
+    pending &= ~__ballot_sync(FULL, mine);
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
+  __shared__ DField s_f;
+  __shared__ DCfg s_c;
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
+  __shared__ uint32_t s_b32[kMaxFoldedAccesses];
   __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
   __shared__ uint32_t s_tc[1024];
   __shared__ long long s_item;
 
   const uint32_t lane = threadIdx.x & 31u;
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t nwarps = blockDim.x >> 5;
   int cur_cf = -1, cur_cfg = -1;
 
   for (;;) {
@@ -117,97 +171,119 @@ __global__ void __launch_bounds__(1024) enum_kernel(EnumArgs a) {
     const int64_t item = s_item;
     if (item >= a.item_hi) break;
     const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, false);
-    const DField &F = a.fld[cf];
-    const DCfg &C = a.cfg[F.cfg];
     if (cf != cur_cf) {
-      const int na = F.n_load + F.n_store;
+      if (threadIdx.x == 0) s_f = a.fld[cf];
+      __syncthreads();
+      const int na = s_f.n_load + s_f.n_store;
       for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        DAcc d = a.acc[F.acc_begin + i];
+        const DAcc d = a.acc[s_f.acc_begin + i];
         s_boff[i] = d.boff;
+        s_b32[i] = (uint32_t)d.boff;
         s_kmin[i] = (uint8_t)d.kmin;
       }
-      if (F.cfg != cur_cfg) {
-        for (int t = threadIdx.x; t < C.T; t += blockDim.x) {
-          uint32_t tx = t % C.B[0], ty = (t / C.B[0]) % C.B[1], tz = t / (C.B[0] * C.B[1]);
+      if (s_f.cfg != cur_cfg) {
+        if (threadIdx.x == 0) s_c = a.cfg[s_f.cfg];
+        __syncthreads();
+        for (int t = threadIdx.x; t < s_c.T; t += blockDim.x) {
+          const uint32_t tx = t % s_c.B[0], ty = (t / s_c.B[0]) % s_c.B[1], tz = t / (s_c.B[0] * s_c.B[1]);
           s_tc[t] = tx | (ty << 10) | (tz << 20);
         }
       }
       __syncthreads();
       cur_cf = cf;
-      cur_cfg = F.cfg;
+      cur_cfg = s_f.cfg;
     }
-    const int64_t mw0 = (item - F.item_begin) * (int64_t)a.chunk;
-    const int64_t mw1 = min(mw0 + (int64_t)a.chunk, F.mw_end);
-    unsigned long long acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0,
-                       acc_addr = 0, acc_wi = 0;
+    // descriptors of this item: read from shared memory where used (broadcast loads)
+    const bool wide = s_f.wide != 0;
+    const uint32_t mw0 = (uint32_t)((item - s_f.item_begin) * (int64_t)a.chunk);
+    const uint32_t mw1 = (uint32_t)min((int64_t)mw0 + a.chunk, s_f.mw_end);
+    uint32_t acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0, acc_addr = 0, acc_wi = 0;
     uint32_t bad = 0;
 
-    for (int64_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
-      int level;
-      int64_t b, j;
-      if (mw < C.lev_end[0]) {
-        level = 0; b = C.rep; j = mw;
-      } else if (mw < C.lev_end[1]) {
-        level = 1; j = mw - C.lev_end[0]; b = C.s + j / C.wpb;
-      } else if (mw < C.lev_end[2]) {
-        level = 2; j = mw - C.lev_end[1]; b = C.y_lo + j / C.wpb;
+    for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
+      uint32_t level, b, j;
+      const FastDiv fwpb = s_c.fd_wpb;
+      if (mw < (uint32_t)s_c.lev_end[0]) {
+        level = 0; j = mw; b = (uint32_t)s_c.rep;
+      } else if (mw < (uint32_t)s_c.lev_end[1]) {
+        level = 1; j = mw - (uint32_t)s_c.lev_end[0]; b = (uint32_t)s_c.s + fdiv(j, fwpb);
+      } else if (mw < (uint32_t)s_c.lev_end[2]) {
+        level = 2; j = mw - (uint32_t)s_c.lev_end[1]; b = (uint32_t)s_c.y_lo + fdiv(j, fwpb);
       } else {
-        level = 3; j = mw - C.lev_end[2]; b = C.z_lo + j / C.wpb;
+        level = 3; j = mw - (uint32_t)s_c.lev_end[2]; b = (uint32_t)s_c.z_lo + fdiv(j, fwpb);
       }
-      const int w = (int)(j % C.wpb);
-      const int32_t bx = (int32_t)(b % C.g[0]);
-      const int64_t bt = b / C.g[0];
-      const int32_t by = (int32_t)(bt % C.g[1]);
-      const int32_t bz = (int32_t)(bt / C.g[1]);
-      if (level == 2 && by == C.g[1] - 1) continue;
-      if (level == 3 && b >= C.y_lo && b < C.y_hi && by != C.g[1] - 1) continue;
+      const uint32_t gx = (uint32_t)s_c.g[0], gy = (uint32_t)s_c.g[1];
+      const uint32_t w = j - fdiv(j, fwpb) * (uint32_t)s_c.wpb;
+      const uint32_t bt = fdiv(b, s_c.fd_gx);
+      const uint32_t bx = b - bt * gx;
+      const uint32_t bz = fdiv(bt, s_c.fd_gy);
+      const uint32_t by = bt - bz * gy;
+      if (level == 2 && by == gy - 1) continue;
+      if (level == 3 && b >= (uint32_t)s_c.y_lo && b < (uint32_t)s_c.y_hi && by != gy - 1) continue;
 
-      const int tid = w * 32 + (int)lane;
-      const bool exists = tid < C.T;
+      const uint32_t tid = w * 32u + lane;
+      const bool exists = tid < (uint32_t)s_c.T;
       const uint32_t tc = exists ? s_tc[tid] : 0u;
-      int32_t x = bx * C.B[0] + (int32_t)(tc & 1023u);
-      int32_t y = by * C.B[1] + (int32_t)((tc >> 10) & 1023u);
-      int32_t z = bz * C.B[2] + (int32_t)(tc >> 20);
-      if (C.fold_axis == 1) y *= C.fold;
-      if (C.fold_axis == 2) z *= C.fold;
-      const bool valid = exists && x < C.N[0] && y < C.N[1] && z < C.N[2];
+      const int32_t x = (int32_t)bx * s_c.B[0] + (int32_t)(tc & 1023u);
+      int32_t y = (int32_t)by * s_c.B[1] + (int32_t)((tc >> 10) & 1023u);
+      int32_t z = (int32_t)bz * s_c.B[2] + (int32_t)(tc >> 20);
+      const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
+      if (faxis == 1) y *= fold;
+      if (faxis == 2) z *= fold;
+      const bool valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
       int kv = 0;
-      if (valid) kv = C.fold_axis == 1 ? min(C.fold, C.N[1] - y) : C.fold_axis == 2 ? min(C.fold, C.N[2] - z) : 1;
-      const int lv = level == 0 ? 0 : 1;
-      const int64_t rel = F.base + (int64_t)F.esize * (F.stride[0] * x + F.stride[1] * y + F.stride[2] * z) -
-                          32 * F.lo[lv];
+      if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+      const int64_t lin = s_f.stride[0] * x + s_f.stride[1] * y + s_f.stride[2] * z;
+      const int n_load = s_f.n_load;
+      const int nst = level <= 1 ? s_f.n_store : 0;
+      acc_addr += __reduce_add_sync(FULL, (uint32_t)(s_f.cnt_load[kv] + (level <= 1 ? s_f.cnt_store[kv] : 0)));
+      acc_wi += (uint32_t)(n_load + nst);
 
-      if (F.n_load > 0) {
-        uint32_t *bm = a.scratch + F.bm[level == 0 ? BM_BL : level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
-        for (int i = 0; i < F.n_load; ++i) {
+      if (level == 0) {
+        // representative block: exact per-instruction counts and bank cycles
+        const int64_t lo0 = s_f.lo[0];
+        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * lo0;
+        uint32_t *const bl = a.scratch + s_f.bm[BM_BL], *const bs = a.scratch + s_f.bm[BM_BS];
+        for (int i = 0; i < n_load; ++i) {
           const bool act = valid && (int)s_kmin[i] < kv;
           const int64_t r = rel + s_boff[i];
-          const uint32_t cnt = bitmap_insert(bm, r, act, lane, F.words[lv], bad);
-          acc_addr += __popc(__ballot_sync(FULL, act));
-          acc_wi += 1;
-          if (level == 0) {
-            acc_req += cnt;
-            acc_bank += bank_cycles_warp(r + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
-          }
+          acc_req += bitmap_insert(bl, r, act, lane, s_f.words[0], bad);
+          acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
         }
-      }
-      if (F.n_store > 0 && level <= 1) {
-        uint32_t *bm = a.scratch + F.bm[level == 0 ? BM_BS : BM_WS];
-        for (int i = F.n_load; i < F.n_load + F.n_store; ++i) {
+        for (int i = n_load; i < n_load + nst; ++i) {
           const bool act = valid && (int)s_kmin[i] < kv;
           const int64_t r = rel + s_boff[i];
-          const uint32_t cnt = bitmap_insert(bm, r, act, lane, F.words[lv], bad);
-          acc_addr += __popc(__ballot_sync(FULL, act));
-          acc_wi += 1;
-          if (level == 0) {
-            acc_st += cnt;
-            acc_bank += bank_cycles_warp(r + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
-          } else {
-            acc_sreq += cnt;
-          }
+          acc_st += bitmap_insert(bs, r, act, lane, s_f.words[0], bad);
+          acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
+        }
+      } else if (!wide) {
+        const uint32_t r0 = (uint32_t)(s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1]);
+        const uint32_t limit = (uint32_t)(s_f.words[1] << 10);
+        uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+#pragma unroll 2
+        for (int i = 0; i < n_load; ++i) {
+          const bool act = valid && (int)s_kmin[i] < kv;
+          runs_insert(bm, r0 + s_b32[i], act, limit, lane, bad, false);
+        }
+        uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
+        for (int i = n_load; i < n_load + nst; ++i) {
+          const bool act = valid && (int)s_kmin[i] < kv;
+          acc_sreq += runs_insert(ws_, r0 + s_b32[i], act, limit, lane, bad, true);
+        }
+      } else {
+        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1];
+        uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+        for (int i = 0; i < n_load; ++i) {
+          const bool act = valid && (int)s_kmin[i] < kv;
+          bitmap_insert(bm, rel + s_boff[i], act, lane, s_f.words[1], bad);
+        }
+        uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
+        for (int i = n_load; i < n_load + nst; ++i) {
+          const bool act = valid && (int)s_kmin[i] < kv;
+          acc_sreq += bitmap_insert(ws_, rel + s_boff[i], act, lane, s_f.words[1], bad);
         }
       }
-      if (F.first_of_cfg && level <= 1) {
+      if (s_f.first_of_cfg && level <= 1) {
         const uint32_t l = __reduce_add_sync(FULL, (uint32_t)kv);
         if (level == 0) acc_lb += l;
         else acc_lw += l;
@@ -215,16 +291,17 @@ __global__ void __launch_bounds__(1024) enum_kernel(EnumArgs a) {
     }
     bad = __reduce_add_sync(FULL, bad);
     if (lane == 0) {
-      unsigned long long *c = (unsigned long long *)(a.counters + (int64_t)F.cfg * N_COUNTERS);
-      if (bad) atomicAdd(c + C_OVERFLOW, (unsigned long long)bad);
-      if (acc_lb) atomicAdd(c + C_LUPS_BLOCK, acc_lb);
-      if (acc_lw) atomicAdd(c + C_LUPS_WAVE, acc_lw);
-      if (acc_req) atomicAdd(c + C_L1_REQ, acc_req);
-      if (acc_st) atomicAdd(c + C_L1_STORE, acc_st);
-      if (acc_bank) atomicAdd(c + C_BANK, acc_bank);
-      if (acc_sreq) atomicAdd(c + C_W_SREQ, acc_sreq);
-      if (acc_addr) atomicAdd(c + C_ADDR, acc_addr);
-      if (acc_wi) atomicAdd(c + C_WINSTR, acc_wi);
+      unsigned long long *c = (unsigned long long *)(a.counters + (int64_t)s_f.cfg * N_COUNTERS);
+      typedef unsigned long long u64;
+      if (bad) atomicAdd(c + C_OVERFLOW, (u64)bad);
+      if (acc_lb) atomicAdd(c + C_LUPS_BLOCK, (u64)acc_lb);
+      if (acc_lw) atomicAdd(c + C_LUPS_WAVE, (u64)acc_lw);
+      if (acc_req) atomicAdd(c + C_L1_REQ, (u64)acc_req);
+      if (acc_st) atomicAdd(c + C_L1_STORE, (u64)acc_st);
+      if (acc_bank) atomicAdd(c + C_BANK, (u64)acc_bank);
+      if (acc_sreq) atomicAdd(c + C_W_SREQ, (u64)acc_sreq);
+      if (acc_addr) atomicAdd(c + C_ADDR, (u64)acc_addr);
+      if (acc_wi) atomicAdd(c + C_WINSTR, (u64)acc_wi);
     }
     __syncthreads();
   }
@@ -266,7 +343,8 @@ __global__ void __launch_bounds__(256) count_kernel(CountArgs a) {
     const int64_t c1 = min(c0 + (int64_t)a.chunk_words, ntot);
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // block part: words [c0, min(c1, nb)) -- BL, BS
-    for (int64_t i = c0 + 4 * threadIdx.x; i < min(c1, nb); i += 4 * blockDim.x) {
+    const int64_t cb = min(c1, nb);
+    for (int64_t i = c0 + 4 * threadIdx.x; i < cb; i += 4 * blockDim.x) {
       if (F.bm[BM_BL] >= 0) {
         uint4 v = ld_clear(a.scratch + F.bm[BM_BL] + i);
         acc[0] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
@@ -278,26 +356,37 @@ __global__ void __launch_bounds__(256) count_kernel(CountArgs a) {
         acc[3] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
       }
     }
-    // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS
-    for (int64_t i = max(c0, nb) + 4 * threadIdx.x; i < c1; i += 4 * blockDim.x) {
-      const int64_t k = i - nb;
-      if (F.bm[BM_W] >= 0) {
-        uint4 w = ld_clear(a.scratch + F.bm[BM_W] + k);
-        uint4 y = ld_clear(a.scratch + F.bm[BM_Y] + k);
-        uint4 z = ld_clear(a.scratch + F.bm[BM_Z] + k);
-        acc[4] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
-        acc[5] += lines_of(w.x) + lines_of(w.y) + lines_of(w.z) + lines_of(w.w);
-        acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
-        acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
-        acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
-        acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) +
-                  __popc(w.w & z.w & ~y.w);
+    // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS; all loads of an
+    // iteration are issued before any of its zero stores
+    const bool has_w = F.bm[BM_W] >= 0, has_ws = F.bm[BM_WS] >= 0;
+    uint4 *const pw = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_W]) : nullptr;
+    uint4 *const py = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr;
+    uint4 *const pz = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr;
+    uint4 *const ps = has_ws ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr;
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t q = (max(c0, nb) - nb) / 4 + threadIdx.x; q < (c1 - nb) / 4; q += blockDim.x) {
+      uint4 w = zero, y = zero, z = zero, v = zero;
+      if (has_w) {
+        w = pw[q];
+        y = py[q];
+        z = pz[q];
       }
-      if (F.bm[BM_WS] >= 0) {
-        uint4 v = ld_clear(a.scratch + F.bm[BM_WS] + k);
-        acc[10] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        acc[11] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+      if (has_ws) v = ps[q];
+      if (has_w) {
+        pw[q] = zero;
+        py[q] = zero;
+        pz[q] = zero;
       }
+      if (has_ws) ps[q] = zero;
+      acc[4] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+      acc[5] += lines_of(w.x) + lines_of(w.y) + lines_of(w.z) + lines_of(w.w);
+      acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
+      acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
+      acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
+      acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) +
+                __popc(w.w & z.w & ~y.w);
+      acc[10] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      acc[11] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {

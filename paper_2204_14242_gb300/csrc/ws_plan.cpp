@@ -122,6 +122,16 @@ static void block_box(int64_t a, int64_t b, const int64_t g[3], int64_t lo[3], i
   }
 }
 
+static FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while (((uint64_t)1 << f.s) < d) ++f.s;
+  f.m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << f.s) - d)) / d + 1);
+  f.pad = 0;
+  return f;
+}
+
 struct Compiled {
   DCfg d{};
   std::vector<DField> f;
@@ -212,6 +222,10 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   d.lev_end[1] = d.lev_end[0] + weff * wpb;
   d.lev_end[2] = d.lev_end[1] + (y_hi - y_lo) * wpb;
   d.lev_end[3] = d.lev_end[2] + (z_hi - z_lo) * wpb;
+  if (d.lev_end[3] >= ((int64_t)1 << 31)) return WS_EINVAL;
+  d.fd_gx = make_fastdiv((uint32_t)g[0]);
+  d.fd_gy = make_fastdiv((uint32_t)g[1]);
+  d.fd_wpb = make_fastdiv((uint32_t)wpb);
 
   // point boxes (valid points only) of the block level and of wave + y + z
   int64_t pb_lo[2][3], pb_hi[2][3];
@@ -332,6 +346,14 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     const bool has_l = df.n_load > 0, has_s = df.n_store > 0;
     df.mw_end = has_l ? d.lev_end[3] : d.lev_end[1];
     df.first_of_cfg = fi == 0;
+    df.wide = (df.words[0] >= ((int64_t)1 << 22) || df.words[1] >= ((int64_t)1 << 22)) ? 1 : 0;
+    for (int kv = 0; kv <= 16; ++kv) {
+      int nl = 0, ns = 0;
+      for (auto &x : fl) nl += x.second < kv;
+      for (auto &x : fs) ns += x.second < kv;
+      df.cnt_load[kv] = (int16_t)nl;
+      df.cnt_store[kv] = (int16_t)ns;
+    }
     for (int k = 0; k < N_BITMAPS; ++k) df.bm[k] = -1;
     int64_t need = 0;
     if (has_l) need += df.words[0] + 3 * df.words[1];
@@ -410,23 +432,31 @@ int64_t ws_plan::take(size_t bytes) {
 
 static void default_tuning(ws_tuning &t) {
   if (t.chunk_warps <= 0) t.chunk_warps = 64;
+  if (t.pass_mb == 0) t.pass_mb = 96;
   if (t.enum_threads <= 0) t.enum_threads = 256;
   if (t.count_words <= 0) t.count_words = 16384;
-  t.enum_threads = std::max(64, std::min(1024, t.enum_threads / 32 * 32));
+  t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
   t.count_words = std::max(256, t.count_words / 4 * 4);
   t.chunk_warps = std::max(1, t.chunk_warps);
+  if (t.pass_mb < 0) t.pass_mb = -1;
 }
 
 // Numbers work items and cuts passes for the current tuning.
 void ws_plan::layout() {
   passes.clear();
+  // pass capacity: the tuned pass size, never below the largest field, never above
+  // the scratch the plan holds
+  int64_t max_need = 0;
+  for (int64_t w : need_words) max_need = std::max(max_need, w);
+  int64_t cap = scratch_words;
+  if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
   int64_t items = 0, citems = 0, used = 0;
   DPass cur{0, 0, 0, 0, 0, 0};
   const int ncf = (int)hfld.size();
   for (int cf = 0; cf < ncf; ++cf) {
     DField &f = hfld[cf];
     int64_t need = need_words[cf];
-    if (used + need > scratch_words && cf > cur.cf_lo) {
+    if (used + need > cap && cf > cur.cf_lo) {
       cur.cf_hi = cf;
       cur.item_hi = items;
       cur.citem_hi = citems;
@@ -987,15 +1017,18 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
   float win_ms = -1.f;
   const int chunks[] = {16, 64, 256, 1024};
   const int threads[] = {256, 512};
+  const int pass_mbs[] = {48, 96, -1};
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   int rc = WS_OK;
   for (int ch : chunks) {
     for (int th : threads) {
+      for (int pm : pass_mbs) {
       p->tune = orig;
       p->tune.chunk_warps = ch;
       p->tune.enum_threads = th;
+      p->tune.pass_mb = pm;
       p->layout();
       if ((rc = p->upload_fields(st)) != WS_OK) break;
       if ((rc = p->enqueue(st, nullptr, nullptr)) != WS_OK) break;  // warm-up
@@ -1010,6 +1043,8 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
         win_ms = ms;
         win = p->tune;
       }
+      }
+      if (rc != WS_OK) break;
     }
     if (rc != WS_OK) break;
   }
@@ -1138,7 +1173,8 @@ extern "C" int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_
 }
 
 // ---------------------------------------------------------------------------------
-// autotuner cache: one line per workload class, "n_cfg_bucket chunk threads words"
+// autotuner cache: one line per workload class,
+// "log2(n_cfg) chunk_warps enum_threads count_words ctas_per_sm pass_mb"
 // ---------------------------------------------------------------------------------
 static int bucket(int n) {
   int b = 0;
@@ -1153,15 +1189,16 @@ void ws::tuning_cache_lookup(ws_ctx *ctx, int n_cfg, ws_tuning *t) {
   const char *path = getenv("WS_TUNE_CACHE");
   if (!path || !*path) return;
   std::ifstream f(path);
-  int b, ch, th, cw, cs;
+  int b, ch, th, cw, cs, pm;
   std::string line;
   while (std::getline(f, line)) {
     std::istringstream is(line);
-    if (is >> b >> ch >> th >> cw >> cs && b == bucket(n_cfg)) {
+    if (is >> b >> ch >> th >> cw >> cs >> pm && b == bucket(n_cfg)) {
       t->chunk_warps = ch;
       t->enum_threads = th;
       t->count_words = cw;
       t->ctas_per_sm = cs;
+      t->pass_mb = pm;
     }
   }
   (void)ctx;
@@ -1172,6 +1209,6 @@ void ws::tuning_cache_store(ws_ctx *ctx, int n_cfg, const ws_tuning &t) {
   if (!path || !*path) return;
   std::ofstream f(path, std::ios::app);
   f << bucket(n_cfg) << " " << t.chunk_warps << " " << t.enum_threads << " " << t.count_words << " "
-    << t.ctas_per_sm << "\n";
+    << t.ctas_per_sm << " " << t.pass_mb << "\n";
   (void)ctx;
 }

@@ -174,13 +174,18 @@ def test_edge_cases(ctx):
 def test_multi_pass_equals_single_pass(ctx):
     cfgs = W.lbm_sweep(N=(128, 96, 64))[::5]
     hw = W.a100()
-    with B.Plan(ctx, cfgs, hw) as p:
+    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": -1}) as p:
         p.execute(B.WS_MODE_BATCHED)
         ref, ref_o = p.results()
         assert p.profile()["passes"] == 1
+    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": 16}) as p:
+        assert p.profile()["passes"] > 4
+        p.execute(B.WS_MODE_BATCHED)
+        r16, o16 = p.results()
+    assert r16.tobytes() == ref.tobytes() and o16.tobytes() == ref_o.tobytes()
     small = B.Context(0, 96 << 20)
     try:
-        with B.Plan(small, cfgs, hw) as p:
+        with B.Plan(small, cfgs, hw, tuning={"pass_mb": -1}) as p:
             prof = p.profile()
             assert prof["passes"] > 1
             p.execute(B.WS_MODE_BATCHED)
@@ -211,7 +216,7 @@ def test_autotune_keeps_results(ctx):
         p.execute(B.WS_MODE_BATCHED)
         r1, o1 = p.results()
         best = p.autotune()
-        assert best["chunk_warps"] in (16, 64, 256, 1024)
+        assert best["chunk_warps"] in (16, 64, 256, 1024) and best["pass_mb"] in (48, 96, -1)
         p.execute(B.WS_MODE_BATCHED)
         r2, o2 = p.results()
         prof = p.profile()
