@@ -244,6 +244,33 @@ int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_fi
                       const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
                       int32_t *order_out, int mode, void *stream);
 
+/* ---- estimation without device allocation ------------------------------------------ */
+/* Size of the fixed device scratch of ws_estimate_batch_noalloc: 32 MiB, reserved on
+ * every GPU that loads this library's device code, for as long as the process lives. */
+#define WS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The paper has no counterpart: this is a deployment variant of ws_estimate_batch for
+ * callers that must not allocate device memory (a code generator running inside an
+ * application whose device memory is owned by another runtime or a fixed pool, or
+ * whose steady state forbids allocation).  Same inputs and outputs as
+ * ws_estimate_batch (host buffers; results and ranking of the whole batch), same
+ * kernels launched directly on `stream` (NULL = legacy default stream), but every
+ * device buffer comes from one fixed array of WS_NOALLOC_SCRATCH_BYTES inside the
+ * library: no cudaMalloc, cudaFree, stream creation or library allocator is called.
+ *   - The first call on a device (that device is made current) looks up the array's
+ *     device address with cudaGetSymbolAddress; make that first call before any
+ *     stream capture.
+ *   - A batch whose descriptors plus its largest field's bitmaps plus 8 MiB of
+ *     headroom exceed the array returns WS_ENOMEM (ws_last_error says by how much);
+ *     larger batches otherwise run in several bitmap passes.
+ *   - All calls on a device share the array and each call clears the bitmaps it
+ *     uses; calls whose device work overlaps (other host threads, other streams)
+ *     race on it and must be serialised by the caller.  Calls from several host
+ *     threads are serialised on the host, but not across processes. */
+int ws_estimate_batch_noalloc(int device, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                              const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
+                              int32_t *order_out, void *stream);
+
 /* Stable ranking on the device (Sec. 5.7): ascending t_pred rounded to 40
  * significant bits, ties by index; NaN ranks as +inf.  res: n host results. */
 int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_out, void *stream);

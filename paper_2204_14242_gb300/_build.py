@@ -15,7 +15,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["ws_kernels.cu", "ws_peaks.cu"]
+CU_SOURCES = ["ws_kernels.cu", "ws_peaks.cu", "ws_noalloc.cu"]
 CPP_SOURCES = ["ws_plan.cpp", "ws_server.cpp"]
 HEADERS = ["ws_internal.h", "ws_kernels.h", "ws_host.h"]
 

@@ -72,7 +72,7 @@ EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_
            "ws_plan_create", "ws_plan_execute", "ws_plan_results", "ws_plan_device_results", "ws_plan_profile",
            "ws_autotune", "ws_plan_destroy", "ws_estimate_batch", "ws_rank", "ws_rank_key", "ws_server_create",
            "ws_server_submit", "ws_server_poll", "ws_server_stats_get", "ws_server_destroy", "ws_describe",
-           "ws_describe_fields", "ws_measure_peaks"]
+           "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc"]
 
 
 class WsError(RuntimeError):
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = False):
             "ws_server_poll": ([P, ctypes.c_uint64, P, P, I64], I), "ws_server_stats_get": ([P, P], I),
             "ws_server_destroy": ([P], I), "ws_describe": ([P, I, P, I, P, I, P, P], I),
             "ws_describe_fields": ([P, P, I, P, I, P, P], I), "ws_measure_peaks": ([P, P, P], I),
+            "ws_estimate_batch_noalloc": ([I, P, I, P, I, P, I, P, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -398,6 +399,23 @@ def ws_estimate_batch(ctx: Context, configs=None, hw=None, mode: int = WS_MODE_B
     _check(lib.ws_estimate_batch(ctx.handle, _ptr(cfg), len(cfg), _ptr(fld), len(fld), _ptr(acc), len(acc),
                                  h.ctypes.data, _ptr(res), _ptr(order), mode, _stream_handle(stream)),
            "ws_estimate_batch")
+    return res, order
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def ws_estimate_batch_noalloc(device: int = 0, configs=None, hw=None, stream=None, arrays=None):
+    """ws_estimate_batch for callers that cannot allocate device memory: every device
+    buffer comes from the library's fixed 32 MiB scratch (no context needed)."""
+    lib = load()
+    cfg, fld, acc = arrays if arrays is not None else marshal(configs)
+    h = hw if isinstance(hw, np.ndarray) else hw_struct(hw)
+    res = np.zeros(len(cfg), RESULT)
+    order = np.zeros(len(cfg), np.int32)
+    _check(lib.ws_estimate_batch_noalloc(device, _ptr(cfg), len(cfg), _ptr(fld), len(fld), _ptr(acc), len(acc),
+                                         h.ctypes.data, _ptr(res), _ptr(order), _stream_handle(stream)),
+           "ws_estimate_batch_noalloc")
     return res, order
 
 
