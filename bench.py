@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--arena-gb", type=float, default=48.0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default tuning instead of autotuning the plan before timing")
+    ap.add_argument("--subset", type=int, default=1,
+                    help="keep every K-th candidate (small cases for profiling); 1 = the whole workload")
     return ap.parse_args()
 
 
@@ -259,6 +263,9 @@ def main():
     from paper_2204_14242_gb300 import workloads as W
 
     cfgs, cfg_meta = workload(args.workload)
+    if args.subset > 1:
+        cfgs = cfgs[::args.subset]
+        cfg_meta = dict(cfg_meta, candidates=len(cfgs), subset=f"every {args.subset}-th candidate")
     hw = W.a100()
     ctx = B.Context(local, int(args.arena_gb * (1 << 30)))
     stream = torch.cuda.Stream()
@@ -266,6 +273,7 @@ def main():
     arrays = B.marshal(cfgs)
     plan = B.Plan(ctx, arrays=arrays, hw=hw)
     prof0 = plan.profile(stream)   # first direct step: also warms up the kernels
+    tuning = plan.autotune(stream) if args.autotune else None
 
     def barrier():
         if dist is not None:
@@ -339,12 +347,13 @@ def main():
 
     out = None
     if rank == 0:
-        base = cpu_baseline(cfgs, hw, args.cpu_seconds) if world == 1 else None
+        base = cpu_baseline(cfgs, hw, args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
                "config": dict(cfg_meta, parallelism=f"replicas x{world} (independent candidates, no collective)",
-                              l2="flushed between steps (256 MiB write)", mode="batched: persistent + CUDA graph"),
+                              l2="flushed between steps (256 MiB write)", mode="batched: persistent + CUDA graph",
+                              tuning=tuning),
                "unique_sectors_per_s": sectors_per_s,
                "e2e": {"value": len(cfgs) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},

@@ -62,6 +62,7 @@ struct DField {
   int64_t item_begin;     // first enumeration work item (global numbering)
   int64_t citem_begin;    // first counting work item
   int64_t mw_end;         // modelled warps this field visits (loads: all levels, stores: block + wave)
+  int64_t mw_block;       // modelled warps of the representative block (work item 0 of the field)
   int32_t esize;
   int32_t n_load, n_store;// folded access counts (loads first, then stores)
   int32_t acc_begin;      // index into the DAcc array

@@ -88,13 +88,30 @@ __device__ int bank_cycles_warp(int64_t addr, bool act, uint32_t lane, int banks
   return __reduce_add_sync(FULL, (uint32_t)cycles);
 }
 
+// Last (candidate, field) index in [lo, hi) whose first work item is <= item.  Items
+// are handed out in increasing order, so a CTA's next item never lies before the field
+// of its previous one (`hint`): gallop forward from there, then bisect.
 __device__ __forceinline__ int find_cf(const DField *__restrict__ fld, int lo, int hi, int64_t item,
-                                       bool counting) {
-  // last cf in [lo, hi) whose first item is <= item
+                                       bool counting, int hint) {
+  auto begin = [&](int i) { return counting ? fld[i].citem_begin : fld[i].item_begin; };
+  if (hint >= lo && hint < hi && begin(hint) <= item) {
+    int step = 1, l = hint, r = hi;
+    for (;;) {
+      const int nx = l + step;
+      if (nx >= hi) break;
+      if (begin(nx) > item) {
+        r = nx;
+        break;
+      }
+      l = nx;
+      step <<= 1;
+    }
+    lo = l;
+    hi = r;
+  }
   while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    int64_t b = counting ? fld[mid].citem_begin : fld[mid].item_begin;
-    if (b <= item) lo = mid;
+    const int mid = (lo + hi) >> 1;
+    if (begin(mid) <= item) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -151,8 +168,15 @@ __device__ __forceinline__ uint32_t runs_insert(uint32_t *__restrict__ bm, uint3
   return cnt;
 }
 
+// Fields with at least this many folded loads enumerate wave / y / z loads lane per
+// access: each lane walks the 32 threads of the modelled warp for its own access and
+// merges consecutive sectors of one bitmap word in a register.
+constexpr int kLanePerAccessMin = 12;
+
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ DField s_f;
+  __shared__ __align__(16) uint32_t s_tbase[16][32];   // per warp: relative address of each thread's first point
+  __shared__ uint8_t s_tkv[16][32];      // per warp: valid folded points of each thread
   __shared__ DCfg s_c;
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
   __shared__ uint32_t s_b32[kMaxFoldedAccesses];
@@ -170,7 +194,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.item_hi) break;
-    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, false);
+    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, false, cur_cf);
     if (cf != cur_cf) {
       if (threadIdx.x == 0) s_f = a.fld[cf];
       __syncthreads();
@@ -195,8 +219,11 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     }
     // descriptors of this item: read from shared memory where used (broadcast loads)
     const bool wide = s_f.wide != 0;
-    const uint32_t mw0 = (uint32_t)((item - s_f.item_begin) * (int64_t)a.chunk);
-    const uint32_t mw1 = (uint32_t)min((int64_t)mw0 + a.chunk, s_f.mw_end);
+    // item 0 of a field covers the representative block, the others chunks of the rest
+    const int64_t k = item - s_f.item_begin;
+    const uint32_t mw0 = k == 0 ? 0u : (uint32_t)(s_f.mw_block + (k - 1) * (int64_t)a.chunk);
+    const uint32_t mw1 = k == 0 ? (uint32_t)s_f.mw_block
+                                : (uint32_t)min(s_f.mw_block + k * (int64_t)a.chunk, s_f.mw_end);
     uint32_t acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0, acc_addr = 0, acc_wi = 0;
     uint32_t bad = 0;
 
@@ -257,13 +284,96 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
           acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
         }
       } else if (!wide) {
-        const uint32_t r0 = (uint32_t)(s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1]);
+        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1];
+        const uint32_t r0 = (uint32_t)rel;
         const uint32_t limit = (uint32_t)(s_f.words[1] << 10);
         uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+        if (n_load >= kLanePerAccessMin) {
+          // lane per access: stage the warp's thread bases, then every lane walks the
+          // threads for its access, merging sectors of one word in a register
+          s_tbase[warp][lane] = r0;
+          s_tkv[warp][lane] = (uint8_t)kv;
+          const uint32_t vmask = __ballot_sync(FULL, valid);
+          // a thread with fewer valid folded points than the fold skips some accesses;
+          // such warps (only at the domain edge) bound-check every address
+          const bool partial = __any_sync(FULL, valid && kv < fold);
+          int64_t mn = valid ? rel : INT64_MAX, mx = valid ? rel : INT64_MIN;
+#pragma unroll
+          for (int off = 16; off >= 1; off >>= 1) {
+            mn = min(mn, (int64_t)__shfl_xor_sync(FULL, (long long)mn, off));
+            mx = max(mx, (int64_t)__shfl_xor_sync(FULL, (long long)mx, off));
+          }
+          __syncwarp();
+          for (int a0 = 0; a0 < n_load && vmask; a0 += 32) {
+            const int ai = a0 + (int)lane;
+            if (ai >= n_load) continue;
+            const uint32_t b32 = s_b32[ai];
+            const int km = s_kmin[ai];
+            uint32_t cw = 0xffffffffu, cb = 0u;
+            if (!partial) {
+              // every valid thread issues every access: one range check per lane
+              const int64_t bo = s_boff[ai];
+              if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
+                bad += __popc(vmask);
+                continue;
+              }
+              // merge the sector bits of one word in a register; a word change flushes
+              // the previous word with one red.or (predicated, no branch)
+              auto step = [&](uint32_t tb) {
+                const uint32_t r = tb + b32;
+                const uint32_t w = r >> 10;
+                const bool flush = w != cw;
+                if (flush && cb) atomicOr(bm + cw, cb);
+                cb = (flush ? 0u : cb) | __funnelshift_l(0u, 1u, r >> 5);
+                cw = w;
+              };
+              const uint4 *tb4 = reinterpret_cast<const uint4 *>(&s_tbase[warp][0]);
+              if (vmask == FULL) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const uint4 v = tb4[q];
+                  step(v.x);
+                  step(v.y);
+                  step(v.z);
+                  step(v.w);
+                }
+              } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const uint4 v = tb4[q];
+                  const uint32_t m = vmask >> (4 * q);
+                  if (m & 1u) step(v.x);
+                  if (m & 2u) step(v.y);
+                  if (m & 4u) step(v.z);
+                  if (m & 8u) step(v.w);
+                }
+              }
+            } else {
+              for (int t = 0; t < 32; ++t) {
+                if (!((vmask >> t) & 1u) || km >= (int)s_tkv[warp][t]) continue;
+                const uint32_t r = s_tbase[warp][t] + b32;
+                if (r >= limit) {
+                  ++bad;
+                  continue;
+                }
+                const uint32_t w = r >> 10;
+                if (w != cw) {
+                  if (cb) atomicOr(bm + cw, cb);
+                  cw = w;
+                  cb = 0u;
+                }
+                cb |= 1u << ((r >> 5) & 31u);
+              }
+            }
+            if (cb) atomicOr(bm + cw, cb);
+          }
+          __syncwarp();
+        } else {
 #pragma unroll 2
-        for (int i = 0; i < n_load; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          runs_insert(bm, r0 + s_b32[i], act, limit, lane, bad, false);
+          for (int i = 0; i < n_load; ++i) {
+            const bool act = valid && (int)s_kmin[i] < kv;
+            runs_insert(bm, r0 + s_b32[i], act, limit, lane, bad, false);
+          }
         }
         uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
         for (int i = n_load; i < n_load + nst; ++i) {
@@ -324,17 +434,35 @@ __device__ __forceinline__ uint4 ld_clear(uint32_t *p) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) count_kernel(CountArgs a) {
+__device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z,
+                                           const uint4 &v) {
+  acc[4] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+  acc[5] += lines_of(w.x) + lines_of(w.y) + lines_of(w.z) + lines_of(w.w);
+  acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
+  acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
+  acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
+  acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
+  acc[10] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+  acc[11] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+}
+
+// Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of
+// words); each thread keeps two 16-byte positions of every bitmap in flight before it
+// clears them.
+__global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
   __shared__ long long s_item;
-  __shared__ uint32_t s_red[8][12];
+  __shared__ uint32_t s_red[16][12];
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
+  int cur = -1;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
   for (;;) {
     if (threadIdx.x == 0) s_item = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.citem_hi) break;
-    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, true);
+    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, true, cur);
+    cur = cf;
     const DField &F = a.fld[cf];
     const bool has_blk = F.bm[BM_BL] >= 0 || F.bm[BM_BS] >= 0;
     const int64_t nb = has_blk ? F.words[0] : 0;
@@ -356,37 +484,47 @@ __global__ void __launch_bounds__(256) count_kernel(CountArgs a) {
         acc[3] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
       }
     }
-    // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS; all loads of an
-    // iteration are issued before any of its zero stores
+    // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS
     const bool has_w = F.bm[BM_W] >= 0, has_ws = F.bm[BM_WS] >= 0;
     uint4 *const pw = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_W]) : nullptr;
     uint4 *const py = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr;
     uint4 *const pz = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr;
     uint4 *const ps = has_ws ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr;
-    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-    for (int64_t q = (max(c0, nb) - nb) / 4 + threadIdx.x; q < (c1 - nb) / 4; q += blockDim.x) {
-      uint4 w = zero, y = zero, z = zero, v = zero;
+    const int64_t q1 = (c1 - nb) / 4;
+    for (int64_t q = (max(c0, nb) - nb) / 4 + threadIdx.x; q < q1; q += 2 * (int64_t)blockDim.x) {
+      const int64_t qb = q + blockDim.x;
+      const bool two = qb < q1;
+      uint4 w0 = zero, y0 = zero, z0 = zero, v0 = zero, w1 = zero, y1 = zero, z1 = zero, v1 = zero;
       if (has_w) {
-        w = pw[q];
-        y = py[q];
-        z = pz[q];
+        w0 = pw[q];
+        y0 = py[q];
+        z0 = pz[q];
+        if (two) {
+          w1 = pw[qb];
+          y1 = py[qb];
+          z1 = pz[qb];
+        }
       }
-      if (has_ws) v = ps[q];
+      if (has_ws) {
+        v0 = ps[q];
+        if (two) v1 = ps[qb];
+      }
       if (has_w) {
         pw[q] = zero;
         py[q] = zero;
         pz[q] = zero;
+        if (two) {
+          pw[qb] = zero;
+          py[qb] = zero;
+          pz[qb] = zero;
+        }
       }
-      if (has_ws) ps[q] = zero;
-      acc[4] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
-      acc[5] += lines_of(w.x) + lines_of(w.y) + lines_of(w.z) + lines_of(w.w);
-      acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
-      acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
-      acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
-      acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) +
-                __popc(w.w & z.w & ~y.w);
-      acc[10] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-      acc[11] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+      if (has_ws) {
+        ps[q] = zero;
+        if (two) ps[qb] = zero;
+      }
+      tally_wave(acc, w0, y0, z0, v0);
+      tally_wave(acc, w1, y1, z1, v1);
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -397,10 +535,7 @@ __global__ void __launch_bounds__(256) count_kernel(CountArgs a) {
     if (threadIdx.x < 12) {
       unsigned long long t = 0;
       for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += s_red[wi][threadIdx.x];
-      if (t) {
-        const int d = kCountDst[threadIdx.x];
-        atomicAdd((unsigned long long *)(a.counters + (int64_t)F.cfg * N_COUNTERS + d), t);
-      }
+      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)F.cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
     }
     __syncthreads();
   }
@@ -559,7 +694,7 @@ cudaError_t launch_enum(const EnumArgs &args, int grid, int threads, cudaStream_
   return cudaGetLastError();
 }
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
-  count_kernel<<<grid, 256, 0, st>>>(args);
+  count_kernel<<<grid, 512, 0, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st) {
@@ -581,7 +716,7 @@ cudaError_t enum_occupancy(int threads, int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, enum_kernel, threads, 0);
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, 256, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, 512, 0);
 }
 
 }  // namespace ws

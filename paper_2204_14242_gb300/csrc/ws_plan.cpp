@@ -345,6 +345,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     }
     const bool has_l = df.n_load > 0, has_s = df.n_store > 0;
     df.mw_end = has_l ? d.lev_end[3] : d.lev_end[1];
+    df.mw_block = d.lev_end[0];
     df.first_of_cfg = fi == 0;
     df.wide = (df.words[0] >= ((int64_t)1 << 22) || df.words[1] >= ((int64_t)1 << 22)) ? 1 : 0;
     for (int kv = 0; kv <= 16; ++kv) {
@@ -431,10 +432,10 @@ int64_t ws_plan::take(size_t bytes) {
 }
 
 static void default_tuning(ws_tuning &t) {
-  if (t.chunk_warps <= 0) t.chunk_warps = 64;
+  if (t.chunk_warps <= 0) t.chunk_warps = 1024;
   if (t.pass_mb == 0) t.pass_mb = 96;
   if (t.enum_threads <= 0) t.enum_threads = 256;
-  if (t.count_words <= 0) t.count_words = 16384;
+  if (t.count_words <= 0) t.count_words = 65536;
   t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
   t.count_words = std::max(256, t.count_words / 4 * 4);
   t.chunk_warps = std::max(1, t.chunk_warps);
@@ -480,7 +481,8 @@ void ws_plan::layout() {
     used = o;
     f.item_begin = items;
     f.citem_begin = citems;
-    items += ceil_div(f.mw_end, tune.chunk_warps);
+    // item 0: the representative block (slow exact path); then chunks of the rest
+    items += 1 + ceil_div(f.mw_end - f.mw_block, tune.chunk_warps);
     citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
   }
   cur.cf_hi = ncf;
@@ -555,7 +557,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ca.cf_hi = P.cf_hi;
     ca.chunk_words = tune.count_words;
     if (P.citem_hi > P.citem_lo) {
-      CU(launch_count(ca, grid_for(256, P.citem_hi - P.citem_lo, true), st));
+      CU(launch_count(ca, grid_for(512, P.citem_hi - P.citem_lo, true), st));
       ++launches;
     }
     if ((rc = mark(2 + 2 * (int)p)) != WS_OK) return rc;
@@ -624,7 +626,7 @@ int ws_plan::run_plain(cudaStream_t st) {
       ca.cf_lo = lo;
       ca.cf_hi = hi;
       ca.chunk_words = tune.count_words;
-      if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(256, ct_hi - ct_lo, true), st));
+      if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(512, ct_hi - ct_lo, true), st));
     }
     ModelArgs ma;
     ma.cfg = (const DCfg *)dev(d_cfg) + i;
@@ -1015,7 +1017,7 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
   const ws_tuning orig = p->tune;
   ws_tuning win = orig;
   float win_ms = -1.f;
-  const int chunks[] = {16, 64, 256, 1024};
+  const int chunks[] = {64, 256, 1024, 4096};
   const int threads[] = {256, 512};
   const int pass_mbs[] = {48, 96, -1};
   cudaEvent_t e0, e1;

@@ -216,7 +216,7 @@ def test_autotune_keeps_results(ctx):
         p.execute(B.WS_MODE_BATCHED)
         r1, o1 = p.results()
         best = p.autotune()
-        assert best["chunk_warps"] in (16, 64, 256, 1024) and best["pass_mb"] in (48, 96, -1)
+        assert best["chunk_warps"] in (64, 256, 1024, 4096) and best["pass_mb"] in (48, 96, -1)
         p.execute(B.WS_MODE_BATCHED)
         r2, o2 = p.results()
         prof = p.profile()
