@@ -146,7 +146,7 @@ typedef struct ws_tuning {
   int32_t enum_threads;    /* threads per CTA of the enumeration kernel (128..1024)      */
   int32_t count_words;     /* bitmap words per counting work item                        */
   int32_t ctas_per_sm;     /* persistent CTAs per SM (0 = occupancy limit)               */
-  int32_t pass_mb;         /* bitmap scratch per pass in MiB, sized to stay in L2 (0 = 96,
+  int32_t pass_mb;         /* bitmap scratch per pass in MiB, e.g. sized to stay in L2 (0 or
                               < 0 = as large as the arena allows); never below one field   */
 } ws_tuning;
 
@@ -239,7 +239,9 @@ int ws_describe_fields(const ws_config *cfg, const ws_field *fld, int n_fld, con
                        const ws_hw *hw, ws_field_info *out);
 
 /* One-shot estimate from host buffers: plan_create + execute + results + destroy.
- * out: n_cfg results; order_out (may be NULL): ranking of the whole batch. */
+ * out: n_cfg results; order_out (may be NULL): ranking of the whole batch.  In
+ * WS_MODE_BATCHED the batched kernels are launched directly (a graph of a one-shot
+ * plan would be replayed only once); results are identical in every mode. */
 int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                       const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
                       int32_t *order_out, int mode, void *stream);

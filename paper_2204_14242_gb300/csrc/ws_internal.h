@@ -69,7 +69,7 @@ struct DField {
   int32_t cfg;            // owning candidate
   int32_t first_of_cfg;   // 1 if this is the candidate's first field (counts LUPs)
   int32_t wide;           // a bitmap spans >= 2^32 bytes: 64-bit address path
-  int32_t pad;
+  int32_t lpa_log2p;      // log2 of P = lanes per thread-slice group for the load walk (P >= n_load, <= 32)
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };

@@ -168,10 +168,52 @@ __device__ __forceinline__ uint32_t runs_insert(uint32_t *__restrict__ bm, uint3
   return cnt;
 }
 
-// Fields with at least this many folded loads enumerate wave / y / z loads lane per
-// access: each lane walks the 32 threads of the modelled warp for its own access and
-// merges consecutive sectors of one bitmap word in a register.
-constexpr int kLanePerAccessMin = 12;
+// Lane-per-access walk of the wave / y / z loads.  With P = the smallest power of two
+// >= the field's folded loads (at most 32), the warp's lanes form 32/P groups of P
+// lanes; lane (g, a) evaluates access a for the P threads g*P .. g*P+P-1 of the
+// modelled warp, merging the sector bits of one bitmap word in a register and
+// flushing it with one red.or when the word changes.  tbase: the slice's relative
+// thread addresses; slice: which of them are valid.
+template <int P>
+__device__ __forceinline__ void lpa_walk(const uint32_t *__restrict__ tbase, uint32_t slice, uint32_t b32,
+                                         uint32_t *__restrict__ bm, uint32_t &cw, uint32_t &cb) {
+  auto step = [&](uint32_t tb) {
+    const uint32_t r = tb + b32;
+    const uint32_t w = r >> 10;
+    const bool flush = w != cw;
+    if (flush && cb) atomicOr(bm + cw, cb);
+    cb = (flush ? 0u : cb) | __funnelshift_l(0u, 1u, r >> 5);
+    cw = w;
+  };
+  constexpr uint32_t full = P == 32 ? 0xffffffffu : ((1u << P) - 1u);
+  if (P >= 4) {
+    const uint4 *t4 = reinterpret_cast<const uint4 *>(tbase);
+    if (slice == full) {
+#pragma unroll
+      for (int q = 0; q < P / 4; ++q) {
+        const uint4 v = t4[q];
+        step(v.x);
+        step(v.y);
+        step(v.z);
+        step(v.w);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < P / 4; ++q) {
+        const uint4 v = t4[q];
+        const uint32_t m = slice >> (4 * q);
+        if (m & 1u) step(v.x);
+        if (m & 2u) step(v.y);
+        if (m & 4u) step(v.z);
+        if (m & 8u) step(v.w);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < P; ++t)
+      if ((slice >> t) & 1u) step(tbase[t]);
+  }
+}
 
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ DField s_f;
@@ -288,9 +330,8 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         const uint32_t r0 = (uint32_t)rel;
         const uint32_t limit = (uint32_t)(s_f.words[1] << 10);
         uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
-        if (n_load >= kLanePerAccessMin) {
-          // lane per access: stage the warp's thread bases, then every lane walks the
-          // threads for its access, merging sectors of one word in a register
+        if (n_load > 0) {
+          // stage the warp's thread addresses, then walk them lane per access
           s_tbase[warp][lane] = r0;
           s_tkv[warp][lane] = (uint8_t)kv;
           const uint32_t vmask = __ballot_sync(FULL, valid);
@@ -304,76 +345,61 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
             mx = max(mx, (int64_t)__shfl_xor_sync(FULL, (long long)mx, off));
           }
           __syncwarp();
-          for (int a0 = 0; a0 < n_load && vmask; a0 += 32) {
-            const int ai = a0 + (int)lane;
-            if (ai >= n_load) continue;
-            const uint32_t b32 = s_b32[ai];
-            const int km = s_kmin[ai];
+          const int lp = s_f.lpa_log2p, P = 1 << lp;
+          const uint32_t al = lane & (uint32_t)(P - 1), g0 = (lane >> lp) << lp;
+          const uint32_t slice = (P == 32 ? vmask : (vmask >> g0) & ((1u << P) - 1u));
+          const uint32_t *tb = &s_tbase[warp][g0];
+          for (int a0 = 0; a0 < n_load && vmask; a0 += P) {
+            const int ai = a0 + (int)al;
             uint32_t cw = 0xffffffffu, cb = 0u;
-            if (!partial) {
-              // every valid thread issues every access: one range check per lane
-              const int64_t bo = s_boff[ai];
-              if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
-                bad += __popc(vmask);
-                continue;
-              }
-              // merge the sector bits of one word in a register; a word change flushes
-              // the previous word with one red.or (predicated, no branch)
-              auto step = [&](uint32_t tb) {
-                const uint32_t r = tb + b32;
-                const uint32_t w = r >> 10;
-                const bool flush = w != cw;
-                if (flush && cb) atomicOr(bm + cw, cb);
-                cb = (flush ? 0u : cb) | __funnelshift_l(0u, 1u, r >> 5);
-                cw = w;
-              };
-              const uint4 *tb4 = reinterpret_cast<const uint4 *>(&s_tbase[warp][0]);
-              if (vmask == FULL) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  const uint4 v = tb4[q];
-                  step(v.x);
-                  step(v.y);
-                  step(v.z);
-                  step(v.w);
+            if (ai < n_load && slice) {
+              const uint32_t b32 = s_b32[ai];
+              if (!partial) {
+                // every valid thread issues every access: one range check per lane
+                const int64_t bo = s_boff[ai];
+                if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
+                  bad += __popc(slice);
+                } else {
+                  switch (lp) {
+                    case 0: lpa_walk<1>(tb, slice, b32, bm, cw, cb); break;
+                    case 1: lpa_walk<2>(tb, slice, b32, bm, cw, cb); break;
+                    case 2: lpa_walk<4>(tb, slice, b32, bm, cw, cb); break;
+                    case 3: lpa_walk<8>(tb, slice, b32, bm, cw, cb); break;
+                    case 4: lpa_walk<16>(tb, slice, b32, bm, cw, cb); break;
+                    default: lpa_walk<32>(tb, slice, b32, bm, cw, cb); break;
+                  }
                 }
               } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  const uint4 v = tb4[q];
-                  const uint32_t m = vmask >> (4 * q);
-                  if (m & 1u) step(v.x);
-                  if (m & 2u) step(v.y);
-                  if (m & 4u) step(v.z);
-                  if (m & 8u) step(v.w);
+                const int km = s_kmin[ai];
+                for (int t = 0; t < P; ++t) {
+                  if (!((slice >> t) & 1u) || km >= (int)s_tkv[warp][g0 + t]) continue;
+                  const uint32_t r = tb[t] + b32;
+                  if (r >= limit) {
+                    ++bad;
+                    continue;
+                  }
+                  const uint32_t w = r >> 10;
+                  if (w != cw) {
+                    if (cb) atomicOr(bm + cw, cb);
+                    cw = w;
+                    cb = 0u;
+                  }
+                  cb |= 1u << ((r >> 5) & 31u);
                 }
-              }
-            } else {
-              for (int t = 0; t < 32; ++t) {
-                if (!((vmask >> t) & 1u) || km >= (int)s_tkv[warp][t]) continue;
-                const uint32_t r = s_tbase[warp][t] + b32;
-                if (r >= limit) {
-                  ++bad;
-                  continue;
-                }
-                const uint32_t w = r >> 10;
-                if (w != cw) {
-                  if (cb) atomicOr(bm + cw, cb);
-                  cw = w;
-                  cb = 0u;
-                }
-                cb |= 1u << ((r >> 5) & 31u);
               }
             }
-            if (cb) atomicOr(bm + cw, cb);
+            if (P == 32) {
+              if (cb) atomicOr(bm + cw, cb);
+            } else {
+              // several slices per access: lanes whose last word coincides (other
+              // slices, other accesses) merge it into one red.or
+              const uint32_t key = cb ? cw : (0x80000000u | lane);
+              const uint32_t m = __match_any_sync(FULL, key);
+              const uint32_t orcb = __reduce_or_sync(m, cb);
+              if (cb && lane == (uint32_t)(__ffs(m) - 1)) atomicOr(bm + cw, orcb);
+            }
           }
           __syncwarp();
-        } else {
-#pragma unroll 2
-          for (int i = 0; i < n_load; ++i) {
-            const bool act = valid && (int)s_kmin[i] < kv;
-            runs_insert(bm, r0 + s_b32[i], act, limit, lane, bad, false);
-          }
         }
         uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
         for (int i = n_load; i < n_load + nst; ++i) {

@@ -14,6 +14,7 @@
 #include <set>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -136,14 +137,107 @@ struct Compiled {
   DCfg d{};
   std::vector<DField> f;
   std::vector<std::vector<DAcc>> acc;
+  std::vector<uint64_t> fkey;       // (field index, folding): equal keys have equal access lists
   std::vector<int64_t> need_words;  // bitmap words per field
 };
 
 typedef std::tuple<int64_t, int64_t, int64_t, int64_t> Off4;
 
-// Returns WS_OK or a per-candidate error status.
+// What a field compiles to for one folding (independent of domain and block shape):
+// folded access list with byte offsets and first needed folded point, the raw offset
+// range, and per-kv issued-access counts.
+struct FieldFold {
+  int status = WS_OK;
+  std::vector<DAcc> da;
+  int32_t n_load = 0, n_store = 0;
+  __int128 omin = 0, omax = 0;
+  int16_t cnt_load[17], cnt_store[17];
+};
+typedef std::map<uint64_t, FieldFold> FieldCache;
+
+static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_acc, int fold_axis, int fold,
+                               FieldFold &out) {
+  out.status = WS_OK;
+  if (F.elem_bytes < 1 || F.elem_bytes > 64 || F.n_access < 1 || F.access_off < 0 ||
+      F.access_off + F.n_access > n_acc) {
+    out.status = WS_EINVAL;
+    return;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (std::llabs(F.stride[k]) >= ((int64_t)1 << 40)) out.status = WS_EINVAL;
+  if (std::llabs(F.align_bytes) >= ((int64_t)1 << 50) || std::llabs(F.const_off) >= ((int64_t)1 << 40))
+    out.status = WS_EINVAL;
+  if (out.status != WS_OK) return;
+  std::set<Off4> L, S;
+  for (int a = 0; a < F.n_access; ++a) {
+    const ws_access &A = acc[F.access_off + a];
+    if (std::abs(A.dx) > 65535 || std::abs(A.dy) > 65535 || std::abs(A.dz) > 65535 ||
+        std::llabs(A.dc) >= ((int64_t)1 << 40) || (A.is_store != 0 && A.is_store != 1)) {
+      out.status = WS_EINVAL;
+      return;
+    }
+    (A.is_store ? S : L).insert(Off4(A.dx, A.dy, A.dz, A.dc));
+  }
+  // thread folding (Sec. 5.1): union over k of offset + k * axis, each with the first
+  // folded point k that needs it
+  auto fold_list = [&](const std::set<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
+    std::map<Off4, int> kmin;
+    for (const Off4 &o : src)
+      for (int k = 0; k < fold; ++k) {
+        Off4 q = o;
+        if (fold_axis == 1) std::get<1>(q) += k;
+        if (fold_axis == 2) std::get<2>(q) += k;
+        auto it = kmin.find(q);
+        if (it == kmin.end() || k < it->second) kmin[q] = k;
+      }
+    for (auto &kv : kmin) dst.push_back(kv);
+  };
+  std::vector<std::pair<Off4, int>> fl, fs;
+  fold_list(L, fl);
+  fold_list(S, fs);
+  if ((int64_t)(fl.size() + fs.size()) > kMaxFoldedAccesses) {
+    out.status = WS_EINVAL;
+    return;
+  }
+  auto off_elems = [&](const Off4 &o) -> __int128 {
+    return (__int128)F.stride[0] * std::get<0>(o) + (__int128)F.stride[1] * std::get<1>(o) +
+           (__int128)F.stride[2] * std::get<2>(o) + std::get<3>(o);
+  };
+  out.da.clear();
+  for (auto *lst : {&fl, &fs})
+    for (auto &kv : *lst) {
+      DAcc x;
+      x.boff = (int64_t)(off_elems(kv.first) * F.elem_bytes);
+      x.kmin = kv.second;
+      x.pad = 0;
+      out.da.push_back(x);
+    }
+  out.n_load = (int32_t)fl.size();
+  out.n_store = (int32_t)fs.size();
+  // An issued folded access o' of a thread whose first point is p0 touches the same
+  // address as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e,
+  // so valid points x raw offsets bound every address of the field.
+  bool first = true;
+  for (auto *src : {&L, &S})
+    for (const Off4 &o : *src) {
+      __int128 e = off_elems(o);
+      if (first || e < out.omin) out.omin = e;
+      if (first || e > out.omax) out.omax = e;
+      first = false;
+    }
+  for (int kv = 0; kv <= 16; ++kv) {
+    int nl = 0, ns = 0;
+    for (auto &x : fl) nl += x.second < kv;
+    for (auto &x : fs) ns += x.second < kv;
+    out.cnt_load[kv] = (int16_t)nl;
+    out.cnt_store[kv] = (int16_t)ns;
+  }
+}
+
+// Returns WS_OK or a per-candidate error status.  `cache` (may be null) memoizes the
+// per-(field, folding) part across candidates that share fields.
 static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
-                          const ws_hw &hw, Compiled &out) {
+                          const ws_hw &hw, Compiled &out, FieldCache *cache = nullptr) {
   DCfg &d = out.d;
   memset(&d, 0, sizeof(d));
   for (int k = 0; k < 3; ++k) {
@@ -257,73 +351,33 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps
   out.f.clear();
   out.acc.clear();
+  out.fkey.clear();
   out.need_words.clear();
   for (int fi = 0; fi < c.n_field; ++fi) {
     const ws_field &F = fld[c.field_off + fi];
-    if (F.elem_bytes < 1 || F.elem_bytes > 64 || F.n_access < 1 || F.access_off < 0 ||
-        F.access_off + F.n_access > n_acc)
-      return WS_EINVAL;
-    for (int k = 0; k < 3; ++k)
-      if (std::llabs(F.stride[k]) >= ((int64_t)1 << 40)) return WS_EINVAL;
-    if (std::llabs(F.align_bytes) >= ((int64_t)1 << 50) || std::llabs(F.const_off) >= ((int64_t)1 << 40))
-      return WS_EINVAL;
-    std::set<Off4> L, S;
-    for (int a = 0; a < F.n_access; ++a) {
-      const ws_access &A = acc[F.access_off + a];
-      if (std::abs(A.dx) > 65535 || std::abs(A.dy) > 65535 || std::abs(A.dz) > 65535 ||
-          std::llabs(A.dc) >= ((int64_t)1 << 40) || (A.is_store != 0 && A.is_store != 1))
-        return WS_EINVAL;
-      (A.is_store ? S : L).insert(Off4(A.dx, A.dy, A.dz, A.dc));
+    FieldFold local;
+    const FieldFold *ff = &local;
+    if (cache) {
+      const uint64_t key = ((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold;
+      auto it = cache->find(key);
+      if (it == cache->end()) {
+        it = cache->emplace(key, FieldFold()).first;
+        compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, it->second);
+      }
+      ff = &it->second;
+    } else {
+      compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, local);
     }
-    auto fold_list = [&](const std::set<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
-      std::map<Off4, int> kmin;
-      for (const Off4 &o : src)
-        for (int k = 0; k < c.fold; ++k) {
-          Off4 q = o;
-          if (c.fold_axis == 1) std::get<1>(q) += k;
-          if (c.fold_axis == 2) std::get<2>(q) += k;
-          auto it = kmin.find(q);
-          if (it == kmin.end() || k < it->second) kmin[q] = k;
-        }
-      for (auto &kv : kmin) dst.push_back(kv);
-    };
-    std::vector<std::pair<Off4, int>> fl, fs;
-    fold_list(L, fl);
-    fold_list(S, fs);
-    if ((int64_t)(fl.size() + fs.size()) > kMaxFoldedAccesses) return WS_EINVAL;
-
+    if (ff->status != WS_OK) return ff->status;
     DField df;
     memset(&df, 0, sizeof(df));
     df.esize = F.elem_bytes;
     for (int k = 0; k < 3; ++k) df.stride[k] = F.stride[k];
     df.base = F.align_bytes + (int64_t)F.elem_bytes * F.const_off;
-    df.n_load = (int32_t)fl.size();
-    df.n_store = (int32_t)fs.size();
-    std::vector<DAcc> da;
-    auto off_elems = [&](const Off4 &o) -> __int128 {
-      return (__int128)F.stride[0] * std::get<0>(o) + (__int128)F.stride[1] * std::get<1>(o) +
-             (__int128)F.stride[2] * std::get<2>(o) + std::get<3>(o);
-    };
-    for (auto *lst : {&fl, &fs})
-      for (auto &kv : *lst) {
-        DAcc x;
-        x.boff = (int64_t)(off_elems(kv.first) * F.elem_bytes);
-        x.kmin = kv.second;
-        x.pad = 0;
-        da.push_back(x);
-      }
-    // An issued folded access o' of a thread whose first point is p0 touches the same
-    // address as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e,
-    // so valid points x raw offsets bound every address of the field.
-    __int128 omin = 0, omax = 0;
-    bool first = true;
-    for (auto *src : {&L, &S})
-      for (const Off4 &o : *src) {
-        __int128 e = off_elems(o);
-        if (first || e < omin) omin = e;
-        if (first || e > omax) omax = e;
-        first = false;
-      }
+    df.n_load = ff->n_load;
+    df.n_store = ff->n_store;
+    const std::vector<DAcc> &da = ff->da;
+    const __int128 omin = ff->omin, omax = ff->omax;
     // address range of each level: valid point box x raw offsets
     for (int lv = 0; lv < 2; ++lv) {
       __int128 pmin = 0, pmax = 0;
@@ -348,12 +402,11 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.mw_block = d.lev_end[0];
     df.first_of_cfg = fi == 0;
     df.wide = (df.words[0] >= ((int64_t)1 << 22) || df.words[1] >= ((int64_t)1 << 22)) ? 1 : 0;
+    df.lpa_log2p = 0;
+    while ((1 << df.lpa_log2p) < std::min(df.n_load, 32)) ++df.lpa_log2p;
     for (int kv = 0; kv <= 16; ++kv) {
-      int nl = 0, ns = 0;
-      for (auto &x : fl) nl += x.second < kv;
-      for (auto &x : fs) ns += x.second < kv;
-      df.cnt_load[kv] = (int16_t)nl;
-      df.cnt_store[kv] = (int16_t)ns;
+      df.cnt_load[kv] = ff->cnt_load[kv];
+      df.cnt_store[kv] = ff->cnt_store[kv];
     }
     for (int k = 0; k < N_BITMAPS; ++k) df.bm[k] = -1;
     int64_t need = 0;
@@ -361,6 +414,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     if (has_s) need += df.words[0] + df.words[1];
     out.f.push_back(df);
     out.acc.push_back(da);
+    out.fkey.push_back(((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold);
     out.need_words.push_back(need);
   }
   d.n_field = c.n_field;
@@ -433,7 +487,7 @@ int64_t ws_plan::take(size_t bytes) {
 
 static void default_tuning(ws_tuning &t) {
   if (t.chunk_warps <= 0) t.chunk_warps = 1024;
-  if (t.pass_mb == 0) t.pass_mb = 96;
+  if (t.pass_mb == 0) t.pass_mb = -1;
   if (t.enum_threads <= 0) t.enum_threads = 256;
   if (t.count_words <= 0) t.count_words = 65536;
   t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
@@ -767,14 +821,36 @@ extern "C" int ws_destroy(ws_ctx *c) {
 
 static cudaStream_t pick_stream(ws_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
 
+// Compiles every candidate; large batches on several host threads, each with its own
+// (field, folding) cache.
+static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                        int n_acc, const ws_hw &hw, std::vector<Compiled> &comp, std::vector<int> &status) {
+  comp.resize(n_cfg);
+  status.assign(n_cfg, WS_OK);
+  int nth = 1;
+  if (n_cfg >= 256) nth = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  auto work = [&](int t) {
+    FieldCache cache;
+    for (int i = t; i < n_cfg; i += nth) status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, comp[i], &cache);
+  };
+  if (nth == 1) {
+    work(0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) pool.emplace_back(work, t);
+  for (auto &th : pool) th.join();
+}
+
 // Bytes of device memory a plan of these candidates needs with one pass.
 int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
                           int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes,
                           size_t *max_field_bytes) {
   size_t dsc = 0, scr = 0, mf = 0;
+  FieldCache cache;
   for (int i = 0; i < n_cfg; ++i) {
     Compiled cc;
-    if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc) != WS_OK) continue;
+    if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc, &cache) != WS_OK) continue;
     for (size_t k = 0; k < cc.f.size(); ++k) {
       dsc += sizeof(DField) + cc.acc[k].size() * sizeof(DAcc);
       scr += (size_t)cc.need_words[k] * 4;
@@ -820,10 +896,11 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
 
   std::vector<DCfg> hcfg(n_cfg);
   std::vector<DAcc> hacc;
+  std::map<uint64_t, int32_t> acc_at;
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
-  std::vector<Compiled> comp(n_cfg);
-  std::vector<int> status(n_cfg, WS_OK);
-  for (int i = 0; i < n_cfg; ++i) status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, comp[i]);
+  std::vector<Compiled> comp;
+  std::vector<int> status;
+  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, comp, status);
   // scratch capacity: what the arena can give after the descriptors
   size_t dsc = 64 * 1024, total_need = 0, max_field = 0;
   for (int i = 0; i < n_cfg; ++i) {
@@ -860,8 +937,13 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
       for (size_t k = 0; k < comp[i].f.size(); ++k) {
         DField f = comp[i].f[k];
         f.cfg = i;
-        f.acc_begin = (int32_t)hacc.size();
-        hacc.insert(hacc.end(), comp[i].acc[k].begin(), comp[i].acc[k].end());
+        // candidates sharing a field and a folding share its access list on the device
+        auto it = acc_at.find(comp[i].fkey[k]);
+        if (it == acc_at.end()) {
+          it = acc_at.emplace(comp[i].fkey[k], (int32_t)hacc.size()).first;
+          hacc.insert(hacc.end(), comp[i].acc[k].begin(), comp[i].acc[k].end());
+        }
+        f.acc_begin = it->second;
         p->hfld.push_back(f);
         p->need_words.push_back(comp[i].need_words[k]);
       }
@@ -874,7 +956,9 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->layout();
 
   // device buffers
-  p->grab_bytes = 16 * std::max<size_t>(p->passes.size(), 1);
+  // one pair of work-stealing counters per pass; any tuning makes at most one pass per
+  // (candidate, field), so size for that (retuning may change the pass count)
+  p->grab_bytes = 16 * (p->hfld.size() + 1);
   p->counters_bytes = p->grab_bytes + (size_t)n_cfg * N_COUNTERS * 8;
   p->d_cfg = p->take(std::max<size_t>(hcfg.size() * sizeof(DCfg), 256));
   p->d_fld = p->take(std::max<size_t>(p->hfld.size() * sizeof(DField), 256));
@@ -1070,7 +1154,8 @@ extern "C" int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, 
   ws_plan *p = nullptr;
   int rc = ws_plan_create(ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, &p);
   if (rc != WS_OK) return rc;
-  rc = ws_plan_execute(p, mode, stream);
+  // a one-shot plan would replay its graph once: launch the batched kernels directly
+  rc = ws_plan_execute(p, mode == WS_MODE_BATCHED ? WS_MODE_DIRECT : mode, stream);
   if (rc == WS_OK) rc = ws_plan_results(p, out, order_out, stream);
   ws_plan_destroy(p);
   return rc;
@@ -1080,11 +1165,12 @@ extern "C" int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld
                            int n_acc, const ws_hw *hw, ws_cfg_info *out) {
   if (n_cfg < 0 || !hw || (n_cfg > 0 && (!cfgs || !out))) return WS_EINVAL;
   if (!hw_valid(*hw)) return WS_EINVAL;
+  FieldCache cache;
   for (int i = 0; i < n_cfg; ++i) {
     Compiled cc;
     ws_cfg_info &o = out[i];
     memset(&o, 0, sizeof(o));
-    o.status = compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc);
+    o.status = compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc, &cache);
     if (o.status != WS_OK) continue;
     const DCfg &d = cc.d;
     for (int k = 0; k < 3; ++k) o.grid[k] = d.g[k];

@@ -195,6 +195,23 @@ def test_multi_pass_equals_single_pass(ctx):
     assert res.tobytes() == ref.tobytes() and order.tobytes() == ref_o.tobytes()
 
 
+def test_retuning_to_more_passes_keeps_results(ctx):
+    """Re-layout after creation (as the autotuner does) to many more passes than the plan
+    was created with; counters of every pass must stay separate from the results."""
+    cfgs = W.lbm_sweep(N=(128, 96, 64))[::9]
+    hw = W.a100()
+    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": -1}) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        ref, ref_o = p.results()
+    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": 96}) as p:
+        assert p.profile()["passes"] >= 1
+        p.autotune()        # tries 48 MiB passes: more passes than at creation
+        for mode in (B.WS_MODE_BATCHED, B.WS_MODE_DIRECT):
+            p.execute(mode)
+            res, order = p.results()
+            assert res.tobytes() == ref.tobytes() and order.tobytes() == ref_o.tobytes()
+
+
 def test_segmented_and_standalone_ranking(ctx):
     cfgs = W.stencil_25pt_sweep(N=(96, 64, 64))[::3]
     hw = W.a100()
