@@ -49,6 +49,8 @@ struct ws_plan {
   ws::DHw dhw;
   ws_tuning tune;
   std::vector<ws::DField> hfld;
+  std::vector<ws::DGroup> hgrp;
+  std::vector<int32_t> cfg_grp_begin;
   std::vector<int64_t> need_words;
   std::vector<int32_t> cfg_cf_begin;
   std::vector<ws::DPass> passes;
@@ -57,6 +59,7 @@ struct ws_plan {
   int64_t item_begin_end = 0, citem_begin_end = 0;
   size_t grab_bytes = 0, counters_bytes = 0;
   int64_t upload_bytes = 0;
+  int64_t d_grp = -1;
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
           d_order = -1, d_scratch = -1;
   std::vector<int64_t> allocs;

@@ -88,15 +88,32 @@ struct DHw {
   int32_t sms, banks, bank_bytes, pair_dist_bytes, capacity_model, pad;
 };
 
-// One pass = a contiguous range of (candidate, field) pairs whose bitmaps fit the
-// scratch together.  Passes run one after the other and reuse the same scratch.
+// A field group: consecutive fields of one candidate enumerated together, so that a
+// modelled warp is decoded once for all of them.  Work items of the enumeration kernel
+// are (group, chunk of modelled warps); item 0 of a group is the representative block.
+struct DGroup {
+  int64_t item_begin;     // first enumeration work item
+  int64_t mw_end;         // modelled warps visited (max over the group's fields)
+  int64_t mw_block;       // modelled warps of the representative block
+  int32_t cfg;            // owning candidate
+  int32_t f_begin;        // fields [f_begin, f_begin + f_count)
+  int32_t f_count;
+  int32_t acc_count;      // folded accesses of all its fields (<= kMaxFoldedAccesses)
+  int32_t first_of_cfg;   // the candidate's first group counts LUPs
+  int32_t pad;
+};
+
+// One pass = a contiguous range of field groups whose bitmaps fit the scratch
+// together.  Passes run one after the other and reuse the same scratch.
 struct DPass {
   int64_t item_lo, item_hi;    // enumeration items of the pass
   int64_t citem_lo, citem_hi;  // counting items of the pass
   int32_t cf_lo, cf_hi;        // (candidate, field) index range
+  int32_t grp_lo, grp_hi;      // field-group index range
 };
 
-constexpr int kMaxFoldedAccesses = 2048;   // per field, staged in shared memory
+constexpr int kMaxFoldedAccesses = 2048;   // per field group, staged in shared memory
+constexpr int kMaxGroupFields = 32;
 constexpr int64_t kMaxBitmapWords = (int64_t)1 << 31;
 
 }  // namespace ws

@@ -174,11 +174,16 @@ __device__ __forceinline__ uint32_t runs_insert(uint32_t *__restrict__ bm, uint3
 // modelled warp, merging the sector bits of one bitmap word in a register and
 // flushing it with one red.or when the word changes.  tbase: the slice's relative
 // thread addresses; slice: which of them are valid.
-template <int P>
+template <int P, bool CHECK>
 __device__ __forceinline__ void lpa_walk(const uint32_t *__restrict__ tbase, uint32_t slice, uint32_t b32,
-                                         uint32_t *__restrict__ bm, uint32_t &cw, uint32_t &cb) {
+                                         uint32_t limit, uint32_t *__restrict__ bm, uint32_t &cw, uint32_t &cb,
+                                         uint32_t &bad) {
   auto step = [&](uint32_t tb) {
     const uint32_t r = tb + b32;
+    if (CHECK && r >= limit) {
+      ++bad;
+      return;
+    }
     const uint32_t w = r >> 10;
     const bool flush = w != cw;
     if (flush && cb) atomicOr(bm + cw, cb);
@@ -215,40 +220,81 @@ __device__ __forceinline__ void lpa_walk(const uint32_t *__restrict__ tbase, uin
   }
 }
 
+// Last field group in [lo, hi) whose first work item is <= item; gallops forward from
+// the CTA's previous group (items are handed out in increasing order).
+__device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, int hi, int64_t item, int hint) {
+  if (hint >= lo && hint < hi && grp[hint].item_begin <= item) {
+    int step = 1, l = hint, r = hi;
+    for (;;) {
+      const int nx = l + step;
+      if (nx >= hi) break;
+      if (grp[nx].item_begin > item) {
+        r = nx;
+        break;
+      }
+      l = nx;
+      step <<= 1;
+    }
+    lo = l;
+    hi = r;
+  }
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (grp[mid].item_begin <= item) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
-  __shared__ DField s_f;
-  __shared__ __align__(16) uint32_t s_tbase[16][32];   // per warp: relative address of each thread's first point
-  __shared__ uint8_t s_tkv[16][32];      // per warp: valid folded points of each thread
   __shared__ DCfg s_c;
+  __shared__ DGroup s_g;
+  __shared__ DField s_fk[kMaxGroupFields];
+  __shared__ int32_t s_aoff[kMaxGroupFields + 1];
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
   __shared__ uint32_t s_b32[kMaxFoldedAccesses];
   __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
   __shared__ uint32_t s_tc[1024];
+  __shared__ __align__(16) uint32_t s_tbase[16][32];   // per warp: relative address of each thread's first point
+  __shared__ uint8_t s_tkv[16][32];                    // per warp: valid folded points of each thread
   __shared__ long long s_item;
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t nwarps = blockDim.x >> 5;
-  int cur_cf = -1, cur_cfg = -1;
+  int cur_g = -1, cur_cfg = -1;
 
   for (;;) {
     if (threadIdx.x == 0) s_item = a.item_lo + (long long)atomicAdd(a.grab, 1ull);
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.item_hi) break;
-    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, false, cur_cf);
-    if (cf != cur_cf) {
-      if (threadIdx.x == 0) s_f = a.fld[cf];
+    const int gi = find_grp(a.grp, a.grp_lo, a.grp_hi, item, cur_g);
+    if (gi != cur_g) {
+      // stage the group: its fields, their folded accesses, the candidate's thread table
+      if (threadIdx.x == 0) s_g = a.grp[gi];
       __syncthreads();
-      const int na = s_f.n_load + s_f.n_store;
-      for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        const DAcc d = a.acc[s_f.acc_begin + i];
-        s_boff[i] = d.boff;
-        s_b32[i] = (uint32_t)d.boff;
-        s_kmin[i] = (uint8_t)d.kmin;
+      for (int k = threadIdx.x; k < s_g.f_count; k += blockDim.x) s_fk[k] = a.fld[s_g.f_begin + k];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int o = 0;
+        for (int k = 0; k < s_g.f_count; ++k) {
+          s_aoff[k] = o;
+          o += s_fk[k].n_load + s_fk[k].n_store;
+        }
+        s_aoff[s_g.f_count] = o;
       }
-      if (s_f.cfg != cur_cfg) {
-        if (threadIdx.x == 0) s_c = a.cfg[s_f.cfg];
+      __syncthreads();
+      for (int j = threadIdx.x; j < s_aoff[s_g.f_count]; j += blockDim.x) {
+        int k = 0;
+        while (s_aoff[k + 1] <= j) ++k;
+        const DAcc d = a.acc[s_fk[k].acc_begin + (j - s_aoff[k])];
+        s_boff[j] = d.boff;
+        s_b32[j] = (uint32_t)d.boff;
+        s_kmin[j] = (uint8_t)d.kmin;
+      }
+      if (s_g.cfg != cur_cfg) {
+        if (threadIdx.x == 0) s_c = a.cfg[s_g.cfg];
         __syncthreads();
         for (int t = threadIdx.x; t < s_c.T; t += blockDim.x) {
           const uint32_t tx = t % s_c.B[0], ty = (t / s_c.B[0]) % s_c.B[1], tz = t / (s_c.B[0] * s_c.B[1]);
@@ -256,20 +302,19 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         }
       }
       __syncthreads();
-      cur_cf = cf;
-      cur_cfg = s_f.cfg;
+      cur_g = gi;
+      cur_cfg = s_g.cfg;
     }
-    // descriptors of this item: read from shared memory where used (broadcast loads)
-    const bool wide = s_f.wide != 0;
-    // item 0 of a field covers the representative block, the others chunks of the rest
-    const int64_t k = item - s_f.item_begin;
-    const uint32_t mw0 = k == 0 ? 0u : (uint32_t)(s_f.mw_block + (k - 1) * (int64_t)a.chunk);
-    const uint32_t mw1 = k == 0 ? (uint32_t)s_f.mw_block
-                                : (uint32_t)min(s_f.mw_block + k * (int64_t)a.chunk, s_f.mw_end);
+    // item 0 of a group covers the representative block, the others chunks of the rest
+    const int64_t kk = item - s_g.item_begin;
+    const uint32_t mw0 = kk == 0 ? 0u : (uint32_t)(s_g.mw_block + (kk - 1) * (int64_t)a.chunk);
+    const uint32_t mw1 = kk == 0 ? (uint32_t)s_g.mw_block
+                                 : (uint32_t)min(s_g.mw_block + kk * (int64_t)a.chunk, s_g.mw_end);
     uint32_t acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0, acc_addr = 0, acc_wi = 0;
     uint32_t bad = 0;
 
     for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
+      // ---- decode the modelled warp once for every field of the group
       uint32_t level, b, j;
       const FastDiv fwpb = s_c.fd_wpb;
       if (mw < (uint32_t)s_c.lev_end[0]) {
@@ -302,132 +347,157 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       const bool valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
       int kv = 0;
       if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
-      const int64_t lin = s_f.stride[0] * x + s_f.stride[1] * y + s_f.stride[2] * z;
-      const int n_load = s_f.n_load;
-      const int nst = level <= 1 ? s_f.n_store : 0;
-      acc_addr += __reduce_add_sync(FULL, (uint32_t)(s_f.cnt_load[kv] + (level <= 1 ? s_f.cnt_store[kv] : 0)));
-      acc_wi += (uint32_t)(n_load + nst);
-
-      if (level == 0) {
-        // representative block: exact per-instruction counts and bank cycles
-        const int64_t lo0 = s_f.lo[0];
-        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * lo0;
-        uint32_t *const bl = a.scratch + s_f.bm[BM_BL], *const bs = a.scratch + s_f.bm[BM_BS];
-        for (int i = 0; i < n_load; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          const int64_t r = rel + s_boff[i];
-          acc_req += bitmap_insert(bl, r, act, lane, s_f.words[0], bad);
-          acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
-        }
-        for (int i = n_load; i < n_load + nst; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          const int64_t r = rel + s_boff[i];
-          acc_st += bitmap_insert(bs, r, act, lane, s_f.words[0], bad);
-          acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
-        }
-      } else if (!wide) {
-        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1];
-        const uint32_t r0 = (uint32_t)rel;
-        const uint32_t limit = (uint32_t)(s_f.words[1] << 10);
-        uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
-        if (n_load > 0) {
-          // stage the warp's thread addresses, then walk them lane per access
-          s_tbase[warp][lane] = r0;
-          s_tkv[warp][lane] = (uint8_t)kv;
-          const uint32_t vmask = __ballot_sync(FULL, valid);
-          // a thread with fewer valid folded points than the fold skips some accesses;
-          // such warps (only at the domain edge) bound-check every address
-          const bool partial = __any_sync(FULL, valid && kv < fold);
-          int64_t mn = valid ? rel : INT64_MAX, mx = valid ? rel : INT64_MIN;
-#pragma unroll
-          for (int off = 16; off >= 1; off >>= 1) {
-            mn = min(mn, (int64_t)__shfl_xor_sync(FULL, (long long)mn, off));
-            mx = max(mx, (int64_t)__shfl_xor_sync(FULL, (long long)mx, off));
-          }
-          __syncwarp();
-          const int lp = s_f.lpa_log2p, P = 1 << lp;
-          const uint32_t al = lane & (uint32_t)(P - 1), g0 = (lane >> lp) << lp;
-          const uint32_t slice = (P == 32 ? vmask : (vmask >> g0) & ((1u << P) - 1u));
-          const uint32_t *tb = &s_tbase[warp][g0];
-          for (int a0 = 0; a0 < n_load && vmask; a0 += P) {
-            const int ai = a0 + (int)al;
-            uint32_t cw = 0xffffffffu, cb = 0u;
-            if (ai < n_load && slice) {
-              const uint32_t b32 = s_b32[ai];
-              if (!partial) {
-                // every valid thread issues every access: one range check per lane
-                const int64_t bo = s_boff[ai];
-                if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
-                  bad += __popc(slice);
-                } else {
-                  switch (lp) {
-                    case 0: lpa_walk<1>(tb, slice, b32, bm, cw, cb); break;
-                    case 1: lpa_walk<2>(tb, slice, b32, bm, cw, cb); break;
-                    case 2: lpa_walk<4>(tb, slice, b32, bm, cw, cb); break;
-                    case 3: lpa_walk<8>(tb, slice, b32, bm, cw, cb); break;
-                    case 4: lpa_walk<16>(tb, slice, b32, bm, cw, cb); break;
-                    default: lpa_walk<32>(tb, slice, b32, bm, cw, cb); break;
-                  }
-                }
-              } else {
-                const int km = s_kmin[ai];
-                for (int t = 0; t < P; ++t) {
-                  if (!((slice >> t) & 1u) || km >= (int)s_tkv[warp][g0 + t]) continue;
-                  const uint32_t r = tb[t] + b32;
-                  if (r >= limit) {
-                    ++bad;
-                    continue;
-                  }
-                  const uint32_t w = r >> 10;
-                  if (w != cw) {
-                    if (cb) atomicOr(bm + cw, cb);
-                    cw = w;
-                    cb = 0u;
-                  }
-                  cb |= 1u << ((r >> 5) & 31u);
-                }
-              }
-            }
-            if (P == 32) {
-              if (cb) atomicOr(bm + cw, cb);
-            } else {
-              // several slices per access: lanes whose last word coincides (other
-              // slices, other accesses) merge it into one red.or
-              const uint32_t key = cb ? cw : (0x80000000u | lane);
-              const uint32_t m = __match_any_sync(FULL, key);
-              const uint32_t orcb = __reduce_or_sync(m, cb);
-              if (cb && lane == (uint32_t)(__ffs(m) - 1)) atomicOr(bm + cw, orcb);
-            }
-          }
-          __syncwarp();
-        }
-        uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
-        for (int i = n_load; i < n_load + nst; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          acc_sreq += runs_insert(ws_, r0 + s_b32[i], act, limit, lane, bad, true);
-        }
-      } else {
-        const int64_t rel = s_f.base + (int64_t)s_f.esize * lin - 32 * s_f.lo[1];
-        uint32_t *const bm = a.scratch + s_f.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
-        for (int i = 0; i < n_load; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          bitmap_insert(bm, rel + s_boff[i], act, lane, s_f.words[1], bad);
-        }
-        uint32_t *const ws_ = a.scratch + s_f.bm[BM_WS];
-        for (int i = n_load; i < n_load + nst; ++i) {
-          const bool act = valid && (int)s_kmin[i] < kv;
-          acc_sreq += bitmap_insert(ws_, rel + s_boff[i], act, lane, s_f.words[1], bad);
-        }
-      }
-      if (s_f.first_of_cfg && level <= 1) {
+      if (s_g.first_of_cfg && level <= 1) {
         const uint32_t l = __reduce_add_sync(FULL, (uint32_t)kv);
         if (level == 0) acc_lb += l;
         else acc_lw += l;
       }
+      const uint32_t vmask = __ballot_sync(FULL, valid);
+      // a thread with fewer valid folded points than the fold skips some accesses; such
+      // warps (only at the domain edge) bound-check every address
+      const bool partial = __any_sync(FULL, valid && kv < fold);
+      uint32_t naddr = 0;
+
+      // ---- every field of the group
+      for (int k = 0; k < s_g.f_count; ++k) {
+        const DField &F = s_fk[k];
+        const int n_load = F.n_load;
+        const int nst = level <= 1 ? F.n_store : 0;
+        if (n_load + (level <= 1 ? nst : 0) == 0 || (level >= 2 && n_load == 0)) continue;
+        const int ao = s_aoff[k];
+        naddr += (uint32_t)(F.cnt_load[kv] + (level <= 1 ? F.cnt_store[kv] : 0));
+        acc_wi += (uint32_t)(n_load + nst);
+        const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
+
+        if (level == 0) {
+          // representative block: exact per-instruction counts and bank cycles
+          const int64_t lo0 = F.lo[0];
+          const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * lo0;
+          uint32_t *const bl = a.scratch + F.bm[BM_BL], *const bs = a.scratch + F.bm[BM_BS];
+          for (int i = 0; i < n_load; ++i) {
+            const bool act = valid && (int)s_kmin[ao + i] < kv;
+            const int64_t r = rel + s_boff[ao + i];
+            acc_req += bitmap_insert(bl, r, act, lane, F.words[0], bad);
+            acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
+          }
+          for (int i = n_load; i < n_load + nst; ++i) {
+            const bool act = valid && (int)s_kmin[ao + i] < kv;
+            const int64_t r = rel + s_boff[ao + i];
+            acc_st += bitmap_insert(bs, r, act, lane, F.words[0], bad);
+            acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
+          }
+        } else if (!F.wide) {
+          const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * F.lo[1];
+          const uint32_t r0 = (uint32_t)rel;
+          const uint32_t limit = (uint32_t)(F.words[1] << 10);
+          uint32_t *const bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+          if (n_load > 0) {
+            // lane per access over slices of P threads (P = 2^lp >= loads, <= 32)
+            const int lp = F.lpa_log2p, P = 1 << lp;
+            if (P > 1) {
+              s_tbase[warp][lane] = r0;
+              s_tkv[warp][lane] = (uint8_t)kv;
+              __syncwarp();
+            }
+            // fields with a full warp per access check each lane's range once
+            int64_t mn = 0, mx = 0;
+            if (P == 32 && !partial) {
+              mn = valid ? rel : INT64_MAX;
+              mx = valid ? rel : INT64_MIN;
+#pragma unroll
+              for (int off = 16; off >= 1; off >>= 1) {
+                mn = min(mn, (int64_t)__shfl_xor_sync(FULL, (long long)mn, off));
+                mx = max(mx, (int64_t)__shfl_xor_sync(FULL, (long long)mx, off));
+              }
+            }
+            const uint32_t al = lane & (uint32_t)(P - 1), g0 = (lane >> lp) << lp;
+            const uint32_t slice = (P == 32 ? vmask : (vmask >> g0) & ((1u << P) - 1u));
+            const uint32_t *tb = &s_tbase[warp][g0];
+            for (int a0 = 0; a0 < n_load && vmask; a0 += P) {
+              const int ai = a0 + (int)al;
+              uint32_t cw = 0xffffffffu, cb = 0u;
+              if (ai < n_load && slice) {
+                const uint32_t b32 = s_b32[ao + ai];
+                if (!partial) {
+                  if (P == 32) {
+                    const int64_t bo = s_boff[ao + ai];
+                    if (mn + bo < 0 || mx + bo >= (int64_t)limit) bad += __popc(slice);
+                    else lpa_walk<32, false>(tb, slice, b32, limit, bm, cw, cb, bad);
+                  } else {
+                    switch (lp) {
+                      case 0: {  // one thread per lane: its own address, no staging
+                        const uint32_t r = r0 + b32;
+                        if (r >= limit) {
+                          ++bad;
+                        } else {
+                          cw = r >> 10;
+                          cb = __funnelshift_l(0u, 1u, r >> 5);
+                        }
+                        break;
+                      }
+                      case 1: lpa_walk<2, true>(tb, slice, b32, limit, bm, cw, cb, bad); break;
+                      case 2: lpa_walk<4, true>(tb, slice, b32, limit, bm, cw, cb, bad); break;
+                      case 3: lpa_walk<8, true>(tb, slice, b32, limit, bm, cw, cb, bad); break;
+                      default: lpa_walk<16, true>(tb, slice, b32, limit, bm, cw, cb, bad); break;
+                    }
+                  }
+                } else {
+                  const int km = s_kmin[ao + ai];
+                  for (int t = 0; t < P; ++t) {
+                    if (!((slice >> t) & 1u) || km >= (P > 1 ? (int)s_tkv[warp][g0 + t] : kv)) continue;
+                    const uint32_t r = (P > 1 ? tb[t] : r0) + b32;
+                    if (r >= limit) {
+                      ++bad;
+                      continue;
+                    }
+                    const uint32_t wd = r >> 10;
+                    if (wd != cw) {
+                      if (cb) atomicOr(bm + cw, cb);
+                      cw = wd;
+                      cb = 0u;
+                    }
+                    cb |= 1u << ((r >> 5) & 31u);
+                  }
+                }
+              }
+              if (P == 32) {
+                if (cb) atomicOr(bm + cw, cb);
+              } else {
+                // several slices per access: lanes whose last word coincides (other
+                // slices, other accesses) merge it into one red.or
+                const uint32_t key = cb ? cw : (0x80000000u | lane);
+                const uint32_t m = __match_any_sync(FULL, key);
+                const uint32_t orcb = __reduce_or_sync(m, cb);
+                if (cb && lane == (uint32_t)(__ffs(m) - 1)) atomicOr(bm + cw, orcb);
+              }
+            }
+            if (P > 1) __syncwarp();
+          }
+          // wave stores: per-instruction unique sectors (partial-store model)
+          uint32_t *const ws_ = a.scratch + F.bm[BM_WS];
+          for (int i = n_load; i < n_load + nst; ++i) {
+            const bool act = valid && (int)s_kmin[ao + i] < kv;
+            acc_sreq += runs_insert(ws_, r0 + s_b32[ao + i], act, limit, lane, bad, true);
+          }
+        } else {
+          const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * F.lo[1];
+          uint32_t *const bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+          for (int i = 0; i < n_load; ++i) {
+            const bool act = valid && (int)s_kmin[ao + i] < kv;
+            bitmap_insert(bm, rel + s_boff[ao + i], act, lane, F.words[1], bad);
+          }
+          uint32_t *const ws_ = a.scratch + F.bm[BM_WS];
+          for (int i = n_load; i < n_load + nst; ++i) {
+            const bool act = valid && (int)s_kmin[ao + i] < kv;
+            acc_sreq += bitmap_insert(ws_, rel + s_boff[ao + i], act, lane, F.words[1], bad);
+          }
+        }
+      }
+      acc_addr += __reduce_add_sync(FULL, naddr);
     }
     bad = __reduce_add_sync(FULL, bad);
     if (lane == 0) {
-      unsigned long long *c = (unsigned long long *)(a.counters + (int64_t)s_f.cfg * N_COUNTERS);
+      unsigned long long *c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
       typedef unsigned long long u64;
       if (bad) atomicAdd(c + C_OVERFLOW, (u64)bad);
       if (acc_lb) atomicAdd(c + C_LUPS_BLOCK, (u64)acc_lb);

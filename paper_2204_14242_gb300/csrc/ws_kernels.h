@@ -9,12 +9,13 @@ namespace ws {
 struct EnumArgs {
   const DCfg *cfg;
   const DField *fld;
+  const DGroup *grp;
   const DAcc *acc;
   uint32_t *scratch;               // bitmaps of the pass
   int64_t *counters;               // [n_cfg][N_COUNTERS]
   unsigned long long *grab;        // work-stealing counter (zeroed before the launch)
   int64_t item_lo, item_hi;        // enumeration items of the pass
-  int32_t cf_lo, cf_hi;            // (candidate, field) range of the pass
+  int32_t grp_lo, grp_hi;          // field-group range of the pass
   int32_t chunk;                   // modelled warps per item
   int32_t banks, bank_bytes, pair_dist;
 };

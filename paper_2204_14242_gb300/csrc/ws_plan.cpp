@@ -499,56 +499,66 @@ static void default_tuning(ws_tuning &t) {
 // Numbers work items and cuts passes for the current tuning.
 void ws_plan::layout() {
   passes.clear();
-  // pass capacity: the tuned pass size, never below the largest field, never above
-  // the scratch the plan holds
+  // pass capacity: the tuned pass size, never below the largest field group, never
+  // above the scratch the plan holds
+  std::vector<int64_t> gneed(hgrp.size(), 0);
   int64_t max_need = 0;
-  for (int64_t w : need_words) max_need = std::max(max_need, w);
+  for (size_t g = 0; g < hgrp.size(); ++g) {
+    for (int k = 0; k < hgrp[g].f_count; ++k) gneed[g] += need_words[hgrp[g].f_begin + k];
+    max_need = std::max(max_need, gneed[g]);
+  }
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
   int64_t items = 0, citems = 0, used = 0;
-  DPass cur{0, 0, 0, 0, 0, 0};
-  const int ncf = (int)hfld.size();
-  for (int cf = 0; cf < ncf; ++cf) {
-    DField &f = hfld[cf];
-    int64_t need = need_words[cf];
-    if (used + need > cap && cf > cur.cf_lo) {
-      cur.cf_hi = cf;
+  DPass cur{0, 0, 0, 0, 0, 0, 0, 0};
+  const int ng = (int)hgrp.size();
+  for (int g = 0; g < ng; ++g) {
+    DGroup &G = hgrp[g];
+    if (used + gneed[g] > cap && g > cur.grp_lo) {
+      cur.cf_hi = G.f_begin;
+      cur.grp_hi = g;
       cur.item_hi = items;
       cur.citem_hi = citems;
       passes.push_back(cur);
-      cur = DPass{items, 0, citems, 0, cf, 0};
+      cur = DPass{items, 0, citems, 0, G.f_begin, 0, g, 0};
       used = 0;
     }
-    int64_t o = used;
-    const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
-    for (int k = 0; k < N_BITMAPS; ++k) f.bm[k] = -1;
-    if (has_l) {
-      f.bm[BM_BL] = o; o += f.words[0];
-      f.bm[BM_W] = o; o += f.words[1];
-      f.bm[BM_Y] = o; o += f.words[1];
-      f.bm[BM_Z] = o; o += f.words[1];
+    for (int k = 0; k < G.f_count; ++k) {
+      DField &f = hfld[G.f_begin + k];
+      int64_t o = used;
+      const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
+      for (int b = 0; b < N_BITMAPS; ++b) f.bm[b] = -1;
+      if (has_l) {
+        f.bm[BM_BL] = o; o += f.words[0];
+        f.bm[BM_W] = o; o += f.words[1];
+        f.bm[BM_Y] = o; o += f.words[1];
+        f.bm[BM_Z] = o; o += f.words[1];
+      }
+      if (has_s) {
+        f.bm[BM_BS] = o; o += f.words[0];
+        f.bm[BM_WS] = o; o += f.words[1];
+      }
+      used = o;
+      f.item_begin = items;
+      f.citem_begin = citems;
+      citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
     }
-    if (has_s) {
-      f.bm[BM_BS] = o; o += f.words[0];
-      f.bm[BM_WS] = o; o += f.words[1];
-    }
-    used = o;
-    f.item_begin = items;
-    f.citem_begin = citems;
     // item 0: the representative block (slow exact path); then chunks of the rest
-    items += 1 + ceil_div(f.mw_end - f.mw_block, tune.chunk_warps);
-    citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
+    G.item_begin = items;
+    items += 1 + ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
   }
-  cur.cf_hi = ncf;
+  cur.cf_hi = (int)hfld.size();
+  cur.grp_hi = ng;
   cur.item_hi = items;
   cur.citem_hi = citems;
-  if (ncf > 0) passes.push_back(cur);
+  if (ng > 0) passes.push_back(cur);
   item_begin_end = items;
   citem_begin_end = citems;
 }
 
 int ws_plan::upload_fields(cudaStream_t st) {
   if (!hfld.empty()) CU(cudaMemcpyAsync(dev(d_fld), hfld.data(), hfld.size() * sizeof(DField), cudaMemcpyHostToDevice, st));
+  if (!hgrp.empty()) CU(cudaMemcpyAsync(dev(d_grp), hgrp.data(), hgrp.size() * sizeof(DGroup), cudaMemcpyHostToDevice, st));
   if (graph_exec) {
     cudaGraphExecDestroy(graph_exec);
     graph_exec = nullptr;
@@ -583,14 +593,15 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     EnumArgs ea;
     ea.cfg = (const DCfg *)dev(d_cfg);
     ea.fld = (const DField *)dev(d_fld);
+    ea.grp = (const DGroup *)dev(d_grp);
     ea.acc = (const DAcc *)dev(d_acc);
     ea.scratch = (uint32_t *)dev(d_scratch);
     ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
     ea.grab = (unsigned long long *)dev(d_counters) + 2 * p;
     ea.item_lo = P.item_lo;
     ea.item_hi = P.item_hi;
-    ea.cf_lo = P.cf_lo;
-    ea.cf_hi = P.cf_hi;
+    ea.grp_lo = P.grp_lo;
+    ea.grp_hi = P.grp_hi;
     ea.chunk = tune.chunk_warps;
     ea.banks = hw.banks;
     ea.bank_bytes = hw.bank_bytes;
@@ -645,26 +656,29 @@ int ws_plan::run_plain(cudaStream_t st) {
   CU(cudaMemsetAsync(dev(d_counters), 0, counters_bytes, st));
   int64_t *counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
   unsigned long long *grab = (unsigned long long *)dev(d_counters);
+  const int ng = (int)hgrp.size(), nf = (int)hfld.size();
   for (int i = 0; i < n_cfg; ++i) {
-    const int cf_a = cfg_cf_begin[i], cf_b = cfg_cf_begin[i + 1];
-    for (size_t p = 0; p < passes.size() && cf_a < cf_b; ++p) {
+    const int g_a = cfg_grp_begin[i], g_b = cfg_grp_begin[i + 1];
+    for (size_t p = 0; p < passes.size() && g_a < g_b; ++p) {
       const DPass &P = passes[p];
-      const int lo = std::max(cf_a, P.cf_lo), hi = std::min(cf_b, P.cf_hi);
-      if (lo >= hi) continue;
-      const int64_t it_lo = hfld[lo].item_begin, it_hi = hi < (int)hfld.size() ? hfld[hi].item_begin : item_begin_end;
-      const int64_t ct_lo = hfld[lo].citem_begin, ct_hi = hi < (int)hfld.size() ? hfld[hi].citem_begin : citem_begin_end;
+      const int glo = std::max(g_a, P.grp_lo), ghi = std::min(g_b, P.grp_hi);
+      if (glo >= ghi) continue;
+      const int64_t it_lo = hgrp[glo].item_begin, it_hi = ghi < ng ? hgrp[ghi].item_begin : item_begin_end;
+      const int cf_lo = hgrp[glo].f_begin, cf_hi = hgrp[ghi - 1].f_begin + hgrp[ghi - 1].f_count;
+      const int64_t ct_lo = hfld[cf_lo].citem_begin, ct_hi = cf_hi < nf ? hfld[cf_hi].citem_begin : citem_begin_end;
       CU(cudaMemsetAsync(grab, 0, 2 * sizeof(unsigned long long), st));
       EnumArgs ea;
       ea.cfg = (const DCfg *)dev(d_cfg);
       ea.fld = (const DField *)dev(d_fld);
+      ea.grp = (const DGroup *)dev(d_grp);
       ea.acc = (const DAcc *)dev(d_acc);
       ea.scratch = (uint32_t *)dev(d_scratch);
       ea.counters = counters;
       ea.grab = grab;
       ea.item_lo = it_lo;
       ea.item_hi = it_hi;
-      ea.cf_lo = lo;
-      ea.cf_hi = hi;
+      ea.grp_lo = glo;
+      ea.grp_hi = ghi;
       ea.chunk = tune.chunk_warps;
       ea.banks = hw.banks;
       ea.bank_bytes = hw.bank_bytes;
@@ -677,8 +691,8 @@ int ws_plan::run_plain(cudaStream_t st) {
       ca.grab = grab + 1;
       ca.citem_lo = ct_lo;
       ca.citem_hi = ct_hi;
-      ca.cf_lo = lo;
-      ca.cf_hi = hi;
+      ca.cf_lo = cf_lo;
+      ca.cf_hi = cf_hi;
       ca.chunk_words = tune.count_words;
       if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(512, ct_hi - ct_lo, true), st));
     }
@@ -953,6 +967,37 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
   p->cfg_cf_begin[n_cfg] = (int32_t)p->hfld.size();
   p->scratch_words = (int64_t)(scratch / 4);
+  // field groups: consecutive fields of a candidate, bounded by the shared-memory
+  // staging (fields, folded accesses) and by what one pass of scratch holds
+  p->cfg_grp_begin.assign(n_cfg + 1, 0);
+  for (int i = 0; i < n_cfg; ++i) {
+    p->cfg_grp_begin[i] = (int32_t)p->hgrp.size();
+    const int a = p->cfg_cf_begin[i], b = p->cfg_cf_begin[i + 1];
+    int k = a;
+    while (k < b) {
+      DGroup G;
+      memset(&G, 0, sizeof(G));
+      G.cfg = i;
+      G.f_begin = k;
+      G.first_of_cfg = k == a;
+      G.mw_block = p->hfld[k].mw_block;
+      int64_t need = 0;
+      while (k < b) {
+        const DField &f = p->hfld[k];
+        const int na = f.n_load + f.n_store;
+        if (G.f_count > 0 && (G.f_count >= kMaxGroupFields || G.acc_count + na > kMaxFoldedAccesses ||
+                              need + p->need_words[k] > p->scratch_words))
+          break;
+        G.f_count += 1;
+        G.acc_count += na;
+        G.mw_end = std::max(G.mw_end, f.mw_end);
+        need += p->need_words[k];
+        ++k;
+      }
+      p->hgrp.push_back(G);
+    }
+  }
+  p->cfg_grp_begin[n_cfg] = (int32_t)p->hgrp.size();
   p->layout();
 
   // device buffers
@@ -961,6 +1006,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->grab_bytes = 16 * (p->hfld.size() + 1);
   p->counters_bytes = p->grab_bytes + (size_t)n_cfg * N_COUNTERS * 8;
   p->d_cfg = p->take(std::max<size_t>(hcfg.size() * sizeof(DCfg), 256));
+  p->d_grp = p->take(std::max<size_t>(p->hgrp.size() * sizeof(DGroup), 256));
   p->d_fld = p->take(std::max<size_t>(p->hfld.size() * sizeof(DField), 256));
   p->d_acc = p->take(std::max<size_t>(hacc.size() * sizeof(DAcc), 256));
   p->d_seg = p->take((seg.size()) * sizeof(int32_t));
@@ -974,7 +1020,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   } else {
     p->d_scratch = p->take(scratch);
   }
-  for (int64_t o : {p->d_cfg, p->d_fld, p->d_acc, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
+  for (int64_t o : {p->d_cfg, p->d_grp, p->d_fld, p->d_acc, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
                     p->d_scratch}) {
     if (o < 0) {
       p->release_all();
@@ -1004,7 +1050,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   if (!upload && (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
   p->scratch_bytes = scratch;
   p->upload_bytes = (int64_t)(hcfg.size() * sizeof(DCfg) + p->hfld.size() * sizeof(DField) +
-                              hacc.size() * sizeof(DAcc) + seg.size() * sizeof(int32_t));
+                              p->hgrp.size() * sizeof(DGroup) + hacc.size() * sizeof(DAcc) +
+                              seg.size() * sizeof(int32_t));
   *out = p;
   return WS_OK;
 }
