@@ -100,7 +100,9 @@ struct DGroup {
   int32_t f_count;
   int32_t acc_count;      // folded accesses of all its fields (<= kMaxFoldedAccesses)
   int32_t first_of_cfg;   // the candidate's first group counts LUPs
-  int32_t pad;
+  int32_t uniform;        // all fields share element size and strides (and none is wide)
+  int32_t n_loads;        // folded loads of all its fields
+  int32_t n_stores;       // folded stores of all its fields
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch

@@ -220,6 +220,50 @@ __device__ __forceinline__ void lpa_walk(const uint32_t *__restrict__ tbase, uin
   }
 }
 
+// The same walk over all 32 threads of a modelled warp, also counting the distinct
+// sectors of the lane's access instruction: the number of sector changes along the
+// walk, exact when the lane's sectors never decrease (`mono`).
+__device__ __forceinline__ void lpa_walk_count(const uint32_t *__restrict__ tbase, uint32_t vmask, uint32_t b32,
+                                               uint32_t *__restrict__ bm, uint32_t &cw, uint32_t &cb,
+                                               uint32_t &nsec, bool &mono) {
+  uint32_t last = 0xffffffffu;
+  auto step = [&](uint32_t tb) {
+    const uint32_t r = tb + b32;
+    const uint32_t sec = r >> 5;
+    nsec += sec != last;
+    mono = mono && (last == 0xffffffffu || sec >= last);
+    last = sec;
+    const uint32_t w = r >> 10;
+    const bool flush = w != cw;
+    if (flush && cb) atomicOr(bm + cw, cb);
+    cb = (flush ? 0u : cb) | __funnelshift_l(0u, 1u, sec);
+    cw = w;
+  };
+  const uint4 *t4 = reinterpret_cast<const uint4 *>(tbase);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint4 v = t4[q];
+    const uint32_t m = vmask >> (4 * q);
+    if (m & 1u) step(v.x);
+    if (m & 2u) step(v.y);
+    if (m & 4u) step(v.z);
+    if (m & 8u) step(v.w);
+  }
+}
+
+// Exact distinct sectors of one instruction whose lanes hold relative addresses r.
+__device__ __forceinline__ uint32_t warp_distinct_sectors(uint32_t r, bool act) {
+  const uint32_t word = r >> 10, bit = 1u << ((r >> 5) & 31u);
+  uint32_t pending = __ballot_sync(FULL, act), cnt = 0;
+  while (pending) {
+    const uint32_t lw = __shfl_sync(FULL, word, __ffs(pending) - 1);
+    const bool mine = act && word == lw;
+    cnt += __popc(__reduce_or_sync(FULL, mine ? bit : 0u));
+    pending &= ~__ballot_sync(FULL, mine);
+  }
+  return cnt;
+}
+
 // Last field group in [lo, hi) whose first work item is <= item; gallops forward from
 // the CTA's previous group (items are handed out in increasing order).
 __device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, int hi, int64_t item, int hint) {
@@ -246,11 +290,17 @@ __device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, 
   return lo;
 }
 
+// A uniform field group walks its loads (stores) lane per access when it has at least
+// this many; with fewer, most lanes of such a walk would idle.
+constexpr int kCombinedWalkMin = 8;
+
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ DCfg s_c;
   __shared__ DGroup s_g;
   __shared__ DField s_fk[kMaxGroupFields];
-  __shared__ int32_t s_aoff[kMaxGroupFields + 1];
+  __shared__ int32_t s_loff[kMaxGroupFields + 1];   // first load of field k in the staged lists
+  __shared__ int32_t s_soff[kMaxGroupFields + 1];   // first store of field k (after all loads)
+  __shared__ uint8_t s_af[kMaxFoldedAccesses];      // field of each staged access
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
   __shared__ uint32_t s_b32[kMaxFoldedAccesses];
   __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
@@ -277,21 +327,37 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       for (int k = threadIdx.x; k < s_g.f_count; k += blockDim.x) s_fk[k] = a.fld[s_g.f_begin + k];
       __syncthreads();
       if (threadIdx.x == 0) {
+        // all loads of the group first (field by field), then all stores
         int o = 0;
         for (int k = 0; k < s_g.f_count; ++k) {
-          s_aoff[k] = o;
-          o += s_fk[k].n_load + s_fk[k].n_store;
+          s_loff[k] = o;
+          o += s_fk[k].n_load;
         }
-        s_aoff[s_g.f_count] = o;
+        s_loff[s_g.f_count] = o;
+        for (int k = 0; k < s_g.f_count; ++k) {
+          s_soff[k] = o;
+          o += s_fk[k].n_store;
+        }
+        s_soff[s_g.f_count] = o;
       }
       __syncthreads();
-      for (int j = threadIdx.x; j < s_aoff[s_g.f_count]; j += blockDim.x) {
+      // uniform groups fold each field's constant into its 32-bit offsets, so that
+      // address = shared thread address + offset for every field
+      for (int j = threadIdx.x; j < s_soff[s_g.f_count]; j += blockDim.x) {
+        const bool st = j >= s_loff[s_g.f_count];
         int k = 0;
-        while (s_aoff[k + 1] <= j) ++k;
-        const DAcc d = a.acc[s_fk[k].acc_begin + (j - s_aoff[k])];
+        if (!st) {
+          while (s_loff[k + 1] <= j) ++k;
+        } else {
+          while (s_soff[k + 1] <= j) ++k;
+        }
+        const DField &F = s_fk[k];
+        const int i = st ? F.n_load + (j - s_soff[k]) : j - s_loff[k];
+        const DAcc d = a.acc[F.acc_begin + i];
         s_boff[j] = d.boff;
-        s_b32[j] = (uint32_t)d.boff;
+        s_b32[j] = (uint32_t)d.boff + (s_g.uniform ? (uint32_t)(F.base - 32 * F.lo[1]) : 0u);
         s_kmin[j] = (uint8_t)d.kmin;
+        s_af[j] = (uint8_t)k;
       }
       if (s_g.cfg != cur_cfg) {
         if (threadIdx.x == 0) s_c = a.cfg[s_g.cfg];
@@ -358,13 +424,101 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       const bool partial = __any_sync(FULL, valid && kv < fold);
       uint32_t naddr = 0;
 
+      // ---- uniform groups, wave / y / z levels: one walk over all the group's accesses
+      bool fields_done = false;
+      if (level >= 1 && s_g.uniform && !partial) {
+        const DField &F0 = s_fk[0];
+        const int64_t el = (int64_t)F0.esize * (F0.stride[0] * x + F0.stride[1] * y + F0.stride[2] * z);
+        s_tbase[warp][lane] = (uint32_t)el;
+        int64_t mn = valid ? el : INT64_MAX, mx = valid ? el : INT64_MIN;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          mn = min(mn, (int64_t)__shfl_xor_sync(FULL, (long long)mn, off));
+          mx = max(mx, (int64_t)__shfl_xor_sync(FULL, (long long)mx, off));
+        }
+        __syncwarp();
+        const int L = s_loff[s_g.f_count];
+        const int S = level == 1 ? s_soff[s_g.f_count] - L : 0;
+        const uint32_t tme = s_tbase[warp][lane];
+        if (L >= kCombinedWalkMin) {
+          // lane per access over all 32 threads of the modelled warp
+          for (int a0 = 0; a0 < L && vmask; a0 += 32) {
+            const int j = a0 + (int)lane;
+            uint32_t cw = 0xffffffffu, cb = 0u;
+            uint32_t *bm = nullptr;
+            if (j < L) {
+              const DField &F = s_fk[s_af[j]];
+              const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+              const uint32_t limit = (uint32_t)(F.words[1] << 10);
+              bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+              if (mn + bo < 0 || mx + bo >= (int64_t)limit) bad += __popc(vmask);
+              else lpa_walk<32, false>(&s_tbase[warp][0], vmask, s_b32[j], limit, bm, cw, cb, bad);
+            }
+            if (cb) atomicOr(bm + cw, cb);
+          }
+        } else {
+          // few accesses: lane per thread, one run-head insertion per access
+          for (int j = 0; j < L; ++j) {
+            const DField &F = s_fk[s_af[j]];
+            const uint32_t limit = (uint32_t)(F.words[1] << 10);
+            uint32_t *const bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
+            runs_insert(bm, tme + s_b32[j], valid, limit, lane, bad, false);
+          }
+        }
+        if (S >= kCombinedWalkMin) {
+          for (int a0 = 0; a0 < S && vmask; a0 += 32) {
+            const int j = L + a0 + (int)lane;
+            uint32_t cw = 0xffffffffu, cb = 0u, nsec = 0u;
+            bool mono = true, ok = false;
+            uint32_t *bm = nullptr;
+            if (j < L + S) {
+              const DField &F = s_fk[s_af[j]];
+              const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+              const uint32_t limit = (uint32_t)(F.words[1] << 10);
+              bm = a.scratch + F.bm[BM_WS];
+              if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
+                bad += __popc(vmask);
+              } else {
+                lpa_walk_count(&s_tbase[warp][0], vmask, s_b32[j], bm, cw, cb, nsec, mono);
+                ok = true;
+              }
+            }
+            if (cb) atomicOr(bm + cw, cb);
+            // per-instruction distinct sectors: the lane's count when its sectors never
+            // decreased, else an exact recount by the whole warp
+            acc_sreq += __reduce_add_sync(FULL, (ok && mono) ? nsec : 0u);
+            uint32_t redo = __ballot_sync(FULL, ok && !mono);
+            while (redo) {
+              const int src = __ffs(redo) - 1;
+              redo &= redo - 1;
+              acc_sreq += warp_distinct_sectors(tme + s_b32[L + a0 + src], valid);
+            }
+          }
+        } else {
+          for (int j = L; j < L + S; ++j) {
+            const DField &F = s_fk[s_af[j]];
+            const uint32_t limit = (uint32_t)(F.words[1] << 10);
+            acc_sreq += runs_insert(a.scratch + F.bm[BM_WS], tme + s_b32[j], valid, limit, lane, bad, true);
+          }
+        }
+        __syncwarp();
+        fields_done = true;
+        for (int k = 0; k < s_g.f_count; ++k) {
+          const DField &F = s_fk[k];
+          const int nst = level <= 1 ? F.n_store : 0;
+          if (F.n_load + nst == 0) continue;
+          naddr += (uint32_t)(F.cnt_load[kv] + (level <= 1 ? F.cnt_store[kv] : 0));
+          acc_wi += (uint32_t)(F.n_load + nst);
+        }
+      }
+
       // ---- every field of the group
-      for (int k = 0; k < s_g.f_count; ++k) {
+      for (int k = 0; k < s_g.f_count && !fields_done; ++k) {
         const DField &F = s_fk[k];
         const int n_load = F.n_load;
         const int nst = level <= 1 ? F.n_store : 0;
         if (n_load + (level <= 1 ? nst : 0) == 0 || (level >= 2 && n_load == 0)) continue;
-        const int ao = s_aoff[k];
+        const int lo_ = s_loff[k], so_ = s_soff[k] - n_load;   // load i at lo_ + i, store i at so_ + i
         naddr += (uint32_t)(F.cnt_load[kv] + (level <= 1 ? F.cnt_store[kv] : 0));
         acc_wi += (uint32_t)(n_load + nst);
         const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
@@ -375,20 +529,21 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
           const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * lo0;
           uint32_t *const bl = a.scratch + F.bm[BM_BL], *const bs = a.scratch + F.bm[BM_BS];
           for (int i = 0; i < n_load; ++i) {
-            const bool act = valid && (int)s_kmin[ao + i] < kv;
-            const int64_t r = rel + s_boff[ao + i];
+            const bool act = valid && (int)s_kmin[lo_ + i] < kv;
+            const int64_t r = rel + s_boff[lo_ + i];
             acc_req += bitmap_insert(bl, r, act, lane, F.words[0], bad);
             acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
           }
           for (int i = n_load; i < n_load + nst; ++i) {
-            const bool act = valid && (int)s_kmin[ao + i] < kv;
-            const int64_t r = rel + s_boff[ao + i];
+            const bool act = valid && (int)s_kmin[so_ + i] < kv;
+            const int64_t r = rel + s_boff[so_ + i];
             acc_st += bitmap_insert(bs, r, act, lane, F.words[0], bad);
             acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
           }
         } else if (!F.wide) {
           const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * F.lo[1];
-          const uint32_t r0 = (uint32_t)rel;
+          // uniform groups staged the field constant into the 32-bit offsets already
+          const uint32_t r0 = s_g.uniform ? (uint32_t)((int64_t)F.esize * lin) : (uint32_t)rel;
           const uint32_t limit = (uint32_t)(F.words[1] << 10);
           uint32_t *const bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
           if (n_load > 0) {
@@ -417,10 +572,10 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
               const int ai = a0 + (int)al;
               uint32_t cw = 0xffffffffu, cb = 0u;
               if (ai < n_load && slice) {
-                const uint32_t b32 = s_b32[ao + ai];
+                const uint32_t b32 = s_b32[lo_ + ai];
                 if (!partial) {
                   if (P == 32) {
-                    const int64_t bo = s_boff[ao + ai];
+                    const int64_t bo = s_boff[lo_ + ai];
                     if (mn + bo < 0 || mx + bo >= (int64_t)limit) bad += __popc(slice);
                     else lpa_walk<32, false>(tb, slice, b32, limit, bm, cw, cb, bad);
                   } else {
@@ -442,7 +597,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
                     }
                   }
                 } else {
-                  const int km = s_kmin[ao + ai];
+                  const int km = s_kmin[lo_ + ai];
                   for (int t = 0; t < P; ++t) {
                     if (!((slice >> t) & 1u) || km >= (P > 1 ? (int)s_tkv[warp][g0 + t] : kv)) continue;
                     const uint32_t r = (P > 1 ? tb[t] : r0) + b32;
@@ -476,20 +631,20 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
           // wave stores: per-instruction unique sectors (partial-store model)
           uint32_t *const ws_ = a.scratch + F.bm[BM_WS];
           for (int i = n_load; i < n_load + nst; ++i) {
-            const bool act = valid && (int)s_kmin[ao + i] < kv;
-            acc_sreq += runs_insert(ws_, r0 + s_b32[ao + i], act, limit, lane, bad, true);
+            const bool act = valid && (int)s_kmin[so_ + i] < kv;
+            acc_sreq += runs_insert(ws_, r0 + s_b32[so_ + i], act, limit, lane, bad, true);
           }
         } else {
           const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * F.lo[1];
           uint32_t *const bm = a.scratch + F.bm[level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z];
           for (int i = 0; i < n_load; ++i) {
-            const bool act = valid && (int)s_kmin[ao + i] < kv;
-            bitmap_insert(bm, rel + s_boff[ao + i], act, lane, F.words[1], bad);
+            const bool act = valid && (int)s_kmin[lo_ + i] < kv;
+            bitmap_insert(bm, rel + s_boff[lo_ + i], act, lane, F.words[1], bad);
           }
           uint32_t *const ws_ = a.scratch + F.bm[BM_WS];
           for (int i = n_load; i < n_load + nst; ++i) {
-            const bool act = valid && (int)s_kmin[ao + i] < kv;
-            acc_sreq += bitmap_insert(ws_, rel + s_boff[ao + i], act, lane, F.words[1], bad);
+            const bool act = valid && (int)s_kmin[so_ + i] < kv;
+            acc_sreq += bitmap_insert(ws_, rel + s_boff[so_ + i], act, lane, F.words[1], bad);
           }
         }
       }

@@ -990,9 +990,20 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
           break;
         G.f_count += 1;
         G.acc_count += na;
+        G.n_loads += f.n_load;
+        G.n_stores += f.n_store;
         G.mw_end = std::max(G.mw_end, f.mw_end);
         need += p->need_words[k];
         ++k;
+      }
+      // uniform layout: a field's relative address is the shared thread address plus a
+      // per-field constant, so all the group's accesses can be walked as one list
+      G.uniform = 1;
+      for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
+        const DField &f = p->hfld[q], &f0 = p->hfld[G.f_begin];
+        if (f.wide || f.esize != f0.esize || f.stride[0] != f0.stride[0] || f.stride[1] != f0.stride[1] ||
+            f.stride[2] != f0.stride[2])
+          G.uniform = 0;
       }
       p->hgrp.push_back(G);
     }
