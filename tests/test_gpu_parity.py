@@ -203,9 +203,9 @@ def test_retuning_to_more_passes_keeps_results(ctx):
     with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": -1}) as p:
         p.execute(B.WS_MODE_BATCHED)
         ref, ref_o = p.results()
-    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": 96}) as p:
+    with B.Plan(ctx, cfgs, hw, tuning={"pass_mb": 200}) as p:
         assert p.profile()["passes"] >= 1
-        p.autotune()        # tries 48 MiB passes: more passes than at creation
+        p.autotune()        # tries 96 MiB passes: more passes than at creation
         for mode in (B.WS_MODE_BATCHED, B.WS_MODE_DIRECT):
             p.execute(mode)
             res, order = p.results()
@@ -233,7 +233,7 @@ def test_autotune_keeps_results(ctx):
         p.execute(B.WS_MODE_BATCHED)
         r1, o1 = p.results()
         best = p.autotune()
-        assert best["chunk_warps"] in (64, 256, 1024, 4096) and best["pass_mb"] in (48, 96, -1)
+        assert best["chunk_warps"] in (64, 256, 1024, 4096) and best["pass_mb"] in (96, 1024, 8192, -1)
         p.execute(B.WS_MODE_BATCHED)
         r2, o2 = p.results()
         prof = p.profile()
