@@ -41,7 +41,7 @@ RESULT_DBL = ["v_l1", "v_l2_load", "v_l2_store", "v_dram_load", "v_dram_store", 
 RESULT = np.dtype([(k, "<i8") for k in RESULT_INT] + [(k, "<f8") for k in RESULT_DBL] +
                   [("limiter", "<i4"), ("status", "<i4")], align=True)
 TUNING = np.dtype([("chunk_warps", "<i4"), ("enum_threads", "<i4"), ("count_words", "<i4"),
-                   ("ctas_per_sm", "<i4"), ("pass_mb", "<i4")], align=True)
+                   ("ctas_per_sm", "<i4"), ("pass_mb", "<i4"), ("walk", "<i4")], align=True)
 PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4"), ("ms_model", "<f4"),
                     ("ms_rank", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),
@@ -67,6 +67,7 @@ assert (ACCESS.itemsize, FIELD.itemsize, CONFIG.itemsize, HW.itemsize, RESULT.it
 WS_OK, WS_EINVAL, WS_ENOMEM, WS_EAGAIN, WS_ETIMEDOUT, WS_EOVERFLOW, WS_ECUDA, WS_ENOTFOUND, WS_ECANCELED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 WS_MODE_PLAIN, WS_MODE_BATCHED, WS_MODE_DIRECT = 0, 1, 2
+WS_WALK_INTERVAL, WS_WALK_ADDRESS = 0, 1
 
 EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_create", "ws_destroy",
            "ws_plan_create", "ws_plan_execute", "ws_plan_results", "ws_plan_device_results", "ws_plan_profile",

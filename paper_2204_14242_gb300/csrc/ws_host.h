@@ -50,6 +50,7 @@ struct ws_plan {
   ws_tuning tune;
   std::vector<ws::DField> hfld;
   std::vector<ws::DGroup> hgrp;
+  std::vector<char> grp_iv_ok;   // group allows the interval walk (used unless tune.walk asks otherwise)
   std::vector<int32_t> cfg_grp_begin;
   std::vector<int64_t> need_words;
   std::vector<int32_t> cfg_cf_begin;
@@ -60,7 +61,8 @@ struct ws_plan {
   size_t grab_bytes = 0, counters_bytes = 0;
   int64_t upload_bytes = 0;
   int64_t d_grp = -1;
-  int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
+  int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
+  int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
           d_order = -1, d_scratch = -1;
   std::vector<int64_t> allocs;
   bool ext_scratch = false;  // scratch lent by a server pool (kept zeroed by the counting kernel)

@@ -70,6 +70,10 @@ struct DField {
   int32_t first_of_cfg;   // 1 if this is the candidate's first field (counts LUPs)
   int32_t wide;           // a bitmap spans >= 2^32 bytes: 64-bit address path
   int32_t lpa_log2p;      // log2 of P = lanes per thread-slice group for the load walk (P >= n_load, <= 32)
+  int32_t iv;             // interval walk possible: not wide and |elem_bytes * stride_x| <= 32
+  int32_t iv_begin;       // first merged load interval (DIv array)
+  int32_t n_iv;           // merged load intervals
+  int32_t pad_iv;
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };
@@ -79,6 +83,16 @@ struct DField {
 struct DAcc {
   int64_t boff;
   int32_t kmin;
+  int32_t pad;
+};
+
+// A merged load interval of a field: folded loads whose sorted byte offsets are at
+// most 32 B apart, so that for a row segment of threads whose addresses step by at
+// most 32 B the union of all their sectors is the single sector range
+// [(lowest thread address + boff) / 32, (highest thread address + boff + ext) / 32].
+struct DIv {
+  int64_t boff;           // smallest byte offset of the run
+  uint32_t ext;           // largest minus smallest byte offset
   int32_t pad;
 };
 
@@ -103,6 +117,8 @@ struct DGroup {
   int32_t uniform;        // all fields share element size and strides (and none is wide)
   int32_t n_loads;        // folded loads of all its fields
   int32_t n_stores;       // folded stores of all its fields
+  int32_t iv;             // uniform and every field allows the interval walk
+  int32_t n_iv;           // merged load intervals of all its fields
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch
@@ -112,6 +128,7 @@ struct DPass {
   int64_t citem_lo, citem_hi;  // counting items of the pass
   int32_t cf_lo, cf_hi;        // (candidate, field) index range
   int32_t grp_lo, grp_hi;      // field-group index range
+  int64_t words;               // scratch words [0, words) holding the pass's bitmaps
 };
 
 constexpr int kMaxFoldedAccesses = 2048;   // per field group, staged in shared memory

@@ -10,10 +10,12 @@
 //                 half-warp bank-conflict cycles.
 //   count_kernel  read-and-clear popcount of the bitmaps: unique sectors, unique 128 B
 //                 lines (nibble OR), y / z overlaps by AND / AND-NOT.  Leaves the
-//                 bitmaps zeroed for the next step.
+//                 bitmaps zeroed for the next step (only non-zero words are written).
 //   model_kernel  fp64 capacity model and limiters (Sec. 2, 3.5), one thread per candidate.
 //   rank_kernel   stable counting rank per segment (Sec. 5.7).
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "ws_internal.h"
 #include "ws_kernels.h"
@@ -294,6 +296,38 @@ __device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, 
 // this many; with fewer, most lanes of such a walk would idle.
 constexpr int kCombinedWalkMin = 8;
 
+// Sets sectors [s0, s1] of a bitmap viewed as 64-bit units (one red.or per unit).
+__device__ __forceinline__ void set_sector_range(unsigned long long *__restrict__ bm, uint32_t s0, uint32_t s1) {
+  const uint32_t u0 = s0 >> 6, u1 = s1 >> 6;
+  const unsigned long long m0 = ~0ull << (s0 & 63u);
+  const unsigned long long m1 = ~0ull >> (63u - (s1 & 63u));
+  if (u0 == u1) {
+    atomicOr(bm + u0, m0 & m1);
+    return;
+  }
+  atomicOr(bm + u0, m0);
+  for (uint32_t u = u0 + 1; u < u1; ++u) atomicOr(bm + u, ~0ull);
+  atomicOr(bm + u1, m1);
+}
+
+// Byte range [lo, hi] (relative to the bitmap origin) of one row segment of a
+// modelled warp under byte offset bo and extent ext.  Thread addresses are kept as
+// their low 32 bits; `mn` is the warp's smallest full thread address, and every valid
+// thread lies less than 2^32 bytes above it (the bitmap of a non-wide field spans
+// less than that), so address - mn is exact in 32 bits.  Returns false when the range
+// leaves [0, limit).
+__device__ __forceinline__ bool segment_range(uint32_t th, uint32_t tt, int64_t mn, int64_t bo, uint32_t ext,
+                                              uint32_t limit, uint32_t &lo, uint32_t &hi) {
+  const uint32_t m32 = (uint32_t)mn;
+  const uint32_t dh = th - m32, dt = tt - m32;
+  const int64_t vlo = mn + (int64_t)min(dh, dt) + bo;
+  const int64_t vhi = mn + (int64_t)max(dh, dt) + bo + (int64_t)ext;
+  if (vlo < 0 || vhi >= (int64_t)limit) return false;
+  lo = (uint32_t)vlo;
+  hi = (uint32_t)vhi;
+  return true;
+}
+
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ DCfg s_c;
   __shared__ DGroup s_g;
@@ -307,7 +341,15 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ uint32_t s_tc[1024];
   __shared__ __align__(16) uint32_t s_tbase[16][32];   // per warp: relative address of each thread's first point
   __shared__ uint8_t s_tkv[16][32];                    // per warp: valid folded points of each thread
+  __shared__ uint32_t s_seg[16][32];                   // per warp: row segments (head lane, tail lane, kv)
+  __shared__ int32_t s_ioff[kMaxGroupFields + 1];      // first merged interval of field k
   __shared__ long long s_item;
+  // merged load intervals of an interval-walk group (dynamic): offset, extent, field
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  const int iv_cap16 = (a.iv_cap + 15) & ~15;
+  int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
+  uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
+  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -339,8 +381,24 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
           o += s_fk[k].n_store;
         }
         s_soff[s_g.f_count] = o;
+        o = 0;
+        for (int k = 0; k < s_g.f_count; ++k) {
+          s_ioff[k] = o;
+          o += s_g.iv ? s_fk[k].n_iv : 0;
+        }
+        s_ioff[s_g.f_count] = o;
       }
       __syncthreads();
+      // merged load intervals, offsets relative to each field's bitmap origin
+      for (int j = threadIdx.x; j < s_ioff[s_g.f_count]; j += blockDim.x) {
+        int k = 0;
+        while (s_ioff[k + 1] <= j) ++k;
+        const DField &F = s_fk[k];
+        const DIv v = a.iv[F.iv_begin + (j - s_ioff[k])];
+        s_ibo[j] = v.boff + F.base - 32 * F.lo[1];
+        s_iext[j] = v.ext;
+        s_iaf[j] = (uint8_t)k;
+      }
       // uniform groups fold each field's constant into its 32-bit offsets, so that
       // address = shared thread address + offset for every field
       for (int j = threadIdx.x; j < s_soff[s_g.f_count]; j += blockDim.x) {
@@ -426,7 +484,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
 
       // ---- uniform groups, wave / y / z levels: one walk over all the group's accesses
       bool fields_done = false;
-      if (level >= 1 && s_g.uniform && !partial) {
+      if (level >= 1 && s_g.uniform && (s_g.iv || !partial)) {
         const DField &F0 = s_fk[0];
         const int64_t el = (int64_t)F0.esize * (F0.stride[0] * x + F0.stride[1] * y + F0.stride[2] * z);
         s_tbase[warp][lane] = (uint32_t)el;
@@ -440,7 +498,101 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         const int L = s_loff[s_g.f_count];
         const int S = level == 1 ? s_soff[s_g.f_count] - L : 0;
         const uint32_t tme = s_tbase[warp][lane];
-        if (L >= kCombinedWalkMin) {
+        if (s_g.iv) {
+          // ---- interval walk (Sec. 3.4's closed-form counting, exact): the warp's
+          // valid threads form row segments of consecutive x; one (segment, merged load
+          // interval) pair is one sector range.  Partial warps take the raw folded
+          // loads, each checked against the segment's valid folded points.
+          const uint32_t tx = tc & 1023u;
+          const uint32_t heads = __ballot_sync(FULL, valid && (lane == 0u || tx == 0u));
+          const uint32_t ends = vmask & ~((vmask & ~heads) >> 1);
+          const uint32_t nseg = __popc(heads);
+          if ((heads >> lane) & 1u) {
+            const uint32_t t = __ffs(ends & (0xffffffffu << lane)) - 1u;
+            s_seg[warp][__popc(heads & ((1u << lane) - 1u))] = lane | (t << 8) | ((uint32_t)kv << 16);
+          }
+          __syncwarp();
+          const int M = partial ? L : s_ioff[s_g.f_count];
+          const uint32_t total = nseg * (uint32_t)M;
+          const uint32_t magic = nseg > 1u ? 0xffffffffu / nseg + 1u : 0u;
+          const int bsel = level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z;
+          for (uint32_t p = lane; p < total; p += 32u) {
+            const uint32_t e = nseg > 1u ? __umulhi(p, magic) : p;
+            const uint32_t sg = s_seg[warp][p - e * nseg];
+            int k;
+            int64_t bo;
+            uint32_t ext;
+            if (!partial) {
+              k = s_iaf[e];
+              bo = s_ibo[e];
+              ext = s_iext[e];
+            } else {
+              if ((uint32_t)s_kmin[e] >= (sg >> 16)) continue;
+              k = s_af[e];
+              bo = s_boff[e] + s_fk[k].base - 32 * s_fk[k].lo[1];
+              ext = 0u;
+            }
+            const DField &F = s_fk[k];
+            uint32_t lo, hi;
+            if (!segment_range(s_tbase[warp][sg & 255u], s_tbase[warp][(sg >> 8) & 255u], mn, bo, ext,
+                               (uint32_t)(F.words[1] << 10), lo, hi)) {
+              ++bad;
+              continue;
+            }
+            set_sector_range(reinterpret_cast<unsigned long long *>(a.scratch + F.bm[bsel]), lo >> 5, hi >> 5);
+          }
+          if (!partial) {
+            // stores: lane per store instruction over the segments, counting the
+            // instruction's distinct sectors (exact for non-decreasing segments)
+            for (int a0 = 0; a0 < S; a0 += 32) {
+              const int j = L + a0 + (int)lane;
+              uint32_t nsec = 0u, plo = 0u, phi = 0u;
+              bool mono = true, ok = false;
+              if (j < L + S) {
+                const DField &F = s_fk[s_af[j]];
+                const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+                const uint32_t limit = (uint32_t)(F.words[1] << 10);
+                unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[BM_WS]);
+                ok = true;
+                for (uint32_t si = 0; si < nseg; ++si) {
+                  const uint32_t sg = s_seg[warp][si];
+                  uint32_t lo, hi;
+                  if (!segment_range(s_tbase[warp][sg & 255u], s_tbase[warp][(sg >> 8) & 255u], mn, bo, 0u, limit,
+                                     lo, hi)) {
+                    ++bad;
+                    ok = false;
+                    continue;
+                  }
+                  const uint32_t s0 = lo >> 5, s1 = hi >> 5;
+                  set_sector_range(bm, s0, s1);
+                  if (si == 0u) {
+                    nsec = s1 - s0 + 1u;
+                  } else {
+                    mono = mono && s0 >= plo && s1 >= phi;
+                    const uint32_t from = max(phi + 1u, s0);
+                    nsec += s1 >= from ? s1 - from + 1u : 0u;
+                  }
+                  plo = s0;
+                  phi = s1;
+                }
+              }
+              acc_sreq += __reduce_add_sync(FULL, (ok && mono) ? nsec : 0u);
+              uint32_t redo = __ballot_sync(FULL, ok && !mono);
+              while (redo) {
+                const int src = __ffs(redo) - 1;
+                redo &= redo - 1;
+                acc_sreq += warp_distinct_sectors(tme + s_b32[L + a0 + src], valid);
+              }
+            }
+          } else {
+            for (int j = L; j < L + S; ++j) {
+              const DField &F = s_fk[s_af[j]];
+              const uint32_t limit = (uint32_t)(F.words[1] << 10);
+              const bool act = valid && (int)s_kmin[j] < kv;
+              acc_sreq += runs_insert(a.scratch + F.bm[BM_WS], tme + s_b32[j], act, limit, lane, bad, true);
+            }
+          }
+        } else if (L >= kCombinedWalkMin) {
           // lane per access over all 32 threads of the modelled warp
           for (int a0 = 0; a0 < L && vmask; a0 += 32) {
             const int j = a0 + (int)lane;
@@ -465,7 +617,9 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
             runs_insert(bm, tme + s_b32[j], valid, limit, lane, bad, false);
           }
         }
-        if (S >= kCombinedWalkMin) {
+        if (s_g.iv) {
+          // stores were walked with the intervals above
+        } else if (S >= kCombinedWalkMin) {
           for (int a0 = 0; a0 < S && vmask; a0 += 32) {
             const int j = L + a0 + (int)lane;
             uint32_t cw = 0xffffffffu, cb = 0u, nsec = 0u;
@@ -678,28 +832,27 @@ __device__ __forceinline__ uint32_t lines_of(uint32_t x) {
   return __popc(t & 0x11111111u);
 }
 
-__device__ __forceinline__ uint4 ld_clear(uint32_t *p) {
-  uint4 *q = reinterpret_cast<uint4 *>(p);
-  uint4 v = *q;
-  *q = make_uint4(0u, 0u, 0u, 0u);
-  return v;
+__device__ __forceinline__ bool nz(const uint4 &v) { return (v.x | v.y | v.z | v.w) != 0u; }
+
+__device__ __forceinline__ void tally_sectors_lines(uint32_t &sec, uint32_t &lin, const uint4 &v) {
+  sec += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+  lin += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
 }
 
-__device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z,
-                                           const uint4 &v) {
-  acc[4] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
-  acc[5] += lines_of(w.x) + lines_of(w.y) + lines_of(w.z) + lines_of(w.w);
+__device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z) {
+  tally_sectors_lines(acc[4], acc[5], w);
   acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
   acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
   acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
   acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
-  acc[10] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-  acc[11] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
 }
 
 // Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of
-// words); each thread keeps two 16-byte positions of every bitmap in flight before it
-// clears them.
+// words); each thread keeps two 16-byte positions of every bitmap in flight.  The
+// bitmaps are sparse: an all-zero position is neither tallied nor written, and a
+// non-zero one is cleared only after its value has arrived, so the clearing store
+// never waits behind the read of its own sector and the written bytes are those of
+// the non-zero positions alone.
 __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
   __shared__ long long s_item;
   __shared__ uint32_t s_red[16][12];
@@ -715,7 +868,10 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
     const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, true, cur);
     cur = cf;
     const DField &F = a.fld[cf];
-    const bool has_blk = F.bm[BM_BL] >= 0 || F.bm[BM_BS] >= 0;
+    const int64_t bm_bl = F.bm[BM_BL], bm_bs = F.bm[BM_BS], bm_w = F.bm[BM_W], bm_ws = F.bm[BM_WS];
+    const int64_t bm_y = F.bm[BM_Y], bm_z = F.bm[BM_Z];
+    const int cfg = F.cfg;
+    const bool has_blk = bm_bl >= 0 || bm_bs >= 0;
     const int64_t nb = has_blk ? F.words[0] : 0;
     const int64_t ntot = nb + F.words[1];
     const int64_t c0 = (item - F.citem_begin) * (int64_t)a.chunk_words;
@@ -723,24 +879,26 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // block part: words [c0, min(c1, nb)) -- BL, BS
     const int64_t cb = min(c1, nb);
-    for (int64_t i = c0 + 4 * threadIdx.x; i < cb; i += 4 * blockDim.x) {
-      if (F.bm[BM_BL] >= 0) {
-        uint4 v = ld_clear(a.scratch + F.bm[BM_BL] + i);
-        acc[0] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        acc[1] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+    uint4 *const pbl = bm_bl >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bl) : nullptr;
+    uint4 *const pbs = bm_bs >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bs) : nullptr;
+    for (int64_t i = c0 / 4 + threadIdx.x; i < cb / 4; i += blockDim.x) {
+      const uint4 l = pbl ? pbl[i] : zero;
+      const uint4 t = pbs ? pbs[i] : zero;
+      if (nz(l)) {
+        tally_sectors_lines(acc[0], acc[1], l);
+        pbl[i] = zero;
       }
-      if (F.bm[BM_BS] >= 0) {
-        uint4 v = ld_clear(a.scratch + F.bm[BM_BS] + i);
-        acc[2] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        acc[3] += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+      if (nz(t)) {
+        tally_sectors_lines(acc[2], acc[3], t);
+        pbs[i] = zero;
       }
     }
     // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS
-    const bool has_w = F.bm[BM_W] >= 0, has_ws = F.bm[BM_WS] >= 0;
-    uint4 *const pw = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_W]) : nullptr;
-    uint4 *const py = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr;
-    uint4 *const pz = has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr;
-    uint4 *const ps = has_ws ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr;
+    const bool has_w = bm_w >= 0, has_ws = bm_ws >= 0;
+    uint4 *const pw = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_w) : nullptr;
+    uint4 *const py = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_y) : nullptr;
+    uint4 *const pz = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_z) : nullptr;
+    uint4 *const ps = has_ws ? reinterpret_cast<uint4 *>(a.scratch + bm_ws) : nullptr;
     const int64_t q1 = (c1 - nb) / 4;
     for (int64_t q = (max(c0, nb) - nb) / 4 + threadIdx.x; q < q1; q += 2 * (int64_t)blockDim.x) {
       const int64_t qb = q + blockDim.x;
@@ -760,22 +918,26 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
         v0 = ps[q];
         if (two) v1 = ps[qb];
       }
-      if (has_w) {
-        pw[q] = zero;
-        py[q] = zero;
-        pz[q] = zero;
-        if (two) {
-          pw[qb] = zero;
-          py[qb] = zero;
-          pz[qb] = zero;
-        }
+      if (nz(w0) | nz(y0) | nz(z0)) {
+        tally_wave(acc, w0, y0, z0);
+        if (nz(w0)) pw[q] = zero;
+        if (nz(y0)) py[q] = zero;
+        if (nz(z0)) pz[q] = zero;
       }
-      if (has_ws) {
+      if (nz(w1) | nz(y1) | nz(z1)) {
+        tally_wave(acc, w1, y1, z1);
+        if (nz(w1)) pw[qb] = zero;
+        if (nz(y1)) py[qb] = zero;
+        if (nz(z1)) pz[qb] = zero;
+      }
+      if (nz(v0)) {
+        tally_sectors_lines(acc[10], acc[11], v0);
         ps[q] = zero;
-        if (two) ps[qb] = zero;
       }
-      tally_wave(acc, w0, y0, z0, v0);
-      tally_wave(acc, w1, y1, z1, v1);
+      if (nz(v1)) {
+        tally_sectors_lines(acc[10], acc[11], v1);
+        ps[qb] = zero;
+      }
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -786,7 +948,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
     if (threadIdx.x < 12) {
       unsigned long long t = 0;
       for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += s_red[wi][threadIdx.x];
-      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)F.cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
+      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
     }
     __syncthreads();
   }
@@ -940,8 +1102,28 @@ __global__ void keys_kernel(const ws_result *__restrict__ res, int n, double *__
 }
 
 // ---- launchers ---------------------------------------------------------------------
+size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 1); }
+
+// Raises the kernel's dynamic shared-memory limit (once per device and size).
+static cudaError_t enum_allow_smem(size_t dyn) {
+  static std::mutex mu;
+  static size_t allowed[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (dyn <= allowed[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) allowed[dev] = dyn;
+  return e;
+}
+
 cudaError_t launch_enum(const EnumArgs &args, int grid, int threads, cudaStream_t st) {
-  enum_kernel<<<grid, threads, 0, st>>>(args);
+  const size_t dyn = enum_dyn_smem(args.iv_cap);
+  cudaError_t e = enum_allow_smem(dyn);
+  if (e != cudaSuccess) return e;
+  enum_kernel<<<grid, threads, dyn, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
@@ -963,8 +1145,11 @@ cudaError_t launch_keys(const ws_result *res, int n, double *keys, cudaStream_t 
   keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(res, n, keys);
   return cudaGetLastError();
 }
-cudaError_t enum_occupancy(int threads, int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, enum_kernel, threads, 0);
+cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm) {
+  const size_t dyn = enum_dyn_smem(iv_cap);
+  cudaError_t e = enum_allow_smem(dyn);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, enum_kernel, threads, dyn);
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, 512, 0);

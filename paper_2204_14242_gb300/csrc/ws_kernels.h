@@ -11,6 +11,8 @@ struct EnumArgs {
   const DField *fld;
   const DGroup *grp;
   const DAcc *acc;
+  const DIv *iv;                   // merged load intervals
+  int32_t iv_cap;                  // dynamic shared memory holds this many staged intervals
   uint32_t *scratch;               // bitmaps of the pass
   int64_t *counters;               // [n_cfg][N_COUNTERS]
   unsigned long long *grab;        // work-stealing counter (zeroed before the launch)
@@ -51,7 +53,8 @@ cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st);
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st);
 cudaError_t launch_rank(const RankArgs &args, cudaStream_t st);
 cudaError_t launch_keys(const ws_result *res, int n, double *keys, cudaStream_t st);
-cudaError_t enum_occupancy(int threads, int *blocks_per_sm);
+cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm);
+size_t enum_dyn_smem(int iv_cap);
 cudaError_t count_occupancy(int *blocks_per_sm);
 
 }  // namespace ws

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <climits>
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -137,6 +138,7 @@ struct Compiled {
   DCfg d{};
   std::vector<DField> f;
   std::vector<std::vector<DAcc>> acc;
+  std::vector<std::vector<DIv>> iv;
   std::vector<uint64_t> fkey;       // (field index, folding): equal keys have equal access lists
   std::vector<int64_t> need_words;  // bitmap words per field
 };
@@ -149,6 +151,7 @@ typedef std::tuple<int64_t, int64_t, int64_t, int64_t> Off4;
 struct FieldFold {
   int status = WS_OK;
   std::vector<DAcc> da;
+  std::vector<DIv> iv;
   int32_t n_load = 0, n_store = 0;
   __int128 omin = 0, omax = 0;
   int16_t cnt_load[17], cnt_store[17];
@@ -214,6 +217,25 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
     }
   out.n_load = (int32_t)fl.size();
   out.n_store = (int32_t)fs.size();
+  // merged load intervals: sorted load offsets cut wherever two neighbours are more than
+  // 32 B apart (a chain of byte addresses with steps of at most 32 B touches every
+  // sector between its ends)
+  {
+    std::vector<int64_t> b;
+    for (int i = 0; i < out.n_load; ++i) b.push_back(out.da[i].boff);
+    std::sort(b.begin(), b.end());
+    out.iv.clear();
+    for (size_t i = 0; i < b.size();) {
+      size_t j = i;
+      while (j + 1 < b.size() && b[j + 1] - b[j] <= 32) ++j;
+      DIv v;
+      v.boff = b[i];
+      v.ext = (uint32_t)(b[j] - b[i]);
+      v.pad = 0;
+      out.iv.push_back(v);
+      i = j + 1;
+    }
+  }
   // An issued folded access o' of a thread whose first point is p0 touches the same
   // address as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e,
   // so valid points x raw offsets bound every address of the field.
@@ -351,6 +373,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps
   out.f.clear();
   out.acc.clear();
+  out.iv.clear();
   out.fkey.clear();
   out.need_words.clear();
   for (int fi = 0; fi < c.n_field; ++fi) {
@@ -404,6 +427,12 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.wide = (df.words[0] >= ((int64_t)1 << 22) || df.words[1] >= ((int64_t)1 << 22)) ? 1 : 0;
     df.lpa_log2p = 0;
     while ((1 << df.lpa_log2p) < std::min(df.n_load, 32)) ++df.lpa_log2p;
+    // row segments of threads step by elem_bytes * stride_x bytes: at most one sector
+    // keeps every segment's sectors contiguous
+    df.iv = (!df.wide && std::llabs(F.stride[0]) * F.elem_bytes <= 32) ? 1 : 0;
+    df.iv_begin = 0;
+    df.n_iv = (int32_t)ff->iv.size();
+    df.pad_iv = 0;
     for (int kv = 0; kv <= 16; ++kv) {
       df.cnt_load[kv] = ff->cnt_load[kv];
       df.cnt_store[kv] = ff->cnt_store[kv];
@@ -414,6 +443,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     if (has_s) need += df.words[0] + df.words[1];
     out.f.push_back(df);
     out.acc.push_back(da);
+    out.iv.push_back(ff->iv);
     out.fkey.push_back(((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold);
     out.need_words.push_back(need);
   }
@@ -494,6 +524,7 @@ static void default_tuning(ws_tuning &t) {
   t.count_words = std::max(256, t.count_words / 4 * 4);
   t.chunk_warps = std::max(1, t.chunk_warps);
   if (t.pass_mb < 0) t.pass_mb = -1;
+  if (t.walk != WS_WALK_ADDRESS) t.walk = WS_WALK_INTERVAL;
 }
 
 // Numbers work items and cuts passes for the current tuning.
@@ -510,7 +541,8 @@ void ws_plan::layout() {
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
   int64_t items = 0, citems = 0, used = 0;
-  DPass cur{0, 0, 0, 0, 0, 0, 0, 0};
+  for (size_t g = 0; g < hgrp.size(); ++g) hgrp[g].iv = grp_iv_ok[g] && tune.walk == WS_WALK_INTERVAL;
+  DPass cur{0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int ng = (int)hgrp.size();
   for (int g = 0; g < ng; ++g) {
     DGroup &G = hgrp[g];
@@ -519,8 +551,9 @@ void ws_plan::layout() {
       cur.grp_hi = g;
       cur.item_hi = items;
       cur.citem_hi = citems;
+      cur.words = used;
       passes.push_back(cur);
-      cur = DPass{items, 0, citems, 0, G.f_begin, 0, g, 0};
+      cur = DPass{items, 0, citems, 0, G.f_begin, 0, g, 0, 0};
       used = 0;
     }
     for (int k = 0; k < G.f_count; ++k) {
@@ -551,6 +584,7 @@ void ws_plan::layout() {
   cur.grp_hi = ng;
   cur.item_hi = items;
   cur.citem_hi = citems;
+  cur.words = used;
   if (ng > 0) passes.push_back(cur);
   item_begin_end = items;
   citem_begin_end = citems;
@@ -569,7 +603,7 @@ int ws_plan::upload_fields(cudaStream_t st) {
 int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
   int occ = 1;
   if (counting) count_occupancy(&occ);
-  else enum_occupancy(threads, &occ);
+  else enum_occupancy(threads, iv_cap, &occ);
   if (tune.ctas_per_sm > 0) occ = std::min(occ, tune.ctas_per_sm);
   occ = std::max(occ, 1);
   int64_t g = (int64_t)ctx->sm_count * occ;
@@ -595,6 +629,8 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.fld = (const DField *)dev(d_fld);
     ea.grp = (const DGroup *)dev(d_grp);
     ea.acc = (const DAcc *)dev(d_acc);
+    ea.iv = (const DIv *)dev(d_iv);
+    ea.iv_cap = iv_cap;
     ea.scratch = (uint32_t *)dev(d_scratch);
     ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
     ea.grab = (unsigned long long *)dev(d_counters) + 2 * p;
@@ -672,6 +708,10 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.fld = (const DField *)dev(d_fld);
       ea.grp = (const DGroup *)dev(d_grp);
       ea.acc = (const DAcc *)dev(d_acc);
+      ea.iv = (const DIv *)dev(d_iv);
+      ea.iv_cap = iv_cap;
+    ea.iv = (const DIv *)dev(d_iv);
+    ea.iv_cap = iv_cap;
       ea.scratch = (uint32_t *)dev(d_scratch);
       ea.counters = counters;
       ea.grab = grab;
@@ -866,7 +906,7 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
     Compiled cc;
     if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc, &cache) != WS_OK) continue;
     for (size_t k = 0; k < cc.f.size(); ++k) {
-      dsc += sizeof(DField) + cc.acc[k].size() * sizeof(DAcc);
+      dsc += sizeof(DField) + sizeof(DGroup) + cc.acc[k].size() * sizeof(DAcc) + cc.iv[k].size() * sizeof(DIv);
       scr += (size_t)cc.need_words[k] * 4;
       mf = std::max(mf, (size_t)cc.need_words[k] * 4);
     }
@@ -910,7 +950,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
 
   std::vector<DCfg> hcfg(n_cfg);
   std::vector<DAcc> hacc;
-  std::map<uint64_t, int32_t> acc_at;
+  std::map<uint64_t, int32_t> acc_at, iv_at;
+  std::vector<DIv> hiv;
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   std::vector<Compiled> comp;
   std::vector<int> status;
@@ -920,7 +961,9 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   for (int i = 0; i < n_cfg; ++i) {
     if (status[i] != WS_OK) continue;
     for (size_t k = 0; k < comp[i].f.size(); ++k) {
-      dsc += sizeof(DField) + comp[i].acc[k].size() * sizeof(DAcc);
+      // a field, its access and interval lists, at most one field group
+      dsc += sizeof(DField) + sizeof(DGroup) + comp[i].acc[k].size() * sizeof(DAcc) +
+             comp[i].iv[k].size() * sizeof(DIv);
       total_need += (size_t)comp[i].need_words[k] * 4;
       max_field = std::max(max_field, (size_t)comp[i].need_words[k] * 4);
     }
@@ -958,6 +1001,12 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
           hacc.insert(hacc.end(), comp[i].acc[k].begin(), comp[i].acc[k].end());
         }
         f.acc_begin = it->second;
+        auto jt = iv_at.find(comp[i].fkey[k]);
+        if (jt == iv_at.end()) {
+          jt = iv_at.emplace(comp[i].fkey[k], (int32_t)hiv.size()).first;
+          hiv.insert(hiv.end(), comp[i].iv[k].begin(), comp[i].iv[k].end());
+        }
+        f.iv_begin = jt->second;
         p->hfld.push_back(f);
         p->need_words.push_back(comp[i].need_words[k]);
       }
@@ -999,17 +1048,34 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
       // uniform layout: a field's relative address is the shared thread address plus a
       // per-field constant, so all the group's accesses can be walked as one list
       G.uniform = 1;
+      G.iv = 1;
       for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
         const DField &f = p->hfld[q], &f0 = p->hfld[G.f_begin];
         if (f.wide || f.esize != f0.esize || f.stride[0] != f0.stride[0] || f.stride[1] != f0.stride[1] ||
             f.stride[2] != f0.stride[2])
           G.uniform = 0;
+        if (!f.iv) G.iv = 0;
+        G.n_iv += f.n_iv;
       }
+      // interval walk: uniform groups whose row segments have contiguous sectors
+      G.iv = G.iv && G.uniform;
+      if (G.iv) p->iv_cap = std::max(p->iv_cap, G.n_iv);
+      p->grp_iv_ok.push_back((char)G.iv);
       p->hgrp.push_back(G);
     }
   }
   p->cfg_grp_begin[n_cfg] = (int32_t)p->hgrp.size();
   p->layout();
+  {
+    // raise the enumeration kernel's shared-memory limit now, outside any capture
+    int occ = 0;
+    cudaError_t e0 = enum_occupancy(p->tune.enum_threads, p->iv_cap, &occ);
+    if (e0 != cudaSuccess) {
+      set_error(std::string("enumeration kernel setup: ") + cudaGetErrorString(e0));
+      delete p;
+      return WS_ECUDA;
+    }
+  }
 
   // device buffers
   // one pair of work-stealing counters per pass; any tuning makes at most one pass per
@@ -1020,6 +1086,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->d_grp = p->take(std::max<size_t>(p->hgrp.size() * sizeof(DGroup), 256));
   p->d_fld = p->take(std::max<size_t>(p->hfld.size() * sizeof(DField), 256));
   p->d_acc = p->take(std::max<size_t>(hacc.size() * sizeof(DAcc), 256));
+  p->d_iv = p->take(std::max<size_t>(hiv.size() * sizeof(DIv), 256));
   p->d_seg = p->take((seg.size()) * sizeof(int32_t));
   p->d_counters = p->take(p->counters_bytes);
   p->d_results = p->take(std::max<size_t>((size_t)n_cfg * sizeof(ws_result), 256));
@@ -1031,7 +1098,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   } else {
     p->d_scratch = p->take(scratch);
   }
-  for (int64_t o : {p->d_cfg, p->d_grp, p->d_fld, p->d_acc, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
+  for (int64_t o : {p->d_cfg, p->d_grp, p->d_fld, p->d_acc, p->d_iv, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
                     p->d_scratch}) {
     if (o < 0) {
       p->release_all();
@@ -1051,6 +1118,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   cudaError_t e;
   if (n_cfg && (e = cudaMemcpyAsync(p->dev(p->d_cfg), hcfg.data(), hcfg.size() * sizeof(DCfg), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if (!hacc.empty() && (e = cudaMemcpyAsync(p->dev(p->d_acc), hacc.data(), hacc.size() * sizeof(DAcc), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
+  if (!hiv.empty() && (e = cudaMemcpyAsync(p->dev(p->d_iv), hiv.data(), hiv.size() * sizeof(DIv), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(p->dev(p->d_seg), seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if (!p->ext_scratch && (e = cudaMemsetAsync(p->dev(p->d_scratch), 0, scratch, st)) != cudaSuccess) return fail(e);
   if ((rc = p->upload_fields(st)) != WS_OK) {
@@ -1062,7 +1130,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->scratch_bytes = scratch;
   p->upload_bytes = (int64_t)(hcfg.size() * sizeof(DCfg) + p->hfld.size() * sizeof(DField) +
                               p->hgrp.size() * sizeof(DGroup) + hacc.size() * sizeof(DAcc) +
-                              seg.size() * sizeof(int32_t));
+                              hiv.size() * sizeof(DIv) + seg.size() * sizeof(int32_t));
   *out = p;
   return WS_OK;
 }

@@ -142,11 +142,46 @@ def test_mixed_set_full_size(ctx):
     assert_match(res, want, idx, "mixed")
 
 
-def test_edge_cases(ctx):
-    hw = W.a100()
+def random_uniform_tiny(rng: W.SplitMix64):
+    """Tiny candidate whose fields share element size and strides (one uniform field
+    group), with row lengths that do not divide a warp, x strides on both sides of the
+    32-byte interval limit, negative x or y strides and ragged folds."""
+    N = (rng.randint(1, 40), rng.randint(1, 12), rng.randint(1, 9))
+    B = rng.choice([(3, 2, 2), (5, 3, 1), (6, 1, 4), (12, 2, 1), (32, 1, 1), (40, 1, 1), (7, 4, 2), (64, 1, 1),
+                    (4, 4, 4), (1, 8, 2)])
+    axis, f = rng.choice([(0, 1), (1, 2), (1, 3), (2, 2), (2, 4), (1, 4)])
+    esize = rng.choice((1, 2, 4, 8, 16))
+    kind = rng.randint(0, 3)
+    px = N[0] + rng.randint(0, 5)
+    if kind == 0:
+        st = (1, px, px * N[1])
+    elif kind == 1:                          # x stride: 2 or 3 elements (AoS)
+        sx = rng.choice((2, 3))
+        st = (sx, sx * px, sx * px * N[1])
+    elif kind == 2:                          # descending x
+        st = (-1, px, px * N[1])
+    else:                                    # descending y
+        st = (1, -px, px * N[1] * 2)
+    fields = []
+    for _ in range(rng.randint(1, 4)):
+        accs = set()
+        r = rng.randint(0, 3)
+        for _ in range(rng.randint(1, 9)):
+            accs.add(W.Access(rng.randint(-r, r), rng.randint(-r, r), rng.randint(-r, r), 0, 0))
+        if rng.randint(0, 2):
+            accs.add(W.Access(0, 0, 0, 1, 0))
+            if rng.randint(0, 3) == 0:
+                accs.add(W.Access(-1, 1, 0, 1, 0))
+        fields.append(W.Field(esize, sorted(accs, key=lambda a: (a.dx, a.dy, a.dz, a.is_store, a.dc)),
+                              align=rng.randint(-70, 70), strides=st, const_off=rng.randint(-5, 5)))
+    return W.Config(N=N, B=B, fields=fields, fold_axis=axis, fold=f,
+                    wave_blocks_override=rng.choice((0, 1, 2, 3, 5)), flops_per_lup=3.0)
+
+
+def edge_configs():
     N = (70, 33, 19)
     st = W.dense_strides(N)
-    cfgs = [
+    return [
         W.Config(N=(5, 3, 2), B=(32, 4, 2), fields=W.copy_fields((5, 3, 2), W.star_offsets(1))),   # domain < block
         W.Config(N=N, B=(32, 4, 2), fields=W.copy_fields(N, W.box_offsets(2))),                   # ragged
         W.Config(N=N, B=(8, 4, 1), fields=W.copy_fields(N, W.star_offsets(3)), fold_axis=1, fold=16),
@@ -160,6 +195,11 @@ def test_edge_cases(ctx):
         W.Config(N=N, B=(64, 32, 1), fields=W.copy_fields(N, [(0, 0, 0)])),                         # invalid
         W.Config(N=N, B=(32, 1, 1), fields=[W.Field(8, [W.Access(0, 0, 0)], strides=(-1, -70, -70 * 33))]),
     ]
+
+
+def test_edge_cases(ctx):
+    hw = W.a100()
+    cfgs = edge_configs()
     want = oracle.estimate(cfgs, hw, threads=THREADS)
     res, order = B.ws_estimate_batch(ctx, cfgs, hw)
     assert res[8]["status"] == B.WS_EINVAL
@@ -169,6 +209,41 @@ def test_edge_cases(ctx):
     # empty batch
     r0, o0 = B.ws_estimate_batch(ctx, [], hw)
     assert len(r0) == 0
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_interval_walk_uniform_groups(ctx, seed):
+    """Uniform field groups take the interval walk: both walks against the oracle."""
+    rng = W.SplitMix64(300 + seed)
+    hw = W.Hardware(sms=3, max_blocks_sm=2)
+    cfgs = [random_uniform_tiny(rng) for _ in range(250)]
+    want = oracle.estimate(cfgs, hw, threads=THREADS)
+    ranks = list(oracle.rank([w["t_pred"] for w in want]))
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ADDRESS):
+        with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
+            p.execute(B.WS_MODE_BATCHED)
+            res, order = p.results()
+        assert_match(res, want, what=f"walk {walk}")
+        assert list(order) == ranks
+
+
+def test_interval_and_address_walks_identical(ctx):
+    """The interval walk and the per-address walk give bit-identical results on the
+    workload families and the edge cases."""
+    hw = W.a100()
+    rng = W.SplitMix64(77)
+    cfgs = (W.stencil_25pt_sweep(N=(160, 128, 96))[::9] + W.lbm_sweep(N=(96, 64, 48))[::37] +
+            W.mixed_set(2000)[::50] + edge_configs() + [random_tiny(rng) for _ in range(100)])
+    outs = []
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ADDRESS):
+        with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
+            p.execute(B.WS_MODE_BATCHED)
+            res, order = p.results()
+            outs.append((res.tobytes(), order.tobytes()))
+            p.execute(B.WS_MODE_PLAIN)
+            res2, order2 = p.results()
+            assert res2.tobytes() == res.tobytes() and order2.tobytes() == order.tobytes()
+    assert outs[0] == outs[1]
 
 
 def test_multi_pass_equals_single_pass(ctx):
