@@ -148,13 +148,16 @@ typedef struct ws_tuning {
   int32_t ctas_per_sm;     /* persistent CTAs per SM (0 = occupancy limit)               */
   int32_t pass_mb;         /* bitmap scratch per pass in MiB, e.g. sized to stay in L2 (0 or
                               < 0 = as large as the arena allows); never below one field   */
-  int32_t walk;            /* WS_WALK_INTERVAL (0): wave / layer-set loads and stores of a
-                              row segment are counted as sector intervals wherever that is
-                              exact (Sec. 3.4's closed-form counting); WS_WALK_ADDRESS (1):
-                              every address is evaluated.  Both give identical counts.     */
+  int32_t walk;            /* How the wave and the y / z layer sets are enumerated; all give
+                              identical counts.  WS_WALK_INTERVAL (0): closed-form interval
+                              counting (Sec. 3.4) wherever it is exact -- whole grid rows of
+                              a level as sector ranges, per-warp store sectors by floor sums,
+                              else row segments of each warp; WS_WALK_SEGMENT (2): intervals
+                              per row segment of each modelled warp only; WS_WALK_ADDRESS
+                              (1): every address evaluated.                                */
 } ws_tuning; /* 24 bytes */
 
-enum { WS_WALK_INTERVAL = 0, WS_WALK_ADDRESS = 1 };
+enum { WS_WALK_INTERVAL = 0, WS_WALK_ADDRESS = 1, WS_WALK_SEGMENT = 2 };
 
 /* Per-kernel device time of one profiled step (CUDA events on the launch stream). */
 typedef struct ws_profile {

@@ -67,7 +67,7 @@ assert (ACCESS.itemsize, FIELD.itemsize, CONFIG.itemsize, HW.itemsize, RESULT.it
 WS_OK, WS_EINVAL, WS_ENOMEM, WS_EAGAIN, WS_ETIMEDOUT, WS_EOVERFLOW, WS_ECUDA, WS_ENOTFOUND, WS_ECANCELED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 WS_MODE_PLAIN, WS_MODE_BATCHED, WS_MODE_DIRECT = 0, 1, 2
-WS_WALK_INTERVAL, WS_WALK_ADDRESS = 0, 1
+WS_WALK_INTERVAL, WS_WALK_ADDRESS, WS_WALK_SEGMENT = 0, 1, 2
 
 EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_create", "ws_destroy",
            "ws_plan_create", "ws_plan_execute", "ws_plan_results", "ws_plan_device_results", "ws_plan_profile",

@@ -51,13 +51,17 @@ struct ws_plan {
   std::vector<ws::DField> hfld;
   std::vector<ws::DGroup> hgrp;
   std::vector<char> grp_iv_ok;   // group allows the interval walk (used unless tune.walk asks otherwise)
+  std::vector<char> grp_rows_ok; // group allows the row walk of levels 1-3
+  std::vector<int64_t> grp_slots;        // row slots of the group's candidate
+  std::vector<int64_t> grp_winstr_rows;  // modelled (warp, instruction) pairs of levels 1-3
+  int32_t chunk_rows() const { return std::max(1, tune.chunk_warps / 16); }
   std::vector<int32_t> cfg_grp_begin;
   std::vector<int64_t> need_words;
   std::vector<int32_t> cfg_cf_begin;
   std::vector<ws::DPass> passes;
   int64_t scratch_words = 0;
   size_t scratch_bytes = 0;
-  int64_t item_begin_end = 0, citem_begin_end = 0;
+  int64_t item_begin_end = 0, ritem_begin_end = 0, citem_begin_end = 0;
   size_t grab_bytes = 0, counters_bytes = 0;
   int64_t upload_bytes = 0;
   int64_t d_grp = -1;
@@ -74,6 +78,7 @@ struct ws_plan {
   void layout();
   int upload_fields(cudaStream_t st);
   int grid_for(int threads, int64_t items, bool counting) const;
+  int grid_rows(int64_t items) const;
   int enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof);
   int run_plain(cudaStream_t st);
   int execute(int mode, cudaStream_t st);

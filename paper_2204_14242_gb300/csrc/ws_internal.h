@@ -51,6 +51,15 @@ struct DCfg {
   int64_t lev_end[4];      // all < 2^31 (checked by the descriptor compiler)
   double flops;
   FastDiv fd_gx, fd_gy, fd_wpb;
+  // Row walk of levels 1-3 (wave, y set, z set).  A block row R = by + g[1] * bz of a
+  // level holds one run of blocks that are consecutive in x; its threads with the same
+  // (ty, tz) form one grid row of consecutive x.  Slot = (block row, thread row); the
+  // z set has two slots per thread row (its run may be cut in two by the y set).
+  int32_t rows_R_lo[3], rows_R_cnt[3];
+  int64_t rows_slot_end[3];    // cumulative slots of the three levels (< 2^31)
+  int32_t rows_per_blk;        // B[1] * B[2]
+  int32_t full_end;            // blocks in x that lie entirely inside N[0]
+  FastDiv fd_rows, fd_b1;
 };
 
 struct DField {
@@ -73,7 +82,7 @@ struct DField {
   int32_t iv;             // interval walk possible: not wide and |elem_bytes * stride_x| <= 32
   int32_t iv_begin;       // first merged load interval (DIv array)
   int32_t n_iv;           // merged load intervals
-  int32_t pad_iv;
+  int32_t rows_ok;        // stores: the row segments of one warp never share a sector
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };
@@ -107,6 +116,7 @@ struct DHw {
 // are (group, chunk of modelled warps); item 0 of a group is the representative block.
 struct DGroup {
   int64_t item_begin;     // first enumeration work item
+  int64_t ritem_begin;    // first row-walk work item (row groups; empty range otherwise)
   int64_t mw_end;         // modelled warps visited (max over the group's fields)
   int64_t mw_block;       // modelled warps of the representative block
   int32_t cfg;            // owning candidate
@@ -119,12 +129,15 @@ struct DGroup {
   int32_t n_stores;       // folded stores of all its fields
   int32_t iv;             // uniform and every field allows the interval walk
   int32_t n_iv;           // merged load intervals of all its fields
+  int32_t rows;           // levels 1-3 take the row walk (work items are chunks of row slots)
+  int32_t pad;
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch
 // together.  Passes run one after the other and reuse the same scratch.
 struct DPass {
   int64_t item_lo, item_hi;    // enumeration items of the pass
+  int64_t ritem_lo, ritem_hi;  // row-walk items of the pass
   int64_t citem_lo, citem_hi;  // counting items of the pass
   int32_t cf_lo, cf_hi;        // (candidate, field) index range
   int32_t grp_lo, grp_hi;      // field-group index range

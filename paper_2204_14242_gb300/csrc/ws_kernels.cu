@@ -268,13 +268,15 @@ __device__ __forceinline__ uint32_t warp_distinct_sectors(uint32_t r, bool act) 
 
 // Last field group in [lo, hi) whose first work item is <= item; gallops forward from
 // the CTA's previous group (items are handed out in increasing order).
+template <bool ROWS = false>
 __device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, int hi, int64_t item, int hint) {
-  if (hint >= lo && hint < hi && grp[hint].item_begin <= item) {
+  auto begin = [&](int g) { return ROWS ? grp[g].ritem_begin : grp[g].item_begin; };
+  if (hint >= lo && hint < hi && begin(hint) <= item) {
     int step = 1, l = hint, r = hi;
     for (;;) {
       const int nx = l + step;
       if (nx >= hi) break;
-      if (grp[nx].item_begin > item) {
+      if (begin(nx) > item) {
         r = nx;
         break;
       }
@@ -286,7 +288,7 @@ __device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, 
   }
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (grp[mid].item_begin <= item) lo = mid;
+    if (begin(mid) <= item) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -310,6 +312,35 @@ __device__ __forceinline__ void set_sector_range(unsigned long long *__restrict_
   atomicOr(bm + u1, m1);
 }
 
+// Adds sectors [s0, s1] to a lane's pending 64-bit unit (cu, cb), flushing it with one
+// red.or when the range leaves that unit; units the range covers entirely are written
+// directly.  The caller flushes the last pending unit.
+__device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, uint32_t &cu, unsigned long long &cb,
+                                          uint32_t s0, uint32_t s1) {
+  const uint32_t u0 = s0 >> 6, u1 = s1 >> 6;
+  const unsigned long long m0 = ~0ull << (s0 & 63u);
+  const unsigned long long m1 = ~0ull >> (63u - (s1 & 63u));
+  if (u0 == u1) {
+    if (u0 == cu) {
+      cb |= m0 & m1;
+      return;
+    }
+    if (cb) atomicOr(bm + cu, cb);
+    cu = u0;
+    cb = m0 & m1;
+    return;
+  }
+  if (u0 == cu) {
+    atomicOr(bm + u0, cb | m0);
+  } else {
+    if (cb) atomicOr(bm + cu, cb);
+    atomicOr(bm + u0, m0);
+  }
+  for (uint32_t u = u0 + 1; u < u1; ++u) atomicOr(bm + u, ~0ull);
+  cu = u1;
+  cb = m1;
+}
+
 // Byte range [lo, hi] (relative to the bitmap origin) of one row segment of a
 // modelled warp under byte offset bo and extent ext.  Thread addresses are kept as
 // their low 32 bits; `mn` is the warp's smallest full thread address, and every valid
@@ -328,6 +359,182 @@ __device__ __forceinline__ bool segment_range(uint32_t th, uint32_t tt, int64_t 
   return true;
 }
 
+// Sum_{i=0}^{n-1} floor((a*i + b) / m) for n, a, b >= 0, m >= 1, by lattice-point
+// counting: with a, b < m and t = floor((a*(n-1) + b) / m) levels, the sum equals
+// t*n minus the number of (i, k) with k <= t and a*i + b < k*m, which is the same kind
+// of sum with the roles of a and m exchanged; the exchanges follow Euclid's algorithm.
+__device__ int64_t floor_sum(int64_t n, int64_t m, int64_t a, int64_t b) {
+  int64_t res = 0, sgn = 1;
+  while (n > 0) {
+    if (a >= m) {
+      res += sgn * (a / m) * (n * (n - 1) / 2);
+      a %= m;
+    }
+    if (b >= m) {
+      res += sgn * (b / m) * n;
+      b %= m;
+    }
+    if (a == 0) break;
+    const int64_t t = (a * (n - 1) + b) / m;
+    if (t == 0) break;
+    res += sgn * t * n;
+    const int64_t nb = m - b + a - 1;
+    n = t;
+    const int64_t om = m;
+    m = a;
+    a = om;
+    b = nb;
+    sgn = -sgn;
+  }
+  return res;
+}
+
+// Sum_{i<n} floor((P*i + c) / 32) where every term's argument is >= 0 (P of any sign).
+__device__ __forceinline__ int64_t sum_floor32(int64_t n, int64_t P, int64_t c) {
+  if (n <= 0) return 0;
+  if (P < 0) {
+    c += P * (n - 1);
+    P = -P;
+  }
+  return floor_sum(n, 32, P, c);
+}
+
+// Distinct sectors of one store instruction summed over the warps of a row walk's grid
+// row: the row's threads are split into warp segments (consecutive threads of one warp
+// within one block; a warp's other segments lie in other rows and share no sector with
+// this one), each counted as floor(last / 32) - floor(first / 32) + 1 bytes-to-sectors.
+// Segments repeat from block to block with the address step B0 * step, so each segment
+// position contributes two floor sums over the row's whole blocks; the block cut by N0
+// is counted directly.  A0 + step * x is the relative address of point x of the row.
+__device__ int64_t row_store_sectors(int64_t A0, int64_t step, int32_t B0, int32_t N0, int32_t full_end,
+                                     uint32_t t, uint32_t bxa, uint32_t bxb) {
+  auto direct = [&](int64_t x0, int64_t x1) -> int64_t {
+    const int64_t p = A0 + step * x0, q = A0 + step * x1;
+    return (max(p, q) >> 5) - (min(p, q) >> 5) + 1;
+  };
+  int64_t cnt = 0;
+  const int64_t xa = (int64_t)bxa * B0, xb = min((int64_t)bxb * B0, (int64_t)N0);
+  if ((B0 & 31) == 0) {
+    // warps tile the row in aligned runs of 32 threads
+    const int64_t nx = xb - xa, nq = nx >> 5;
+    if (nq > 0) {
+      const int64_t p0 = A0 + step * xa, p1 = A0 + step * (xa + 31);
+      cnt += sum_floor32(nq, 32 * step, max(p0, p1)) - sum_floor32(nq, 32 * step, min(p0, p1)) + nq;
+    }
+    if (nx & 31) cnt += direct(xa + (nq << 5), xb - 1);
+    return cnt;
+  }
+  const int32_t f1 = (int32_t)((32 - (((int64_t)t * B0) & 31)) & 31);
+  const uint32_t bfe = min(bxb, (uint32_t)full_end);
+  const int64_t nfull = bfe > bxa ? (int64_t)(bfe - bxa) : 0;
+  const int64_t P = (int64_t)B0 * step;
+  for (int32_t ta = 0; ta < B0;) {
+    const int32_t tb = (ta == 0 && f1 > 0) ? min(f1, B0) : min(ta + 32, B0);
+    if (nfull > 0) {
+      const int64_t p0 = A0 + step * (xa + ta), p1 = A0 + step * (xa + tb - 1);
+      cnt += sum_floor32(nfull, P, max(p0, p1)) - sum_floor32(nfull, P, min(p0, p1)) + nfull;
+    }
+    if (bxb > bfe) {
+      const int64_t xs = (int64_t)full_end * B0 + ta, xe = min((int64_t)full_end * B0 + tb, (int64_t)N0);
+      if (xe > xs) cnt += direct(xs, xe - 1);
+    }
+    ta = tb;
+  }
+  return cnt;
+}
+
+// Shared-memory images of one field group, staged by the enumeration and row kernels.
+struct StageSmem {
+  DCfg *c;
+  DGroup *g;
+  DField *fk;
+  int32_t *loff, *soff, *ioff;   // first load / store / merged interval of field k
+  uint8_t *af;                   // field of each staged access
+  int64_t *boff;                 // byte offset of each staged access
+  uint32_t *b32;                 // uniform groups: 32-bit offset from the shared thread address (may be null)
+  uint8_t *kmin;                 // first folded point that needs each access
+  int32_t (*gad)[17];            // issued accesses per thread by valid folded points, [0] levels 0-1, [1] 2-3
+  int32_t *gwi;                  // access instructions, [0] levels 0-1, [1] 2-3
+  int64_t *ibo;                  // merged load runs: offset relative to the field's bitmap origin
+  uint32_t *iext;                //   extent
+  uint8_t *iaf;                  //   field
+};
+
+// Stages group gi (and its candidate when it differs from cur_cfg); ends with a barrier.
+// Returns true when the candidate changed.
+__device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageSmem &m) {
+  if (threadIdx.x == 0) *m.g = a.grp[gi];
+  __syncthreads();
+  const DGroup &G = *m.g;
+  for (int k = threadIdx.x; k < G.f_count; k += blockDim.x) m.fk[k] = a.fld[G.f_begin + k];
+  const bool new_cfg = G.cfg != cur_cfg;
+  if (new_cfg && threadIdx.x == 0) *m.c = a.cfg[G.cfg];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // all loads of the group first (field by field), then all stores
+    int o = 0;
+    for (int k = 0; k < G.f_count; ++k) {
+      m.loff[k] = o;
+      o += m.fk[k].n_load;
+    }
+    m.loff[G.f_count] = o;
+    for (int k = 0; k < G.f_count; ++k) {
+      m.soff[k] = o;
+      o += m.fk[k].n_store;
+    }
+    m.soff[G.f_count] = o;
+    o = 0;
+    for (int k = 0; k < G.f_count; ++k) {
+      m.ioff[k] = o;
+      o += G.iv ? m.fk[k].n_iv : 0;
+    }
+    m.ioff[G.f_count] = o;
+  }
+  for (int t = threadIdx.x; t < 34; t += blockDim.x) {
+    // issued accesses per thread (by valid folded points) and access instructions,
+    // summed over the group's fields: [0] block and wave (loads and stores), [1] y / z
+    const int lv = t / 17, kv = t % 17;
+    int ad = 0, wi = 0;
+    for (int k = 0; k < G.f_count; ++k) {
+      ad += m.fk[k].cnt_load[kv] + (lv == 0 ? m.fk[k].cnt_store[kv] : 0);
+      wi += m.fk[k].n_load + (lv == 0 ? m.fk[k].n_store : 0);
+    }
+    m.gad[lv][kv] = ad;
+    if (kv == 0) m.gwi[lv] = wi;
+  }
+  __syncthreads();
+  // merged load runs, offsets relative to each field's bitmap origin
+  for (int j = threadIdx.x; j < m.ioff[G.f_count]; j += blockDim.x) {
+    int k = 0;
+    while (m.ioff[k + 1] <= j) ++k;
+    const DField &F = m.fk[k];
+    const DIv v = a.iv[F.iv_begin + (j - m.ioff[k])];
+    m.ibo[j] = v.boff + F.base - 32 * F.lo[1];
+    m.iext[j] = v.ext;
+    m.iaf[j] = (uint8_t)k;
+  }
+  // raw folded accesses; uniform groups fold each field's constant into the 32-bit
+  // offsets, so that address = shared thread address + offset for every field
+  for (int j = threadIdx.x; j < m.soff[G.f_count]; j += blockDim.x) {
+    const bool st = j >= m.loff[G.f_count];
+    int k = 0;
+    if (!st) {
+      while (m.loff[k + 1] <= j) ++k;
+    } else {
+      while (m.soff[k + 1] <= j) ++k;
+    }
+    const DField &F = m.fk[k];
+    const int i = st ? F.n_load + (j - m.soff[k]) : j - m.loff[k];
+    const DAcc d = a.acc[F.acc_begin + i];
+    m.boff[j] = d.boff;
+    if (m.b32) m.b32[j] = (uint32_t)d.boff + (G.uniform ? (uint32_t)(F.base - 32 * F.lo[1]) : 0u);
+    m.kmin[j] = (uint8_t)d.kmin;
+    m.af[j] = (uint8_t)k;
+  }
+  __syncthreads();
+  return new_cfg;
+}
+
 __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ DCfg s_c;
   __shared__ DGroup s_g;
@@ -343,6 +550,10 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   __shared__ uint8_t s_tkv[16][32];                    // per warp: valid folded points of each thread
   __shared__ uint32_t s_seg[16][32];                   // per warp: row segments (head lane, tail lane, kv)
   __shared__ int32_t s_ioff[kMaxGroupFields + 1];      // first merged interval of field k
+  __shared__ uint16_t s_lg[2][32];                     // interval walk lanes: entry | segment phase << 8
+  __shared__ uint32_t s_lgG[2];                        //   lanes per entry ([0] merged runs, [1] raw loads)
+  __shared__ int32_t s_gad[2][17];                     // group's issued accesses per thread with kv points
+  __shared__ int32_t s_gwi[2];                         // group's access instructions ([0] levels 0-1, [1] 2-3)
   __shared__ long long s_item;
   // merged load intervals of an interval-walk group (dynamic): offset, extent, field
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -350,6 +561,8 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
   uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
   uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
+  const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, s_b32, s_kmin, s_gad, s_gwi,
+                     s_ibo, s_iext, s_iaf};
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -363,63 +576,18 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     if (item >= a.item_hi) break;
     const int gi = find_grp(a.grp, a.grp_lo, a.grp_hi, item, cur_g);
     if (gi != cur_g) {
-      // stage the group: its fields, their folded accesses, the candidate's thread table
-      if (threadIdx.x == 0) s_g = a.grp[gi];
-      __syncthreads();
-      for (int k = threadIdx.x; k < s_g.f_count; k += blockDim.x) s_fk[k] = a.fld[s_g.f_begin + k];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // all loads of the group first (field by field), then all stores
-        int o = 0;
-        for (int k = 0; k < s_g.f_count; ++k) {
-          s_loff[k] = o;
-          o += s_fk[k].n_load;
-        }
-        s_loff[s_g.f_count] = o;
-        for (int k = 0; k < s_g.f_count; ++k) {
-          s_soff[k] = o;
-          o += s_fk[k].n_store;
-        }
-        s_soff[s_g.f_count] = o;
-        o = 0;
-        for (int k = 0; k < s_g.f_count; ++k) {
-          s_ioff[k] = o;
-          o += s_g.iv ? s_fk[k].n_iv : 0;
-        }
-        s_ioff[s_g.f_count] = o;
+      // stage the group, then the interval walk's lane layout and the thread table
+      const bool new_cfg = stage_group(a, gi, cur_cfg, sm);
+      // with M < 32 entries, G = 32 / M lanes share an entry and take every G-th row segment
+      if (threadIdx.x < 64) {
+        const int pi = threadIdx.x >> 5, l = threadIdx.x & 31;
+        const int M = pi == 0 ? s_ioff[s_g.f_count] : s_loff[s_g.f_count];
+        const int G = (M > 0 && M < 32) ? 32 / M : 1;
+        const int e = G > 1 ? l % M : l, g = G > 1 ? l / M : 0;
+        s_lg[pi][l] = (uint16_t)(e | (g << 8));
+        if (l == 0) s_lgG[pi] = (uint32_t)G;
       }
-      __syncthreads();
-      // merged load intervals, offsets relative to each field's bitmap origin
-      for (int j = threadIdx.x; j < s_ioff[s_g.f_count]; j += blockDim.x) {
-        int k = 0;
-        while (s_ioff[k + 1] <= j) ++k;
-        const DField &F = s_fk[k];
-        const DIv v = a.iv[F.iv_begin + (j - s_ioff[k])];
-        s_ibo[j] = v.boff + F.base - 32 * F.lo[1];
-        s_iext[j] = v.ext;
-        s_iaf[j] = (uint8_t)k;
-      }
-      // uniform groups fold each field's constant into its 32-bit offsets, so that
-      // address = shared thread address + offset for every field
-      for (int j = threadIdx.x; j < s_soff[s_g.f_count]; j += blockDim.x) {
-        const bool st = j >= s_loff[s_g.f_count];
-        int k = 0;
-        if (!st) {
-          while (s_loff[k + 1] <= j) ++k;
-        } else {
-          while (s_soff[k + 1] <= j) ++k;
-        }
-        const DField &F = s_fk[k];
-        const int i = st ? F.n_load + (j - s_soff[k]) : j - s_loff[k];
-        const DAcc d = a.acc[F.acc_begin + i];
-        s_boff[j] = d.boff;
-        s_b32[j] = (uint32_t)d.boff + (s_g.uniform ? (uint32_t)(F.base - 32 * F.lo[1]) : 0u);
-        s_kmin[j] = (uint8_t)d.kmin;
-        s_af[j] = (uint8_t)k;
-      }
-      if (s_g.cfg != cur_cfg) {
-        if (threadIdx.x == 0) s_c = a.cfg[s_g.cfg];
-        __syncthreads();
+      if (new_cfg) {
         for (int t = threadIdx.x; t < s_c.T; t += blockDim.x) {
           const uint32_t tx = t % s_c.B[0], ty = (t / s_c.B[0]) % s_c.B[1], tz = t / (s_c.B[0] * s_c.B[1]);
           s_tc[t] = tx | (ty << 10) | (tz << 20);
@@ -436,7 +604,6 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
                                  : (uint32_t)min(s_g.mw_block + kk * (int64_t)a.chunk, s_g.mw_end);
     uint32_t acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0, acc_addr = 0, acc_wi = 0;
     uint32_t bad = 0;
-
     for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
       // ---- decode the modelled warp once for every field of the group
       uint32_t level, b, j;
@@ -482,9 +649,157 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       const bool partial = __any_sync(FULL, valid && kv < fold);
       uint32_t naddr = 0;
 
-      // ---- uniform groups, wave / y / z levels: one walk over all the group's accesses
       bool fields_done = false;
-      if (level >= 1 && s_g.uniform && (s_g.iv || !partial)) {
+      if (level >= 1 && s_g.iv) {
+        // ---- interval walk (exact closed-form counting, Sec. 3.4): the warp's valid
+        // threads form row segments of consecutive x, and a (segment, merged load run)
+        // pair covers one contiguous sector range.  Partial warps (a thread with fewer
+        // valid folded points than the fold) take the raw folded loads instead, each
+        // checked against the segment's valid points.
+        const DField &F0 = s_fk[0];
+        const int64_t el = (int64_t)F0.esize * (F0.stride[0] * x + F0.stride[1] * y + F0.stride[2] * z);
+        const uint32_t tme = (uint32_t)el;
+        s_tbase[warp][lane] = tme;
+        const int L = s_loff[s_g.f_count];
+        const int S = level == 1 ? s_soff[s_g.f_count] - L : 0;
+        if (vmask) {
+          // the warp's address range: offsets from its first valid thread fit 32 bits
+          // (every bitmap of an interval group spans less than 2^31 bytes); anything
+          // else is a descriptor error and the warp is skipped
+          const int64_t e0 = (int64_t)__shfl_sync(FULL, (long long)el, __ffs(vmask) - 1);
+          const int64_t dd = el - e0;
+          const bool fits = !valid || (dd >= -(int64_t)0x7fffffff && dd <= (int64_t)0x7fffffff);
+          if (__all_sync(FULL, fits)) {
+            const int32_t d = (int32_t)dd;
+            const int64_t mn = e0 + __reduce_min_sync(FULL, valid ? d : 0x7fffffff);
+            const int64_t mx = e0 + __reduce_max_sync(FULL, valid ? d : -0x7fffffff);
+            const uint32_t tx = tc & 1023u;
+            const uint32_t heads = __ballot_sync(FULL, valid && (lane == 0u || tx == 0u));
+            const uint32_t ends = vmask & ~((vmask & ~heads) >> 1);
+            const uint32_t nseg = __popc(heads);
+            if ((heads >> lane) & 1u) {
+              const uint32_t t = __ffs(ends & (0xffffffffu << lane)) - 1u;
+              s_seg[warp][__popc(heads & ((1u << lane) - 1u))] = lane | (t << 8) | ((uint32_t)kv << 16);
+            }
+            __syncwarp();
+            // loads: a lane takes one entry and every G-th segment (G lanes share an
+            // entry when there are fewer than 32)
+            const int pi = partial ? 1 : 0;
+            const int M = partial ? L : s_ioff[s_g.f_count];
+            const uint32_t G = s_lgG[pi], lg = s_lg[pi][lane];
+            const uint32_t e_l = lg & 255u, g_l = lg >> 8;
+            const int bsel = level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z;
+            for (int r0 = 0; r0 < M; r0 += 32) {
+              const int e = r0 + (int)e_l;
+              if (e >= M || g_l >= G) continue;
+              int k;
+              int64_t bo;
+              uint32_t ext;
+              if (!partial) {
+                k = s_iaf[e];
+                bo = s_ibo[e];
+                ext = s_iext[e];
+              } else {
+                k = s_af[e];
+                bo = s_boff[e] + s_fk[k].base - 32 * s_fk[k].lo[1];
+                ext = 0u;
+              }
+              const DField &F = s_fk[k];
+              const uint32_t limit = (uint32_t)(F.words[1] << 10);
+              unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[bsel]);
+              uint32_t cu = 0xffffffffu;
+              unsigned long long cb = 0ull;
+              if (!partial) {
+                // every segment issues the entry: one exact range check for the warp
+                if (mn + bo < 0 || mx + bo + (int64_t)ext >= (int64_t)limit) {
+                  ++bad;
+                  continue;
+                }
+                const uint32_t b32 = (uint32_t)bo;
+                for (uint32_t si = g_l; si < nseg; si += G) {
+                  const uint32_t sg = s_seg[warp][si];
+                  const uint32_t ra = s_tbase[warp][sg & 255u] + b32, rb = s_tbase[warp][(sg >> 8) & 255u] + b32;
+                  put_range(bm, cu, cb, min(ra, rb) >> 5, (max(ra, rb) + ext) >> 5);
+                }
+              } else {
+                const uint32_t kmin = s_kmin[e];
+                for (uint32_t si = g_l; si < nseg; si += G) {
+                  const uint32_t sg = s_seg[warp][si];
+                  if (kmin >= (sg >> 16)) continue;
+                  uint32_t lo, hi;
+                  if (!segment_range(s_tbase[warp][sg & 255u], s_tbase[warp][(sg >> 8) & 255u], mn, bo, 0u, limit,
+                                     lo, hi)) {
+                    ++bad;
+                    continue;
+                  }
+                  put_range(bm, cu, cb, lo >> 5, hi >> 5);
+                }
+              }
+              if (cb) atomicOr(bm + cu, cb);
+            }
+            if (!partial) {
+              // stores: lane per store instruction over all segments, counting the
+              // instruction's distinct sectors (exact for non-decreasing segments)
+              for (int a0 = 0; a0 < S; a0 += 32) {
+                const int j = L + a0 + (int)lane;
+                uint32_t nsec = 0u, plo = 0u, phi = 0u;
+                bool mono = true, ok = false;
+                if (j < L + S) {
+                  const DField &F = s_fk[s_af[j]];
+                  const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+                  const uint32_t limit = (uint32_t)(F.words[1] << 10);
+                  unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[BM_WS]);
+                  if (mn + bo < 0 || mx + bo >= (int64_t)limit) {
+                    ++bad;
+                  } else {
+                    ok = true;
+                    const uint32_t b32 = (uint32_t)bo;
+                    uint32_t cu = 0xffffffffu;
+                    unsigned long long cb = 0ull;
+                    for (uint32_t si = 0; si < nseg; ++si) {
+                      const uint32_t sg = s_seg[warp][si];
+                      const uint32_t ra = s_tbase[warp][sg & 255u] + b32, rb = s_tbase[warp][(sg >> 8) & 255u] + b32;
+                      const uint32_t s0 = min(ra, rb) >> 5, s1 = max(ra, rb) >> 5;
+                      put_range(bm, cu, cb, s0, s1);
+                      if (si == 0u) {
+                        nsec = s1 - s0 + 1u;
+                      } else {
+                        mono = mono && s0 >= plo && s1 >= phi;
+                        const uint32_t from = max(phi + 1u, s0);
+                        nsec += s1 >= from ? s1 - from + 1u : 0u;
+                      }
+                      plo = s0;
+                      phi = s1;
+                    }
+                    if (cb) atomicOr(bm + cu, cb);
+                  }
+                }
+                acc_sreq += __reduce_add_sync(FULL, (ok && mono) ? nsec : 0u);
+                uint32_t redo = __ballot_sync(FULL, ok && !mono);
+                while (redo) {
+                  const int src = __ffs(redo) - 1;
+                  redo &= redo - 1;
+                  acc_sreq += warp_distinct_sectors(tme + s_b32[L + a0 + src], valid);
+                }
+              }
+            } else {
+              for (int j = L; j < L + S; ++j) {
+                const DField &F = s_fk[s_af[j]];
+                const uint32_t limit = (uint32_t)(F.words[1] << 10);
+                const bool act = valid && (int)s_kmin[j] < kv;
+                acc_sreq += runs_insert(a.scratch + F.bm[BM_WS], tme + s_b32[j], act, limit, lane, bad, true);
+              }
+            }
+          } else if (lane == 0u) {
+            ++bad;
+          }
+        }
+        __syncwarp();
+        fields_done = true;
+        naddr += (uint32_t)s_gad[level <= 1 ? 0 : 1][kv];
+        acc_wi += (uint32_t)s_gwi[level <= 1 ? 0 : 1];
+      } else if (level >= 1 && s_g.uniform && !partial) {
+        // ---- uniform groups, wave / y / z levels: one walk over all the group's accesses
         const DField &F0 = s_fk[0];
         const int64_t el = (int64_t)F0.esize * (F0.stride[0] * x + F0.stride[1] * y + F0.stride[2] * z);
         s_tbase[warp][lane] = (uint32_t)el;
@@ -498,101 +813,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         const int L = s_loff[s_g.f_count];
         const int S = level == 1 ? s_soff[s_g.f_count] - L : 0;
         const uint32_t tme = s_tbase[warp][lane];
-        if (s_g.iv) {
-          // ---- interval walk (Sec. 3.4's closed-form counting, exact): the warp's
-          // valid threads form row segments of consecutive x; one (segment, merged load
-          // interval) pair is one sector range.  Partial warps take the raw folded
-          // loads, each checked against the segment's valid folded points.
-          const uint32_t tx = tc & 1023u;
-          const uint32_t heads = __ballot_sync(FULL, valid && (lane == 0u || tx == 0u));
-          const uint32_t ends = vmask & ~((vmask & ~heads) >> 1);
-          const uint32_t nseg = __popc(heads);
-          if ((heads >> lane) & 1u) {
-            const uint32_t t = __ffs(ends & (0xffffffffu << lane)) - 1u;
-            s_seg[warp][__popc(heads & ((1u << lane) - 1u))] = lane | (t << 8) | ((uint32_t)kv << 16);
-          }
-          __syncwarp();
-          const int M = partial ? L : s_ioff[s_g.f_count];
-          const uint32_t total = nseg * (uint32_t)M;
-          const uint32_t magic = nseg > 1u ? 0xffffffffu / nseg + 1u : 0u;
-          const int bsel = level == 1 ? BM_W : level == 2 ? BM_Y : BM_Z;
-          for (uint32_t p = lane; p < total; p += 32u) {
-            const uint32_t e = nseg > 1u ? __umulhi(p, magic) : p;
-            const uint32_t sg = s_seg[warp][p - e * nseg];
-            int k;
-            int64_t bo;
-            uint32_t ext;
-            if (!partial) {
-              k = s_iaf[e];
-              bo = s_ibo[e];
-              ext = s_iext[e];
-            } else {
-              if ((uint32_t)s_kmin[e] >= (sg >> 16)) continue;
-              k = s_af[e];
-              bo = s_boff[e] + s_fk[k].base - 32 * s_fk[k].lo[1];
-              ext = 0u;
-            }
-            const DField &F = s_fk[k];
-            uint32_t lo, hi;
-            if (!segment_range(s_tbase[warp][sg & 255u], s_tbase[warp][(sg >> 8) & 255u], mn, bo, ext,
-                               (uint32_t)(F.words[1] << 10), lo, hi)) {
-              ++bad;
-              continue;
-            }
-            set_sector_range(reinterpret_cast<unsigned long long *>(a.scratch + F.bm[bsel]), lo >> 5, hi >> 5);
-          }
-          if (!partial) {
-            // stores: lane per store instruction over the segments, counting the
-            // instruction's distinct sectors (exact for non-decreasing segments)
-            for (int a0 = 0; a0 < S; a0 += 32) {
-              const int j = L + a0 + (int)lane;
-              uint32_t nsec = 0u, plo = 0u, phi = 0u;
-              bool mono = true, ok = false;
-              if (j < L + S) {
-                const DField &F = s_fk[s_af[j]];
-                const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
-                const uint32_t limit = (uint32_t)(F.words[1] << 10);
-                unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[BM_WS]);
-                ok = true;
-                for (uint32_t si = 0; si < nseg; ++si) {
-                  const uint32_t sg = s_seg[warp][si];
-                  uint32_t lo, hi;
-                  if (!segment_range(s_tbase[warp][sg & 255u], s_tbase[warp][(sg >> 8) & 255u], mn, bo, 0u, limit,
-                                     lo, hi)) {
-                    ++bad;
-                    ok = false;
-                    continue;
-                  }
-                  const uint32_t s0 = lo >> 5, s1 = hi >> 5;
-                  set_sector_range(bm, s0, s1);
-                  if (si == 0u) {
-                    nsec = s1 - s0 + 1u;
-                  } else {
-                    mono = mono && s0 >= plo && s1 >= phi;
-                    const uint32_t from = max(phi + 1u, s0);
-                    nsec += s1 >= from ? s1 - from + 1u : 0u;
-                  }
-                  plo = s0;
-                  phi = s1;
-                }
-              }
-              acc_sreq += __reduce_add_sync(FULL, (ok && mono) ? nsec : 0u);
-              uint32_t redo = __ballot_sync(FULL, ok && !mono);
-              while (redo) {
-                const int src = __ffs(redo) - 1;
-                redo &= redo - 1;
-                acc_sreq += warp_distinct_sectors(tme + s_b32[L + a0 + src], valid);
-              }
-            }
-          } else {
-            for (int j = L; j < L + S; ++j) {
-              const DField &F = s_fk[s_af[j]];
-              const uint32_t limit = (uint32_t)(F.words[1] << 10);
-              const bool act = valid && (int)s_kmin[j] < kv;
-              acc_sreq += runs_insert(a.scratch + F.bm[BM_WS], tme + s_b32[j], act, limit, lane, bad, true);
-            }
-          }
-        } else if (L >= kCombinedWalkMin) {
+        if (L >= kCombinedWalkMin) {
           // lane per access over all 32 threads of the modelled warp
           for (int a0 = 0; a0 < L && vmask; a0 += 32) {
             const int j = a0 + (int)lane;
@@ -617,9 +838,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
             runs_insert(bm, tme + s_b32[j], valid, limit, lane, bad, false);
           }
         }
-        if (s_g.iv) {
-          // stores were walked with the intervals above
-        } else if (S >= kCombinedWalkMin) {
+        if (S >= kCombinedWalkMin) {
           for (int a0 = 0; a0 < S && vmask; a0 += 32) {
             const int j = L + a0 + (int)lane;
             uint32_t cw = 0xffffffffu, cb = 0u, nsec = 0u;
@@ -657,13 +876,8 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         }
         __syncwarp();
         fields_done = true;
-        for (int k = 0; k < s_g.f_count; ++k) {
-          const DField &F = s_fk[k];
-          const int nst = level <= 1 ? F.n_store : 0;
-          if (F.n_load + nst == 0) continue;
-          naddr += (uint32_t)(F.cnt_load[kv] + (level <= 1 ? F.cnt_store[kv] : 0));
-          acc_wi += (uint32_t)(F.n_load + nst);
-        }
+        naddr += (uint32_t)s_gad[level <= 1 ? 0 : 1][kv];
+        acc_wi += (uint32_t)s_gwi[level <= 1 ? 0 : 1];
       }
 
       // ---- every field of the group
@@ -818,6 +1032,177 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       if (acc_addr) atomicAdd(c + C_ADDR, (u64)acc_addr);
       if (acc_wi) atomicAdd(c + C_WINSTR, (u64)acc_wi);
     }
+    __syncthreads();
+  }
+}
+
+
+// Row walk of the wave and the y / z layer sets (exact closed-form interval counting,
+// Sec. 3.4).  The blocks of a level that share a block row are consecutive in x, so
+// the threads of those blocks with one (ty, tz) form one grid row of consecutive x.
+// Work item = (field group, chunk of row slots); one grid row per warp.  Each merged
+// load run (raw loads when the row has fewer valid folded points than the fold) is one
+// sector range of the row; wave stores also add their per-warp sector counts in closed
+// form (row_store_sectors).
+__global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
+  __shared__ DCfg s_c;
+  __shared__ DGroup s_g;
+  __shared__ DField s_fk[kMaxGroupFields];
+  __shared__ int32_t s_loff[kMaxGroupFields + 1];
+  __shared__ int32_t s_soff[kMaxGroupFields + 1];
+  __shared__ int32_t s_ioff[kMaxGroupFields + 1];
+  __shared__ uint8_t s_af[kMaxFoldedAccesses];
+  __shared__ int64_t s_boff[kMaxFoldedAccesses];
+  __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
+  __shared__ int32_t s_gad[2][17];
+  __shared__ int32_t s_gwi[2];
+  __shared__ long long s_item;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  const int iv_cap16 = (a.iv_cap + 15) & ~15;
+  int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
+  uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
+  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
+  const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, nullptr, s_kmin, s_gad, s_gwi,
+                     s_ibo, s_iext, s_iaf};
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t nwarps = blockDim.x >> 5;
+  int cur_g = -1, cur_cfg = -1;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = a.ritem_lo + (long long)atomicAdd(a.rgrab, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= a.ritem_hi) break;
+    const int gi = find_grp<true>(a.grp, a.grp_lo, a.grp_hi, item, cur_g);
+    if (gi != cur_g) {
+      stage_group(a, gi, cur_cfg, sm);
+      cur_g = gi;
+      cur_cfg = s_g.cfg;
+    }
+    const int64_t kk = item - s_g.ritem_begin;
+    uint32_t bad = 0;
+    {
+      // ---- row walk of levels 1-3: one grid row (block run x thread row) per warp; each
+      // merged load run (raw loads when the row has fewer valid folded points than the
+      // fold) is one sector range of the row, stores also add their per-warp sector
+      // counts in closed form
+      const int64_t q0 = kk * (int64_t)a.chunk_rows;
+      const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[2]);
+      const int L = s_loff[s_g.f_count];
+      const int S = s_soff[s_g.f_count] - L;
+      const int Mfull = s_ioff[s_g.f_count];
+      const DField &F0 = s_fk[0];
+      const int64_t es = F0.esize, sxe = es * F0.stride[0];
+      for (int64_t slot = q0 + warp; slot < q1; slot += nwarps) {
+        int lv;
+        int64_t loc;
+        if (slot < s_c.rows_slot_end[0]) {
+          lv = 0; loc = slot;
+        } else if (slot < s_c.rows_slot_end[1]) {
+          lv = 1; loc = slot - s_c.rows_slot_end[0];
+        } else {
+          lv = 2; loc = slot - s_c.rows_slot_end[1];
+        }
+        const uint32_t pq = fdiv((uint32_t)loc, s_c.fd_rows);
+        const uint32_t t = (uint32_t)loc - pq * (uint32_t)s_c.rows_per_blk;
+        const uint32_t R = (uint32_t)s_c.rows_R_lo[lv] + (lv == 2 ? (pq >> 1) : pq);
+        const uint32_t piece = lv == 2 ? (pq & 1u) : 0u;
+        const uint32_t gx = (uint32_t)s_c.g[0], gy = (uint32_t)s_c.g[1];
+        const uint32_t bz = fdiv(R, s_c.fd_gy), by = R - bz * gy;
+        const int64_t rb0 = (int64_t)R * gx, rb1 = rb0 + gx;
+        int64_t ba, bb;
+        if (lv == 0) {
+          ba = max(s_c.s, rb0);
+          bb = min(s_c.s + s_c.weff, rb1);
+        } else if (lv == 1) {
+          if (by == gy - 1) continue;
+          ba = max(s_c.y_lo, rb0);
+          bb = min(s_c.y_hi, rb1);
+        } else {
+          ba = max(s_c.z_lo, rb0);
+          bb = min(s_c.z_hi, rb1);
+          if (by != gy - 1 && s_c.y_hi > s_c.y_lo) {
+            if (piece == 0u) bb = min(bb, s_c.y_lo);
+            else ba = max(ba, s_c.y_hi);
+          } else if (piece) {
+            continue;
+          }
+        }
+        if (ba >= bb) continue;
+        const uint32_t bxa = (uint32_t)(ba - rb0), bxb = (uint32_t)(bb - rb0);
+        const uint32_t tz = fdiv(t, s_c.fd_b1), ty = t - tz * (uint32_t)s_c.B[1];
+        int32_t y = (int32_t)(by * (uint32_t)s_c.B[1] + ty), z = (int32_t)(bz * (uint32_t)s_c.B[2] + tz);
+        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
+        if (faxis == 1) y *= fold;
+        if (faxis == 2) z *= fold;
+        if (y >= s_c.N[1] || z >= s_c.N[2]) continue;
+        const int32_t xa = (int32_t)bxa * s_c.B[0], xb = min((int32_t)bxb * s_c.B[0], s_c.N[0]);
+        const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+        const int64_t nx = xb - xa;
+        unsigned long long *const ctr = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
+        if (lane == 0u) {
+          if (lv == 0 && s_g.first_of_cfg) atomicAdd(ctr + C_LUPS_WAVE, (unsigned long long)(nx * kv));
+          atomicAdd(ctr + C_ADDR, (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]));
+        }
+        const int64_t el0 = es * (F0.stride[1] * y + F0.stride[2] * z);
+        const int64_t ea = el0 + sxe * xa, eb = el0 + sxe * (xb - 1);
+        const int64_t lo = min(ea, eb), hi = max(ea, eb);
+        const bool fullk = kv == fold;
+        const int M = fullk ? Mfull : L;
+        const int bsel = lv == 0 ? BM_W : lv == 1 ? BM_Y : BM_Z;
+        for (int e = (int)lane; e < M; e += 32) {
+          int k;
+          int64_t bo;
+          uint32_t ext;
+          if (fullk) {
+            k = s_iaf[e];
+            bo = s_ibo[e];
+            ext = s_iext[e];
+          } else {
+            if ((int)s_kmin[e] >= kv) continue;
+            k = s_af[e];
+            bo = s_boff[e] + s_fk[k].base - 32 * s_fk[k].lo[1];
+            ext = 0u;
+          }
+          const DField &F = s_fk[k];
+          const int64_t a0 = lo + bo, a1 = hi + bo + (int64_t)ext;
+          if (a0 < 0 || a1 >= (F.words[1] << 10)) {
+            ++bad;
+            continue;
+          }
+          unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[bsel]);
+          uint32_t cu = 0xffffffffu;
+          unsigned long long cb = 0ull;
+          put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+          if (cb) atomicOr(bm + cu, cb);
+        }
+        if (lv == 0) {
+          for (int j = L + (int)lane; j < L + S; j += 32) {
+            if ((int)s_kmin[j] >= kv) continue;
+            const DField &F = s_fk[s_af[j]];
+            const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+            const int64_t a0 = lo + bo, a1 = hi + bo;
+            if (a0 < 0 || a1 >= (F.words[1] << 10)) {
+              ++bad;
+              continue;
+            }
+            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[BM_WS]);
+            uint32_t cu = 0xffffffffu;
+            unsigned long long cb = 0ull;
+            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+            if (cb) atomicOr(bm + cu, cb);
+            atomicAdd(ctr + C_W_SREQ,
+                      (unsigned long long)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb));
+          }
+        }
+      }
+    }
+
+    bad = __reduce_add_sync(FULL, bad);
+    if (lane == 0 && bad)
+      atomicAdd((unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS + C_OVERFLOW), (unsigned long long)bad);
     __syncthreads();
   }
 }
@@ -1104,7 +1489,8 @@ __global__ void keys_kernel(const ws_result *__restrict__ res, int n, double *__
 // ---- launchers ---------------------------------------------------------------------
 size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 1); }
 
-// Raises the kernel's dynamic shared-memory limit (once per device and size).
+// Raises the dynamic shared-memory limit of the enumeration and row kernels (once per
+// device and size).
 static cudaError_t enum_allow_smem(size_t dyn) {
   static std::mutex mu;
   static size_t allowed[64] = {};
@@ -1115,6 +1501,7 @@ static cudaError_t enum_allow_smem(size_t dyn) {
   std::lock_guard<std::mutex> g(mu);
   if (dyn <= allowed[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e == cudaSuccess) allowed[dev] = dyn;
   return e;
 }
@@ -1124,6 +1511,13 @@ cudaError_t launch_enum(const EnumArgs &args, int grid, int threads, cudaStream_
   cudaError_t e = enum_allow_smem(dyn);
   if (e != cudaSuccess) return e;
   enum_kernel<<<grid, threads, dyn, st>>>(args);
+  return cudaGetLastError();
+}
+cudaError_t launch_rows(const EnumArgs &args, int grid, cudaStream_t st) {
+  const size_t dyn = enum_dyn_smem(args.iv_cap);
+  cudaError_t e = enum_allow_smem(dyn);
+  if (e != cudaSuccess) return e;
+  rows_kernel<<<grid, kRowsThreads, dyn, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
@@ -1150,6 +1544,12 @@ cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm) {
   cudaError_t e = enum_allow_smem(dyn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, enum_kernel, threads, dyn);
+}
+cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm) {
+  const size_t dyn = enum_dyn_smem(iv_cap);
+  cudaError_t e = enum_allow_smem(dyn);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rows_kernel, kRowsThreads, dyn);
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, 512, 0);

@@ -16,9 +16,12 @@ struct EnumArgs {
   uint32_t *scratch;               // bitmaps of the pass
   int64_t *counters;               // [n_cfg][N_COUNTERS]
   unsigned long long *grab;        // work-stealing counter (zeroed before the launch)
+  unsigned long long *rgrab;       //   of the row kernel
   int64_t item_lo, item_hi;        // enumeration items of the pass
+  int64_t ritem_lo, ritem_hi;      // row-walk items of the pass
   int32_t grp_lo, grp_hi;          // field-group range of the pass
   int32_t chunk;                   // modelled warps per item
+  int32_t chunk_rows;              // row slots per item (row walk)
   int32_t banks, bank_bytes, pair_dist;
 };
 
@@ -49,12 +52,15 @@ struct RankArgs {
 };
 
 cudaError_t launch_enum(const EnumArgs &args, int grid, int threads, cudaStream_t st);
+cudaError_t launch_rows(const EnumArgs &args, int grid, cudaStream_t st);
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st);
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st);
 cudaError_t launch_rank(const RankArgs &args, cudaStream_t st);
 cudaError_t launch_keys(const ws_result *res, int n, double *keys, cudaStream_t st);
 cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm);
 size_t enum_dyn_smem(int iv_cap);
+cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm);
+constexpr int kRowsThreads = 256;
 cudaError_t count_occupancy(int *blocks_per_sm);
 
 }  // namespace ws

@@ -136,6 +136,8 @@ static FastDiv make_fastdiv(uint32_t d) {
 
 struct Compiled {
   DCfg d{};
+  int64_t lvl_blocks[3] = {0, 0, 0};  // blocks of the wave, y set and z set
+  bool rows_geom_ok = false;          // row slots fit the kernel's 32-bit decode
   std::vector<DField> f;
   std::vector<std::vector<DAcc>> acc;
   std::vector<std::vector<DIv>> iv;
@@ -341,6 +343,40 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   if (d.lev_end[3] >= ((int64_t)1 << 31)) return WS_EINVAL;
   d.fd_gx = make_fastdiv((uint32_t)g[0]);
   d.fd_gy = make_fastdiv((uint32_t)g[1]);
+  // row walk geometry: block rows of each level, slots, and the blocks per level left
+  // after the y / z set rules (for the modelled-warp statistics)
+  {
+    d.rows_per_blk = (int32_t)(c.B[1] * c.B[2]);
+    d.full_end = (int32_t)(c.N[0] / c.B[0]);
+    d.fd_rows = make_fastdiv((uint32_t)d.rows_per_blk);
+    d.fd_b1 = make_fastdiv((uint32_t)c.B[1]);
+    const int64_t rng[3][2] = {{s, s + weff}, {y_lo, y_hi}, {z_lo, z_hi}};
+    int64_t cum = 0;
+    for (int lv = 0; lv < 3; ++lv) {
+      d.rows_R_lo[lv] = 0;
+      d.rows_R_cnt[lv] = 0;
+      out.lvl_blocks[lv] = 0;
+      if (rng[lv][1] > rng[lv][0]) {
+        const int64_t R0 = rng[lv][0] / g[0], R1 = (rng[lv][1] - 1) / g[0];
+        d.rows_R_lo[lv] = (int32_t)R0;
+        d.rows_R_cnt[lv] = (int32_t)(R1 - R0 + 1);
+        for (int64_t R = R0; R <= R1; ++R) {
+          const int64_t a = std::max(rng[lv][0], R * g[0]), b = std::min(rng[lv][1], (R + 1) * g[0]);
+          const int64_t by = R % g[1];
+          if (lv == 0) out.lvl_blocks[lv] += b - a;
+          if (lv == 1 && by != g[1] - 1) out.lvl_blocks[lv] += b - a;
+          if (lv == 2) {
+            int64_t n = b - a;
+            if (by != g[1] - 1 && y_hi > y_lo) n -= std::max<int64_t>(0, std::min(b, y_hi) - std::max(a, y_lo));
+            out.lvl_blocks[lv] += n;
+          }
+        }
+      }
+      cum += (int64_t)d.rows_R_cnt[lv] * (lv == 2 ? 2 : 1) * d.rows_per_blk;
+      d.rows_slot_end[lv] = cum;
+    }
+    out.rows_geom_ok = cum < ((int64_t)1 << 31);
+  }
   d.fd_wpb = make_fastdiv((uint32_t)wpb);
 
   // point boxes (valid points only) of the block level and of wave + y + z
@@ -428,11 +464,33 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.lpa_log2p = 0;
     while ((1 << df.lpa_log2p) < std::min(df.n_load, 32)) ++df.lpa_log2p;
     // row segments of threads step by elem_bytes * stride_x bytes: at most one sector
-    // keeps every segment's sectors contiguous
-    df.iv = (!df.wide && std::llabs(F.stride[0]) * F.elem_bytes <= 32) ? 1 : 0;
+    // keeps every segment's sectors contiguous; the walk keeps a warp's addresses as
+    // 32-bit offsets, so the wave bitmap must span less than 2^31 bytes
+    df.iv = (!df.wide && df.words[1] < ((int64_t)1 << 21) && std::llabs(F.stride[0]) * F.elem_bytes <= 32) ? 1 : 0;
     df.iv_begin = 0;
     df.n_iv = (int32_t)ff->iv.size();
-    df.pad_iv = 0;
+    // per-instruction store sectors of the row walk add up the row segments of a warp,
+    // exact when no two rows of one warp can touch a common sector: their starts lie
+    // further apart than a row's byte span plus 31
+    df.rows_ok = 1;
+    if (ff->n_store > 0) {
+      const int64_t span = (int64_t)F.elem_bytes * std::llabs(F.stride[0]) * (c.B[0] - 1);
+      const int64_t fy2 = c.fold_axis == 1 ? c.fold : 1, fz2 = c.fold_axis == 2 ? c.fold : 1;
+      for (int64_t w = 0; w < d.wpb && df.rows_ok; ++w) {
+        const int64_t t0 = (32 * w) / c.B[0], t1 = std::min<int64_t>((32 * w + 31) / c.B[0], (int64_t)c.B[1] * c.B[2] - 1);
+        for (int64_t ta = t0; ta <= t1 && df.rows_ok; ++ta)
+          for (int64_t tb = ta + 1; tb <= t1; ++tb) {
+            const __int128 dy = (__int128)(tb % c.B[1] - ta % c.B[1]) * fy2 * F.stride[1];
+            const __int128 dz = (__int128)(tb / c.B[1] - ta / c.B[1]) * fz2 * F.stride[2];
+            __int128 delta = (dy + dz) * F.elem_bytes;
+            if (delta < 0) delta = -delta;
+            if (delta <= (__int128)span + 31) {
+              df.rows_ok = 0;
+              break;
+            }
+          }
+      }
+    }
     for (int kv = 0; kv <= 16; ++kv) {
       df.cnt_load[kv] = ff->cnt_load[kv];
       df.cnt_store[kv] = ff->cnt_store[kv];
@@ -524,7 +582,7 @@ static void default_tuning(ws_tuning &t) {
   t.count_words = std::max(256, t.count_words / 4 * 4);
   t.chunk_warps = std::max(1, t.chunk_warps);
   if (t.pass_mb < 0) t.pass_mb = -1;
-  if (t.walk != WS_WALK_ADDRESS) t.walk = WS_WALK_INTERVAL;
+  if (t.walk != WS_WALK_ADDRESS && t.walk != WS_WALK_SEGMENT) t.walk = WS_WALK_INTERVAL;
 }
 
 // Numbers work items and cuts passes for the current tuning.
@@ -540,9 +598,13 @@ void ws_plan::layout() {
   }
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
-  int64_t items = 0, citems = 0, used = 0;
-  for (size_t g = 0; g < hgrp.size(); ++g) hgrp[g].iv = grp_iv_ok[g] && tune.walk == WS_WALK_INTERVAL;
-  DPass cur{0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t items = 0, ritems = 0, citems = 0, used = 0;
+  for (size_t g = 0; g < hgrp.size(); ++g) {
+    hgrp[g].iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
+    hgrp[g].rows = grp_rows_ok[g] && tune.walk == WS_WALK_INTERVAL;
+  }
+  DPass cur;
+  memset(&cur, 0, sizeof(cur));
   const int ng = (int)hgrp.size();
   for (int g = 0; g < ng; ++g) {
     DGroup &G = hgrp[g];
@@ -550,10 +612,16 @@ void ws_plan::layout() {
       cur.cf_hi = G.f_begin;
       cur.grp_hi = g;
       cur.item_hi = items;
+      cur.ritem_hi = ritems;
       cur.citem_hi = citems;
       cur.words = used;
       passes.push_back(cur);
-      cur = DPass{items, 0, citems, 0, G.f_begin, 0, g, 0, 0};
+      memset(&cur, 0, sizeof(cur));
+      cur.item_lo = items;
+      cur.ritem_lo = ritems;
+      cur.citem_lo = citems;
+      cur.cf_lo = G.f_begin;
+      cur.grp_lo = g;
       used = 0;
     }
     for (int k = 0; k < G.f_count; ++k) {
@@ -576,17 +644,27 @@ void ws_plan::layout() {
       f.citem_begin = citems;
       citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
     }
-    // item 0: the representative block (slow exact path); then chunks of the rest
+    // enumeration item 0: the representative block (exact path); then chunks of the
+    // remaining modelled warps, or, for the row walk, chunks of row slots as items of
+    // the row kernel
     G.item_begin = items;
-    items += 1 + ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
+    G.ritem_begin = ritems;
+    if (G.rows) {
+      items += 1;
+      ritems += ceil_div(grp_slots[g], chunk_rows());
+    } else {
+      items += 1 + ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
+    }
   }
   cur.cf_hi = (int)hfld.size();
   cur.grp_hi = ng;
   cur.item_hi = items;
+  cur.ritem_hi = ritems;
   cur.citem_hi = citems;
   cur.words = used;
   if (ng > 0) passes.push_back(cur);
   item_begin_end = items;
+  ritem_begin_end = ritems;
   citem_begin_end = citems;
 }
 
@@ -598,6 +676,16 @@ int ws_plan::upload_fields(cudaStream_t st) {
     graph_exec = nullptr;
   }
   return WS_OK;
+}
+
+int ws_plan::grid_rows(int64_t items) const {
+  int occ = 1;
+  rows_occupancy(iv_cap, &occ);
+  if (tune.ctas_per_sm > 0) occ = std::min(occ, tune.ctas_per_sm);
+  occ = std::max(occ, 1);
+  int64_t g = (int64_t)ctx->sm_count * occ;
+  g = std::min<int64_t>(g, std::max<int64_t>(items, 1));
+  return (int)g;
 }
 
 int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
@@ -633,12 +721,16 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.iv_cap = iv_cap;
     ea.scratch = (uint32_t *)dev(d_scratch);
     ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
-    ea.grab = (unsigned long long *)dev(d_counters) + 2 * p;
+    ea.grab = (unsigned long long *)dev(d_counters) + 3 * p;
+    ea.rgrab = ea.grab + 1;
+    ea.ritem_lo = P.ritem_lo;
+    ea.ritem_hi = P.ritem_hi;
     ea.item_lo = P.item_lo;
     ea.item_hi = P.item_hi;
     ea.grp_lo = P.grp_lo;
     ea.grp_hi = P.grp_hi;
     ea.chunk = tune.chunk_warps;
+    ea.chunk_rows = chunk_rows();
     ea.banks = hw.banks;
     ea.bank_bytes = hw.bank_bytes;
     ea.pair_dist = hw.pair_dist_bytes;
@@ -646,12 +738,16 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
       CU(launch_enum(ea, grid_for(tune.enum_threads, P.item_hi - P.item_lo, false), tune.enum_threads, st));
       ++launches;
     }
+    if (P.ritem_hi > P.ritem_lo) {
+      CU(launch_rows(ea, grid_rows(P.ritem_hi - P.ritem_lo), st));
+      ++launches;
+    }
     if ((rc = mark(1 + 2 * (int)p)) != WS_OK) return rc;
     CountArgs ca;
     ca.fld = ea.fld;
     ca.scratch = ea.scratch;
     ca.counters = ea.counters;
-    ca.grab = ea.grab + 1;
+    ca.grab = ea.grab + 2;
     ca.citem_lo = P.citem_lo;
     ca.citem_hi = P.citem_hi;
     ca.cf_lo = P.cf_lo;
@@ -702,7 +798,8 @@ int ws_plan::run_plain(cudaStream_t st) {
       const int64_t it_lo = hgrp[glo].item_begin, it_hi = ghi < ng ? hgrp[ghi].item_begin : item_begin_end;
       const int cf_lo = hgrp[glo].f_begin, cf_hi = hgrp[ghi - 1].f_begin + hgrp[ghi - 1].f_count;
       const int64_t ct_lo = hfld[cf_lo].citem_begin, ct_hi = cf_hi < nf ? hfld[cf_hi].citem_begin : citem_begin_end;
-      CU(cudaMemsetAsync(grab, 0, 2 * sizeof(unsigned long long), st));
+      const int64_t rt_lo = hgrp[glo].ritem_begin, rt_hi = ghi < ng ? hgrp[ghi].ritem_begin : ritem_begin_end;
+      CU(cudaMemsetAsync(grab, 0, 3 * sizeof(unsigned long long), st));
       EnumArgs ea;
       ea.cfg = (const DCfg *)dev(d_cfg);
       ea.fld = (const DField *)dev(d_fld);
@@ -710,25 +807,28 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.acc = (const DAcc *)dev(d_acc);
       ea.iv = (const DIv *)dev(d_iv);
       ea.iv_cap = iv_cap;
-    ea.iv = (const DIv *)dev(d_iv);
-    ea.iv_cap = iv_cap;
       ea.scratch = (uint32_t *)dev(d_scratch);
       ea.counters = counters;
       ea.grab = grab;
+      ea.rgrab = grab + 1;
       ea.item_lo = it_lo;
       ea.item_hi = it_hi;
+      ea.ritem_lo = rt_lo;
+      ea.ritem_hi = rt_hi;
       ea.grp_lo = glo;
       ea.grp_hi = ghi;
       ea.chunk = tune.chunk_warps;
+      ea.chunk_rows = chunk_rows();
       ea.banks = hw.banks;
       ea.bank_bytes = hw.bank_bytes;
       ea.pair_dist = hw.pair_dist_bytes;
       if (it_hi > it_lo) CU(launch_enum(ea, grid_for(tune.enum_threads, it_hi - it_lo, false), tune.enum_threads, st));
+      if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
       CountArgs ca;
       ca.fld = ea.fld;
       ca.scratch = ea.scratch;
       ca.counters = counters;
-      ca.grab = grab + 1;
+      ca.grab = grab + 2;
       ca.citem_lo = ct_lo;
       ca.citem_hi = ct_hi;
       ca.cf_lo = cf_lo;
@@ -1060,7 +1160,20 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
       // interval walk: uniform groups whose row segments have contiguous sectors
       G.iv = G.iv && G.uniform;
       if (G.iv) p->iv_cap = std::max(p->iv_cap, G.n_iv);
+      // row walk: interval groups whose store counts add up per row segment
+      bool rows = G.iv && comp[i].rows_geom_ok;
+      int64_t instr_w = 0, instr_yz = 0;
+      for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
+        rows = rows && p->hfld[q].rows_ok;
+        instr_w += p->hfld[q].n_load + p->hfld[q].n_store;
+        instr_yz += p->hfld[q].n_load;
+      }
+      const DCfg &dc = comp[i].d;
       p->grp_iv_ok.push_back((char)G.iv);
+      p->grp_rows_ok.push_back((char)rows);
+      p->grp_slots.push_back(dc.rows_slot_end[2]);
+      p->grp_winstr_rows.push_back(
+          (comp[i].lvl_blocks[0] * instr_w + (comp[i].lvl_blocks[1] + comp[i].lvl_blocks[2]) * instr_yz) * dc.wpb);
       p->hgrp.push_back(G);
     }
   }
@@ -1078,9 +1191,10 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
 
   // device buffers
-  // one pair of work-stealing counters per pass; any tuning makes at most one pass per
+  // three work-stealing counters per pass (enumeration, row walk, counting); any tuning
+  // makes at most one pass per
   // (candidate, field), so size for that (retuning may change the pass count)
-  p->grab_bytes = 16 * (p->hfld.size() + 1);
+  p->grab_bytes = 24 * (p->hfld.size() + 1);
   p->counters_bytes = p->grab_bytes + (size_t)n_cfg * N_COUNTERS * 8;
   p->d_cfg = p->take(std::max<size_t>(hcfg.size() * sizeof(DCfg), 256));
   p->d_grp = p->take(std::max<size_t>(p->hgrp.size() * sizeof(DGroup), 256));
@@ -1190,7 +1304,7 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
     out->ms_rank = ms;
     cudaEventElapsedTime(&ms, ev[0], ev[2 + 2 * np]);
     out->ms_total = ms;
-    out->enum_items = p->item_begin_end;
+    out->enum_items = p->item_begin_end + p->ritem_begin_end;
     out->count_items = p->citem_begin_end;
     out->passes = (int64_t)p->passes.size();
     out->upload_bytes = p->upload_bytes;
@@ -1201,6 +1315,10 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
       out->addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR];
       out->warp_instr += cnt[(size_t)i * N_COUNTERS + C_WINSTR];
     }
+    // the row walk visits no modelled warps at levels 1-3: their (warp, instruction)
+    // pairs are known from the block counts
+    for (size_t g = 0; g < p->hgrp.size(); ++g)
+      if (p->hgrp[g].rows) out->warp_instr += p->grp_winstr_rows[g];
     int64_t bm = 0;
     for (size_t k = 0; k < p->hfld.size(); ++k) bm += p->need_words[k] * 4;
     out->bitmap_bytes = 2 * bm;

@@ -219,7 +219,7 @@ def test_interval_walk_uniform_groups(ctx, seed):
     cfgs = [random_uniform_tiny(rng) for _ in range(250)]
     want = oracle.estimate(cfgs, hw, threads=THREADS)
     ranks = list(oracle.rank([w["t_pred"] for w in want]))
-    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ADDRESS):
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
             res, order = p.results()
@@ -228,14 +228,14 @@ def test_interval_walk_uniform_groups(ctx, seed):
 
 
 def test_interval_and_address_walks_identical(ctx):
-    """The interval walk and the per-address walk give bit-identical results on the
-    workload families and the edge cases."""
+    """The row walk, the per-warp interval walk and the per-address walk give
+    bit-identical results on the workload families and the edge cases."""
     hw = W.a100()
     rng = W.SplitMix64(77)
     cfgs = (W.stencil_25pt_sweep(N=(160, 128, 96))[::9] + W.lbm_sweep(N=(96, 64, 48))[::37] +
             W.mixed_set(2000)[::50] + edge_configs() + [random_tiny(rng) for _ in range(100)])
     outs = []
-    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ADDRESS):
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
             res, order = p.results()
@@ -243,7 +243,7 @@ def test_interval_and_address_walks_identical(ctx):
             p.execute(B.WS_MODE_PLAIN)
             res2, order2 = p.results()
             assert res2.tobytes() == res.tobytes() and order2.tobytes() == order.tobytes()
-    assert outs[0] == outs[1]
+    assert outs[0] == outs[1] == outs[2]
 
 
 def test_multi_pass_equals_single_pass(ctx):
@@ -313,7 +313,8 @@ def test_autotune_keeps_results(ctx):
         r2, o2 = p.results()
         prof = p.profile()
     assert r1.tobytes() == r2.tobytes() and o1.tobytes() == o2.tobytes()
-    assert prof["launches"] == 4 and prof["addresses"] > 0 and prof["ms_enum"] > 0
+    # per pass enumeration, row walk and counting; then model and ranking
+    assert prof["launches"] == 3 * prof["passes"] + 2 and prof["addresses"] > 0 and prof["ms_enum"] > 0
 
 
 def test_server_results_same_alone_and_in_the_mix(ctx):
