@@ -162,6 +162,7 @@ enum { WS_WALK_INTERVAL = 0, WS_WALK_ADDRESS = 1, WS_WALK_SEGMENT = 2 };
 /* Per-kernel device time of one profiled step (CUDA events on the launch stream). */
 typedef struct ws_profile {
   float ms_total, ms_enum, ms_count, ms_model, ms_rank;
+  float ms_rows;             /* row-walk kernel (levels 1-3 of row-walk groups)            */
   int32_t launches;          /* kernels launched by the step                             */
   int64_t enum_items, count_items;
   int64_t warp_instr;        /* modelled (warp, access) pairs evaluated                  */

@@ -43,7 +43,7 @@ RESULT = np.dtype([(k, "<i8") for k in RESULT_INT] + [(k, "<f8") for k in RESULT
 TUNING = np.dtype([("chunk_warps", "<i4"), ("enum_threads", "<i4"), ("count_words", "<i4"),
                    ("ctas_per_sm", "<i4"), ("pass_mb", "<i4"), ("walk", "<i4")], align=True)
 PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4"), ("ms_model", "<f4"),
-                    ("ms_rank", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
+                    ("ms_rank", "<f4"), ("ms_rows", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),
                     ("upload_bytes", "<i8")], align=True)
 SERVER_OPTS = np.dtype([("mem_budget", "<u8"), ("max_inflight", "<i4"), ("max_step_cfgs", "<i4"),

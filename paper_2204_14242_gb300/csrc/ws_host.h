@@ -79,6 +79,7 @@ struct ws_plan {
   int upload_fields(cudaStream_t st);
   int grid_for(int threads, int64_t items, bool counting) const;
   int grid_rows(int64_t items) const;
+  int bank_shift() const;
   int enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof);
   int run_plain(cudaStream_t st);
   int execute(int mode, cudaStream_t st);

@@ -130,7 +130,7 @@ struct DGroup {
   int32_t iv;             // uniform and every field allows the interval walk
   int32_t n_iv;           // merged load intervals of all its fields
   int32_t rows;           // levels 1-3 take the row walk (work items are chunks of row slots)
-  int32_t pad;
+  int32_t n0_items;       // enumeration items of the representative block
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch

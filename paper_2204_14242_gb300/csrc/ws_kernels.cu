@@ -90,6 +90,31 @@ __device__ int bank_cycles_warp(int64_t addr, bool act, uint32_t lane, int banks
   return __reduce_add_sync(FULL, (uint32_t)cycles);
 }
 
+// The same visitor for power-of-two banks x bank width (their product dividing 1024)
+// on 32-bit byte addresses relative to a 1024-byte aligned origin, which have the same
+// banks and pairing distances as the absolute ones.
+__device__ int bank_cycles_rel32(uint32_t rel, bool act, uint32_t lane, uint32_t bshift, uint32_t bmask,
+                                 uint32_t pair_dist) {
+  const uint32_t word = rel >> bshift, bank = word & bmask;
+  const uint32_t actm = __ballot_sync(FULL, act);
+  const uint32_t halfm = lane < 16 ? 0x0000ffffu : 0xffff0000u;
+  const uint32_t same = __match_any_sync(FULL, word) & actm & halfm;
+  const bool uniq = act && lane == (uint32_t)(__ffs(same) - 1);
+  uint32_t todo = __ballot_sync(FULL, uniq);
+  int cycles = 0;
+  while (todo) {
+    const bool mine = (todo >> lane) & 1u;
+    const uint32_t v = __reduce_min_sync(halfm, mine ? word : 0xffffffffu);
+    const bool member = mine && ((word - v) << bshift) < pair_dist;
+    const uint32_t mm = __ballot_sync(FULL, member);
+    const uint32_t sameb = __match_any_sync(FULL, bank) & mm & halfm;
+    const uint32_t c = __reduce_max_sync(halfm, member ? (uint32_t)__popc(sameb) : 0u);
+    if ((lane & 15u) == 0) cycles += (int)c;
+    todo &= ~mm;
+  }
+  return (int)__reduce_add_sync(FULL, (uint32_t)cycles);
+}
+
 // Last (candidate, field) index in [lo, hi) whose first work item is <= item.  Items
 // are handed out in increasing order, so a CTA's next item never lies before the field
 // of its previous one (`hint`): gallop forward from there, then bisect.
@@ -597,13 +622,62 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       cur_g = gi;
       cur_cfg = s_g.cfg;
     }
-    // item 0 of a group covers the representative block, the others chunks of the rest
+    // the first n0_items items of a group cover the representative block as chunks of
+    // (modelled warp, access instruction) pairs; the others chunks of the remaining
+    // modelled warps (groups without the row walk)
     const int64_t kk = item - s_g.item_begin;
-    const uint32_t mw0 = kk == 0 ? 0u : (uint32_t)(s_g.mw_block + (kk - 1) * (int64_t)a.chunk);
-    const uint32_t mw1 = kk == 0 ? (uint32_t)s_g.mw_block
-                                 : (uint32_t)min(s_g.mw_block + kk * (int64_t)a.chunk, s_g.mw_end);
+    const bool blk = kk < s_g.n0_items;
+    const uint32_t mw0 = blk ? 0u : (uint32_t)(s_g.mw_block + (kk - s_g.n0_items) * (int64_t)a.chunk);
+    const uint32_t mw1 = blk ? 0u : (uint32_t)min(s_g.mw_block + (kk - s_g.n0_items + 1) * (int64_t)a.chunk,
+                                                   s_g.mw_end);
     uint32_t acc_lb = 0, acc_lw = 0, acc_req = 0, acc_st = 0, acc_bank = 0, acc_sreq = 0, acc_addr = 0, acc_wi = 0;
     uint32_t bad = 0;
+
+    if (blk) {
+      // ---- representative block (Sec. 3.2, 3.3): every (warp, instruction) exactly --
+      // distinct sectors per instruction (L1 requests / write-through stores), the block
+      // footprint bitmaps, and half-warp bank cycles
+      const uint32_t LS = (uint32_t)s_soff[s_g.f_count], L = (uint32_t)s_loff[s_g.f_count];
+      const int64_t np = (int64_t)s_g.mw_block * LS;
+      const int64_t p0 = kk * (int64_t)a.block_pairs, p1 = min(p0 + (int64_t)a.block_pairs, np);
+      const bool fast_banks = a.bank_shift >= 0;
+      for (int64_t pp = p0 + warp; pp < p1; pp += nwarps) {
+        const uint32_t mw = (uint32_t)(pp / LS), j = (uint32_t)(pp - (int64_t)mw * LS);
+        const uint32_t b = (uint32_t)s_c.rep;
+        const uint32_t bt = fdiv(b, s_c.fd_gx);
+        const uint32_t bx = b - bt * (uint32_t)s_c.g[0];
+        const uint32_t bz = fdiv(bt, s_c.fd_gy);
+        const uint32_t by = bt - bz * (uint32_t)s_c.g[1];
+        const uint32_t tid = mw * 32u + lane;
+        const bool exists = tid < (uint32_t)s_c.T;
+        const uint32_t tc = exists ? s_tc[tid] : 0u;
+        const int32_t x = (int32_t)bx * s_c.B[0] + (int32_t)(tc & 1023u);
+        int32_t y = (int32_t)by * s_c.B[1] + (int32_t)((tc >> 10) & 1023u);
+        int32_t z = (int32_t)bz * s_c.B[2] + (int32_t)(tc >> 20);
+        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
+        if (faxis == 1) y *= fold;
+        if (faxis == 2) z *= fold;
+        const bool valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
+        int kv = 0;
+        if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+        if (j == 0u) {
+          if (s_g.first_of_cfg) acc_lb += __reduce_add_sync(FULL, (uint32_t)kv);
+          acc_addr += __reduce_add_sync(FULL, (uint32_t)s_gad[0][kv]);
+          acc_wi += (uint32_t)s_gwi[0];
+        }
+        const DField &F = s_fk[s_af[j]];
+        const bool act = valid && (int)s_kmin[j] < kv;
+        const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
+        const int64_t r = F.base + (int64_t)F.esize * lin - 32 * F.lo[0] + s_boff[j];
+        if (j < L) acc_req += bitmap_insert(a.scratch + F.bm[BM_BL], r, act, lane, F.words[0], bad);
+        else acc_st += bitmap_insert(a.scratch + F.bm[BM_BS], r, act, lane, F.words[0], bad);
+        if (fast_banks && !F.wide)
+          acc_bank += bank_cycles_rel32((uint32_t)r, act && r >= 0 && r < (F.words[0] << 10), lane,
+                                        (uint32_t)a.bank_shift, (uint32_t)(a.banks - 1), (uint32_t)a.pair_dist);
+        else
+          acc_bank += bank_cycles_warp(r + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
+      }
+    }
     for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
       // ---- decode the modelled warp once for every field of the group
       uint32_t level, b, j;
@@ -891,24 +965,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         acc_wi += (uint32_t)(n_load + nst);
         const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
 
-        if (level == 0) {
-          // representative block: exact per-instruction counts and bank cycles
-          const int64_t lo0 = F.lo[0];
-          const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * lo0;
-          uint32_t *const bl = a.scratch + F.bm[BM_BL], *const bs = a.scratch + F.bm[BM_BS];
-          for (int i = 0; i < n_load; ++i) {
-            const bool act = valid && (int)s_kmin[lo_ + i] < kv;
-            const int64_t r = rel + s_boff[lo_ + i];
-            acc_req += bitmap_insert(bl, r, act, lane, F.words[0], bad);
-            acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
-          }
-          for (int i = n_load; i < n_load + nst; ++i) {
-            const bool act = valid && (int)s_kmin[so_ + i] < kv;
-            const int64_t r = rel + s_boff[so_ + i];
-            acc_st += bitmap_insert(bs, r, act, lane, F.words[0], bad);
-            acc_bank += bank_cycles_warp(r + 32 * lo0, act, lane, a.banks, a.bank_bytes, a.pair_dist);
-          }
-        } else if (!F.wide) {
+        if (!F.wide) {
           const int64_t rel = F.base + (int64_t)F.esize * lin - 32 * F.lo[1];
           // uniform groups staged the field constant into the 32-bit offsets already
           const uint32_t r0 = s_g.uniform ? (uint32_t)((int64_t)F.esize * lin) : (uint32_t)rel;

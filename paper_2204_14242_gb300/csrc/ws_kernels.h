@@ -23,6 +23,8 @@ struct EnumArgs {
   int32_t chunk;                   // modelled warps per item
   int32_t chunk_rows;              // row slots per item (row walk)
   int32_t banks, bank_bytes, pair_dist;
+  int32_t bank_shift;              // log2(bank_bytes) when banks x bank_bytes is a power of two <= 1024, else -1
+  int32_t block_pairs;             // (modelled warp, instruction) pairs per representative-block item
 };
 
 struct CountArgs {
@@ -61,6 +63,7 @@ cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm);
 size_t enum_dyn_smem(int iv_cap);
 cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm);
 constexpr int kRowsThreads = 256;
+constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
 cudaError_t count_occupancy(int *blocks_per_sm);
 
 }  // namespace ws

@@ -644,17 +644,15 @@ void ws_plan::layout() {
       f.citem_begin = citems;
       citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
     }
-    // enumeration item 0: the representative block (exact path); then chunks of the
-    // remaining modelled warps, or, for the row walk, chunks of row slots as items of
-    // the row kernel
+    // enumeration items: the representative block (exact path) in chunks of (modelled
+    // warp, instruction) pairs; then chunks of the remaining modelled warps, or, for the
+    // row walk, chunks of row slots as items of the row kernel
     G.item_begin = items;
     G.ritem_begin = ritems;
-    if (G.rows) {
-      items += 1;
-      ritems += ceil_div(grp_slots[g], chunk_rows());
-    } else {
-      items += 1 + ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
-    }
+    G.n0_items = (int32_t)std::max<int64_t>(1, ceil_div(G.mw_block * (int64_t)G.acc_count, kBlockPairs));
+    items += G.n0_items;
+    if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
+    else items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
   }
   cur.cf_hi = (int)hfld.size();
   cur.grp_hi = ng;
@@ -676,6 +674,17 @@ int ws_plan::upload_fields(cudaStream_t st) {
     graph_exec = nullptr;
   }
   return WS_OK;
+}
+
+// log2 of the bank width when banks x width is a power of two dividing 1024 (so that
+// bitmap-relative addresses have the absolute banks), else -1.
+int ws_plan::bank_shift() const {
+  const int64_t b = hw.banks, w = hw.bank_bytes;
+  auto pow2 = [](int64_t v) { return v > 0 && (v & (v - 1)) == 0; };
+  if (!pow2(b) || !pow2(w) || b * w > 1024 || hw.pair_dist_bytes <= 0) return -1;
+  int sh = 0;
+  while ((1ll << sh) < w) ++sh;
+  return sh;
 }
 
 int ws_plan::grid_rows(int64_t items) const {
@@ -700,7 +709,8 @@ int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
 }
 
 // Enqueues one batched step (all passes, model, rank) on `st`; `ev` (may be null)
-// receives events [start, after enum_k, after count_k ..., after model, after rank].
+// receives events [start, per pass (after enumeration, after row walk, after counting),
+// after model, after rank].
 int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof) {
   auto mark = [&](int k) -> int {
     if (ev) CU(cudaEventRecord((*ev)[k], st));
@@ -734,15 +744,18 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.banks = hw.banks;
     ea.bank_bytes = hw.bank_bytes;
     ea.pair_dist = hw.pair_dist_bytes;
+    ea.bank_shift = bank_shift();
+    ea.block_pairs = kBlockPairs;
     if (P.item_hi > P.item_lo) {
       CU(launch_enum(ea, grid_for(tune.enum_threads, P.item_hi - P.item_lo, false), tune.enum_threads, st));
       ++launches;
     }
+    if ((rc = mark(1 + 3 * (int)p)) != WS_OK) return rc;
     if (P.ritem_hi > P.ritem_lo) {
       CU(launch_rows(ea, grid_rows(P.ritem_hi - P.ritem_lo), st));
       ++launches;
     }
-    if ((rc = mark(1 + 2 * (int)p)) != WS_OK) return rc;
+    if ((rc = mark(2 + 3 * (int)p)) != WS_OK) return rc;
     CountArgs ca;
     ca.fld = ea.fld;
     ca.scratch = ea.scratch;
@@ -757,7 +770,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
       CU(launch_count(ca, grid_for(512, P.citem_hi - P.citem_lo, true), st));
       ++launches;
     }
-    if ((rc = mark(2 + 2 * (int)p)) != WS_OK) return rc;
+    if ((rc = mark(3 + 3 * (int)p)) != WS_OK) return rc;
   }
   ModelArgs ma;
   ma.cfg = (const DCfg *)dev(d_cfg);
@@ -768,7 +781,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
   ma.hw = dhw;
   CU(launch_model(ma, st));
   launches += n_cfg > 0;
-  if ((rc = mark(1 + 2 * (int)passes.size())) != WS_OK) return rc;
+  if ((rc = mark(1 + 3 * (int)passes.size())) != WS_OK) return rc;
   RankArgs ra;
   ra.keys = (const double *)dev(d_keys);
   ra.seg = (const int32_t *)dev(d_seg);
@@ -777,7 +790,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
   ra.n_seg = n_seg;
   CU(launch_rank(ra, st));
   launches += n_cfg > 0;
-  if ((rc = mark(2 + 2 * (int)passes.size())) != WS_OK) return rc;
+  if ((rc = mark(2 + 3 * (int)passes.size())) != WS_OK) return rc;
   if (prof) prof->launches = launches;
   return WS_OK;
 }
@@ -822,6 +835,8 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.banks = hw.banks;
       ea.bank_bytes = hw.bank_bytes;
       ea.pair_dist = hw.pair_dist_bytes;
+      ea.bank_shift = bank_shift();
+      ea.block_pairs = kBlockPairs;
       if (it_hi > it_lo) CU(launch_enum(ea, grid_for(tune.enum_threads, it_hi - it_lo, false), tune.enum_threads, st));
       if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
       CountArgs ca;
@@ -1284,7 +1299,7 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
   CU(cudaSetDevice(p->ctx->device));
   cudaStream_t st = pick_stream(p->ctx, stream);
   memset(out, 0, sizeof(*out));
-  const int nev = 3 + 2 * (int)p->passes.size();
+  const int nev = 3 + 3 * (int)p->passes.size();
   std::vector<cudaEvent_t> ev(nev);
   for (auto &e : ev) CU(cudaEventCreate(&e));
   int rc = p->enqueue(st, &ev, out);
@@ -1293,16 +1308,18 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
     float ms = 0;
     const int np = (int)p->passes.size();
     for (int k = 0; k < np; ++k) {
-      cudaEventElapsedTime(&ms, ev[k == 0 ? 0 : 2 * k], ev[1 + 2 * k]);
+      cudaEventElapsedTime(&ms, ev[3 * k], ev[1 + 3 * k]);
       out->ms_enum += ms;
-      cudaEventElapsedTime(&ms, ev[1 + 2 * k], ev[2 + 2 * k]);
+      cudaEventElapsedTime(&ms, ev[1 + 3 * k], ev[2 + 3 * k]);
+      out->ms_rows += ms;
+      cudaEventElapsedTime(&ms, ev[2 + 3 * k], ev[3 + 3 * k]);
       out->ms_count += ms;
     }
-    cudaEventElapsedTime(&ms, ev[2 * np], ev[1 + 2 * np]);
+    cudaEventElapsedTime(&ms, ev[3 * np], ev[1 + 3 * np]);
     out->ms_model = ms;
-    cudaEventElapsedTime(&ms, ev[1 + 2 * np], ev[2 + 2 * np]);
+    cudaEventElapsedTime(&ms, ev[1 + 3 * np], ev[2 + 3 * np]);
     out->ms_rank = ms;
-    cudaEventElapsedTime(&ms, ev[0], ev[2 + 2 * np]);
+    cudaEventElapsedTime(&ms, ev[0], ev[2 + 3 * np]);
     out->ms_total = ms;
     out->enum_items = p->item_begin_end + p->ritem_begin_end;
     out->count_items = p->citem_begin_end;

@@ -67,6 +67,18 @@ def test_random_tiny_candidates(ctx, seed):
     assert list(order) == list(oracle.rank([w["t_pred"] for w in want]))
 
 
+@pytest.mark.parametrize("banks,bank_bytes,pair", [(12, 8, 1024), (32, 4, 512), (16, 8, 96)])
+def test_bank_layouts(ctx, banks, bank_bytes, pair):
+    """Bank-conflict cycles for other bank layouts (the power-of-two fast path and the
+    general one) against the oracle."""
+    rng = W.SplitMix64(900 + banks + pair)
+    hw = W.Hardware(sms=3, max_blocks_sm=2, banks=banks, bank_bytes=bank_bytes, pair_dist_bytes=pair)
+    cfgs = [random_tiny(rng) for _ in range(120)] + [random_uniform_tiny(rng) for _ in range(80)]
+    want = oracle.estimate(cfgs, hw, threads=THREADS)
+    res, order = B.ws_estimate_batch(ctx, cfgs, hw)
+    assert_match(res, want, what=f"banks {banks}x{bank_bytes}/{pair}")
+
+
 def test_modes_are_bit_identical(ctx):
     rng = W.SplitMix64(55)
     hw = W.Hardware(sms=5)
