@@ -12,7 +12,11 @@ replayed as a CUDA graph, descriptors already resident on the device.  Reported:
              compile, host->device copies, kernels, device->host results) per step
   plain      candidates/s of the plain form (one synchronous launch sequence per candidate)
   served     the Poisson request stream through the continuous-batching server (p50/p99)
-  roofline   the enumeration kernel against the measured integer-add rate
+  roofline   the kernel with the largest share of the step, against the rate that bounds
+             it (all three under roofline.kernels): the representative-block kernel
+             (exact per-address path) against the measured int32-add rate, the row walk
+             against the measured L2 red.or rate, the counting kernel against the
+             measured HBM copy bandwidth (MEASURED_PEAKS.json)
   cpu_baseline  the CPU oracle on a bounded sample of the same sweep, all host cores
 
 --impl reference times the CPU oracle itself on bounded samples of the same workload.
@@ -197,6 +201,48 @@ def cpu_baseline(cfgs, hw, seconds):
                       f"one candidate per thread, {dt:.1f} s"}
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth measured on the GB300s (driver-written), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def kernel_rooflines(profs, peaks):
+    """Each kernel's achieved rate against the device rate that bounds it; the one with
+    the largest share of the step is reported at the top level.
+
+    enum_kernel  representative block, exact per-address path: addresses evaluated
+                 (valid threads x issued accesses of the block) / s vs int32 adds / s
+    rows_kernel  row walk: 64-bit red.or inserts (one per bitmap unit a sector range
+                 covers) / s vs the measured L2 red.or rate on distinct words
+    count_kernel bitmap bytes read / s vs the measured HBM copy bandwidth
+    """
+    med = lambda k: statistics.median(p[k] for p in profs)
+    last = profs[-1]
+    block_addresses = int(last["block_addresses"])
+    ms = {"enum_kernel": med("ms_enum"), "rows_kernel": med("ms_rows"), "count_kernel": med("ms_count")}
+    hbm, hbm_src = measured_hbm_gbs()
+    k = {}
+    a = block_addresses / (ms["enum_kernel"] * 1e-3) if ms["enum_kernel"] > 0 else 0.0
+    k["enum_kernel"] = {"bound": "alu", "achieved": a / 1e9, "peak": peaks["int_ops_per_s"] / 1e9,
+                        "unit": "G addresses/s vs G int32-add/s (measured)", "frac": a / peaks["int_ops_per_s"],
+                        "per_launch": block_addresses, "ms": ms["enum_kernel"]}
+    r = last["row_reds"] / (ms["rows_kernel"] * 1e-3) if ms["rows_kernel"] > 0 else 0.0
+    k["rows_kernel"] = {"bound": "l2_atomic", "achieved": r / 1e9, "peak": peaks["l2_red_per_s"] / 1e9,
+                        "unit": "G red.or/s (measured)", "frac": r / peaks["l2_red_per_s"],
+                        "per_launch": int(last["row_reds"]), "ms": ms["rows_kernel"]}
+    b = last["bitmap_bytes"] / (ms["count_kernel"] * 1e-3) if ms["count_kernel"] > 0 else 0.0
+    k["count_kernel"] = {"bound": "hbm", "achieved": b / 1e9, "peak": hbm, "unit": f"GB/s ({hbm_src})",
+                         "frac": b / 1e9 / hbm, "per_launch": int(last["bitmap_bytes"]), "ms": ms["count_kernel"]}
+    top = max(ms, key=ms.get)
+    out = dict(k[top])
+    out.update({"kernel": top, "traffic": None, "share": ms[top] / last["ms_total"], "kernels": k})
+    return out
+
+
 def serve(B, W, ctx, hw, seconds, seed=20222, rate_hz=200.0):
     """Poisson request stream through the server; latency from arrival to completed poll."""
     n_req = max(1, int(seconds * rate_hz))
@@ -323,12 +369,9 @@ def main():
                          + res["wave_store_sectors"].sum())
     sectors_per_s = world * unique_sectors / (ms_step * 1e-3)
 
-    # roofline of the enumeration kernel: events around it on its own launch stream
+    # per-kernel rooflines: CUDA events around each kernel on its own launch stream
     profs = [plan.profile(stream) for _ in range(3)]
-    ms_enum = statistics.median(p["ms_enum"] for p in profs)
-    ms_count = statistics.median(p["ms_count"] for p in profs)
-    addresses = profs[-1]["addresses"]
-    achieved = addresses / (ms_enum * 1e-3)
+    roofline = kernel_rooflines(profs, peaks)
     launches_per_step = profs[-1]["launches"]
 
     extra = {}
@@ -377,11 +420,7 @@ def main():
                "unique_sectors_per_s": sectors_per_s,
                "e2e": {"value": len(cfgs) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
-               "roofline": {"bound": "alu", "kernel": "enum_kernel", "achieved": achieved / 1e9,
-                            "peak": peaks["int_ops_per_s"] / 1e9, "unit": "Gaddr/s vs G int32-add/s",
-                            "frac": achieved / peaks["int_ops_per_s"], "traffic": None,
-                            "ms_enum": ms_enum, "ms_count": ms_count, "addresses_per_launch": addresses,
-                            "l2_red_peak_per_s": peaks["l2_red_per_s"], "enum_share": ms_enum / profs[-1]["ms_total"]},
+               "roofline": roofline,
                "gpu_launches": launches_per_step * args.steps,
                "clocks": clk, "cpu_baseline": base}
         out.update(extra)

@@ -167,10 +167,14 @@ typedef struct ws_profile {
   int64_t enum_items, count_items;
   int64_t warp_instr;        /* modelled (warp, access) pairs evaluated                  */
   int64_t addresses;         /* valid (thread, access) address evaluations               */
-  int64_t bitmap_bytes;      /* bitmap bytes read + cleared by the counting kernel        */
+  int64_t bitmap_bytes;      /* bitmap bytes the counting kernel reads (it writes back only
+                                the non-zero 16-byte positions, as zeros)                  */
   int64_t passes;            /* scratch passes the plan needed                            */
   int64_t upload_bytes;      /* descriptor bytes the plan copied host -> device           */
-} ws_profile;
+  int64_t row_reds;          /* 64-bit red.or issued by the row walk                      */
+  int64_t block_addresses;   /* (thread, access) address evaluations of the representative
+                                blocks (the exact per-address path)                        */
+} ws_profile; /* 104 bytes */
 
 typedef struct ws_ctx ws_ctx;
 typedef struct ws_plan ws_plan;

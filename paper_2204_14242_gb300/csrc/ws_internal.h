@@ -16,6 +16,8 @@ enum Counter {
   C_ADDR,      // valid address evaluations (diagnostic, for the roofline)
   C_WINSTR,    // modelled (warp, access) pairs (diagnostic)
   C_OVERFLOW,  // bitmap indices outside the bitmap (skipped; the candidate fails)
+  C_RED,       // 64-bit red.or issued by the row walk (diagnostic)
+  C_ADDR0,     // address evaluations of the representative block (diagnostic)
   N_COUNTERS
 };
 

@@ -1087,6 +1087,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       if (acc_bank) atomicAdd(c + C_BANK, (u64)acc_bank);
       if (acc_sreq) atomicAdd(c + C_W_SREQ, (u64)acc_sreq);
       if (acc_addr) atomicAdd(c + C_ADDR, (u64)acc_addr);
+      if (acc_addr && blk) atomicAdd(c + C_ADDR0, (u64)acc_addr);
       if (acc_wi) atomicAdd(c + C_WINSTR, (u64)acc_wi);
     }
     __syncthreads();
@@ -1139,7 +1140,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       cur_cfg = s_g.cfg;
     }
     const int64_t kk = item - s_g.ritem_begin;
-    uint32_t bad = 0;
+    uint32_t bad = 0, nred = 0;
     {
       // ---- row walk of levels 1-3: one grid row (block run x thread row) per warp; each
       // merged load run (raw loads when the row has fewer valid folded points than the
@@ -1234,6 +1235,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           unsigned long long cb = 0ull;
           put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
           if (cb) atomicOr(bm + cu, cb);
+          nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
         }
         if (lv == 0) {
           for (int j = L + (int)lane; j < L + S; j += 32) {
@@ -1250,6 +1252,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             unsigned long long cb = 0ull;
             put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
             if (cb) atomicOr(bm + cu, cb);
+            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
             atomicAdd(ctr + C_W_SREQ,
                       (unsigned long long)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb));
           }
@@ -1258,8 +1261,12 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
     }
 
     bad = __reduce_add_sync(FULL, bad);
-    if (lane == 0 && bad)
-      atomicAdd((unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS + C_OVERFLOW), (unsigned long long)bad);
+    nred = __reduce_add_sync(FULL, nred);
+    if (lane == 0) {
+      unsigned long long *const c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
+      if (bad) atomicAdd(c + C_OVERFLOW, (unsigned long long)bad);
+      if (nred) atomicAdd(c + C_RED, (unsigned long long)nred);
+    }
     __syncthreads();
   }
 }

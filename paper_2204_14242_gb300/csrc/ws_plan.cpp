@@ -1331,6 +1331,8 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
     for (int i = 0; i < p->n_cfg; ++i) {
       out->addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR];
       out->warp_instr += cnt[(size_t)i * N_COUNTERS + C_WINSTR];
+      out->row_reds += cnt[(size_t)i * N_COUNTERS + C_RED];
+      out->block_addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR0];
     }
     // the row walk visits no modelled warps at levels 1-3: their (warp, instruction)
     // pairs are known from the block counts
@@ -1338,7 +1340,7 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
       if (p->hgrp[g].rows) out->warp_instr += p->grp_winstr_rows[g];
     int64_t bm = 0;
     for (size_t k = 0; k < p->hfld.size(); ++k) bm += p->need_words[k] * 4;
-    out->bitmap_bytes = 2 * bm;
+    out->bitmap_bytes = bm;
   }
   for (auto &x : ev) cudaEventDestroy(x);
   if (rc != WS_OK) return rc;

@@ -49,6 +49,7 @@ def test_struct_layouts_match_the_header():
     assert int(sizes["ws_result"]) == B.RESULT.itemsize
     assert int(sizes["ws_cfg_info"]) == B.CFG_INFO.itemsize
     assert int(sizes["ws_tuning"]) == B.TUNING.itemsize
+    assert int(sizes["ws_profile"]) == B.PROFILE.itemsize
 
 
 def test_host_constants_and_rank_key():
