@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "warpspeed.h"
@@ -26,6 +27,29 @@ struct Arena {
   size_t largest_free();
   size_t used();
 };
+
+// Allocator whose resize() leaves trivially constructible elements uninitialised, so
+// that large descriptor arrays are first touched by the threads that fill them.
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = DefaultInitAlloc<U>;
+  };
+  DefaultInitAlloc() = default;
+  template <class U>
+  DefaultInitAlloc(const DefaultInitAlloc<U> &) {}
+  template <class U>
+  void construct(U *p) {
+    ::new ((void *)p) U;
+  }
+  template <class U, class... Args>
+  void construct(U *p, Args &&...args) {
+    ::new ((void *)p) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using HostVec = std::vector<T, DefaultInitAlloc<T>>;
 
 void set_error(const std::string &s);
 const char *last_error();
@@ -48,7 +72,7 @@ struct ws_plan {
   ws_hw hw;
   ws::DHw dhw;
   ws_tuning tune;
-  std::vector<ws::DField> hfld;
+  ws::HostVec<ws::DField> hfld;
   std::vector<ws::DGroup> hgrp;
   std::vector<char> grp_iv_ok;   // group allows the interval walk (used unless tune.walk asks otherwise)
   std::vector<char> grp_rows_ok; // group allows the row walk of levels 1-3
@@ -56,7 +80,7 @@ struct ws_plan {
   std::vector<int64_t> grp_winstr_rows;  // modelled (warp, instruction) pairs of levels 1-3
   int32_t chunk_rows() const { return std::max(1, tune.chunk_warps / 16); }
   std::vector<int32_t> cfg_grp_begin;
-  std::vector<int64_t> need_words;
+  ws::HostVec<int64_t> need_words;
   std::vector<int32_t> cfg_cf_begin;
   std::vector<ws::DPass> passes;
   int64_t scratch_words = 0;

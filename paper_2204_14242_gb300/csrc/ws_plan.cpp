@@ -11,6 +11,7 @@
 #include <climits>
 #include <fstream>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <set>
 #include <sstream>
@@ -173,7 +174,8 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
   if (std::llabs(F.align_bytes) >= ((int64_t)1 << 50) || std::llabs(F.const_off) >= ((int64_t)1 << 40))
     out.status = WS_EINVAL;
   if (out.status != WS_OK) return;
-  std::set<Off4> L, S;
+  std::vector<Off4> L, S;
+  L.reserve(F.n_access);
   for (int a = 0; a < F.n_access; ++a) {
     const ws_access &A = acc[F.access_off + a];
     if (std::abs(A.dx) > 65535 || std::abs(A.dy) > 65535 || std::abs(A.dz) > 65535 ||
@@ -181,21 +183,27 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
       out.status = WS_EINVAL;
       return;
     }
-    (A.is_store ? S : L).insert(Off4(A.dx, A.dy, A.dz, A.dc));
+    (A.is_store ? S : L).push_back(Off4(A.dx, A.dy, A.dz, A.dc));
+  }
+  for (auto *v : {&L, &S}) {
+    std::sort(v->begin(), v->end());
+    v->erase(std::unique(v->begin(), v->end()), v->end());
   }
   // thread folding (Sec. 5.1): union over k of offset + k * axis, each with the first
-  // folded point k that needs it
-  auto fold_list = [&](const std::set<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
-    std::map<Off4, int> kmin;
+  // folded point k that needs it (ascending offsets)
+  auto fold_list = [&](const std::vector<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
+    std::vector<std::pair<Off4, int>> all;
+    all.reserve(src.size() * fold);
     for (const Off4 &o : src)
       for (int k = 0; k < fold; ++k) {
         Off4 q = o;
         if (fold_axis == 1) std::get<1>(q) += k;
         if (fold_axis == 2) std::get<2>(q) += k;
-        auto it = kmin.find(q);
-        if (it == kmin.end() || k < it->second) kmin[q] = k;
+        all.emplace_back(q, k);
       }
-    for (auto &kv : kmin) dst.push_back(kv);
+    std::sort(all.begin(), all.end());
+    for (size_t i = 0; i < all.size(); ++i)
+      if (i == 0 || all[i].first != all[i - 1].first) dst.push_back(all[i]);
   };
   std::vector<std::pair<Off4, int>> fl, fs;
   fold_list(L, fl);
@@ -355,27 +363,27 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     for (int lv = 0; lv < 3; ++lv) {
       d.rows_R_lo[lv] = 0;
       d.rows_R_cnt[lv] = 0;
-      out.lvl_blocks[lv] = 0;
       if (rng[lv][1] > rng[lv][0]) {
         const int64_t R0 = rng[lv][0] / g[0], R1 = (rng[lv][1] - 1) / g[0];
         d.rows_R_lo[lv] = (int32_t)R0;
         d.rows_R_cnt[lv] = (int32_t)(R1 - R0 + 1);
-        for (int64_t R = R0; R <= R1; ++R) {
-          const int64_t a = std::max(rng[lv][0], R * g[0]), b = std::min(rng[lv][1], (R + 1) * g[0]);
-          const int64_t by = R % g[1];
-          if (lv == 0) out.lvl_blocks[lv] += b - a;
-          if (lv == 1 && by != g[1] - 1) out.lvl_blocks[lv] += b - a;
-          if (lv == 2) {
-            int64_t n = b - a;
-            if (by != g[1] - 1 && y_hi > y_lo) n -= std::max<int64_t>(0, std::min(b, y_hi) - std::max(a, y_lo));
-            out.lvl_blocks[lv] += n;
-          }
-        }
       }
       cum += (int64_t)d.rows_R_cnt[lv] * (lv == 2 ? 2 : 1) * d.rows_per_blk;
       d.rows_slot_end[lv] = cum;
     }
     out.rows_geom_ok = cum < ((int64_t)1 << 31);
+    // blocks b < n of the last block row (by = g[1] - 1)
+    auto last_row = [&](int64_t n) {
+      const int64_t per = g[0] * g[1];
+      int64_t c = (n / per) * g[0];
+      const int64_t r = n % per - (g[1] - 1) * g[0];
+      return r > 0 ? c + r : c;
+    };
+    out.lvl_blocks[0] = weff;
+    out.lvl_blocks[1] = y_hi > y_lo ? (y_hi - y_lo) - (last_row(y_hi) - last_row(y_lo)) : 0;
+    out.lvl_blocks[2] = z_hi - z_lo;
+    const int64_t oa = std::max(z_lo, y_lo), ob = std::min(z_hi, y_hi);
+    if (z_hi > z_lo && y_hi > y_lo && ob > oa) out.lvl_blocks[2] -= (ob - oa) - (last_row(ob) - last_row(oa));
   }
   d.fd_wpb = make_fastdiv((uint32_t)wpb);
 
@@ -574,7 +582,7 @@ int64_t ws_plan::take(size_t bytes) {
 }
 
 static void default_tuning(ws_tuning &t) {
-  if (t.chunk_warps <= 0) t.chunk_warps = 1024;
+  if (t.chunk_warps <= 0) t.chunk_warps = 4096;
   if (t.pass_mb == 0) t.pass_mb = -1;
   if (t.enum_threads <= 0) t.enum_threads = 256;
   if (t.count_words <= 0) t.count_words = 65536;
@@ -1064,9 +1072,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   default_tuning(p->tune);
 
   std::vector<DCfg> hcfg(n_cfg);
-  std::vector<DAcc> hacc;
-  std::map<uint64_t, int32_t> acc_at, iv_at;
-  std::vector<DIv> hiv;
+  HostVec<DAcc> hacc;
+  HostVec<DIv> hiv;
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   std::vector<Compiled> comp;
   std::vector<int> status;
@@ -1095,38 +1102,76 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     for (int64_t w : comp[i].need_words)
       if ((size_t)w * 4 > scratch) status[i] = WS_ENOMEM;
   }
-  for (int i = 0; i < n_cfg; ++i) {
-    DCfg &d = hcfg[i];
-    if (status[i] == WS_OK) {
-      d = comp[i].d;
-    } else {
-      memset(&d, 0, sizeof(d));
+  // descriptors: fields in candidate order; candidates sharing a field and a folding
+  // share its access and interval lists on the device (dedup by sorting fold keys)
+  std::vector<int64_t> cf_off(n_cfg + 1, 0);
+  for (int i = 0; i < n_cfg; ++i) cf_off[i + 1] = cf_off[i] + (status[i] == WS_OK ? (int64_t)comp[i].f.size() : 0);
+  const int64_t nf = cf_off[n_cfg];
+  std::vector<std::pair<uint64_t, int64_t>> keys((size_t)nf);
+  std::vector<int32_t> cf_cfg((size_t)nf);
+  for (int i = 0; i < n_cfg; ++i)
+    for (int64_t j = cf_off[i]; j < cf_off[i + 1]; ++j) {
+      keys[(size_t)j] = std::make_pair(comp[i].fkey[(size_t)(j - cf_off[i])], j);
+      cf_cfg[(size_t)j] = i;
     }
-    d.status = status[i];
-    d.field_begin = (int32_t)p->hfld.size();
-    p->cfg_cf_begin[i] = (int32_t)p->hfld.size();
-    if (status[i] == WS_OK) {
+  std::sort(keys.begin(), keys.end());
+  std::vector<int32_t> acc_b((size_t)nf), iv_b((size_t)nf);
+  std::vector<char> owner((size_t)nf, 0);
+  int64_t na = 0, ni = 0;
+  for (size_t r = 0; r < keys.size();) {
+    size_t e = r;
+    while (e < keys.size() && keys[e].first == keys[r].first) ++e;
+    const int64_t j0 = keys[r].second;
+    const int i0 = cf_cfg[(size_t)j0];
+    const size_t k0 = (size_t)(j0 - cf_off[i0]);
+    owner[(size_t)j0] = 1;
+    for (size_t q = r; q < e; ++q) {
+      acc_b[(size_t)keys[q].second] = (int32_t)na;
+      iv_b[(size_t)keys[q].second] = (int32_t)ni;
+    }
+    na += (int64_t)comp[i0].acc[k0].size();
+    ni += (int64_t)comp[i0].iv[k0].size();
+    r = e;
+  }
+  hacc.resize((size_t)na);
+  hiv.resize((size_t)ni);
+  p->hfld.resize((size_t)nf);
+  p->need_words.resize((size_t)nf);
+  for (int i = 0; i <= n_cfg; ++i) p->cfg_cf_begin[i] = (int32_t)cf_off[i];
+  auto fill = [&](int t, int nth) {
+    for (int i = t; i < n_cfg; i += nth) {
+      DCfg &d = hcfg[i];
+      if (status[i] == WS_OK) d = comp[i].d;
+      else memset(&d, 0, sizeof(d));
+      d.status = status[i];
+      d.field_begin = (int32_t)cf_off[i];
+      if (status[i] != WS_OK) {
+        d.n_field = 0;
+        continue;
+      }
       for (size_t k = 0; k < comp[i].f.size(); ++k) {
+        const size_t j = (size_t)cf_off[i] + k;
         DField f = comp[i].f[k];
         f.cfg = i;
-        // candidates sharing a field and a folding share its access list on the device
-        auto it = acc_at.find(comp[i].fkey[k]);
-        if (it == acc_at.end()) {
-          it = acc_at.emplace(comp[i].fkey[k], (int32_t)hacc.size()).first;
-          hacc.insert(hacc.end(), comp[i].acc[k].begin(), comp[i].acc[k].end());
+        f.acc_begin = acc_b[j];
+        f.iv_begin = iv_b[j];
+        p->hfld[j] = f;
+        p->need_words[j] = comp[i].need_words[k];
+        if (owner[j]) {
+          std::copy(comp[i].acc[k].begin(), comp[i].acc[k].end(), hacc.begin() + acc_b[j]);
+          std::copy(comp[i].iv[k].begin(), comp[i].iv[k].end(), hiv.begin() + iv_b[j]);
         }
-        f.acc_begin = it->second;
-        auto jt = iv_at.find(comp[i].fkey[k]);
-        if (jt == iv_at.end()) {
-          jt = iv_at.emplace(comp[i].fkey[k], (int32_t)hiv.size()).first;
-          hiv.insert(hiv.end(), comp[i].iv[k].begin(), comp[i].iv[k].end());
-        }
-        f.iv_begin = jt->second;
-        p->hfld.push_back(f);
-        p->need_words.push_back(comp[i].need_words[k]);
       }
+    }
+  };
+  {
+    const int nth = n_cfg >= 256 ? (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency())) : 1;
+    if (nth == 1) {
+      fill(0, 1);
     } else {
-      d.n_field = 0;
+      std::vector<std::thread> pool;
+      for (int t = 0; t < nth; ++t) pool.emplace_back(fill, t, nth);
+      for (auto &th : pool) th.join();
     }
   }
   p->cfg_cf_begin[n_cfg] = (int32_t)p->hfld.size();

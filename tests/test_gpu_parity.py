@@ -246,7 +246,7 @@ def test_interval_and_address_walks_identical(ctx):
     rng = W.SplitMix64(77)
     cfgs = (W.stencil_25pt_sweep(N=(160, 128, 96))[::9] + W.lbm_sweep(N=(96, 64, 48))[::37] +
             W.mixed_set(2000)[::50] + edge_configs() + [random_tiny(rng) for _ in range(100)])
-    outs = []
+    outs, stats = [], []
     for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
@@ -255,7 +255,13 @@ def test_interval_and_address_walks_identical(ctx):
             p.execute(B.WS_MODE_PLAIN)
             res2, order2 = p.results()
             assert res2.tobytes() == res.tobytes() and order2.tobytes() == order.tobytes()
+            prof = p.profile()
+            # address evaluations and modelled (warp, instruction) pairs are properties of
+            # the candidates, however they are walked
+            stats.append((prof["addresses"], prof["warp_instr"], prof["block_addresses"]))
     assert outs[0] == outs[1] == outs[2]
+    assert stats[0] == stats[1] == stats[2], stats
+    assert stats[0][0] > stats[0][2] > 0
 
 
 def test_multi_pass_equals_single_pass(ctx):
