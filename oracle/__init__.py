@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CFG_NI, FLD_NI, ACC_NI, HW_ND = 12, 8, 5, 26
+CFG_NI, FLD_NI, ACC_NI, HW_ND = 13, 8, 5, 26
 INT_KEYS = ["status", "lups_block", "lups_wave", "l1_req_sectors", "l1_bank_cycles",
             "l1_store_sectors", "blk_load_sectors", "blk_load_lines", "blk_store_sectors",
             "blk_store_lines", "wave_load_sectors", "wave_load_lines", "wave_store_sectors",
@@ -89,7 +89,8 @@ def flatten(configs, hw):
                 for a in f.accesses:
                     accs.append([a.dx, a.dy, a.dz, a.is_store, a.dc])
         cfg_i[i] = [c.N[0], c.N[1], c.N[2], c.B[0], c.B[1], c.B[2], c.fold_axis, c.fold,
-                    len(c.fields), seen[key], c.regs_per_thread, c.wave_blocks_override]
+                    len(c.fields), seen[key], c.regs_per_thread, c.wave_blocks_override,
+                    getattr(c, "address_mode", 0)]
         cfg_d[i] = c.flops_per_lup
     fld_i = np.array(flds, np.int64).reshape(-1, FLD_NI)
     acc_i = np.array(accs, np.int64).reshape(-1, ACC_NI)

@@ -8,7 +8,8 @@
 //     x 8 B, 1024 B pairing distance);
 //   * one representative block (Sec. 3.3) and one wave of co-resident blocks in the
 //     middle of the grid (Sec. 3.4), plus the y and z layer-condition thread sets
-//     (Sec. 3.4.2);
+//     (Sec. 3.4.2), the wave-level sets in linear addresses or, optionally, in the
+//     multi-dimensional address space of Sec. 3.4.1;
 //   * capacity misses (Sec. 3.5, Eqs. for V_cap and R_hit(O)) and the four-limiter
 //     performance model (Sec. 2).
 // Every set is a std::set; every count is the size of a set.  Floating point is fp64
@@ -35,7 +36,7 @@ struct OField {
 };
 
 struct OCfg {
-  int64_t N[3], B[3], fold_axis, fold, regs, wave_override;
+  int64_t N[3], B[3], fold_axis, fold, regs, wave_override, addr_mode;
   double flops;
   std::vector<OField> fields;
 };
@@ -153,10 +154,23 @@ int64_t bank_cycles(const OHw &hw, const std::vector<int64_t> &addrs) {
   return cycles;
 }
 
+// A sector or line of the wave-level sets.  Linear addresses: (address / unit, 0, 0).
+// Multi-dimensional address space (Sec. 3.4.1): the innermost coordinate in bytes
+// divided by the unit, and the y and z array coordinates; the base alignment is not
+// part of it, and two tuples are distinct when any coordinate differs.
+typedef std::tuple<int64_t, int64_t, int64_t> Key3;
+
+Key3 wave_key(const OCfg &c, const OField &f, const Thread &t, const Off &o, int64_t unit) {
+  if (c.addr_mode == 0) return Key3(floordiv(address(f, t, o), unit), 0, 0);
+  // reading: the constant and component offsets are part of the innermost coordinate
+  const int64_t xe = f.stride[0] * (t.p[0] + std::get<0>(o)) + f.c + std::get<3>(o);
+  return Key3(floordiv(f.esize * xe, unit), t.p[1] + std::get<1>(o), t.p[2] + std::get<2>(o));
+}
+
 struct FieldSets {
   std::set<int64_t> blk_ls, blk_ll, blk_ss, blk_sl;            // block: load/store sectors/lines
-  std::set<int64_t> w_ls, w_ll, w_ss, w_sl;                    // wave
-  std::set<int64_t> y_ls, y_ll, z_ls, z_ll;                    // layer-condition sets
+  std::set<Key3> w_ls, w_ll, w_ss, w_sl;                       // wave
+  std::set<Key3> y_ls, y_ll, z_ls, z_ll;                       // layer-condition sets
 };
 
 double rhat(const double h[3], double O) { return h[0] * std::exp(-h[1] * std::exp(-h[2] * O)); }
@@ -169,7 +183,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
   int64_t T = c.B[0] * c.B[1] * c.B[2];
   bool ok = c.fields.size() > 0 && T >= 1 && T <= 1024 && c.B[2] <= 64 && c.fold >= 1 &&
             c.fold <= 16 && (c.fold_axis != 0 || c.fold == 1) && c.fold_axis >= 0 &&
-            c.fold_axis <= 2;
+            c.fold_axis <= 2 && (c.addr_mode == 0 || c.addr_mode == 1);
   for (int d = 0; d < 3; ++d) ok = ok && c.N[d] >= 1 && c.B[d] >= 1;
   for (const OField &f : c.fields) ok = ok && f.esize >= 1 && (f.loads.size() + f.stores.size()) > 0;
   // blocks per SM: thread slots are allocated per warp
@@ -272,12 +286,11 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
             const std::vector<Off> &list = st ? f.fstore : f.fload;
             const std::set<Off> &offs = st ? f.stores : f.loads;
             for (const Off &o : list) {
-              std::set<int64_t> warp_sectors;
+              std::set<Key3> warp_sectors;
               for (int64_t l = 0; l < 32; ++l) {
                 const Thread &t = lanes[l];
                 if (!t.valid || !access_needed(c, offs, o, t.kv)) continue;
-                int64_t a = address(f, t, o);
-                int64_t sec = floordiv(a, 32), line = floordiv(a, 128);
+                const Key3 sec = wave_key(c, f, t, o, 32), line = wave_key(c, f, t, o, 128);
                 if (lev == 0 && st) {
                   fs[fi].w_ss.insert(sec);
                   fs[fi].w_sl.insert(line);
@@ -308,7 +321,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
     bls += f.blk_ls.size(); bll += f.blk_ll.size(); bss += f.blk_ss.size(); bsl += f.blk_sl.size();
     wls += f.w_ls.size(); wll += f.w_ll.size(); wss += f.w_ss.size(); wsl += f.w_sl.size();
     yl += f.y_ll.size(); zl += f.z_ll.size();
-    for (int64_t x : f.w_ls) {
+    for (const Key3 &x : f.w_ls) {
       if (f.y_ls.count(x)) ovy += 1;
       else if (f.z_ls.count(x)) ovz += 1;   // in the z footprint but not the y footprint
     }
@@ -412,6 +425,7 @@ extern "C" int orc_estimate(int n_cfg, const int64_t *cfg_i, const double *cfg_d
     c.fold = ci[7];
     c.regs = ci[10];
     c.wave_override = ci[11];
+    c.addr_mode = ci[12];
     c.flops = cfg_d[i];
     for (int64_t fi = 0; fi < ci[8]; ++fi) {
       const int64_t *f = fld_i + (ci[9] + fi) * ORC_FLD_NI;

@@ -10,7 +10,7 @@
  * Flat input layout (all arrays row-major, one row per item):
  *   cfg_i [n_cfg][ORC_CFG_NI] int64:
  *       Nx Ny Nz Bx By Bz fold_axis(0 none,1 y,2 z) fold n_field field_off
- *       regs_per_thread wave_blocks_override
+ *       regs_per_thread wave_blocks_override address_mode(0 linear, 1 multi-dimensional)
  *   cfg_d [n_cfg] double: flops per lattice update
  *   fld_i [..][ORC_FLD_NI] int64:
  *       elem_bytes align sx sy sz const_off n_access access_off
@@ -26,7 +26,7 @@
 #define WS_ORACLE_H
 #include <stdint.h>
 
-#define ORC_CFG_NI 12
+#define ORC_CFG_NI 13
 #define ORC_FLD_NI 8
 #define ORC_ACC_NI 5
 #define ORC_HW_ND 26

@@ -68,6 +68,7 @@ class Config:
     regs_per_thread: int = 0
     wave_blocks_override: int = 0
     name: str = ""
+    address_mode: int = 0        # 0 linear addresses, 1 multi-dimensional address space (Sec. 3.4.1)
 
 
 @dataclass

@@ -94,6 +94,20 @@ def addresses(f, p, o):
     return f.align + f.elem_bytes * e
 
 
+def wave_keys(c, f, p, o, unit):
+    """Sector (unit 32) or line (unit 128) identities of the wave-level sets.  Linear
+    mode: the address divided by the unit.  Multi-dimensional address space (Sec. 3.4.1):
+    the tuple (innermost coordinate in bytes // unit, y, z) without the base alignment,
+    packed into one integer (tiny grids only)."""
+    if getattr(c, "address_mode", 0) == 0:
+        return np.floor_divide(addresses(f, p, o), unit)
+    xe = f.strides[0] * (p[0] + o[0]) + f.const_off + o[3]
+    xu = np.floor_divide(f.elem_bytes * xe, unit)
+    yy, zz = p[1] + o[1], p[2] + o[2]
+    assert np.all(np.abs(xu) < (1 << 29)) and np.all(np.abs(yy) < 1000) and np.all(np.abs(zz) < 1000)
+    return (xu + (1 << 30)) + (1 << 31) * ((yy + 1024) + 2048 * (zz + 1024))
+
+
 def bank_cycles(addrs, hw):
     words = np.unique(np.floor_divide(addrs, hw.bank_bytes))
     cycles, i = 0, 0
@@ -130,13 +144,18 @@ def count(c, hw):
             for st, offs in ((0, loads), (1, stores)):
                 if st and level in ("y", "z"):
                     continue
-                all_a = []
+                all_s, all_l = [], []
                 for o in folded(c, offs):
                     m = needed(c, offs, o, kv)
                     a = addresses(f, p, o)[m]
-                    all_a.append(a)
+                    if level == "rep":
+                        ks, kl = np.floor_divide(a, 32), np.floor_divide(a, 128)
+                    else:
+                        ks, kl = wave_keys(c, f, p, o, 32)[m], wave_keys(c, f, p, o, 128)[m]
+                    all_s.append(ks)
+                    all_l.append(kl)
                     if level in ("rep", "wave"):
-                        wsec = np.unique(np.stack([warp[m], np.floor_divide(a, 32)]), axis=1)
+                        wsec = np.unique(np.stack([warp[m], ks]), axis=1)
                         if level == "rep":
                             res["l1_store_sectors" if st else "l1_req_sectors"] += wsec.shape[1]
                         elif st:
@@ -145,8 +164,9 @@ def count(c, hw):
                         hw_id = warp[m] * 2 + lane[m] // 16
                         for h in np.unique(hw_id):
                             res["l1_bank_cycles"] += bank_cycles(a[hw_id == h], hw)
-                a = np.concatenate(all_a) if all_a else np.zeros(0, np.int64)
-                sets[(level, st)] = (np.unique(np.floor_divide(a, 32)), np.unique(np.floor_divide(a, 128)))
+                ks = np.concatenate(all_s) if all_s else np.zeros(0, np.int64)
+                kl = np.concatenate(all_l) if all_l else np.zeros(0, np.int64)
+                sets[(level, st)] = (np.unique(ks), np.unique(kl))
         res["blk_load_sectors"] += len(sets[("rep", 0)][0])
         res["blk_load_lines"] += len(sets[("rep", 0)][1])
         res["blk_store_sectors"] += len(sets[("rep", 1)][0])
