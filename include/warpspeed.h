@@ -100,8 +100,15 @@ typedef struct ws_config {
   int64_t field_off;
   double flops_per_lup;
   int32_t wave_blocks_override;
-  int32_t reserved; /* must be 0 */
+  int32_t address_mode; /* WS_ADDR_LINEAR: linear byte addresses everywhere.
+                           WS_ADDR_MULTIDIM: the wave and the y / z layer sets count in the
+                           multi-dimensional address space of Sec. 3.4.1 -- a sector is
+                           (innermost coordinate in bytes / 32, y, z), the base alignment is
+                           ignored and a line wrapping to the next row counts at both ends;
+                           the representative block keeps linear addresses.               */
 } ws_config; /* 64 bytes */
+
+enum { WS_ADDR_LINEAR = 0, WS_ADDR_MULTIDIM = 1 };
 
 /* Modelled GPU (Table 1 of the paper; the A100-SXM4-40G column with a 20 MB effective
  * L2 is the reference setting).  Rates in bytes/s, flop/s and Hz; sizes in bytes.
@@ -248,9 +255,29 @@ typedef struct ws_field_info {
  * argument; per-candidate problems go to out[i].status. */
 int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
                 const ws_hw *hw, ws_cfg_info *out);
-/* Per-field bitmap ranges of one candidate; out holds cfg->n_field entries. */
+/* Per-field bitmap ranges of one candidate; out holds cfg->n_field entries (for
+ * WS_ADDR_MULTIDIM the wave range is the one of the virtual row-slab layout). */
 int ws_describe_fields(const ws_config *cfg, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
                        const ws_hw *hw, ws_field_info *out);
+
+/* Sizes of the plan a batch would make (host only, no device needed): the descriptor
+ * compiler, the sharing of access lists, field groups, scratch passes and work items run
+ * exactly as in ws_plan_create, with `scratch_bytes` of bitmap scratch available. */
+typedef struct ws_plan_summary {
+  int64_t candidates_ok;      /* candidates that compiled (the others get an error status) */
+  int64_t fields;             /* field descriptors (a multi-dimensional candidate has two per field) */
+  int64_t groups;             /* field groups */
+  int64_t passes;             /* scratch passes */
+  int64_t enum_items, row_items, count_items;   /* work items of the three kernels */
+  int64_t access_entries;     /* folded access list entries after sharing */
+  int64_t interval_entries;   /* merged load run entries after sharing */
+  int64_t descriptor_bytes;   /* device bytes of descriptors, counters and results */
+  int64_t scratch_bytes;      /* bitmap scratch the plan takes */
+  int64_t bitmap_bytes;       /* bitmap bytes of all fields (what one pass would need) */
+} ws_plan_summary; /* 96 bytes */
+int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
+                    int n_acc, const ws_hw *hw, const ws_tuning *tuning, size_t scratch_bytes,
+                    ws_plan_summary *out);
 
 /* One-shot estimate from host buffers: plan_create + execute + results + destroy.
  * out: n_cfg results; order_out (may be NULL): ranking of the whole batch.  In

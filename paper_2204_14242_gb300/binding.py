@@ -26,7 +26,7 @@ FIELD = np.dtype([("elem_bytes", "<i4"), ("n_access", "<i4"), ("align_bytes", "<
                   ("const_off", "<i8"), ("access_off", "<i8")], align=True)
 CONFIG = np.dtype([("N", "<i4", (3,)), ("B", "<i4", (3,)), ("fold_axis", "<i4"), ("fold", "<i4"),
                    ("n_field", "<i4"), ("regs_per_thread", "<i4"), ("field_off", "<i8"),
-                   ("flops_per_lup", "<f8"), ("wave_blocks_override", "<i4"), ("reserved", "<i4")], align=True)
+                   ("flops_per_lup", "<f8"), ("wave_blocks_override", "<i4"), ("address_mode", "<i4")], align=True)
 HW = np.dtype([("sms", "<i4"), ("max_threads_sm", "<i4"), ("max_blocks_sm", "<i4"), ("regs_sm", "<i4"),
                ("clock_hz", "<f8"), ("l1_bytes", "<f8"), ("l2_bytes", "<f8"), ("bw_l2", "<f8"),
                ("bw_dram", "<f8"), ("fp_peak", "<f8"), ("banks", "<i4"), ("bank_bytes", "<i4"),
@@ -42,6 +42,9 @@ RESULT = np.dtype([(k, "<i8") for k in RESULT_INT] + [(k, "<f8") for k in RESULT
                   [("limiter", "<i4"), ("status", "<i4")], align=True)
 TUNING = np.dtype([("chunk_warps", "<i4"), ("enum_threads", "<i4"), ("count_words", "<i4"),
                    ("ctas_per_sm", "<i4"), ("pass_mb", "<i4"), ("walk", "<i4")], align=True)
+PLAN_SUMMARY = np.dtype([(k, "<i8") for k in (
+    "candidates_ok", "fields", "groups", "passes", "enum_items", "row_items", "count_items", "access_entries",
+    "interval_entries", "descriptor_bytes", "scratch_bytes", "bitmap_bytes")], align=True)
 PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4"), ("ms_model", "<f4"),
                     ("ms_rank", "<f4"), ("ms_rows", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),
@@ -68,12 +71,13 @@ WS_OK, WS_EINVAL, WS_ENOMEM, WS_EAGAIN, WS_ETIMEDOUT, WS_EOVERFLOW, WS_ECUDA, WS
     0, -1, -2, -3, -4, -5, -6, -7, -8
 WS_MODE_PLAIN, WS_MODE_BATCHED, WS_MODE_DIRECT = 0, 1, 2
 WS_WALK_INTERVAL, WS_WALK_ADDRESS, WS_WALK_SEGMENT = 0, 1, 2
+WS_ADDR_LINEAR, WS_ADDR_MULTIDIM = 0, 1
 
 EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_create", "ws_destroy",
            "ws_plan_create", "ws_plan_execute", "ws_plan_results", "ws_plan_device_results", "ws_plan_profile",
            "ws_autotune", "ws_plan_destroy", "ws_estimate_batch", "ws_rank", "ws_rank_key", "ws_server_create",
            "ws_server_submit", "ws_server_poll", "ws_server_stats_get", "ws_server_destroy", "ws_describe",
-           "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc"]
+           "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc", "ws_plan_dry_run"]
 
 
 class WsError(RuntimeError):
@@ -128,6 +132,7 @@ def load(build_if_missing: bool = False):
             "ws_server_destroy": ([P], I), "ws_describe": ([P, I, P, I, P, I, P, P], I),
             "ws_describe_fields": ([P, P, I, P, I, P, P], I), "ws_measure_peaks": ([P, P, P], I),
             "ws_estimate_batch_noalloc": ([I, P, I, P, I, P, I, P, P, P, P], I),
+            "ws_plan_dry_run": ([P, I, P, I, P, I, P, P, ctypes.c_size_t, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -181,6 +186,7 @@ def marshal(configs: Sequence) -> tuple:
         row["field_off"] = seen[key]
         row["flops_per_lup"] = c.flops_per_lup
         row["wave_blocks_override"] = c.wave_blocks_override
+        row["address_mode"] = getattr(c, "address_mode", 0)
     fld = np.array(fields_rows, FIELD) if fields_rows else np.zeros(0, FIELD)
     acc = np.array(acc_rows, ACCESS) if acc_rows else np.zeros(0, ACCESS)
     return cfg, fld, acc
@@ -224,6 +230,23 @@ def ws_describe_fields(config, hw) -> np.ndarray:
     _check(load().ws_describe_fields(cfg.ctypes.data, _ptr(fld), len(fld), _ptr(acc), len(acc), h.ctypes.data,
                                      out.ctypes.data), "ws_describe_fields")
     return out
+
+
+def ws_plan_dry_run(configs=None, hw=None, tuning=None, scratch_bytes=48 << 30, arrays=None) -> dict:
+    """Sizes of the plan a batch would make, without a device (host descriptor compiler,
+    list sharing, groups, passes, work items)."""
+    cfg, fld, acc = arrays if arrays is not None else marshal(configs)
+    h = hw if isinstance(hw, np.ndarray) else hw_struct(hw)
+    tun = None
+    if tuning is not None:
+        tun = np.zeros(1, TUNING)
+        for k, v in dict(tuning).items():
+            tun[0][k] = v
+    out = np.zeros(1, PLAN_SUMMARY)
+    _check(load().ws_plan_dry_run(_ptr(cfg), len(cfg), _ptr(fld), len(fld), _ptr(acc), len(acc), h.ctypes.data,
+                                  tun.ctypes.data if tun is not None else None, int(scratch_bytes),
+                                  out.ctypes.data), "ws_plan_dry_run")
+    return {k: int(out[0][k]) for k in PLAN_SUMMARY.names}
 
 
 def ws_version() -> int:

@@ -85,6 +85,7 @@ struct DField {
   int32_t iv_begin;       // first merged load interval (DIv array)
   int32_t n_iv;           // merged load intervals
   int32_t rows_ok;        // stores: the row segments of one warp never share a sector
+  int32_t level_mask;     // levels served: 1 the representative block, 2 wave + y / z sets
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };
@@ -133,6 +134,8 @@ struct DGroup {
   int32_t n_iv;           // merged load intervals of all its fields
   int32_t rows;           // levels 1-3 take the row walk (work items are chunks of row slots)
   int32_t n0_items;       // enumeration items of the representative block
+  int32_t levels;         // level mask of its fields (1 block, 2 wave + y / z, 3 both)
+  int32_t first_wave;     // the candidate's first group with wave work counts the wave LUPs
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch

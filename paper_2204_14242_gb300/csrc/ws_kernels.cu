@@ -712,11 +712,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       const bool valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
       int kv = 0;
       if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
-      if (s_g.first_of_cfg && level <= 1) {
-        const uint32_t l = __reduce_add_sync(FULL, (uint32_t)kv);
-        if (level == 0) acc_lb += l;
-        else acc_lw += l;
-      }
+      if (s_g.first_wave && level == 1) acc_lw += __reduce_add_sync(FULL, (uint32_t)kv);
       const uint32_t vmask = __ballot_sync(FULL, valid);
       // a thread with fewer valid folded points than the fold skips some accesses; such
       // warps (only at the domain edge) bound-check every address
@@ -1201,7 +1197,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         const int64_t nx = xb - xa;
         unsigned long long *const ctr = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
         if (lane == 0u) {
-          if (lv == 0 && s_g.first_of_cfg) atomicAdd(ctr + C_LUPS_WAVE, (unsigned long long)(nx * kv));
+          if (lv == 0 && s_g.first_wave) atomicAdd(ctr + C_LUPS_WAVE, (unsigned long long)(nx * kv));
           atomicAdd(ctr + C_ADDR, (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]));
         }
         const int64_t el0 = es * (F0.stride[1] * y + F0.stride[2] * z);

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <climits>
 #include <fstream>
+#include <functional>
 #include <map>
 #include <unordered_map>
 #include <mutex>
@@ -266,6 +267,12 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
   }
 }
 
+// Key of a field's folded access list: equal keys have equal lists.
+static uint64_t fold_key(const ws_config &c, int fi) {
+  return ((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold;
+}
+static const uint64_t kNoShare = ~(uint64_t)0;   // a list that no other descriptor shares
+
 // Returns WS_OK or a per-candidate error status.  `cache` (may be null) memoizes the
 // per-(field, folding) part across candidates that share fields.
 static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
@@ -283,6 +290,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   if (c.fold_axis == 0 && c.fold != 1) return WS_EINVAL;
   if (c.n_field < 1 || c.field_off < 0 || c.field_off + c.n_field > n_fld) return WS_EINVAL;
   if (c.regs_per_thread < 0 || c.wave_blocks_override < 0) return WS_EINVAL;
+  if (c.address_mode != WS_ADDR_LINEAR && c.address_mode != WS_ADDR_MULTIDIM) return WS_EINVAL;
   if (!(c.flops_per_lup >= 0.0) || std::isinf(c.flops_per_lup)) return WS_EINVAL;
   d.fold_axis = c.fold_axis;
   d.fold = c.fold;
@@ -414,28 +422,15 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     }
   }
 
-  // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps
+  // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps.
+  // `mask`: levels the descriptor serves (1 the representative block, 2 the wave and the
+  // y / z sets); `key`: list-sharing key (kNoShare = never shared)
   out.f.clear();
   out.acc.clear();
   out.iv.clear();
   out.fkey.clear();
   out.need_words.clear();
-  for (int fi = 0; fi < c.n_field; ++fi) {
-    const ws_field &F = fld[c.field_off + fi];
-    FieldFold local;
-    const FieldFold *ff = &local;
-    if (cache) {
-      const uint64_t key = ((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold;
-      auto it = cache->find(key);
-      if (it == cache->end()) {
-        it = cache->emplace(key, FieldFold()).first;
-        compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, it->second);
-      }
-      ff = &it->second;
-    } else {
-      compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, local);
-    }
-    if (ff->status != WS_OK) return ff->status;
+  auto emit = [&](const ws_field &F, const FieldFold *ff, int mask, uint64_t key, bool first) -> int {
     DField df;
     memset(&df, 0, sizeof(df));
     df.esize = F.elem_bytes;
@@ -443,10 +438,13 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.base = F.align_bytes + (int64_t)F.elem_bytes * F.const_off;
     df.n_load = ff->n_load;
     df.n_store = ff->n_store;
-    const std::vector<DAcc> &da = ff->da;
+    df.level_mask = mask;
     const __int128 omin = ff->omin, omax = ff->omax;
     // address range of each level: valid point box x raw offsets
     for (int lv = 0; lv < 2; ++lv) {
+      df.lo[lv] = 0;
+      df.words[lv] = 0;
+      if (!(mask & (1 << lv))) continue;
       __int128 pmin = 0, pmax = 0;
       for (int k = 0; k < 3; ++k) {
         __int128 a0 = (__int128)F.stride[k] * pb_lo[lv][k], a1 = (__int128)F.stride[k] * pb_hi[lv][k];
@@ -465,9 +463,9 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       df.words[lv] = words;
     }
     const bool has_l = df.n_load > 0, has_s = df.n_store > 0;
-    df.mw_end = has_l ? d.lev_end[3] : d.lev_end[1];
     df.mw_block = d.lev_end[0];
-    df.first_of_cfg = fi == 0;
+    df.mw_end = !(mask & 2) ? d.lev_end[0] : has_l ? d.lev_end[3] : d.lev_end[1];
+    df.first_of_cfg = first;
     df.wide = (df.words[0] >= ((int64_t)1 << 22) || df.words[1] >= ((int64_t)1 << 22)) ? 1 : 0;
     df.lpa_log2p = 0;
     while ((1 << df.lpa_log2p) < std::min(df.n_load, 32)) ++df.lpa_log2p;
@@ -508,10 +506,95 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     if (has_l) need += df.words[0] + 3 * df.words[1];
     if (has_s) need += df.words[0] + df.words[1];
     out.f.push_back(df);
-    out.acc.push_back(da);
+    out.acc.push_back(ff->da);
     out.iv.push_back(ff->iv);
-    out.fkey.push_back(((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold);
+    out.fkey.push_back(key);
     out.need_words.push_back(need);
+    return WS_OK;
+  };
+  auto fold_of = [&](int fi, FieldFold &local) -> const FieldFold * {
+    const ws_field &F = fld[c.field_off + fi];
+    if (!cache) {
+      compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, local);
+      return &local;
+    }
+    auto it = cache->find(fold_key(c, fi));
+    if (it == cache->end()) {
+      it = cache->emplace(fold_key(c, fi), FieldFold()).first;
+      compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, it->second);
+    }
+    return &it->second;
+  };
+  if (c.address_mode == WS_ADDR_LINEAR) {
+    for (int fi = 0; fi < c.n_field; ++fi) {
+      FieldFold local;
+      const FieldFold *ff = fold_of(fi, local);
+      if (ff->status != WS_OK) return ff->status;
+      const int rc = emit(fld[c.field_off + fi], ff, 3, fold_key(c, fi), fi == 0);
+      if (rc != WS_OK) return rc;
+    }
+  } else {
+    // Multi-dimensional address space (Sec. 3.4.1) for the wave and the y / z sets: a
+    // sector is (innermost bytes / 32, y, z), without the base alignment.  Each field
+    // becomes a block descriptor (linear addresses, as the per-instruction statistics
+    // of the representative block need) and a wave descriptor over a virtual linear
+    // layout in which every (y, z) row is its own 128-byte aligned slab of RS bytes:
+    // virtual address = Xbias + innermost bytes + RS * (y - y0) + PS * (z - z0), so
+    // that virtual sectors and lines are exactly the tuples.  RS and PS are common to
+    // the candidate's fields (equal layouts stay one uniform group).
+    std::vector<const FieldFold *> ffs(c.n_field);
+    std::vector<FieldFold> locals(c.n_field);
+    for (int fi = 0; fi < c.n_field; ++fi) {
+      ffs[fi] = fold_of(fi, locals[fi]);
+      if (ffs[fi]->status != WS_OK) return ffs[fi]->status;
+      const int rc = emit(fld[c.field_off + fi], ffs[fi], 1, fold_key(c, fi), fi == 0);
+      if (rc != WS_OK) return rc;
+    }
+    __int128 ymin = 0, ymax = 0, zmin = 0, zmax = 0;
+    std::vector<__int128> xlo(c.n_field), xhi(c.n_field);
+    int64_t L = 128;
+    for (int fi = 0; fi < c.n_field; ++fi) {
+      const ws_field &F = fld[c.field_off + fi];
+      int64_t r[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // dx dy dz dc ranges of the raw offsets
+      for (int a = 0; a < F.n_access; ++a) {
+        const ws_access &A = acc[F.access_off + a];
+        const int64_t v[4] = {A.dx, A.dy, A.dz, A.dc};
+        for (int q = 0; q < 4; ++q) {
+          r[q][0] = a == 0 ? v[q] : std::min(r[q][0], v[q]);
+          r[q][1] = a == 0 ? v[q] : std::max(r[q][1], v[q]);
+        }
+      }
+      const __int128 x0 = (__int128)F.stride[0] * (pb_lo[1][0] + r[0][0]), x1 = (__int128)F.stride[0] * (pb_hi[1][0] + r[0][1]);
+      xlo[fi] = (__int128)F.elem_bytes * (std::min(x0, x1) + F.const_off + r[3][0]);
+      xhi[fi] = (__int128)F.elem_bytes * (std::max(x0, x1) + F.const_off + r[3][1]);
+      const __int128 y0 = pb_lo[1][1] + r[1][0], y1 = pb_hi[1][1] + r[1][1];
+      const __int128 z0 = pb_lo[1][2] + r[2][0], z1 = pb_hi[1][2] + r[2][1];
+      ymin = fi == 0 ? y0 : std::min(ymin, y0);
+      ymax = fi == 0 ? y1 : std::max(ymax, y1);
+      zmin = fi == 0 ? z0 : std::min(zmin, z0);
+      zmax = fi == 0 ? z1 : std::max(zmax, z1);
+      L = L / std::__gcd(L, (int64_t)F.elem_bytes) * F.elem_bytes;
+    }
+    __int128 row = 0;
+    std::vector<__int128> xbias(c.n_field);
+    for (int fi = 0; fi < c.n_field; ++fi) {
+      xbias[fi] = -floor_div128(xlo[fi], 128) * 128;
+      row = std::max(row, xhi[fi] + xbias[fi] + 1);
+    }
+    const __int128 RS = (row + L - 1) / L * L, PS = RS * (ymax - ymin + 1);
+    if (PS * (zmax - zmin + 1) >= ((__int128)1 << 50)) return WS_ENOMEM;
+    for (int fi = 0; fi < c.n_field; ++fi) {
+      const ws_field &F = fld[c.field_off + fi];
+      ws_field V = F;
+      V.stride[1] = (int64_t)(RS / F.elem_bytes);
+      V.stride[2] = (int64_t)(PS / F.elem_bytes);
+      V.align_bytes = (int64_t)(xbias[fi] - RS * ymin - PS * zmin);
+      FieldFold vf;
+      compile_field_fold(V, acc, n_acc, c.fold_axis, c.fold, vf);
+      if (vf.status != WS_OK) return vf.status;
+      const int rc = emit(V, &vf, 2, kNoShare, false);
+      if (rc != WS_OK) return rc;
+    }
   }
   d.n_field = c.n_field;
   return WS_OK;
@@ -657,10 +740,11 @@ void ws_plan::layout() {
     // row walk, chunks of row slots as items of the row kernel
     G.item_begin = items;
     G.ritem_begin = ritems;
-    G.n0_items = (int32_t)std::max<int64_t>(1, ceil_div(G.mw_block * (int64_t)G.acc_count, kBlockPairs));
+    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div(G.mw_block * (int64_t)G.acc_count, kBlockPairs))
+                                : 0;
     items += G.n0_items;
     if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
-    else items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
+    else if (G.levels & 2) items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
   }
   cur.cf_hi = (int)hfld.size();
   cur.grp_hi = ng;
@@ -1041,39 +1125,23 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
   return WS_OK;
 }
 
-int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
-                         const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
-                         const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,
-                         int64_t ext_scratch, size_t ext_scratch_bytes) {
-  if (!ctx || !out || !hw || n_cfg < 0 || n_fld < 0 || n_acc < 0) return WS_EINVAL;
-  if (n_cfg > 0 && (!cfgs || (n_fld > 0 && !fld) || (n_acc > 0 && !acc))) return WS_EINVAL;
-  if (!hw_valid(*hw)) return WS_EINVAL;
-  *out = nullptr;
-  CU(cudaSetDevice(ctx->device));
-  std::vector<int32_t> seg;
-  if (seg_begin && n_seg > 0) {
-    if (seg_begin[0] != 0 || seg_begin[n_seg] != n_cfg) return WS_EINVAL;
-    for (int k = 0; k < n_seg; ++k)
-      if (seg_begin[k + 1] < seg_begin[k]) return WS_EINVAL;
-    seg.assign(seg_begin, seg_begin + n_seg + 1);
-  } else {
-    seg = {0, n_cfg};
-    n_seg = 1;
-  }
-  Plan *p = new Plan();
-  p->ctx = ctx;
-  p->n_cfg = n_cfg;
-  p->n_seg = n_seg;
-  p->hw = *hw;
-  p->dhw = to_dhw(*hw);
-  memset(&p->tune, 0, sizeof(p->tune));
-  if (tuning) p->tune = *tuning;
-  else ws::tuning_cache_lookup(ctx, n_cfg, &p->tune);
-  default_tuning(p->tune);
-
-  std::vector<DCfg> hcfg(n_cfg);
+// Host half of plan creation: compiles the candidates, deduplicates their access lists,
+// builds field groups and cuts passes.  avail_fn(descriptor bytes) gives the scratch
+// capacity.  Needs no device.
+struct HostDesc {
+  std::vector<DCfg> hcfg;
   HostVec<DAcc> hacc;
   HostVec<DIv> hiv;
+  size_t scratch = 0, desc_bytes = 0;
+};
+
+static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                       const ws_access *acc, int n_acc, const ws_hw *hw,
+                       const std::function<size_t(size_t)> &avail_fn, HostDesc &h) {
+  std::vector<DCfg> &hcfg = h.hcfg;
+  HostVec<DAcc> &hacc = h.hacc;
+  HostVec<DIv> &hiv = h.hiv;
+  hcfg.resize(n_cfg);
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   std::vector<Compiled> comp;
   std::vector<int> status;
@@ -1091,12 +1159,11 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     }
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4);
-  size_t avail = ctx->arena->largest_free();
-  avail = avail > dsc + (8 << 20) ? avail - dsc - (8 << 20) : 0;
-  if (ext_scratch >= 0) avail = ext_scratch_bytes;
-  if (scratch_cap) avail = std::min(avail, scratch_cap);
+  const size_t avail = avail_fn(dsc);
   size_t scratch = std::min(total_need, avail);
   scratch = std::max<size_t>(scratch, 16);
+  h.scratch = scratch;
+  h.desc_bytes = dsc;
   for (int i = 0; i < n_cfg; ++i) {
     if (status[i] != WS_OK) continue;
     for (int64_t w : comp[i].need_words)
@@ -1119,8 +1186,9 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   std::vector<char> owner((size_t)nf, 0);
   int64_t na = 0, ni = 0;
   for (size_t r = 0; r < keys.size();) {
-    size_t e = r;
-    while (e < keys.size() && keys[e].first == keys[r].first) ++e;
+    // a run of equal keys shares one list; kNoShare keys are runs of one
+    size_t e = r + 1;
+    while (e < keys.size() && keys[e].first == keys[r].first && keys[r].first != kNoShare) ++e;
     const int64_t j0 = keys[r].second;
     const int i0 = cf_cfg[(size_t)j0];
     const size_t k0 = (size_t)(j0 - cf_off[i0]);
@@ -1183,6 +1251,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     p->cfg_grp_begin[i] = (int32_t)p->hgrp.size();
     const int a = p->cfg_cf_begin[i], b = p->cfg_cf_begin[i + 1];
     int k = a;
+    bool wave_seen = false;
     while (k < b) {
       DGroup G;
       memset(&G, 0, sizeof(G));
@@ -1190,12 +1259,15 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
       G.f_begin = k;
       G.first_of_cfg = k == a;
       G.mw_block = p->hfld[k].mw_block;
+      G.levels = p->hfld[k].level_mask;
+      G.first_wave = (G.levels & 2) && !wave_seen;
+      wave_seen = wave_seen || (G.levels & 2);
       int64_t need = 0;
       while (k < b) {
         const DField &f = p->hfld[k];
         const int na = f.n_load + f.n_store;
         if (G.f_count > 0 && (G.f_count >= kMaxGroupFields || G.acc_count + na > kMaxFoldedAccesses ||
-                              need + p->need_words[k] > p->scratch_words))
+                              need + p->need_words[k] > p->scratch_words || f.level_mask != G.levels))
           break;
         G.f_count += 1;
         G.acc_count += na;
@@ -1221,7 +1293,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
       G.iv = G.iv && G.uniform;
       if (G.iv) p->iv_cap = std::max(p->iv_cap, G.n_iv);
       // row walk: interval groups whose store counts add up per row segment
-      bool rows = G.iv && comp[i].rows_geom_ok;
+      bool rows = G.iv && comp[i].rows_geom_ok && (G.levels & 2);
       int64_t instr_w = 0, instr_yz = 0;
       for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
         rows = rows && p->hfld[q].rows_ok;
@@ -1239,6 +1311,50 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
   p->cfg_grp_begin[n_cfg] = (int32_t)p->hgrp.size();
   p->layout();
+}
+
+int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                         const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
+                         const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,
+                         int64_t ext_scratch, size_t ext_scratch_bytes) {
+  if (!ctx || !out || !hw || n_cfg < 0 || n_fld < 0 || n_acc < 0) return WS_EINVAL;
+  if (n_cfg > 0 && (!cfgs || (n_fld > 0 && !fld) || (n_acc > 0 && !acc))) return WS_EINVAL;
+  if (!hw_valid(*hw)) return WS_EINVAL;
+  *out = nullptr;
+  CU(cudaSetDevice(ctx->device));
+  std::vector<int32_t> seg;
+  if (seg_begin && n_seg > 0) {
+    if (seg_begin[0] != 0 || seg_begin[n_seg] != n_cfg) return WS_EINVAL;
+    for (int k = 0; k < n_seg; ++k)
+      if (seg_begin[k + 1] < seg_begin[k]) return WS_EINVAL;
+    seg.assign(seg_begin, seg_begin + n_seg + 1);
+  } else {
+    seg = {0, n_cfg};
+    n_seg = 1;
+  }
+  Plan *p = new Plan();
+  p->ctx = ctx;
+  p->n_cfg = n_cfg;
+  p->n_seg = n_seg;
+  p->hw = *hw;
+  p->dhw = to_dhw(*hw);
+  memset(&p->tune, 0, sizeof(p->tune));
+  if (tuning) p->tune = *tuning;
+  else ws::tuning_cache_lookup(ctx, n_cfg, &p->tune);
+  default_tuning(p->tune);
+
+  HostDesc h;
+  build_host(p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t dsc) {
+    size_t avail = ctx->arena->largest_free();
+    avail = avail > dsc + (8 << 20) ? avail - dsc - (8 << 20) : 0;
+    if (ext_scratch >= 0) avail = ext_scratch_bytes;
+    if (scratch_cap) avail = std::min(avail, scratch_cap);
+    return avail;
+  }, h);
+  std::vector<DCfg> &hcfg = h.hcfg;
+  HostVec<DAcc> &hacc = h.hacc;
+  HostVec<DIv> &hiv = h.hiv;
+  const size_t scratch = h.scratch;
   {
     // raise the enumeration kernel's shared-memory limit now, outside any capture
     int occ = 0;
@@ -1512,16 +1628,51 @@ extern "C" int ws_describe_fields(const ws_config *cfg, const ws_field *fld, int
   Compiled cc;
   int rc = compile_config(*cfg, fld, n_fld, acc, n_acc, *hw, cc);
   if (rc != WS_OK) return rc;
-  for (size_t k = 0; k < cc.f.size(); ++k) {
+  // multi-dimensional candidates compile to a block and a wave descriptor per field:
+  // the block bitmap range comes from the first, the wave range (in the virtual layout)
+  // from the second
+  const size_t n = (size_t)cfg->n_field, w = cfg->address_mode == WS_ADDR_MULTIDIM ? n : 0;
+  for (size_t k = 0; k < n; ++k) {
     ws_field_info &o = out[k];
     memset(&o, 0, sizeof(o));
-    for (int j = 0; j < 2; ++j) {
-      o.lo_sector[j] = cc.f[k].lo[j];
-      o.words[j] = cc.f[k].words[j];
-    }
+    o.lo_sector[0] = cc.f[k].lo[0];
+    o.words[0] = cc.f[k].words[0];
+    o.lo_sector[1] = cc.f[w + k].lo[1];
+    o.words[1] = cc.f[w + k].words[1];
     o.n_load = cc.f[k].n_load;
     o.n_store = cc.f[k].n_store;
   }
+  return WS_OK;
+}
+
+extern "C" int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
+                               const ws_access *acc, int n_acc, const ws_hw *hw, const ws_tuning *tuning,
+                               size_t scratch_bytes, ws_plan_summary *out) {
+  if (!hw || !out || n_cfg < 0 || n_fld < 0 || n_acc < 0) return WS_EINVAL;
+  if (n_cfg > 0 && (!cfgs || (n_fld > 0 && !fld) || (n_acc > 0 && !acc))) return WS_EINVAL;
+  if (!hw_valid(*hw)) return WS_EINVAL;
+  memset(out, 0, sizeof(*out));
+  Plan p;
+  p.n_cfg = n_cfg;
+  p.hw = *hw;
+  p.dhw = to_dhw(*hw);
+  memset(&p.tune, 0, sizeof(p.tune));
+  if (tuning) p.tune = *tuning;
+  default_tuning(p.tune);
+  HostDesc h;
+  build_host(&p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t) { return scratch_bytes; }, h);
+  for (const DCfg &d : h.hcfg) out->candidates_ok += d.status == WS_OK;
+  out->fields = (int64_t)p.hfld.size();
+  out->groups = (int64_t)p.hgrp.size();
+  out->passes = (int64_t)p.passes.size();
+  out->enum_items = p.item_begin_end;
+  out->row_items = p.ritem_begin_end;
+  out->count_items = p.citem_begin_end;
+  out->access_entries = (int64_t)h.hacc.size();
+  out->interval_entries = (int64_t)h.hiv.size();
+  out->descriptor_bytes = (int64_t)h.desc_bytes;
+  out->scratch_bytes = (int64_t)h.scratch;
+  for (int64_t w : p.need_words) out->bitmap_bytes += 4 * w;
   return WS_OK;
 }
 

@@ -50,6 +50,7 @@ def test_struct_layouts_match_the_header():
     assert int(sizes["ws_cfg_info"]) == B.CFG_INFO.itemsize
     assert int(sizes["ws_tuning"]) == B.TUNING.itemsize
     assert int(sizes["ws_profile"]) == B.PROFILE.itemsize
+    assert int(sizes["ws_plan_summary"]) == B.PLAN_SUMMARY.itemsize
 
 
 def test_host_constants_and_rank_key():

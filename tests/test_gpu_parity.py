@@ -264,6 +264,33 @@ def test_interval_and_address_walks_identical(ctx):
     assert stats[0][0] > stats[0][2] > 0
 
 
+def test_multidim_address_space(ctx):
+    """The multi-dimensional address space of Sec. 3.4.1 for the wave-level sets, under
+    each walk, against the oracle; the 7-point case against its closed form."""
+    import dataclasses
+    rng = W.SplitMix64(808)
+    hw = W.Hardware(sms=3, max_blocks_sm=2)
+    md = lambda c: dataclasses.replace(c, address_mode=B.WS_ADDR_MULTIDIM)
+    cfgs = ([md(random_tiny(rng)) for _ in range(150)] + [md(random_uniform_tiny(rng)) for _ in range(150)] +
+            [md(c) for c in edge_configs()])
+    want = oracle.estimate(cfgs, hw, threads=THREADS)
+    for w in want:
+        if w["status"] != 0:
+            w["status"] = B.WS_EINVAL
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
+        with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
+            p.execute(B.WS_MODE_BATCHED)
+            res, order = p.results()
+        assert_match(res, want, what=f"md walk {walk}")
+    res, order = B.ws_estimate_batch(ctx, [md(W.stencil_7pt_128())], W.a100())
+    assert res[0]["wave_load_sectors"] == 848 and res[0]["wave_load_lines"] == 224
+    assert res[0]["ov_y"] == 64 and res[0]["ov_z"] == 480 and res[0]["blk_load_sectors"] == 120
+    sweep = [md(c) for c in W.stencil_25pt_sweep(N=(160, 128, 96))[::29]]
+    want = oracle.estimate(sweep, W.a100(), threads=THREADS)
+    res, order = B.ws_estimate_batch(ctx, sweep, W.a100())
+    assert_match(res, want, what="md 25pt")
+
+
 def test_multi_pass_equals_single_pass(ctx):
     cfgs = W.lbm_sweep(N=(128, 96, 64))[::5]
     hw = W.a100()

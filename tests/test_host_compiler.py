@@ -92,3 +92,37 @@ def test_folded_instruction_counts():
             # 2r + f points, the 4r points off that axis are repeated f times
             assert info["folded_loads"] == 2 * r + f + 4 * r * f
             assert info["folded_stores"] == f
+
+
+@pytest.mark.timeout(120)
+def test_plan_dry_run_host_pipeline():
+    """The host half of plan creation (compile, list sharing, groups, passes, items) on
+    linear and multi-dimensional batches, without a device."""
+    import dataclasses
+    from test_gpu_parity import random_uniform_tiny, edge_configs
+    B.load()
+    hw = W.a100()
+    sweep = W.stencil_25pt_sweep(N=(160, 128, 96))
+    one = B.ws_plan_dry_run(sweep, hw)
+    two = B.ws_plan_dry_run(sweep + sweep, hw)
+    assert one["candidates_ok"] == len(sweep) and one["fields"] == 2 * len(sweep) and one["passes"] == 1
+    # candidates sharing a field and a folding share its lists on the device
+    assert two["access_entries"] == one["access_entries"] and two["fields"] == 2 * one["fields"]
+    assert one["scratch_bytes"] == one["bitmap_bytes"]
+    small = B.ws_plan_dry_run(sweep, hw, scratch_bytes=one["bitmap_bytes"] // 7)
+    assert small["passes"] > 1 and small["count_items"] == one["count_items"]
+    seg = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_SEGMENT})
+    adr = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_ADDRESS})
+    assert one["row_items"] > 0 and seg["row_items"] == 0 and adr["row_items"] == 0
+    assert seg["enum_items"] == adr["enum_items"] > one["enum_items"]
+    # multi-dimensional candidates: a block and a wave descriptor per field; the wave
+    # lists (virtual strides of the candidate) are never shared
+    md = lambda c: dataclasses.replace(c, address_mode=B.WS_ADDR_MULTIDIM)
+    rng = W.SplitMix64(808)
+    batch = [random_tiny(rng) for _ in range(150)] + [random_uniform_tiny(rng) for _ in range(150)] + edge_configs()
+    lin = B.ws_plan_dry_run(batch, W.Hardware(sms=3, max_blocks_sm=2))
+    mdr = B.ws_plan_dry_run([md(c) for c in batch], W.Hardware(sms=3, max_blocks_sm=2))
+    assert mdr["candidates_ok"] == lin["candidates_ok"] and mdr["fields"] == 2 * lin["fields"]
+    m1 = B.ws_plan_dry_run([md(c) for c in sweep[:40]], hw)
+    m2 = B.ws_plan_dry_run([md(c) for c in sweep[:40]] * 2, hw)
+    assert m2["access_entries"] > m1["access_entries"]
