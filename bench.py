@@ -239,7 +239,8 @@ def kernel_rooflines(profs, peaks):
                          "frac": b / 1e9 / hbm, "per_launch": int(last["bitmap_bytes"]), "ms": ms["count_kernel"]}
     top = max(ms, key=ms.get)
     out = dict(k[top])
-    out.update({"kernel": top, "traffic": None, "share": ms[top] / last["ms_total"], "kernels": k})
+    out.update({"kernel": top, "traffic": None, "share": ms[top] / last["ms_total"], "kernels": k,
+                "ms_model": med("ms_model"), "ms_rank": med("ms_rank"), "ms_step_profiled": med("ms_total")})
     return out
 
 

@@ -91,7 +91,7 @@ struct ws_plan {
   int64_t d_grp = -1;
   int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
-          d_order = -1, d_scratch = -1;
+          d_order = -1, d_rank = -1, d_scratch = -1;
   std::vector<int64_t> allocs;
   bool ext_scratch = false;  // scratch lent by a server pool (kept zeroed by the counting kernel)
   cudaGraphExec_t graph_exec = nullptr;

@@ -1,18 +1,19 @@
 // Device side of the metric estimator (sm_103a).
 //
-//   enum_kernel   persistent, work-stealing enumeration of (modelled warp, access) pairs
-//                 of the representative block, the wave and the y / z layer sets
-//                 (Sec. 3.2-3.4).  Each lane evaluates its address expression; the warp
-//                 merges lanes that fall into the same bitmap word (__reduce_or_sync) and
-//                 one lane per word issues a red.or into the field's L2-resident sector
-//                 bitmap.  The same merge yields the per-instruction unique sector count
-//                 (L1 request / write-through volumes).  Block-level warps also compute
-//                 half-warp bank-conflict cycles.
-//   count_kernel  read-and-clear popcount of the bitmaps: unique sectors, unique 128 B
-//                 lines (nibble OR), y / z overlaps by AND / AND-NOT.  Leaves the
-//                 bitmaps zeroed for the next step (only non-zero words are written).
+//   enum_kernel   persistent, work-stealing CTAs.  Representative block (Sec. 3.2, 3.3):
+//                 every (warp, access instruction) pair exactly -- per-instruction unique
+//                 sectors (L1 request / write-through volumes), half-warp bank cycles and
+//                 the block bitmaps.  Wave / y / z sets of field groups that cannot take
+//                 the row walk: per modelled warp, as sector intervals of row segments
+//                 (segment walk) or address by address.
+//   rows_kernel   wave, y set and z set as whole grid rows: each merged load run of a
+//                 row is one sector range set with 64-bit red.or; per-warp store sectors
+//                 by floor sums (Sec. 3.4, closed-form counting instead of implicit sets).
+//   count_kernel  popcounts of the bitmaps: unique sectors, unique 128 B lines (nibble
+//                 OR), y / z overlaps by AND / AND-NOT.  Leaves the bitmaps zeroed for
+//                 the next step (only non-zero positions are written).
 //   model_kernel  fp64 capacity model and limiters (Sec. 2, 3.5), one thread per candidate.
-//   rank_kernel   stable counting rank per segment (Sec. 5.7).
+//   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.7).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -384,28 +385,29 @@ __device__ __forceinline__ bool segment_range(uint32_t th, uint32_t tt, int64_t 
   return true;
 }
 
-// Sum_{i=0}^{n-1} floor((a*i + b) / m) for n, a, b >= 0, m >= 1, by lattice-point
-// counting: with a, b < m and t = floor((a*(n-1) + b) / m) levels, the sum equals
-// t*n minus the number of (i, k) with k <= t and a*i + b < k*m, which is the same kind
-// of sum with the roles of a and m exchanged; the exchanges follow Euclid's algorithm.
-__device__ int64_t floor_sum(int64_t n, int64_t m, int64_t a, int64_t b) {
+// Sum_{i=0}^{n-1} floor((a*i + b) / m) for a, b < m <= 32 and n < 2^31, by lattice-point
+// counting: with t = floor((a*(n-1) + b) / m) levels the sum equals t*n minus the
+// number of (i, k) with k <= t and a*i + b < k*m, which is the same kind of sum with the
+// roles of a and m exchanged; the exchanges follow Euclid's algorithm on (m, a), so all
+// divisors stay below 33.
+__device__ int64_t floor_sum_small(int64_t n, uint32_t m, uint32_t a, uint32_t b) {
   int64_t res = 0, sgn = 1;
   while (n > 0) {
     if (a >= m) {
-      res += sgn * (a / m) * (n * (n - 1) / 2);
+      res += sgn * (int64_t)(a / m) * (n * (n - 1) / 2);
       a %= m;
     }
     if (b >= m) {
-      res += sgn * (b / m) * n;
+      res += sgn * (int64_t)(b / m) * n;
       b %= m;
     }
     if (a == 0) break;
-    const int64_t t = (a * (n - 1) + b) / m;
+    const int64_t t = ((int64_t)a * (n - 1) + b) / m;
     if (t == 0) break;
     res += sgn * t * n;
-    const int64_t nb = m - b + a - 1;
+    const uint32_t nb = m - b + a - 1;
     n = t;
-    const int64_t om = m;
+    const uint32_t om = m;
     m = a;
     a = om;
     b = nb;
@@ -415,13 +417,19 @@ __device__ int64_t floor_sum(int64_t n, int64_t m, int64_t a, int64_t b) {
 }
 
 // Sum_{i<n} floor((P*i + c) / 32) where every term's argument is >= 0 (P of any sign).
+// The multiple-of-32 part of P and c comes out in closed form; what is left is a sum
+// with a, b < 32 (none at all when P is a multiple of 32, as for every fp64 row of four
+// or more threads).
 __device__ __forceinline__ int64_t sum_floor32(int64_t n, int64_t P, int64_t c) {
   if (n <= 0) return 0;
   if (P < 0) {
     c += P * (n - 1);
     P = -P;
   }
-  return floor_sum(n, 32, P, c);
+  int64_t res = (P >> 5) * (n * (n - 1) / 2) + (c >> 5) * n;
+  const uint32_t a = (uint32_t)(P & 31), b = (uint32_t)(c & 31);
+  if (a != 0) res += floor_sum_small(n, 32u, a, b);
+  return res;
 }
 
 // Distinct sectors of one store instruction summed over the warps of a row walk's grid
@@ -1497,47 +1505,52 @@ __global__ void model_kernel(ModelArgs a) {
 
 // Stable rank within segments: rank(i) = #{j in seg : key_j < key_i or
 // (key_j == key_i and j < i)}; NaN counts as +inf.  order[seg_begin + rank(i)] = i.
-__global__ void __launch_bounds__(256) rank_kernel(RankArgs a) {
-  __shared__ double s_key[1024];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i_first = (int64_t)blockIdx.x * blockDim.x;
-  const int64_t i_last = min((int64_t)a.n, i_first + (int64_t)blockDim.x) - 1;
+// Block (x, y) compares its kRankTile candidates with the y-th tile of kRankTile keys of
+// their segments and adds the partial counts to rank[i] (zeroed before); the scatter
+// kernel then places every candidate.
+constexpr int kRankTile = 256;
+
+__device__ __forceinline__ int rank_seg_of(const RankArgs &a, int64_t x) {
+  int lo = 0, hi = a.n_seg;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.seg[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double rank_key_of(double v) {
+  return isnan(v) ? __longlong_as_double(0x7ff0000000000000ll) : v;
+}
+
+__global__ void __launch_bounds__(kRankTile) rank_count_kernel(RankArgs a) {
+  __shared__ double s_key[kRankTile];
+  const int64_t i_first = (int64_t)blockIdx.x * kRankTile;
   if (i_first >= a.n) return;
-  auto seg_of = [&](int64_t x) {
-    int lo = 0, hi = a.n_seg;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (a.seg[mid] <= x) lo = mid;
-      else hi = mid;
-    }
-    return lo;
-  };
-  const int s_first = seg_of(i_first), s_last = seg_of(i_last);
-  const int64_t j_lo = a.seg[s_first], j_hi = a.seg[s_last + 1];
-  int my_seg = i < a.n ? seg_of(i) : -1;
-  int64_t my_lo = my_seg >= 0 ? a.seg[my_seg] : 0, my_hi = my_seg >= 0 ? a.seg[my_seg + 1] : 0;
-  double ki = 0.0;
-  if (i < a.n) {
-    ki = a.keys[i];
-    if (isnan(ki)) ki = __longlong_as_double(0x7ff0000000000000ll);
+  const int64_t i = i_first + threadIdx.x;
+  const int64_t i_last = min((int64_t)a.n, i_first + kRankTile) - 1;
+  const int64_t j_lo = a.seg[rank_seg_of(a, i_first)], j_hi = a.seg[rank_seg_of(a, i_last) + 1];
+  const int64_t t0 = j_lo + (int64_t)blockIdx.y * kRankTile;
+  if (t0 >= j_hi) return;
+  if (t0 + threadIdx.x < j_hi) s_key[threadIdx.x] = rank_key_of(a.keys[t0 + threadIdx.x]);
+  __syncthreads();
+  if (i >= a.n) return;
+  const int my_seg = rank_seg_of(a, i);
+  const int64_t a0 = max(t0, (int64_t)a.seg[my_seg]), a1 = min(t0 + kRankTile, (int64_t)a.seg[my_seg + 1]);
+  const double ki = rank_key_of(a.keys[i]);
+  int cnt = 0;
+  for (int64_t j = a0; j < a1; ++j) {
+    const double kj = s_key[j - t0];
+    cnt += (kj < ki) || (kj == ki && j < i);
   }
-  int64_t rank = 0;
-  for (int64_t t0 = j_lo; t0 < j_hi; t0 += 1024) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < 1024 && t0 + k < j_hi; k += blockDim.x) {
-      double v = a.keys[t0 + k];
-      s_key[k] = isnan(v) ? __longlong_as_double(0x7ff0000000000000ll) : v;
-    }
-    __syncthreads();
-    if (i < a.n) {
-      const int64_t a0 = max(t0, my_lo), a1 = min(t0 + 1024, my_hi);
-      for (int64_t j = a0; j < a1; ++j) {
-        double kj = s_key[j - t0];
-        rank += (kj < ki) || (kj == ki && j < i);
-      }
-    }
-  }
-  if (i < a.n) a.order[my_lo + rank] = (int32_t)i;
+  if (cnt) atomicAdd(a.rank + i, cnt);
+}
+
+__global__ void rank_scatter_kernel(RankArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  a.order[a.seg[rank_seg_of(a, i)] + a.rank[i]] = (int32_t)i;
 }
 
 // Rank keys of given results (used when ranking results that came from the host).
@@ -1591,7 +1604,11 @@ cudaError_t launch_model(const ModelArgs &args, cudaStream_t st) {
 }
 cudaError_t launch_rank(const RankArgs &args, cudaStream_t st) {
   if (args.n <= 0) return cudaSuccess;
-  rank_kernel<<<(args.n + 255) / 256, 256, 0, st>>>(args);
+  cudaError_t e = cudaMemsetAsync(args.rank, 0, (size_t)args.n * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const unsigned tiles = (unsigned)((args.n + kRankTile - 1) / kRankTile);
+  rank_count_kernel<<<dim3(tiles, tiles), kRankTile, 0, st>>>(args);
+  rank_scatter_kernel<<<tiles, kRankTile, 0, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_keys(const ws_result *res, int n, double *keys, cudaStream_t st) {

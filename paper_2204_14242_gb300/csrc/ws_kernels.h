@@ -50,6 +50,7 @@ struct RankArgs {
   const double *keys;
   const int32_t *seg;              // n_seg + 1 segment starts
   int32_t *order;
+  int32_t *rank;                   // n scratch counters
   int32_t n, n_seg;
 };
 

@@ -878,10 +878,11 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
   ra.keys = (const double *)dev(d_keys);
   ra.seg = (const int32_t *)dev(d_seg);
   ra.order = (int32_t *)dev(d_order);
+  ra.rank = (int32_t *)dev(d_rank);
   ra.n = n_cfg;
   ra.n_seg = n_seg;
   CU(launch_rank(ra, st));
-  launches += n_cfg > 0;
+  launches += n_cfg > 0 ? 2 : 0;   // counting rank + scatter
   if ((rc = mark(2 + 3 * (int)passes.size())) != WS_OK) return rc;
   if (prof) prof->launches = launches;
   return WS_OK;
@@ -957,6 +958,7 @@ int ws_plan::run_plain(cudaStream_t st) {
   ra.keys = (const double *)dev(d_keys);
   ra.seg = (const int32_t *)dev(d_seg);
   ra.order = (int32_t *)dev(d_order);
+  ra.rank = (int32_t *)dev(d_rank);
   ra.n = n_cfg;
   ra.n_seg = n_seg;
   CU(launch_rank(ra, st));
@@ -1158,7 +1160,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
       max_field = std::max(max_field, (size_t)comp[i].need_words[k] * 4);
     }
   }
-  dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4);
+  dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
   const size_t avail = avail_fn(dsc);
   size_t scratch = std::min(total_need, avail);
   scratch = std::max<size_t>(scratch, 16);
@@ -1382,13 +1384,14 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->d_results = p->take(std::max<size_t>((size_t)n_cfg * sizeof(ws_result), 256));
   p->d_keys = p->take(std::max<size_t>((size_t)n_cfg * sizeof(double), 256));
   p->d_order = p->take(std::max<size_t>((size_t)n_cfg * sizeof(int32_t), 256));
+  p->d_rank = p->take(std::max<size_t>((size_t)n_cfg * sizeof(int32_t), 256));
   if (ext_scratch >= 0) {
     p->d_scratch = ext_scratch;
     p->ext_scratch = true;
   } else {
     p->d_scratch = p->take(scratch);
   }
-  for (int64_t o : {p->d_cfg, p->d_grp, p->d_fld, p->d_acc, p->d_iv, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order,
+  for (int64_t o : {p->d_cfg, p->d_grp, p->d_fld, p->d_acc, p->d_iv, p->d_seg, p->d_counters, p->d_results, p->d_keys, p->d_order, p->d_rank,
                     p->d_scratch}) {
     if (o < 0) {
       p->release_all();
@@ -1690,9 +1693,9 @@ extern "C" int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_
   cudaStream_t st = pick_stream(ctx, stream);
   const size_t rb = (size_t)n * sizeof(ws_result);
   int64_t o_res = ctx->arena->alloc(rb), o_keys = ctx->arena->alloc((size_t)n * 8),
-          o_ord = ctx->arena->alloc((size_t)n * 4), o_seg = ctx->arena->alloc(8);
+          o_ord = ctx->arena->alloc((size_t)n * 4), o_seg = ctx->arena->alloc(8), o_rnk = ctx->arena->alloc((size_t)n * 4);
   int rc = WS_OK;
-  if (o_res < 0 || o_keys < 0 || o_ord < 0 || o_seg < 0) rc = WS_ENOMEM;
+  if (o_res < 0 || o_keys < 0 || o_ord < 0 || o_seg < 0 || o_rnk < 0) rc = WS_ENOMEM;
   char *b = ctx->arena->base;
   if (rc == WS_OK) {
     int32_t seg[2] = {0, n};
@@ -1704,6 +1707,7 @@ extern "C" int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_
       ra.keys = (const double *)(b + o_keys);
       ra.seg = (const int32_t *)(b + o_seg);
       ra.order = (int32_t *)(b + o_ord);
+      ra.rank = (int32_t *)(b + o_rnk);
       ra.n = n;
       ra.n_seg = 1;
       e = launch_rank(ra, st);
@@ -1715,7 +1719,7 @@ extern "C" int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_
       rc = WS_ECUDA;
     }
   }
-  for (int64_t o : {o_res, o_keys, o_ord, o_seg}) ctx->arena->release(o);
+  for (int64_t o : {o_res, o_keys, o_ord, o_seg, o_rnk}) ctx->arena->release(o);
   return rc;
 }
 

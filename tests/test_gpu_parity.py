@@ -358,8 +358,8 @@ def test_autotune_keeps_results(ctx):
         r2, o2 = p.results()
         prof = p.profile()
     assert r1.tobytes() == r2.tobytes() and o1.tobytes() == o2.tobytes()
-    # per pass enumeration, row walk and counting; then model and ranking
-    assert prof["launches"] == 3 * prof["passes"] + 2 and prof["addresses"] > 0 and prof["ms_enum"] > 0
+    # per pass enumeration, row walk and counting; then model, counting rank and scatter
+    assert prof["launches"] == 3 * prof["passes"] + 3 and prof["addresses"] > 0 and prof["ms_enum"] > 0
 
 
 def test_server_results_same_alone_and_in_the_mix(ctx):
