@@ -77,6 +77,7 @@ struct ws_plan {
   std::vector<char> grp_iv_ok;   // group allows the interval walk (used unless tune.walk asks otherwise)
   std::vector<char> grp_rows_ok; // group allows the row walk of levels 1-3
   std::vector<int64_t> grp_slots;        // row slots of the group's candidate
+  std::vector<ws::WarpClasses> grp_classes;  // block warp classes per group (used with the row walk)
   std::vector<int64_t> grp_winstr_rows;  // modelled (warp, instruction) pairs of levels 1-3
   int32_t chunk_rows() const { return std::max(1, tune.chunk_warps / 16); }
   std::vector<int32_t> cfg_grp_begin;

@@ -57,8 +57,9 @@ struct DCfg {
   // level holds one run of blocks that are consecutive in x; its threads with the same
   // (ty, tz) form one grid row of consecutive x.  Slot = (block row, thread row); the
   // z set has two slots per thread row (its run may be cut in two by the y set).
-  int32_t rows_R_lo[3], rows_R_cnt[3];
-  int64_t rows_slot_end[3];    // cumulative slots of the three levels (< 2^31)
+  // Level 3 of the row walk is the representative block itself (its block bitmaps).
+  int32_t rows_R_lo[4], rows_R_cnt[4];
+  int64_t rows_slot_end[4];    // cumulative slots: wave, y set, z set, block (< 2^31)
   int32_t rows_per_blk;        // B[1] * B[2]
   int32_t full_end;            // blocks in x that lie entirely inside N[0]
   FastDiv fd_rows, fd_b1;
@@ -136,6 +137,20 @@ struct DGroup {
   int32_t n0_items;       // enumeration items of the representative block
   int32_t levels;         // level mask of its fields (1 block, 2 wave + y / z, 3 both)
   int32_t first_wave;     // the candidate's first group with wave work counts the wave LUPs
+  // Representative-block warps to evaluate and the number of warps each one stands for
+  // (warps with the same lane layout whose addresses differ by a multiple of the bank and
+  // sector period give the same per-instruction counts); all warps, once each, unless the
+  // row walk builds the block bitmaps.
+  int32_t n_rep;
+  uint8_t rep_warp[32];
+  uint8_t rep_mult[32];
+  int32_t pad2;
+};
+
+// Classes of representative-block warps with identical per-instruction counts (host).
+struct WarpClasses {
+  int32_t n = 0;
+  uint8_t warp[32], mult[32];
 };
 
 // One pass = a contiguous range of field groups whose bitmaps fit the scratch

@@ -646,11 +646,14 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       // distinct sectors per instruction (L1 requests / write-through stores), the block
       // footprint bitmaps, and half-warp bank cycles
       const uint32_t LS = (uint32_t)s_soff[s_g.f_count], L = (uint32_t)s_loff[s_g.f_count];
-      const int64_t np = (int64_t)s_g.mw_block * LS;
+      const int64_t np = (int64_t)s_g.n_rep * LS;
       const int64_t p0 = kk * (int64_t)a.block_pairs, p1 = min(p0 + (int64_t)a.block_pairs, np);
       const bool fast_banks = a.bank_shift >= 0;
+      // with the row walk the block bitmaps are built there: count only, one warp per class
+      const bool count_only = s_g.rows;
       for (int64_t pp = p0 + warp; pp < p1; pp += nwarps) {
-        const uint32_t mw = (uint32_t)(pp / LS), j = (uint32_t)(pp - (int64_t)mw * LS);
+        const uint32_t r = (uint32_t)(pp / LS), j = (uint32_t)(pp - (int64_t)r * LS);
+        const uint32_t mw = s_g.rep_warp[r], mult = s_g.rep_mult[r];
         const uint32_t b = (uint32_t)s_c.rep;
         const uint32_t bt = fdiv(b, s_c.fd_gx);
         const uint32_t bx = b - bt * (uint32_t)s_c.g[0];
@@ -669,21 +672,25 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
         int kv = 0;
         if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
         if (j == 0u) {
-          if (s_g.first_of_cfg) acc_lb += __reduce_add_sync(FULL, (uint32_t)kv);
-          acc_addr += __reduce_add_sync(FULL, (uint32_t)s_gad[0][kv]);
-          acc_wi += (uint32_t)s_gwi[0];
+          if (s_g.first_of_cfg) acc_lb += mult * __reduce_add_sync(FULL, (uint32_t)kv);
+          acc_addr += mult * __reduce_add_sync(FULL, (uint32_t)s_gad[0][kv]);
+          acc_wi += mult * (uint32_t)s_gwi[0];
         }
         const DField &F = s_fk[s_af[j]];
         const bool act = valid && (int)s_kmin[j] < kv;
         const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
-        const int64_t r = F.base + (int64_t)F.esize * lin - 32 * F.lo[0] + s_boff[j];
-        if (j < L) acc_req += bitmap_insert(a.scratch + F.bm[BM_BL], r, act, lane, F.words[0], bad);
-        else acc_st += bitmap_insert(a.scratch + F.bm[BM_BS], r, act, lane, F.words[0], bad);
+        const int64_t rr = F.base + (int64_t)F.esize * lin - 32 * F.lo[0] + s_boff[j];
+        const bool inside = rr >= 0 && rr < (F.words[0] << 10);
+        uint32_t nsec;
+        if (count_only) nsec = warp_distinct_sectors((uint32_t)rr, act && inside);
+        else nsec = bitmap_insert(a.scratch + F.bm[j < L ? BM_BL : BM_BS], rr, act, lane, F.words[0], bad);
+        if (j < L) acc_req += mult * nsec;
+        else acc_st += mult * nsec;
         if (fast_banks && !F.wide)
-          acc_bank += bank_cycles_rel32((uint32_t)r, act && r >= 0 && r < (F.words[0] << 10), lane,
-                                        (uint32_t)a.bank_shift, (uint32_t)(a.banks - 1), (uint32_t)a.pair_dist);
+          acc_bank += mult * bank_cycles_rel32((uint32_t)rr, act && inside, lane, (uint32_t)a.bank_shift,
+                                               (uint32_t)(a.banks - 1), (uint32_t)a.pair_dist);
         else
-          acc_bank += bank_cycles_warp(r + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
+          acc_bank += mult * bank_cycles_warp(rr + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
       }
     }
     for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
@@ -1151,7 +1158,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       // fold) is one sector range of the row, stores also add their per-warp sector
       // counts in closed form
       const int64_t q0 = kk * (int64_t)a.chunk_rows;
-      const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[2]);
+      const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[(s_g.levels & 1) ? 3 : 2]);
       const int L = s_loff[s_g.f_count];
       const int S = s_soff[s_g.f_count] - L;
       const int Mfull = s_ioff[s_g.f_count];
@@ -1164,8 +1171,10 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           lv = 0; loc = slot;
         } else if (slot < s_c.rows_slot_end[1]) {
           lv = 1; loc = slot - s_c.rows_slot_end[0];
-        } else {
+        } else if (slot < s_c.rows_slot_end[2]) {
           lv = 2; loc = slot - s_c.rows_slot_end[1];
+        } else {
+          lv = 3; loc = slot - s_c.rows_slot_end[2];   // the representative block's rows
         }
         const uint32_t pq = fdiv((uint32_t)loc, s_c.fd_rows);
         const uint32_t t = (uint32_t)loc - pq * (uint32_t)s_c.rows_per_blk;
@@ -1178,6 +1187,9 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         if (lv == 0) {
           ba = max(s_c.s, rb0);
           bb = min(s_c.s + s_c.weff, rb1);
+        } else if (lv == 3) {
+          ba = s_c.rep;
+          bb = s_c.rep + 1;
         } else if (lv == 1) {
           if (by == gy - 1) continue;
           ba = max(s_c.y_lo, rb0);
@@ -1204,7 +1216,9 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
         const int64_t nx = xb - xa;
         unsigned long long *const ctr = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
-        if (lane == 0u) {
+        // the block level only fills the block bitmaps: its counts come from enum_kernel
+        const bool blk = lv == 3;
+        if (lane == 0u && !blk) {
           if (lv == 0 && s_g.first_wave) atomicAdd(ctr + C_LUPS_WAVE, (unsigned long long)(nx * kv));
           atomicAdd(ctr + C_ADDR, (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]));
         }
@@ -1213,7 +1227,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         const int64_t lo = min(ea, eb), hi = max(ea, eb);
         const bool fullk = kv == fold;
         const int M = fullk ? Mfull : L;
-        const int bsel = lv == 0 ? BM_W : lv == 1 ? BM_Y : BM_Z;
+        const int bsel = lv == 0 ? BM_W : lv == 1 ? BM_Y : lv == 2 ? BM_Z : BM_BL;
+        const int lvi = blk ? 0 : 1;   // bitmap origin / size index
         for (int e = (int)lane; e < M; e += 32) {
           int k;
           int64_t bo;
@@ -1229,8 +1244,9 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             ext = 0u;
           }
           const DField &F = s_fk[k];
+          if (blk) bo += 32 * (F.lo[1] - F.lo[0]);   // staged offsets are relative to the wave origin
           const int64_t a0 = lo + bo, a1 = hi + bo + (int64_t)ext;
-          if (a0 < 0 || a1 >= (F.words[1] << 10)) {
+          if (a0 < 0 || a1 >= (F.words[lvi] << 10)) {
             ++bad;
             continue;
           }
@@ -1241,24 +1257,25 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           if (cb) atomicOr(bm + cu, cb);
           nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
         }
-        if (lv == 0) {
+        if (lv == 0 || blk) {
           for (int j = L + (int)lane; j < L + S; j += 32) {
             if ((int)s_kmin[j] >= kv) continue;
             const DField &F = s_fk[s_af[j]];
-            const int64_t bo = s_boff[j] + F.base - 32 * F.lo[1];
+            const int64_t bo = s_boff[j] + F.base - 32 * F.lo[lvi];
             const int64_t a0 = lo + bo, a1 = hi + bo;
-            if (a0 < 0 || a1 >= (F.words[1] << 10)) {
+            if (a0 < 0 || a1 >= (F.words[lvi] << 10)) {
               ++bad;
               continue;
             }
-            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[BM_WS]);
+            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[blk ? BM_BS : BM_WS]);
             uint32_t cu = 0xffffffffu;
             unsigned long long cb = 0ull;
             put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
             if (cb) atomicOr(bm + cu, cb);
             nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-            atomicAdd(ctr + C_W_SREQ,
-                      (unsigned long long)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb));
+            if (!blk)
+              atomicAdd(ctr + C_W_SREQ,
+                        (unsigned long long)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb));
           }
         }
       }

@@ -138,6 +138,7 @@ static FastDiv make_fastdiv(uint32_t d) {
 
 struct Compiled {
   DCfg d{};
+  WarpClasses cls;                    // block warp classes for the layout of field 0
   int64_t lvl_blocks[3] = {0, 0, 0};  // blocks of the wave, y set and z set
   bool rows_geom_ok = false;          // row slots fit the kernel's 32-bit decode
   std::vector<DField> f;
@@ -267,6 +268,72 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
   }
 }
 
+// Classes of the representative block's warps that give identical per-instruction counts
+// (distinct sectors, half-warp bank cycles) for every access of fields with one element
+// size and strides: warps whose lanes sit at the same relative points with the same valid
+// folded points, and whose lane-0 addresses differ by a multiple of lcm(32, banks * bank
+// width) (a translation by such a multiple moves no lane to another sector position or
+// bank, and the pairing groups depend on differences only).
+static void block_warp_classes(const DCfg &d, int64_t esize, const int64_t stride[3], const ws_hw &hw,
+                               WarpClasses &out) {
+  auto gcd = [](int64_t a, int64_t b) {
+    while (b) {
+      const int64_t t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  const int64_t bankp = (int64_t)hw.banks * hw.bank_bytes;
+  const int64_t period = 32 / gcd(32, bankp) * bankp;
+  const int64_t g0 = d.g[0], g1 = d.g[1];
+  const int64_t bx = d.rep % g0, by = (d.rep / g0) % g1, bz = d.rep / (g0 * g1);
+  const int64_t fy = d.fold_axis == 1 ? d.fold : 1, fz = d.fold_axis == 2 ? d.fold : 1;
+  // lane points relative to lane 0 and valid folded points (kv, -1 = no thread)
+  int32_t rel[32][32][4];
+  int64_t ref[32][3];
+  for (int w = 0; w < d.wpb; ++w)
+    for (int l = 0; l < 32; ++l) {
+      const int64_t tid = 32 * w + l;
+      int64_t x = 0, y = 0, z = 0, kv = -1;
+      if (tid < d.T) {
+        const int64_t tx = tid % d.B[0], ty = (tid / d.B[0]) % d.B[1], tz = tid / (d.B[0] * d.B[1]);
+        x = bx * d.B[0] + tx;
+        y = (by * d.B[1] + ty) * fy;
+        z = (bz * d.B[2] + tz) * fz;
+        const bool valid = x < d.N[0] && y < d.N[1] && z < d.N[2];
+        kv = !valid ? 0 : d.fold_axis == 1 ? std::min<int64_t>(d.fold, d.N[1] - y)
+                        : d.fold_axis == 2 ? std::min<int64_t>(d.fold, d.N[2] - z) : 1;
+      }
+      if (l == 0) {
+        ref[w][0] = x;
+        ref[w][1] = y;
+        ref[w][2] = z;
+      }
+      rel[w][l][0] = (int32_t)(x - ref[w][0]);
+      rel[w][l][1] = (int32_t)(y - ref[w][1]);
+      rel[w][l][2] = (int32_t)(z - ref[w][2]);
+      rel[w][l][3] = (int32_t)kv;
+    }
+  out.n = 0;
+  for (int w = 0; w < d.wpb; ++w) {
+    int c = 0;
+    for (; c < out.n; ++c) {
+      const int r = out.warp[c];
+      const __int128 delta = (__int128)esize * (stride[0] * (ref[w][0] - ref[r][0]) + stride[1] * (ref[w][1] - ref[r][1]) +
+                                                stride[2] * (ref[w][2] - ref[r][2]));
+      if (delta % period == 0 && memcmp(rel[w], rel[r], sizeof(rel[w])) == 0) break;
+    }
+    if (c < out.n) {
+      out.mult[c] += 1;
+    } else {
+      out.warp[out.n] = (uint8_t)w;
+      out.mult[out.n] = 1;
+      out.n += 1;
+    }
+  }
+}
+
 // Key of a field's folded access list: equal keys have equal lists.
 static uint64_t fold_key(const ws_config &c, int fi) {
   return ((uint64_t)(c.field_off + fi) << 8) | ((uint64_t)c.fold_axis << 5) | (uint64_t)c.fold;
@@ -366,9 +433,9 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     d.full_end = (int32_t)(c.N[0] / c.B[0]);
     d.fd_rows = make_fastdiv((uint32_t)d.rows_per_blk);
     d.fd_b1 = make_fastdiv((uint32_t)c.B[1]);
-    const int64_t rng[3][2] = {{s, s + weff}, {y_lo, y_hi}, {z_lo, z_hi}};
+    const int64_t rng[4][2] = {{s, s + weff}, {y_lo, y_hi}, {z_lo, z_hi}, {rep, rep + 1}};
     int64_t cum = 0;
-    for (int lv = 0; lv < 3; ++lv) {
+    for (int lv = 0; lv < 4; ++lv) {
       d.rows_R_lo[lv] = 0;
       d.rows_R_cnt[lv] = 0;
       if (rng[lv][1] > rng[lv][0]) {
@@ -597,6 +664,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     }
   }
   d.n_field = c.n_field;
+  if (!out.f.empty()) block_warp_classes(d, out.f[0].esize, out.f[0].stride, hw, out.cls);
   return WS_OK;
 }
 
@@ -691,8 +759,18 @@ void ws_plan::layout() {
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
   int64_t items = 0, ritems = 0, citems = 0, used = 0;
   for (size_t g = 0; g < hgrp.size(); ++g) {
-    hgrp[g].iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
-    hgrp[g].rows = grp_rows_ok[g] && tune.walk == WS_WALK_INTERVAL;
+    DGroup &G = hgrp[g];
+    G.iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
+    G.rows = grp_rows_ok[g] && tune.walk == WS_WALK_INTERVAL;
+    // the row walk builds the block bitmaps, so the block path counts one warp per
+    // class; otherwise it inserts every warp
+    const bool classes = G.rows && (G.levels & 1) && grp_classes[g].n > 0;
+    const int wpb = (int)G.mw_block;
+    G.n_rep = classes ? grp_classes[g].n : wpb;
+    for (int r = 0; r < G.n_rep; ++r) {
+      G.rep_warp[r] = classes ? grp_classes[g].warp[r] : (uint8_t)r;
+      G.rep_mult[r] = classes ? grp_classes[g].mult[r] : (uint8_t)1;
+    }
   }
   DPass cur;
   memset(&cur, 0, sizeof(cur));
@@ -740,7 +818,7 @@ void ws_plan::layout() {
     // row walk, chunks of row slots as items of the row kernel
     G.item_begin = items;
     G.ritem_begin = ritems;
-    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div(G.mw_block * (int64_t)G.acc_count, kBlockPairs))
+    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div((int64_t)G.n_rep * G.acc_count, kBlockPairs))
                                 : 0;
     items += G.n0_items;
     if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
@@ -1305,7 +1383,20 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
       const DCfg &dc = comp[i].d;
       p->grp_iv_ok.push_back((char)G.iv);
       p->grp_rows_ok.push_back((char)rows);
-      p->grp_slots.push_back(dc.rows_slot_end[2]);
+      // with the block level when the group also serves the representative block
+      p->grp_slots.push_back(dc.rows_slot_end[(G.levels & 1) ? 3 : 2]);
+      {
+        const DField &f0 = p->hfld[G.f_begin], &c0 = p->hfld[p->cfg_cf_begin[i]];
+        WarpClasses wc;
+        if (rows && (G.levels & 1)) {
+          if (f0.esize == c0.esize && f0.stride[0] == c0.stride[0] && f0.stride[1] == c0.stride[1] &&
+              f0.stride[2] == c0.stride[2])
+            wc = comp[i].cls;
+          else
+            block_warp_classes(dc, f0.esize, f0.stride, *hw, wc);
+        }
+        p->grp_classes.push_back(wc);
+      }
       p->grp_winstr_rows.push_back(
           (comp[i].lvl_blocks[0] * instr_w + (comp[i].lvl_blocks[1] + comp[i].lvl_blocks[2]) * instr_yz) * dc.wpb);
       p->hgrp.push_back(G);
