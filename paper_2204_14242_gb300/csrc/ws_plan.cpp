@@ -4,11 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <climits>
+#include <condition_variable>
 #include <fstream>
 #include <functional>
 #include <map>
@@ -1164,23 +1166,104 @@ static cudaStream_t pick_stream(ws_ctx *c, void *s) { return s ? (cudaStream_t)s
 
 // Compiles every candidate; large batches on several host threads, each with its own
 // (field, folding) cache.
+// Persistent host worker pool for the descriptor compiler: a call runs fn(t) for
+// t = 0..width-1 on the workers and the calling thread.  Workers wait on a condition
+// variable between calls; a call that finds the pool busy (another host thread is
+// creating a plan) runs on its own thread alone.
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool;
+    return pool;
+  }
+  int width() const { return (int)workers_.size() + 1; }
+  void run(int width, const std::function<void(int)> &fn) {
+    std::unique_lock<std::mutex> busy(busy_, std::try_to_lock);
+    if (!busy.owns_lock() || width <= 1 || workers_.empty()) {
+      for (int t = 0; t < width; ++t) fn(t);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      job_ = &fn;
+      width_ = width;
+      next_ = 0;
+      active_ = (int)workers_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_.wait(g, [&] { return active_ == 0; });
+    job_ = nullptr;
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto &t : workers_) t.join();
+  }
+
+ private:
+  HostPool() {
+    const unsigned n = std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+    for (unsigned i = 1; i < n; ++i) workers_.emplace_back([this] { loop(); });
+  }
+  void work() {
+    for (;;) {
+      int t;
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        t = next_ < width_ ? next_++ : -1;
+      }
+      if (t < 0) return;
+      (*job_)(t);
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      work();
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        --active_;
+      }
+      done_.notify_all();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex mu_, busy_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)> *job_ = nullptr;
+  int width_ = 0, next_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
 static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
                         int n_acc, const ws_hw &hw, std::vector<Compiled> &comp, std::vector<int> &status) {
   comp.resize(n_cfg);
   status.assign(n_cfg, WS_OK);
-  int nth = 1;
-  if (n_cfg >= 256) nth = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-  auto work = [&](int t) {
+  // chunks of consecutive candidates handed out dynamically; each thread keeps its fold
+  // cache across its chunks (neighbouring candidates often share fields)
+  const int nth = n_cfg >= 64 ? HostPool::get().width() : 1;
+  const int chunk = 32;
+  std::atomic<int> next(0);
+  HostPool::get().run(nth, [&](int) {
     FieldCache cache;
-    for (int i = t; i < n_cfg; i += nth) status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, comp[i], &cache);
-  };
-  if (nth == 1) {
-    work(0);
-    return;
-  }
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nth; ++t) pool.emplace_back(work, t);
-  for (auto &th : pool) th.join();
+    for (int c = next.fetch_add(1); c * chunk < n_cfg; c = next.fetch_add(1))
+      for (int i = c * chunk; i < std::min(n_cfg, (c + 1) * chunk); ++i)
+        status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, comp[i], &cache);
+  });
 }
 
 // Bytes of device memory a plan of these candidates needs with one pass.
@@ -1313,14 +1396,8 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
     }
   };
   {
-    const int nth = n_cfg >= 256 ? (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency())) : 1;
-    if (nth == 1) {
-      fill(0, 1);
-    } else {
-      std::vector<std::thread> pool;
-      for (int t = 0; t < nth; ++t) pool.emplace_back(fill, t, nth);
-      for (auto &th : pool) th.join();
-    }
+    const int nth = n_cfg >= 256 ? HostPool::get().width() : 1;
+    HostPool::get().run(nth, [&](int t) { fill(t, nth); });
   }
   p->cfg_cf_begin[n_cfg] = (int32_t)p->hfld.size();
   p->scratch_words = (int64_t)(scratch / 4);
