@@ -15,14 +15,14 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["ws_kernels.cu", "ws_peaks.cu", "ws_noalloc.cu"]
+CU_SOURCES = ["ws_kernels.cu", "ws_peaks.cu", "ws_noalloc.cu", "ws_validate.cu"]
 CPP_SOURCES = ["ws_plan.cpp", "ws_server.cpp"]
 HEADERS = ["ws_internal.h", "ws_kernels.h", "ws_host.h"]
 
 
 def _newest_input() -> float:
     files = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
-    files.append(os.path.join(INCLUDE, "warpspeed.h"))
+    files += [os.path.join(INCLUDE, h) for h in ("warpspeed.h", "warpspeed_validate.h")]
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 

@@ -113,6 +113,17 @@ def v100() -> Hardware:
                     bw_l2=2500e9, bw_dram=800e9, fp_peak=3.5e12)
 
 
+def gb300(l2_bytes: float = 89.6e6, bw_l2: float = 15555e9, bw_dram: float = 6081e9,
+          fp_peak: float = 528.8e9, clock_hz: float = 2.07e9, sms: int = 152) -> Hardware:
+    """GB300 descriptor: 152 SMs, 2.07 GHz, 256 KiB L1 per SM; the defaults of the effective
+    L2 size (LOAD rate above 90 % of its L2 level up to 89.6 MB), L2 bandwidth (LOAD on L2
+    data sets, 15.6 TB/s), DRAM bandwidth (SCALE on data sets >= 1 GiB, 6.08 TB/s) and fp64
+    rate (half of the measured 1.06 TFLOP/s FMA rate, for add-dominated stencils) are the
+    values `validation.calibrate` measured on a GB300; pass others to override."""
+    return Hardware(sms=sms, clock_hz=clock_hz, l1_bytes=256.0 * 1024, l2_bytes=l2_bytes, bw_l2=bw_l2,
+                    bw_dram=bw_dram, fp_peak=fp_peak)
+
+
 # --------------------------------------------------------------------------------------
 # splitmix64 (Steele, Lea, Flood 2014; constants as published by S. Vigna)
 # --------------------------------------------------------------------------------------
