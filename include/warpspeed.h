@@ -5,11 +5,11 @@
  *
  * For every code-generation candidate the library evaluates the address expression
  * of every thread of a representative thread block and of a wave of co-resident
- * blocks (Sec. 3.2-3.4), collapses the addresses to unique 32 B sectors and 128 B
- * lines, derives bank-conflict cycles (Sec. 3.2), L1/L2/DRAM volumes per lattice
- * update with layer-condition reuse (Sec. 3.4.2) and capacity misses (Sec. 3.5), and
+ * blocks (Sec. 4.2-4.4), collapses the addresses to unique 32 B sectors and 128 B
+ * lines, derives bank-conflict cycles (Sec. 4.2), L1/L2/DRAM volumes per lattice
+ * update with layer-condition reuse (Sec. 4.4.2) and capacity misses (Sec. 4.5), and
  * combines them in the four-limiter performance model (Sec. 2) into a predicted time
- * and a ranking (Sec. 5.7).
+ * and a ranking (Sec. 5.8).
  *
  * Conventions
  *   - All structs are plain C with natural alignment; sizes are fixed (see the
@@ -25,7 +25,7 @@
  *   - Address expressions are affine (Sec. 1.2): for a thread whose grid point is p,
  *     access (o, dc) of field f touches the byte
  *         align + elem_bytes * (stride . (p + o) + const_off + dc)
- *     i.e. the unknown base pointer is replaced by the field alignment (Sec. 3.3).
+ *     i.e. the unknown base pointer is replaced by the field alignment (Sec. 4.3).
  */
 #ifndef WARPSPEED_H
 #define WARPSPEED_H
@@ -61,7 +61,7 @@ extern "C" {
 #define WS_LIMITER_DRAM 2  /* DRAM <-> L2 bandwidth                                       */
 #define WS_LIMITER_FP 3    /* floating-point throughput                                   */
 
-/* One relative access of a field (Sec. 1.2, 3.3): grid offset (dx, dy, dz) from the
+/* One relative access of a field (Sec. 1.2, 4.3): grid offset (dx, dy, dz) from the
  * updated point, plus an extra element offset dc (components of AoS layouts).
  * is_store: 0 = load, 1 = store.  |dx|,|dy|,|dz| <= 65535, |dc| < 2^40. */
 typedef struct ws_access {
@@ -70,7 +70,7 @@ typedef struct ws_access {
   int64_t dc;
 } ws_access; /* 24 bytes */
 
-/* One array.  Fields never alias (Sec. 3.3): sectors are counted per field and then
+/* One array.  Fields never alias (Sec. 4.3): sectors are counted per field and then
  * summed.  elem_bytes in 1..64; stride[d] in elements (|stride| < 2^40, any sign);
  * align_bytes replaces the base pointer (|align| < 2^50, any value, negative allowed);
  * the field's accesses are acc[access_off .. access_off + n_access). */
@@ -83,7 +83,7 @@ typedef struct ws_field {
   int64_t access_off;
 } ws_field; /* 56 bytes */
 
-/* One candidate (Sec. 5.1): domain N (points), thread-block shape B, thread folding
+/* One candidate (Sec. 5.1, 5.2): domain N (points), thread-block shape B, thread folding
  * (fold_axis 0 = none, 1 = y, 2 = z; each thread updates `fold` consecutive points
  * along that axis, fold in 1..16, fold == 1 when fold_axis == 0), its fields
  * fld[field_off .. field_off + n_field), flops per lattice update (0 = no FP limiter),
@@ -102,7 +102,7 @@ typedef struct ws_config {
   int32_t wave_blocks_override;
   int32_t address_mode; /* WS_ADDR_LINEAR: linear byte addresses everywhere.
                            WS_ADDR_MULTIDIM: the wave and the y / z layer sets count in the
-                           multi-dimensional address space of Sec. 3.4.1 -- a sector is
+                           multi-dimensional address space of Sec. 4.4.1 -- a sector is
                            (innermost coordinate in bytes / 32, y, z), the base alignment is
                            ignored and a line wrapping to the next row counts at both ends;
                            the representative block keeps linear addresses.               */
@@ -113,7 +113,7 @@ enum { WS_ADDR_LINEAR = 0, WS_ADDR_MULTIDIM = 1 };
 /* Modelled GPU (Table 1 of the paper; the A100-SXM4-40G column with a 20 MB effective
  * L2 is the reference setting).  Rates in bytes/s, flop/s and Hz; sizes in bytes.
  * hit[i] = (a, b, c) of the capacity hit-rate fit R(O) = a*exp(-b*exp(-c*O))
- * (Sec. 3.5) for i = 0 L1 redundant loads, 1 L2 y-layer overlap, 2 L2 z-layer
+ * (Sec. 4.5) for i = 0 L1 redundant loads, 1 L2 y-layer overlap, 2 L2 z-layer
  * overlap, 3 L2 redundant stores.  capacity_model = 0 sets every R to 1. */
 typedef struct ws_hw {
   int32_t sms, max_threads_sm, max_blocks_sm, regs_sm;
@@ -157,7 +157,7 @@ typedef struct ws_tuning {
                               < 0 = as large as the arena allows); never below one field   */
   int32_t walk;            /* How the wave and the y / z layer sets are enumerated; all give
                               identical counts.  WS_WALK_INTERVAL (0): closed-form interval
-                              counting (Sec. 3.4) wherever it is exact -- whole grid rows of
+                              counting (Sec. 4.4) wherever it is exact -- whole grid rows of
                               a level as sector ranges, per-warp store sectors by floor sums,
                               else row segments of each warp; WS_WALK_SEGMENT (2): intervals
                               per row segment of each modelled warp only; WS_WALK_ADDRESS
@@ -192,7 +192,7 @@ const char *ws_status_string(int status);
 /* Text of the last CUDA or allocation failure seen by the calling thread. */
 const char *ws_last_error(void);
 
-/* Default modelled hardware: A100-SXM4-40G (Table 1, 20 MB effective L2, Sec. 4),
+/* Default modelled hardware: A100-SXM4-40G (Table 1, 20 MB effective L2, Sec. 3),
  * illustrative hit-rate coefficients (the paper prints none). */
 void ws_hw_a100(ws_hw *hw);
 
@@ -204,7 +204,7 @@ int ws_destroy(ws_ctx *ctx);
 
 /* Compiles n_cfg candidates into device-resident descriptors (host descriptor
  * compiler: grid, representative block and wave, y/z sets, folded access lists,
- * bitmap ranges; Sec. 3.2-3.4) and reserves their scratch.  cfgs[i].field_off indexes
+ * bitmap ranges; Sec. 4.2-4.4) and reserves their scratch.  cfgs[i].field_off indexes
  * fld[0..n_fld), fld[j].access_off indexes acc[0..n_acc).  seg_begin (n_seg + 1
  * entries, ascending, seg_begin[0] = 0, seg_begin[n_seg] = n_cfg) splits the
  * candidates into independently ranked lists; NULL = one list.  tuning may be NULL.
@@ -236,7 +236,7 @@ typedef struct ws_cfg_info {
   int32_t grid[3];                /* thread-block grid (after folding)                   */
   int32_t threads, warps_per_block, blocks_per_sm, n_field;
   int64_t total_blocks, rep_block;            /* representative block: grid middle      */
-  int64_t wave_first, wave_blocks;            /* representative wave (Sec. 3.4)         */
+  int64_t wave_first, wave_blocks;            /* representative wave (Sec. 4.4)         */
   int64_t y_lo, y_hi, z_lo, z_hi;             /* y / z layer-set candidate block ranges */
   int64_t y_dist, z_dist;                     /* blocks since the first y / z set block */
   int64_t modelled_warps;                     /* warps enumerated per loaded field      */
@@ -251,7 +251,7 @@ typedef struct ws_field_info {
 } ws_field_info; /* 40 bytes */
 
 /* Compiles candidates on the host only and reports what the device would run
- * (Sec. 3.3-3.4 thread groups).  out: n_cfg entries.  Returns WS_EINVAL on a bad
+ * (Sec. 4.3-4.4 thread groups).  out: n_cfg entries.  Returns WS_EINVAL on a bad
  * argument; per-candidate problems go to out[i].status. */
 int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
                 const ws_hw *hw, ws_cfg_info *out);
@@ -314,7 +314,7 @@ int ws_estimate_batch_noalloc(int device, const ws_config *cfgs, int n_cfg, cons
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
                               int32_t *order_out, void *stream);
 
-/* Stable ranking on the device (Sec. 5.7): ascending t_pred rounded to 40
+/* Stable ranking on the device (Sec. 5.8): ascending t_pred rounded to 40
  * significant bits, ties by index; NaN ranks as +inf.  res: n host results. */
 int ws_rank(ws_ctx *ctx, const ws_result *res, int n, int32_t *order_out, void *stream);
 /* The rank key: t rounded to 40 significant mantissa bits, half to even. */

@@ -4,8 +4,8 @@
  * The estimator predicts data volumes of stencil kernels without running them.  These
  * entry points run such kernels, so that the predictions can be compared with the
  * hardware counters the paper uses (L2 sectors requested by the SMs,
- * lts__t_sectors_srcunit_tex_op_read, and DRAM bytes; Sec. 2, 5.4), and measure the
- * rates a GB300 hardware descriptor needs (Sec. 2: the LOAD / SCALE streaming kernels on
+ * lts__t_sectors_srcunit_tex_op_read, and DRAM bytes; Sec. 3, 5.5), and measure the
+ * rates a GB300 hardware descriptor needs (Sec. 3: the LOAD / SCALE streaming kernels on
  * a repeated data set give the effective L2 size and the L2 / DRAM bandwidths).
  *
  * All pointers are device pointers owned by the caller; `stream` is a cudaStream_t (NULL
@@ -20,7 +20,7 @@
 extern "C" {
 #endif
 
-/* Streaming kernels of Sec. 2 on a repeated data set of `elems` doubles: thread g of
+/* Streaming kernels of Sec. 3 on a repeated data set of `elems` doubles: thread g of
  * `blocks` x `threads` (the grid) touches element g mod elems, `iters` times over
  * strided rounds.  kind 0 = LOAD (c = A[i], the values combined so the loads are not
  * eliminated); kind 1 = SCALE (B[i] = c * A[i] with c = -1).  Values move as 8-byte bit

@@ -9,7 +9,7 @@ path and the CUDA path imports nothing from it.
 Parity status per function (see the tests under ``tests/``):
   * sector / line / LUP / warp / bank counts: pinned by the numpy brute force of the
     paper's grid iteration, by closed forms (7-point block and wave, wave-depth law of
-    Sec. 5.6, streaming copy, D3Q15 240 B/LUP) and by invariants;
+    Sec. 5.7, streaming copy, D3Q15 240 B/LUP) and by invariants;
   * layer-condition overlaps ov_y / ov_z: pinned by brute force and the 7-point closed
     form under the stated reading of the thread sets;
   * capacity model and limiters: pinned at the special cases the paper fixes

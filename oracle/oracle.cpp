@@ -1,16 +1,16 @@
 // CPU oracle of the metric estimator -- TEST INFRASTRUCTURE, not part of the product.
 //
 // A plain, slow enumerator written to be checked by eye against the paper:
-//   * grid iteration (Sec. 3.2, listing "grid iteration"): every thread of a thread
+//   * grid iteration (Sec. 4.2, listing "grid iteration"): every thread of a thread
 //     group, every address expression of a field;
-//   * unique 32 B sectors and 128 B lines per group (Sec. 3.3, CL32 visitor);
-//   * bank-conflict cycles per half-warp (Sec. 3.2, bank-conflict visitor, 16 banks
+//   * unique 32 B sectors and 128 B lines per group (Sec. 4.3, CL32 visitor);
+//   * bank-conflict cycles per half-warp (Sec. 4.2, bank-conflict visitor, 16 banks
 //     x 8 B, 1024 B pairing distance);
-//   * one representative block (Sec. 3.3) and one wave of co-resident blocks in the
-//     middle of the grid (Sec. 3.4), plus the y and z layer-condition thread sets
-//     (Sec. 3.4.2), the wave-level sets in linear addresses or, optionally, in the
-//     multi-dimensional address space of Sec. 3.4.1;
-//   * capacity misses (Sec. 3.5, Eqs. for V_cap and R_hit(O)) and the four-limiter
+//   * one representative block (Sec. 4.3) and one wave of co-resident blocks in the
+//     middle of the grid (Sec. 4.4), plus the y and z layer-condition thread sets
+//     (Sec. 4.4.2), the wave-level sets in linear addresses or, optionally, in the
+//     multi-dimensional address space of Sec. 4.4.1;
+//   * capacity misses (Sec. 4.5, Eqs. for V_cap and R_hit(O)) and the four-limiter
 //     performance model (Sec. 2).
 // Every set is a std::set; every count is the size of a set.  Floating point is fp64
 // in one fixed order.  Readings of points the paper leaves open are noted inline.
@@ -71,9 +71,9 @@ Off sub(const Off &a, const Off &b) {
              std::get<2>(a) - std::get<2>(b), std::get<3>(a) - std::get<3>(b));
 }
 
-// Thread folding (Sec. 5.1): a thread updates `fold` consecutive points along the
+// Thread folding (Sec. 5.2): a thread updates `fold` consecutive points along the
 // folding axis.  Its loads are the union over k of (offset + k * axis); each distinct
-// address is loaded once and reused from registers (Sec. 5.3).  Stores likewise.
+// address is loaded once and reused from registers (Sec. 5.4).  Stores likewise.
 std::vector<Off> fold_list(const OCfg &c, const std::set<Off> &offs) {
   std::set<Off> u;
   for (const Off &o : offs)
@@ -95,7 +95,7 @@ struct Thread {
   int64_t kv;    // number of its folded points inside the domain
 };
 
-// Thread `tid` (linear, x fastest) of block `bid` (linear, X-Y-Z order, Sec. 3.4).
+// Thread `tid` (linear, x fastest) of block `bid` (linear, X-Y-Z order, Sec. 4.4).
 Thread make_thread(const OCfg &c, const int64_t g[3], int64_t bid, int64_t tid) {
   Thread t;
   int64_t T = c.B[0] * c.B[1] * c.B[2];
@@ -111,7 +111,7 @@ Thread make_thread(const OCfg &c, const int64_t g[3], int64_t bid, int64_t tid) 
   t.p[2] = bz * c.B[2] + tz;
   if (c.fold_axis == 1) t.p[1] *= c.fold;
   if (c.fold_axis == 2) t.p[2] *= c.fold;
-  // domain guard on every folded point (Sec. 3.4.1)
+  // domain guard on every folded point (Sec. 4.4.1)
   for (int64_t k = 0; k < c.fold; ++k) {
     int64_t q[3] = {t.p[0], t.p[1], t.p[2]};
     if (c.fold_axis == 1) q[1] += k;
@@ -124,14 +124,14 @@ Thread make_thread(const OCfg &c, const int64_t g[3], int64_t bid, int64_t tid) 
   return t;
 }
 
-// Address expression with the base pointer replaced by the field alignment (Sec. 3.3).
+// Address expression with the base pointer replaced by the field alignment (Sec. 4.3).
 int64_t address(const OField &f, const Thread &t, const Off &o) {
   int64_t e = f.stride[0] * (t.p[0] + std::get<0>(o)) + f.stride[1] * (t.p[1] + std::get<1>(o)) +
               f.stride[2] * (t.p[2] + std::get<2>(o)) + f.c + std::get<3>(o);
   return f.align + f.esize * e;
 }
 
-// Bank-conflict visitor for one half-warp instruction (Sec. 3.2).  Unique bank words,
+// Bank-conflict visitor for one half-warp instruction (Sec. 4.2).  Unique bank words,
 // in ascending order, are split greedily into groups whose span stays below the
 // pairing distance; each group costs as many cycles as its most used bank.
 int64_t bank_cycles(const OHw &hw, const std::vector<int64_t> &addrs) {
@@ -155,7 +155,7 @@ int64_t bank_cycles(const OHw &hw, const std::vector<int64_t> &addrs) {
 }
 
 // A sector or line of the wave-level sets.  Linear addresses: (address / unit, 0, 0).
-// Multi-dimensional address space (Sec. 3.4.1): the innermost coordinate in bytes
+// Multi-dimensional address space (Sec. 4.4.1): the innermost coordinate in bytes
 // divided by the unit, and the y and z array coordinates; the base alignment is not
 // part of it, and two tuples are distinct when any coordinate differs.
 typedef std::tuple<int64_t, int64_t, int64_t> Key3;
@@ -200,7 +200,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
     return;
   }
 
-  // ---- launch geometry and the thread groups (Sec. 3.3, 3.4) ----------------------
+  // ---- launch geometry and the thread groups (Sec. 4.3, 4.4) ----------------------
   int64_t fy = c.fold_axis == 1 ? c.fold : 1, fz = c.fold_axis == 2 ? c.fold : 1;
   int64_t g[3] = {ceildiv(c.N[0], c.B[0]), ceildiv(c.N[1], c.B[1] * fy), ceildiv(c.N[2], c.B[2] * fz)};
   int64_t total = g[0] * g[1] * g[2];
@@ -314,7 +314,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
     }
   }
 
-  // ---- per-field counts, summed over fields (fields do not alias, Sec. 3.3) ----------
+  // ---- per-field counts, summed over fields (fields do not alias, Sec. 4.3) ----------
   int64_t bls = 0, bll = 0, bss = 0, bsl = 0, wls = 0, wll = 0, wss = 0, wsl = 0;
   int64_t ovy = 0, ovz = 0, yl = 0, zl = 0;
   for (const FieldSets &f : fs) {
@@ -346,7 +346,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
   // ---- volumes per lattice update, capacity misses, limiters (fp64) ----------------
   double lb = (double)lups_block, lw = (double)lups_wave;
   bool cap = hw.cap != 0;
-  // L1: V_up = per-instruction sector requests, V_comp = block footprint (Sec. 3.3, 3.5)
+  // L1: V_up = per-instruction sector requests, V_comp = block footprint (Sec. 4.3, 4.5)
   double v_l1 = 32.0 * (double)l1_req / lb;
   double v_l1_comp = 32.0 * (double)bls / lb;
   double o_l1 = 128.0 * (double)bll * (double)bpsm / hw.l1;
@@ -354,7 +354,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
   double v_l2_load = v_l1_comp + (1.0 - r_l1) * (v_l1 - v_l1_comp);
   double v_l2_store = 32.0 * (double)l1_store / lb;   // write-through: every store request
   // DRAM: wave footprint minus reuse from the y / z layer sets, plus reads caused by
-  // evicted partially written sectors (Sec. 3.4, 5.5)
+  // evicted partially written sectors (Sec. 4.4, 5.6)
   double v_dram_comp = 32.0 * (double)wls / lw;
   double alloc_per_block = 128.0 * (double)wll / (double)Weff;
   double o_y = (double)ydist * alloc_per_block / hw.l2;
@@ -367,7 +367,7 @@ void estimate_one(const OCfg &c, const OHw &hw, int64_t *oi, double *od) {
   double v_dram_load = v_dram_comp - (r_y * (32.0 * (double)ovy) + r_z * (32.0 * (double)ovz)) / lw +
                        (1.0 - r_st) * v_red_st;
   double v_dram_store = 32.0 * (double)wss / lw;
-  // limiters, seconds per lattice update for the whole GPU (Sec. 2, 3.2)
+  // limiters, seconds per lattice update for the whole GPU (Sec. 2, 4.2)
   double t_l1 = ((double)bank / lb) / (hw.clock * (double)hw.sms);
   double t_l2 = (v_l2_load + v_l2_store) / hw.bw_l2;
   double t_dram = (v_dram_load + v_dram_store) / hw.bw_dram;

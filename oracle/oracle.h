@@ -2,7 +2,7 @@
  * CPU oracle of the metric estimator (test infrastructure only).
  *
  * Plain, slow, obviously correct: every thread's addresses are walked into
- * std::set containers of 32 B sectors and 128 B lines per level (Sec. 3.2-3.4 of
+ * std::set containers of 32 B sectors and 128 B lines per level (Sec. 4.2-4.4 of
  * the paper), and the capacity and performance model is evaluated in fp64.
  * Only the test suite, the smoke check and the CPU-baseline leg of the benchmark
  * may load this library.  It shares no code, header or constant with the CUDA path.

@@ -1,6 +1,6 @@
 // Device side of the metric estimator (sm_103a).
 //
-//   enum_kernel   persistent, work-stealing CTAs.  Representative block (Sec. 3.2, 3.3):
+//   enum_kernel   persistent, work-stealing CTAs.  Representative block (Sec. 4.2, 4.3):
 //                 every (warp, access instruction) pair exactly -- per-instruction unique
 //                 sectors (L1 request / write-through volumes), half-warp bank cycles and
 //                 the block bitmaps.  Wave / y / z sets of field groups that cannot take
@@ -8,12 +8,12 @@
 //                 (segment walk) or address by address.
 //   rows_kernel   wave, y set and z set as whole grid rows: each merged load run of a
 //                 row is one sector range set with 64-bit red.or; per-warp store sectors
-//                 by floor sums (Sec. 3.4, closed-form counting instead of implicit sets).
+//                 by floor sums (Sec. 4.4, closed-form counting instead of implicit sets).
 //   count_kernel  popcounts of the bitmaps: unique sectors, unique 128 B lines (nibble
 //                 OR), y / z overlaps by AND / AND-NOT.  Leaves the bitmaps zeroed for
 //                 the next step (only non-zero positions are written).
-//   model_kernel  fp64 capacity model and limiters (Sec. 2, 3.5), one thread per candidate.
-//   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.7).
+//   model_kernel  fp64 capacity model and limiters (Sec. 2, 4.5), one thread per candidate.
+//   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.8).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -57,7 +57,7 @@ __device__ __forceinline__ uint32_t bitmap_insert(uint32_t *__restrict__ bm, int
   return cnt;
 }
 
-// Bank-conflict visitor for both half warps of one instruction (Sec. 3.2): unique
+// Bank-conflict visitor for both half warps of one instruction (Sec. 4.2): unique
 // bank words of each half warp, split greedily (ascending) into groups spanning less
 // than the pairing distance, each group costs its most used bank.  The result is the
 // sum over both halves, valid in every lane.
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     uint32_t bad = 0;
 
     if (blk) {
-      // ---- representative block (Sec. 3.2, 3.3): every (warp, instruction) exactly --
+      // ---- representative block (Sec. 4.2, 4.3): every (warp, instruction) exactly --
       // distinct sectors per instruction (L1 requests / write-through stores), the block
       // footprint bitmaps, and half-warp bank cycles
       const uint32_t LS = (uint32_t)s_soff[s_g.f_count], L = (uint32_t)s_loff[s_g.f_count];
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
 
       bool fields_done = false;
       if (level >= 1 && s_g.iv) {
-        // ---- interval walk (exact closed-form counting, Sec. 3.4): the warp's valid
+        // ---- interval walk (exact closed-form counting, Sec. 4.4): the warp's valid
         // threads form row segments of consecutive x, and a (segment, merged load run)
         // pair covers one contiguous sector range.  Partial warps (a thread with fewer
         // valid folded points than the fold) take the raw folded loads instead, each
@@ -1107,7 +1107,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
 
 
 // Row walk of the wave and the y / z layer sets (exact closed-form interval counting,
-// Sec. 3.4).  The blocks of a level that share a block row are consecutive in x, so
+// Sec. 4.4).  The blocks of a level that share a block row are consecutive in x, so
 // the threads of those blocks with one (ty, tz) form one grid row of consecutive x.
 // Work item = (field group, chunk of row slots); one grid row per warp.  Each merged
 // load run (raw loads when the row has fewer valid folded points than the fold) is one
@@ -1424,7 +1424,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
   }
 }
 
-// R(O) = a * exp(-b * exp(-c * O)), Sec. 3.5
+// R(O) = a * exp(-b * exp(-c * O)), Sec. 4.5
 __device__ __forceinline__ double rhat_dev(const double h[3], double O) {
   return __dmul_rn(h[0], exp(-__dmul_rn(h[1], exp(-__dmul_rn(h[2], O)))));
 }

@@ -193,7 +193,7 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
     std::sort(v->begin(), v->end());
     v->erase(std::unique(v->begin(), v->end()), v->end());
   }
-  // thread folding (Sec. 5.1): union over k of offset + k * axis, each with the first
+  // thread folding (Sec. 5.2): union over k of offset + k * axis, each with the first
   // folded point k that needs it (ascending offsets)
   auto fold_list = [&](const std::vector<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
     std::vector<std::pair<Off4, int>> all;
@@ -491,7 +491,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     }
   }
 
-  // fields: folded access lists (Sec. 5.1 thread folding), address ranges, bitmaps.
+  // fields: folded access lists (Sec. 5.2 thread folding), address ranges, bitmaps.
   // `mask`: levels the descriptor serves (1 the representative block, 2 the wave and the
   // y / z sets); `key`: list-sharing key (kNoShare = never shared)
   out.f.clear();
@@ -603,7 +603,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       if (rc != WS_OK) return rc;
     }
   } else {
-    // Multi-dimensional address space (Sec. 3.4.1) for the wave and the y / z sets: a
+    // Multi-dimensional address space (Sec. 4.4.1) for the wave and the y / z sets: a
     // sector is (innermost bytes / 32, y, z), without the base alignment.  Each field
     // becomes a block descriptor (linear addresses, as the per-instruction statistics
     // of the representative block need) and a wave descriptor over a virtual linear

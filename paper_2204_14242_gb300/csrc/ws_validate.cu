@@ -1,5 +1,5 @@
 // Validation and calibration kernels (see include/warpspeed_validate.h): the streaming
-// kernels of Sec. 2 and the two kernel families the estimator is evaluated on in Sec. 5
+// kernels of Sec. 3 and the two kernel families the estimator is evaluated on in Sec. 5
 // (a 3D star stencil with thread folding, a pull lattice-Boltzmann step), written plainly
 // so that their memory traffic is what the estimator's address model describes.
 #include <cuda_runtime.h>
@@ -9,7 +9,7 @@
 
 namespace {
 
-// ---- streaming kernels on a repeated data set (Sec. 2) -----------------------------------
+// ---- streaming kernels on a repeated data set (Sec. 3) -----------------------------------
 // The values are moved as 8-byte bit patterns with integer operations: GB300's fp64 pipe
 // is far slower than its memory system, so an fp64 add or multiply per element would
 // measure the fp64 rate instead of the transfer rate.
@@ -79,7 +79,7 @@ __device__ __forceinline__ bool thread_point(const Geo &G, int32_t &x, int32_t &
 
 // ---- 3D star stencil, radius R, FOLD consecutive points along AXIS per thread -----------
 // The folded points of a thread are unrolled with compile-time offsets, so every distinct
-// source address of the thread is loaded once and reused from registers (Sec. 5.3).
+// source address of the thread is loaded once and reused from registers (Sec. 5.4).
 template <int R, int AXIS, int FOLD>
 __global__ void star_kernel(const double *__restrict__ src, double *__restrict__ dst, Geo G) {
   int32_t x, y0, z0;

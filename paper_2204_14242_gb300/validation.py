@@ -2,7 +2,7 @@
 
 Two things the paper does on its own hardware, done here on GB300:
 
-* calibration (Sec. 2): the LOAD and SCALE streaming kernels on repeated data sets of
+* calibration (Sec. 3): the LOAD and SCALE streaming kernels on repeated data sets of
   growing size give the effective L2 size (where the transfer rate falls from the L2
   level) and the L2 and DRAM bandwidths; an fp64 FMA loop gives the fp64 rate.  Together
   with the device's SM count they form a GB300 hardware descriptor.
@@ -12,7 +12,7 @@ Two things the paper does on its own hardware, done here on GB300:
   store volumes and the time; the measured volumes come from the counters the paper uses
   (lts__t_sectors_srcunit_tex_op_read, dram__bytes_read / _write) in an ncu run of the
   same command, and `report` compares them and refits the hit-rate coefficients of the
-  capacity model (Sec. 3.5) to the measurements.
+  capacity model (Sec. 4.5) to the measurements.
 
 Commands (one GPU):
   python -m paper_2204_14242_gb300.validation calibrate > calib.json
@@ -105,7 +105,7 @@ def calibrate(device: int = 0) -> dict:
     sz = np.array([r["bytes"] for r in rows], float)
     l2_level = float(np.median(load[sz <= 16 << 20]))
     dram_level = float(np.median(load[sz >= 1 << 30]))
-    # effective L2 (Sec. 2: the data-set size up to which L2 hits can be relied on): where
+    # effective L2 (Sec. 3: the data-set size up to which L2 hits can be relied on): where
     # the LOAD rate falls below 90 % of its small-data-set level, interpolated in log size
     thr = 0.9 * l2_level
     eff = float(sz[-1])
@@ -168,7 +168,7 @@ SCAN_XY = [128, 192, 256, 320, 384, 448, 512, 576, 640, 768, 896, 1024]
 
 
 def sizescan_set():
-    """Layer-condition size scan (Sec. 5.6): the 25-point star on domains with square XY
+    """Layer-condition size scan (Sec. 5.7): the 25-point star on domains with square XY
     planes of growing size and a constant total of 2^27 points (z = 2^27 / XY^2), for block
     shapes of increasing z extent (waves of 1 .. 32 layers)."""
     out = []

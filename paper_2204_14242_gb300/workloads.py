@@ -48,7 +48,7 @@ class Access:
 
 @dataclass
 class Field:
-    """One array.  Fields never alias (Sec. 3.3); the base pointer is replaced by `align`."""
+    """One array.  Fields never alias (Sec. 4.3); the base pointer is replaced by `align`."""
     elem_bytes: int
     accesses: List[Access]
     align: int = 0
@@ -68,7 +68,7 @@ class Config:
     regs_per_thread: int = 0
     wave_blocks_override: int = 0
     name: str = ""
-    address_mode: int = 0        # 0 linear addresses, 1 multi-dimensional address space (Sec. 3.4.1)
+    address_mode: int = 0        # 0 linear addresses, 1 multi-dimensional address space (Sec. 4.4.1)
 
 
 @dataclass
@@ -78,7 +78,7 @@ class Hardware:
     Values not printed in the paper: max_blocks_sm (32, an A100 datasheet value) and
     regs_sm (65536).  fp_peak = 3.5 Flop/B machine balance x 1400 GB/s (Sec. 5.2).
     hit[i] = (a, b, c) of R(O) = a*exp(-b*exp(-c*O)) for L1, L2 y-layer, L2 z-layer,
-    L2 store (Sec. 3.4); the paper prints no coefficients, these are illustrative.
+    L2 store (Sec. 4.4); the paper prints no coefficients, these are illustrative.
     """
     sms: int = 108
     max_threads_sm: int = 2048
@@ -237,7 +237,7 @@ def stencil_7pt_128() -> Config:
 
 
 def stencil_25pt_sweep(N=(640, 512, 512), variants=FOLD_VARIANTS) -> List[Config]:
-    """3D 25-point star (radius 4), fp64: every block shape x folding variant (Sec. 5.1)."""
+    """3D 25-point star (radius 4), fp64: every block shape x folding variant (Sec. 5.2)."""
     fields = copy_fields(N, star_offsets(4))
     out = []
     for B in block_shapes():

@@ -1,6 +1,6 @@
 """Brute-force counter for tiny grids, written the way the paper evaluates its visitors.
 
-Sec. 3.2 of the paper enumerates thread indices with numpy's ``meshgrid`` and
+Sec. 4.2 of the paper enumerates thread indices with numpy's ``meshgrid`` and
 deduplicates addresses with ``unique``; this module does exactly that, vectorised,
 for one candidate at a time.  It is independent of the C++ oracle (different
 language, different data flow) and is used only to pin it on grids of at most a
@@ -96,7 +96,7 @@ def addresses(f, p, o):
 
 def wave_keys(c, f, p, o, unit):
     """Sector (unit 32) or line (unit 128) identities of the wave-level sets.  Linear
-    mode: the address divided by the unit.  Multi-dimensional address space (Sec. 3.4.1):
+    mode: the address divided by the unit.  Multi-dimensional address space (Sec. 4.4.1):
     the tuple (innermost coordinate in bytes // unit, y, z) without the base alignment,
     packed into one integer (tiny grids only)."""
     if getattr(c, "address_mode", 0) == 0:

@@ -265,7 +265,7 @@ def test_interval_and_address_walks_identical(ctx):
 
 
 def test_multidim_address_space(ctx):
-    """The multi-dimensional address space of Sec. 3.4.1 for the wave-level sets, under
+    """The multi-dimensional address space of Sec. 4.4.1 for the wave-level sets, under
     each walk, against the oracle; the 7-point case against its closed form."""
     import dataclasses
     rng = W.SplitMix64(808)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's multi-dimensional address space (Sec. 3.4.1).
+"""Pins of the oracle's multi-dimensional address space (Sec. 4.4.1).
 
 In that space a wave-level sector is the tuple (innermost coordinate in bytes // 32,
 y, z): two tuples differ when any coordinate differs, the base alignment is not part

@@ -1,12 +1,12 @@
 """Pins of the CPU oracle against things other than itself (all CPU, no GPU).
 
-* brute force: the numpy meshgrid + unique evaluation of Sec. 3.2 on tiny grids;
+* brute force: the numpy meshgrid + unique evaluation of Sec. 4.2 on tiny grids;
 * closed forms: 7-point block and wave (derived from the geometry below), the
-  wave-depth law of Sec. 5.6, the bank-conflict examples of Sec. 3.2, a streaming
-  copy, the D3Q15 240 B/LUP of Sec. 5.2;
+  wave-depth law of Sec. 5.7, the bank-conflict examples of Sec. 4.2, a streaming
+  copy, the D3Q15 240 B/LUP of Sec. 5.3;
 * invariants: inclusion between levels, sector/line bounds, monotonicity in the
   stencil radius, invariance under a one-line shift of the alignment;
-* model special cases fixed by the paper (Sec. 3.5, Sec. 5.4, Sec. 2).
+* model special cases fixed by the paper (Sec. 4.5, Sec. 5.5, Sec. 2).
 """
 import json
 import math
@@ -135,7 +135,7 @@ def test_7pt_block_and_wave_closed_form():
                                           (8, (32, 1, 4), 2), (32, (32, 1, 8), 4),
                                           (16, (32, 1, 16), 1)])
 def test_wave_depth_law(depth, B, fold):
-    """Sec. 5.6: a wave of d whole xy layers loads (d+8)/d values per LUP for the
+    """Sec. 5.7: a wave of d whole xy layers loads (d+8)/d values per LUP for the
     range-4 star (no z reuse): 72/40/24/16/10 B/LUP for d = 1/2/4/8/32."""
     g = golden("wave_depth_law.json")
     N = (32, 32, 256)
@@ -157,7 +157,7 @@ def test_wave_depth_law(depth, B, fold):
 
 @pytest.mark.parametrize("stride", [1, 2, 16])
 def test_bank_conflict_examples(stride):
-    """Sec. 3.2: doubles at A[tid], B[2 tid], D[16 tid] take 1 / 2 / 16 cycles per half warp."""
+    """Sec. 4.2: doubles at A[tid], B[2 tid], D[16 tid] take 1 / 2 / 16 cycles per half warp."""
     g = golden("bank_conflicts.json")
     N = (64, 4, 4)
     f = W.Field(8, [W.Access(0, 0, 0, 0)], strides=(stride, 64 * stride, 256 * stride))
@@ -169,7 +169,7 @@ def test_bank_conflict_examples(stride):
 
 @pytest.mark.parametrize("B", [(16, 2, 1), (16, 4, 8), (32, 2, 2), (64, 1, 4), (256, 4, 1)])
 def test_contiguous_half_warps_take_one_wavefront(B):
-    """Sec. 5.3: a block at least 16 wide loads one contiguous block per half warp."""
+    """Sec. 5.4: a block at least 16 wide loads one contiguous block per half warp."""
     g = golden("bank_conflicts.json")
     N = (256, 64, 64)
     c = W.Config(N=N, B=B, fields=W.copy_fields(N, W.star_offsets(2)))
@@ -180,7 +180,7 @@ def test_contiguous_half_warps_take_one_wavefront(B):
 
 
 def test_narrow_blocks_increase_bank_cycles():
-    """Sec. 5.3: each halving of the block width below 16 adds bank conflicts."""
+    """Sec. 5.4: each halving of the block width below 16 adds bank conflicts."""
     N = (256, 256, 64)
     prev = None
     for B in [(16, 8, 1), (8, 16, 1), (4, 32, 1), (2, 64, 1), (1, 128, 1)]:
@@ -213,7 +213,7 @@ def contiguous_sectors(first_byte, nbytes):
 
 
 def test_d3q15_streaming_volume():
-    """Sec. 5.2: the D3Q15 pull kernel streams 2 x 15 x 8 = 240 B/LUP.
+    """Sec. 5.3: the D3Q15 pull kernel streams 2 x 15 x 8 = 240 B/LUP.
 
     The wave below covers four whole planes, so each array's footprint is one contiguous
     run of 4096 doubles shifted by -c_i: its sectors follow in closed form."""
@@ -280,7 +280,7 @@ def test_one_line_alignment_shift_changes_nothing():
 
 
 def test_model_special_cases_fixed_by_the_paper():
-    """Sec. 3.5 / 5.4: with R_hit = 1 the L2->L1 volume is the compulsory one; with
+    """Sec. 4.5 / 5.5: with R_hit = 1 the L2->L1 volume is the compulsory one; with
     R_hit = 0 it is the whole L1 request volume (upper bound); in between it is linear
     in R_hit.  Sec. 2: the prediction is the slowest limiter."""
     c = W.stencil_25pt_sweep(variants=[(0, 1)])[40]
@@ -318,7 +318,7 @@ def test_model_special_cases_fixed_by_the_paper():
 
 
 def test_fp_is_never_the_limiter_of_the_25pt_stencil():
-    """Sec. 3.1 / 5.1: 25 flops per LUP against >= 16 B/LUP stays below the machine balance."""
+    """Sec. 4.1 / 5.2: 25 flops per LUP against >= 16 B/LUP stays below the machine balance."""
     gold = golden("streaming_volumes.json")["arithmetic_intensity"]
     hw = W.a100()
     assert math.isclose(hw.fp_peak / hw.bw_dram, gold["machine_balance"], rel_tol=1e-12)
