@@ -181,7 +181,11 @@ typedef struct ws_profile {
   int64_t row_reds;          /* 64-bit red.or issued by the row walk                      */
   int64_t block_addresses;   /* (thread, access) address evaluations of the representative
                                 blocks (the exact per-address path)                        */
-} ws_profile; /* 104 bytes */
+  float ms_create_host;      /* wall time of the plan's creation on the host: descriptor
+                                compilation, list sharing, grouping, pass layout           */
+  float ms_create_device;    /* wall time of the rest of the creation: device memory,
+                                descriptor upload, scratch zeroing, stream synchronisation */
+} ws_profile; /* 112 bytes */
 
 typedef struct ws_ctx ws_ctx;
 typedef struct ws_plan ws_plan;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <string>
@@ -28,8 +29,16 @@ struct Arena {
   size_t used();
 };
 
+// Blocks of at least kHostBlockMin bytes for large host arrays, from a process-wide
+// cache (up to 1 GiB of returned blocks is kept), so that creating plan after plan does
+// not fault in fresh pages each time.
+constexpr size_t kHostBlockMin = (size_t)1 << 20;
+void *host_block_alloc(size_t bytes);
+void host_block_free(void *p);
+
 // Allocator whose resize() leaves trivially constructible elements uninitialised, so
-// that large descriptor arrays are first touched by the threads that fill them.
+// that large descriptor arrays are first touched by the threads that fill them; large
+// arrays come from the block cache.
 template <class T>
 struct DefaultInitAlloc : std::allocator<T> {
   template <class U>
@@ -39,6 +48,14 @@ struct DefaultInitAlloc : std::allocator<T> {
   DefaultInitAlloc() = default;
   template <class U>
   DefaultInitAlloc(const DefaultInitAlloc<U> &) {}
+  T *allocate(size_t n) {
+    if (n * sizeof(T) >= kHostBlockMin) return static_cast<T *>(host_block_alloc(n * sizeof(T)));
+    return std::allocator<T>::allocate(n);
+  }
+  void deallocate(T *p, size_t n) {
+    if (n * sizeof(T) >= kHostBlockMin) host_block_free(p);
+    else std::allocator<T>::deallocate(p, n);
+  }
   template <class U>
   void construct(U *p) {
     ::new ((void *)p) U;
@@ -89,6 +106,7 @@ struct ws_plan {
   int64_t item_begin_end = 0, ritem_begin_end = 0, citem_begin_end = 0;
   size_t grab_bytes = 0, counters_bytes = 0;
   int64_t upload_bytes = 0;
+  float ms_create_host = 0, ms_create_device = 0;   // wall times of the creation (host part, device part)
   int64_t d_grp = -1;
   int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,

@@ -16,6 +16,7 @@
 #include <map>
 #include <unordered_map>
 #include <mutex>
+#include <new>
 #include <set>
 #include <sstream>
 #include <string>
@@ -98,9 +99,61 @@ size_t Arena::used() {
 // ---------------------------------------------------------------------------------
 // descriptor compiler
 // ---------------------------------------------------------------------------------
+// Process-wide cache of large host blocks (sizes rounded up to 2 MiB; a cached block
+// serves a request of at least half its size).  Never destroyed: plans may outlive
+// static destructors at exit.
+namespace {
+struct HostBlockCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> free_;         // cached blocks by size
+  std::unordered_map<void *, size_t> size_;    // size of every live or cached block
+  size_t cached = 0;
+};
+HostBlockCache &host_blocks() {
+  static HostBlockCache *c = new HostBlockCache;
+  return *c;
+}
+}  // namespace
+
+void *host_block_alloc(size_t bytes) {
+  const size_t unit = (size_t)2 << 20, need = (bytes + unit - 1) / unit * unit;
+  HostBlockCache &c = host_blocks();
+  {
+    std::lock_guard<std::mutex> g(c.mu);
+    auto it = c.free_.lower_bound(need);
+    if (it != c.free_.end() && it->first <= 2 * need) {
+      void *p = it->second;
+      c.cached -= it->first;
+      c.free_.erase(it);
+      return p;
+    }
+  }
+  void *p = aligned_alloc(4096, need);
+  if (!p) throw std::bad_alloc();
+  std::lock_guard<std::mutex> g(c.mu);
+  c.size_[p] = need;
+  return p;
+}
+
+void host_block_free(void *p) {
+  if (!p) return;
+  HostBlockCache &c = host_blocks();
+  std::lock_guard<std::mutex> g(c.mu);
+  auto it = c.size_.find(p);
+  if (it == c.size_.end()) return;
+  if (c.cached + it->second <= ((size_t)1 << 30)) {
+    c.free_.emplace(it->second, p);
+    c.cached += it->second;
+  } else {
+    c.size_.erase(it);
+    free(p);
+  }
+}
+
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 static int64_t floor_div128(__int128 a, int64_t b) {
+  if (b > 0 && (b & (b - 1)) == 0) return (int64_t)(a >> __builtin_ctzll((unsigned long long)b));   // arithmetic shift = floor
   __int128 q = a / b;
   if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
   return (int64_t)q;
@@ -144,13 +197,14 @@ struct Compiled {
   int64_t lvl_blocks[3] = {0, 0, 0};  // blocks of the wave, y set and z set
   bool rows_geom_ok = false;          // row slots fit the kernel's 32-bit decode
   std::vector<DField> f;
-  std::vector<std::vector<DAcc>> acc;
-  std::vector<std::vector<DIv>> iv;
+  std::vector<DAcc> acc;            // access lists of all its fields, field k at [acc_off[k], acc_off[k + 1])
+  std::vector<DIv> iv;              // merged load intervals likewise
+  std::vector<int32_t> acc_off, iv_off;
   std::vector<uint64_t> fkey;       // (field index, folding): equal keys have equal access lists
   std::vector<int64_t> need_words;  // bitmap words per field
+  size_t dsc_bytes = 0;             // descriptor bytes of its fields, lists and groups
+  size_t need_sum = 0, need_max = 0;  // bitmap bytes of all its fields / of its largest
 };
-
-typedef std::tuple<int64_t, int64_t, int64_t, int64_t> Off4;
 
 // What a field compiles to for one folding (independent of domain and block shape):
 // folded access list with byte offsets and first needed folded point, the raw offset
@@ -165,6 +219,22 @@ struct FieldFold {
 };
 typedef std::map<uint64_t, FieldFold> FieldCache;
 
+// A folded offset (dx, dy, dz, dc) packed so that unsigned order is lexicographic order:
+// |dx|, |dy|, |dz| <= 65535 + 15 fit 18 bits after a 2^17 bias, |dc| < 2^40 fits 41 bits
+// after a 2^40 bias; the low 4 bits carry the folded point k (< 16).
+typedef unsigned __int128 OffKey;
+static inline OffKey off_key(int64_t dx, int64_t dy, int64_t dz, int64_t dc, int k) {
+  return ((OffKey)(uint64_t)(dx + (1 << 17)) << 81) | ((OffKey)(uint64_t)(dy + (1 << 17)) << 63) |
+         ((OffKey)(uint64_t)(dz + (1 << 17)) << 45) | ((OffKey)(uint64_t)(dc + ((int64_t)1 << 40)) << 4) |
+         (OffKey)(unsigned)k;
+}
+static inline void off_unkey(OffKey q, int64_t o[4]) {
+  o[0] = (int64_t)(uint64_t)(q >> 81) - (1 << 17);
+  o[1] = (int64_t)((uint64_t)(q >> 63) & ((1u << 18) - 1)) - (1 << 17);
+  o[2] = (int64_t)((uint64_t)(q >> 45) & ((1u << 18) - 1)) - (1 << 17);
+  o[3] = (int64_t)((uint64_t)(q >> 4) & (((uint64_t)1 << 41) - 1)) - ((int64_t)1 << 40);
+}
+
 static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_acc, int fold_axis, int fold,
                                FieldFold &out) {
   out.status = WS_OK;
@@ -178,8 +248,18 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
   if (std::llabs(F.align_bytes) >= ((int64_t)1 << 50) || std::llabs(F.const_off) >= ((int64_t)1 << 40))
     out.status = WS_EINVAL;
   if (out.status != WS_OK) return;
-  std::vector<Off4> L, S;
-  L.reserve(F.n_access);
+  auto off_elems = [&](int64_t dx, int64_t dy, int64_t dz, int64_t dc) -> __int128 {
+    return (__int128)F.stride[0] * dx + (__int128)F.stride[1] * dy + (__int128)F.stride[2] * dz + dc;
+  };
+  // thread folding (Sec. 5.2): union over k of offset + k * axis, each with the first
+  // folded point k that needs it (ascending offsets); loads and stores separately.  An
+  // issued folded access o' of a thread whose first point is p0 touches the same address
+  // as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e, so valid
+  // points x raw offsets bound every address of the field.
+  static thread_local std::vector<OffKey> lk, sk;
+  lk.clear();
+  sk.clear();
+  bool first = true;
   for (int a = 0; a < F.n_access; ++a) {
     const ws_access &A = acc[F.access_off + a];
     if (std::abs(A.dx) > 65535 || std::abs(A.dy) > 65535 || std::abs(A.dz) > 65535 ||
@@ -187,56 +267,48 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
       out.status = WS_EINVAL;
       return;
     }
-    (A.is_store ? S : L).push_back(Off4(A.dx, A.dy, A.dz, A.dc));
+    const __int128 e = off_elems(A.dx, A.dy, A.dz, A.dc);
+    if (first || e < out.omin) out.omin = e;
+    if (first || e > out.omax) out.omax = e;
+    first = false;
+    std::vector<OffKey> &v = A.is_store ? sk : lk;
+    for (int k = 0; k < fold; ++k)
+      v.push_back(off_key(A.dx, A.dy + (fold_axis == 1 ? k : 0), A.dz + (fold_axis == 2 ? k : 0), A.dc, k));
   }
-  for (auto *v : {&L, &S}) {
-    std::sort(v->begin(), v->end());
-    v->erase(std::unique(v->begin(), v->end()), v->end());
+  int hist[2][16] = {{0}};
+  for (int ls = 0; ls < 2; ++ls) {
+    std::vector<OffKey> &v = ls ? sk : lk;
+    std::sort(v.begin(), v.end());
+    size_t m = 0;
+    for (size_t i = 0; i < v.size(); ++i)
+      if (i == 0 || (v[i] >> 4) != (v[m - 1] >> 4)) v[m++] = v[i];
+    v.resize(m);
   }
-  // thread folding (Sec. 5.2): union over k of offset + k * axis, each with the first
-  // folded point k that needs it (ascending offsets)
-  auto fold_list = [&](const std::vector<Off4> &src, std::vector<std::pair<Off4, int>> &dst) {
-    std::vector<std::pair<Off4, int>> all;
-    all.reserve(src.size() * fold);
-    for (const Off4 &o : src)
-      for (int k = 0; k < fold; ++k) {
-        Off4 q = o;
-        if (fold_axis == 1) std::get<1>(q) += k;
-        if (fold_axis == 2) std::get<2>(q) += k;
-        all.emplace_back(q, k);
-      }
-    std::sort(all.begin(), all.end());
-    for (size_t i = 0; i < all.size(); ++i)
-      if (i == 0 || all[i].first != all[i - 1].first) dst.push_back(all[i]);
-  };
-  std::vector<std::pair<Off4, int>> fl, fs;
-  fold_list(L, fl);
-  fold_list(S, fs);
-  if ((int64_t)(fl.size() + fs.size()) > kMaxFoldedAccesses) {
+  if ((int64_t)(lk.size() + sk.size()) > kMaxFoldedAccesses) {
     out.status = WS_EINVAL;
     return;
   }
-  auto off_elems = [&](const Off4 &o) -> __int128 {
-    return (__int128)F.stride[0] * std::get<0>(o) + (__int128)F.stride[1] * std::get<1>(o) +
-           (__int128)F.stride[2] * std::get<2>(o) + std::get<3>(o);
-  };
-  out.da.clear();
-  for (auto *lst : {&fl, &fs})
-    for (auto &kv : *lst) {
-      DAcc x;
-      x.boff = (int64_t)(off_elems(kv.first) * F.elem_bytes);
-      x.kmin = kv.second;
+  out.da.resize(lk.size() + sk.size());
+  size_t n = 0;
+  for (int ls = 0; ls < 2; ++ls)
+    for (OffKey q : ls ? sk : lk) {
+      int64_t o[4];
+      off_unkey(q, o);
+      DAcc &x = out.da[n++];
+      x.boff = (int64_t)(off_elems(o[0], o[1], o[2], o[3]) * F.elem_bytes);
+      x.kmin = (int32_t)(q & 15);
       x.pad = 0;
-      out.da.push_back(x);
+      hist[ls][x.kmin] += 1;
     }
-  out.n_load = (int32_t)fl.size();
-  out.n_store = (int32_t)fs.size();
+  out.n_load = (int32_t)lk.size();
+  out.n_store = (int32_t)sk.size();
   // merged load intervals: sorted load offsets cut wherever two neighbours are more than
   // 32 B apart (a chain of byte addresses with steps of at most 32 B touches every
   // sector between its ends)
   {
-    std::vector<int64_t> b;
-    for (int i = 0; i < out.n_load; ++i) b.push_back(out.da[i].boff);
+    static thread_local std::vector<int64_t> b;
+    b.resize((size_t)out.n_load);
+    for (int i = 0; i < out.n_load; ++i) b[(size_t)i] = out.da[(size_t)i].boff;
     std::sort(b.begin(), b.end());
     out.iv.clear();
     for (size_t i = 0; i < b.size();) {
@@ -250,23 +322,15 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
       i = j + 1;
     }
   }
-  // An issued folded access o' of a thread whose first point is p0 touches the same
-  // address as the raw offset o = o' - kmin * e from the valid point p0 + kmin * e,
-  // so valid points x raw offsets bound every address of the field.
-  bool first = true;
-  for (auto *src : {&L, &S})
-    for (const Off4 &o : *src) {
-      __int128 e = off_elems(o);
-      if (first || e < out.omin) out.omin = e;
-      if (first || e > out.omax) out.omax = e;
-      first = false;
-    }
+  // issued accesses of a thread with kv valid folded points: those with kmin < kv
+  int nl = 0, ns = 0;
   for (int kv = 0; kv <= 16; ++kv) {
-    int nl = 0, ns = 0;
-    for (auto &x : fl) nl += x.second < kv;
-    for (auto &x : fs) ns += x.second < kv;
     out.cnt_load[kv] = (int16_t)nl;
     out.cnt_store[kv] = (int16_t)ns;
+    if (kv < 16) {
+      nl += hist[0][kv];
+      ns += hist[1][kv];
+    }
   }
 }
 
@@ -291,40 +355,108 @@ static void block_warp_classes(const DCfg &d, int64_t esize, const int64_t strid
   const int64_t g0 = d.g[0], g1 = d.g[1];
   const int64_t bx = d.rep % g0, by = (d.rep / g0) % g1, bz = d.rep / (g0 * g1);
   const int64_t fy = d.fold_axis == 1 ? d.fold : 1, fz = d.fold_axis == 2 ? d.fold : 1;
-  // lane points relative to lane 0 and valid folded points (kv, -1 = no thread)
-  int32_t rel[32][32][4];
-  int64_t ref[32][3];
-  for (int w = 0; w < d.wpb; ++w)
-    for (int l = 0; l < 32; ++l) {
-      const int64_t tid = 32 * w + l;
-      int64_t x = 0, y = 0, z = 0, kv = -1;
-      if (tid < d.T) {
-        const int64_t tx = tid % d.B[0], ty = (tid / d.B[0]) % d.B[1], tz = tid / (d.B[0] * d.B[1]);
-        x = bx * d.B[0] + tx;
-        y = (by * d.B[1] + ty) * fy;
-        z = (bz * d.B[2] + tz) * fz;
-        const bool valid = x < d.N[0] && y < d.N[1] && z < d.N[2];
-        kv = !valid ? 0 : d.fold_axis == 1 ? std::min<int64_t>(d.fold, d.N[1] - y)
-                        : d.fold_axis == 2 ? std::min<int64_t>(d.fold, d.N[2] - z) : 1;
+  const int64_t B0 = d.B[0], B1 = d.B[1];
+  int64_t ref[32][3];   // lane-0 point of each warp
+  int32_t id[32];       // warps with equal ids have equal lane layouts and valid points
+  // A block whose points are all inside the domain with whole folds gives every thread
+  // the same valid folded points, and a full warp's lane offsets from lane 0 depend only
+  // on where its thread index carries into y (first lane c1) and into z (first lane c2).
+  // Such warps are keyed by (c1, c2); keys whose layouts coincide share an id.  Other
+  // blocks compare the lanes of every warp.
+  const bool interior = (bx + 1) * B0 <= d.N[0] && (by + 1) * B1 * fy <= d.N[1] && (bz + 1) * d.B[2] * fz <= d.N[2];
+  if (interior) {
+    int32_t key[32][2], nk = 0, kid[32];
+    int32_t rel[32][32][3];   // lane offsets of each distinct key
+    for (int w = 0; w < d.wpb; ++w) {
+      const int64_t t0 = 32 * (int64_t)w, tx0 = t0 % B0, ty0 = (t0 / B0) % B1, tz0 = t0 / (B0 * B1);
+      ref[w][0] = bx * B0 + tx0;
+      ref[w][1] = (by * B1 + ty0) * fy;
+      ref[w][2] = (bz * d.B[2] + tz0) * fz;
+      if (d.T - t0 < 32) {   // the partial last warp: its missing lanes make it unique
+        id[w] = -1 - w;
+        continue;
       }
-      if (l == 0) {
-        ref[w][0] = x;
-        ref[w][1] = y;
-        ref[w][2] = z;
+      const int32_t c1 = (int32_t)std::min<int64_t>(B0 - tx0, 32), c2 = (int32_t)std::min<int64_t>((B1 - ty0) * B0 - tx0, 32);
+      int k = 0;
+      while (k < nk && !(key[k][0] == c1 && key[k][1] == c2)) ++k;
+      if (k == nk) {
+        key[k][0] = c1;
+        key[k][1] = c2;
+        int64_t tx = tx0, ty = ty0, tz = 0;
+        for (int l = 0; l < 32; ++l) {
+          rel[k][l][0] = (int32_t)(tx - tx0);
+          rel[k][l][1] = (int32_t)((ty - ty0) * fy);
+          rel[k][l][2] = (int32_t)(tz * fz);
+          if (++tx == B0) {
+            tx = 0;
+            if (++ty == B1) {
+              ty = 0;
+              ++tz;
+            }
+          }
+        }
+        kid[k] = k;
+        for (int q = 0; q < k; ++q)
+          if (kid[q] == q && memcmp(rel[q], rel[k], sizeof(rel[k])) == 0) {
+            kid[k] = q;
+            break;
+          }
+        ++nk;
       }
-      rel[w][l][0] = (int32_t)(x - ref[w][0]);
-      rel[w][l][1] = (int32_t)(y - ref[w][1]);
-      rel[w][l][2] = (int32_t)(z - ref[w][2]);
-      rel[w][l][3] = (int32_t)kv;
+      id[w] = kid[k];
     }
+  } else {
+    // lane points relative to lane 0 and valid folded points (kv, -1 = no thread); the
+    // thread coordinates advance incrementally in x-y-z order
+    int32_t rel[32][32][4];
+    int64_t tx = 0, ty = 0, tz = 0;
+    for (int w = 0; w < d.wpb; ++w) {
+      for (int l = 0; l < 32; ++l) {
+        const int64_t tid = 32 * w + l;
+        int64_t x = 0, y = 0, z = 0, kv = -1;
+        if (tid < d.T) {
+          x = bx * B0 + tx;
+          y = (by * B1 + ty) * fy;
+          z = (bz * d.B[2] + tz) * fz;
+          const bool valid = x < d.N[0] && y < d.N[1] && z < d.N[2];
+          kv = !valid ? 0 : d.fold_axis == 1 ? std::min<int64_t>(d.fold, d.N[1] - y)
+                          : d.fold_axis == 2 ? std::min<int64_t>(d.fold, d.N[2] - z) : 1;
+          if (++tx == B0) {
+            tx = 0;
+            if (++ty == B1) {
+              ty = 0;
+              ++tz;
+            }
+          }
+        }
+        if (l == 0) {
+          ref[w][0] = x;
+          ref[w][1] = y;
+          ref[w][2] = z;
+        }
+        int32_t *r = rel[w][l];
+        r[0] = (int32_t)(x - ref[w][0]);
+        r[1] = (int32_t)(y - ref[w][1]);
+        r[2] = (int32_t)(z - ref[w][2]);
+        r[3] = (int32_t)kv;
+      }
+      id[w] = w;
+      for (int q = 0; q < w; ++q)
+        if (id[q] == q && memcmp(rel[q], rel[w], sizeof(rel[w])) == 0) {
+          id[w] = q;
+          break;
+        }
+    }
+  }
   out.n = 0;
   for (int w = 0; w < d.wpb; ++w) {
     int c = 0;
     for (; c < out.n; ++c) {
       const int r = out.warp[c];
+      if (id[w] != id[r]) continue;
       const __int128 delta = (__int128)esize * (stride[0] * (ref[w][0] - ref[r][0]) + stride[1] * (ref[w][1] - ref[r][1]) +
                                                 stride[2] * (ref[w][2] - ref[r][2]));
-      if (delta % period == 0 && memcmp(rel[w], rel[r], sizeof(rel[w])) == 0) break;
+      if (delta % period == 0) break;
     }
     if (c < out.n) {
       out.mult[c] += 1;
@@ -345,7 +477,8 @@ static const uint64_t kNoShare = ~(uint64_t)0;   // a list that no other descrip
 // Returns WS_OK or a per-candidate error status.  `cache` (may be null) memoizes the
 // per-(field, folding) part across candidates that share fields.
 static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
-                          const ws_hw &hw, Compiled &out, FieldCache *cache = nullptr) {
+                          const ws_hw &hw, Compiled &out, FieldCache *cache = nullptr,
+                          const uint8_t *field_refs = nullptr) {
   DCfg &d = out.d;
   memset(&d, 0, sizeof(d));
   for (int k = 0; k < 3; ++k) {
@@ -496,9 +629,40 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   // y / z sets); `key`: list-sharing key (kNoShare = never shared)
   out.f.clear();
   out.acc.clear();
+  out.acc_off.assign(1, 0);
+  out.iv_off.assign(1, 0);
   out.iv.clear();
   out.fkey.clear();
   out.need_words.clear();
+  {
+    const size_t nd = (size_t)c.n_field * (c.address_mode == WS_ADDR_MULTIDIM ? 2 : 1);
+    out.f.reserve(nd);
+    out.acc_off.reserve(nd + 1);
+    out.iv_off.reserve(nd + 1);
+    out.fkey.reserve(nd);
+    out.need_words.reserve(nd);
+  }
+  // Pairs of thread rows (t = ty + B1 * tz) ta < tb = ta + j that share a warp.  With
+  // jq = j / B1 and jr = j % B1 their (ty, tz) offsets are (jr, jq) when ta % B1 + jr < B1
+  // and (jr - B1, jq + 1) otherwise; bit 0 / bit 1 of pair_kind[j] record which occur.
+  // The rows of a warp are consecutive, so the residues ta % B1 of its pairs at distance
+  // j form one cyclic run starting at t0 % B1.
+  uint8_t pair_kind[32] = {0};
+  bool pairs_done = false;
+  auto row_pairs = [&]() {
+    if (pairs_done) return;
+    pairs_done = true;
+    const int64_t B1 = c.B[1], nrows = (int64_t)c.B[1] * c.B[2];
+    for (int64_t w = 0; w < d.wpb; ++w) {
+      const int64_t t0 = (32 * w) / c.B[0], t1 = std::min<int64_t>((32 * w + 31) / c.B[0], nrows - 1);
+      const int64_t r0 = t0 % B1;
+      for (int64_t j = 1; j <= t1 - t0; ++j) {
+        const int64_t jr = j % B1, last = r0 + (t1 - j - t0);   // residues r0 .. last (mod B1)
+        if (r0 < B1 - jr || last >= B1) pair_kind[j] |= 1;
+        if (jr > 0 && last >= B1 - jr) pair_kind[j] |= 2;
+      }
+    }
+  };
   auto emit = [&](const ws_field &F, const FieldFold *ff, int mask, uint64_t key, bool first) -> int {
     DField df;
     memset(&df, 0, sizeof(df));
@@ -549,22 +713,20 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     // further apart than a row's byte span plus 31
     df.rows_ok = 1;
     if (ff->n_store > 0) {
+      row_pairs();
       const int64_t span = (int64_t)F.elem_bytes * std::llabs(F.stride[0]) * (c.B[0] - 1);
-      const int64_t fy2 = c.fold_axis == 1 ? c.fold : 1, fz2 = c.fold_axis == 2 ? c.fold : 1;
-      for (int64_t w = 0; w < d.wpb && df.rows_ok; ++w) {
-        const int64_t t0 = (32 * w) / c.B[0], t1 = std::min<int64_t>((32 * w + 31) / c.B[0], (int64_t)c.B[1] * c.B[2] - 1);
-        for (int64_t ta = t0; ta <= t1 && df.rows_ok; ++ta)
-          for (int64_t tb = ta + 1; tb <= t1; ++tb) {
-            const __int128 dy = (__int128)(tb % c.B[1] - ta % c.B[1]) * fy2 * F.stride[1];
-            const __int128 dz = (__int128)(tb / c.B[1] - ta / c.B[1]) * fz2 * F.stride[2];
-            __int128 delta = (dy + dz) * F.elem_bytes;
-            if (delta < 0) delta = -delta;
-            if (delta <= (__int128)span + 31) {
-              df.rows_ok = 0;
-              break;
-            }
+      const int64_t B1 = c.B[1];
+      for (int64_t j = 1; j < 32 && df.rows_ok; ++j)
+        for (int k = 0; k < 2; ++k) {
+          if (!((pair_kind[j] >> k) & 1)) continue;
+          const int64_t dyr = k ? j % B1 - B1 : j % B1, dzr = k ? j / B1 + 1 : j / B1;
+          __int128 delta = ((__int128)dyr * fy * F.stride[1] + (__int128)dzr * fz * F.stride[2]) * F.elem_bytes;
+          if (delta < 0) delta = -delta;
+          if (delta <= (__int128)span + 31) {
+            df.rows_ok = 0;
+            break;
           }
-      }
+        }
     }
     for (int kv = 0; kv <= 16; ++kv) {
       df.cnt_load[kv] = ff->cnt_load[kv];
@@ -575,15 +737,22 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     if (has_l) need += df.words[0] + 3 * df.words[1];
     if (has_s) need += df.words[0] + df.words[1];
     out.f.push_back(df);
-    out.acc.push_back(ff->da);
-    out.iv.push_back(ff->iv);
+    out.acc.insert(out.acc.end(), ff->da.begin(), ff->da.end());
+    out.iv.insert(out.iv.end(), ff->iv.begin(), ff->iv.end());
+    out.acc_off.push_back((int32_t)out.acc.size());
+    out.iv_off.push_back((int32_t)out.iv.size());
     out.fkey.push_back(key);
     out.need_words.push_back(need);
     return WS_OK;
   };
-  auto fold_of = [&](int fi, FieldFold &local) -> const FieldFold * {
+  // the folded lists of field fi: from the cache when other candidates use the field too,
+  // else compiled into `local` (then *own = true: the list is this candidate's alone);
+  // tl_fold is this thread's reusable one
+  static thread_local FieldFold tl_fold;
+  auto fold_of = [&](int fi, FieldFold &local, bool *own) -> FieldFold * {
     const ws_field &F = fld[c.field_off + fi];
-    if (!cache) {
+    *own = !cache || (field_refs && field_refs[c.field_off + fi] < 2);
+    if (*own) {
       compile_field_fold(F, acc, n_acc, c.fold_axis, c.fold, local);
       return &local;
     }
@@ -596,10 +765,10 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
   };
   if (c.address_mode == WS_ADDR_LINEAR) {
     for (int fi = 0; fi < c.n_field; ++fi) {
-      FieldFold local;
-      const FieldFold *ff = fold_of(fi, local);
+      bool own;
+      FieldFold *ff = fold_of(fi, tl_fold, &own);
       if (ff->status != WS_OK) return ff->status;
-      const int rc = emit(fld[c.field_off + fi], ff, 3, fold_key(c, fi), fi == 0);
+      const int rc = emit(fld[c.field_off + fi], ff, 3, own ? kNoShare : fold_key(c, fi), fi == 0);
       if (rc != WS_OK) return rc;
     }
   } else {
@@ -611,12 +780,11 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     // virtual address = Xbias + innermost bytes + RS * (y - y0) + PS * (z - z0), so
     // that virtual sectors and lines are exactly the tuples.  RS and PS are common to
     // the candidate's fields (equal layouts stay one uniform group).
-    std::vector<const FieldFold *> ffs(c.n_field);
-    std::vector<FieldFold> locals(c.n_field);
     for (int fi = 0; fi < c.n_field; ++fi) {
-      ffs[fi] = fold_of(fi, locals[fi]);
-      if (ffs[fi]->status != WS_OK) return ffs[fi]->status;
-      const int rc = emit(fld[c.field_off + fi], ffs[fi], 1, fold_key(c, fi), fi == 0);
+      bool own;
+      FieldFold *ff = fold_of(fi, tl_fold, &own);
+      if (ff->status != WS_OK) return ff->status;
+      const int rc = emit(fld[c.field_off + fi], ff, 1, own ? kNoShare : fold_key(c, fi), fi == 0);
       if (rc != WS_OK) return rc;
     }
     __int128 ymin = 0, ymax = 0, zmin = 0, zmax = 0;
@@ -658,10 +826,9 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       V.stride[1] = (int64_t)(RS / F.elem_bytes);
       V.stride[2] = (int64_t)(PS / F.elem_bytes);
       V.align_bytes = (int64_t)(xbias[fi] - RS * ymin - PS * zmin);
-      FieldFold vf;
-      compile_field_fold(V, acc, n_acc, c.fold_axis, c.fold, vf);
-      if (vf.status != WS_OK) return vf.status;
-      const int rc = emit(V, &vf, 2, kNoShare, false);
+      compile_field_fold(V, acc, n_acc, c.fold_axis, c.fold, tl_fold);
+      if (tl_fold.status != WS_OK) return tl_fold.status;
+      const int rc = emit(V, &tl_fold, 2, kNoShare, false);
       if (rc != WS_OK) return rc;
     }
   }
@@ -1255,14 +1422,40 @@ static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, i
   status.assign(n_cfg, WS_OK);
   // chunks of consecutive candidates handed out dynamically; each thread keeps its fold
   // cache across its chunks (neighbouring candidates often share fields)
+  // candidates per field (saturated at 2): only fields that several candidates use go
+  // through the fold cache
+  std::vector<uint8_t> refs((size_t)n_fld, 0);
+  {
+    std::vector<int32_t> diff((size_t)n_fld + 1, 0);
+    for (int i = 0; i < n_cfg; ++i) {
+      const ws_config &c = cfgs[i];
+      if (c.n_field < 1 || c.field_off < 0 || c.field_off + c.n_field > n_fld) continue;
+      diff[(size_t)c.field_off] += 1;
+      diff[(size_t)(c.field_off + c.n_field)] -= 1;
+    }
+    int32_t run = 0;
+    for (int f = 0; f < n_fld; ++f) {
+      run += diff[(size_t)f];
+      refs[(size_t)f] = (uint8_t)std::min(run, 2);
+    }
+  }
   const int nth = n_cfg >= 64 ? HostPool::get().width() : 1;
   const int chunk = 32;
   std::atomic<int> next(0);
   HostPool::get().run(nth, [&](int) {
     FieldCache cache;
     for (int c = next.fetch_add(1); c * chunk < n_cfg; c = next.fetch_add(1))
-      for (int i = c * chunk; i < std::min(n_cfg, (c + 1) * chunk); ++i)
-        status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, comp[i], &cache);
+      for (int i = c * chunk; i < std::min(n_cfg, (c + 1) * chunk); ++i) {
+        Compiled &cc = comp[i];
+        status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, cc, &cache, refs.data());
+        if (status[i] != WS_OK) continue;
+        for (size_t k = 0; k < cc.f.size(); ++k) {
+          cc.dsc_bytes += sizeof(DField) + sizeof(DGroup) + (size_t)(cc.acc_off[k + 1] - cc.acc_off[k]) * sizeof(DAcc) +
+                          (size_t)(cc.iv_off[k + 1] - cc.iv_off[k]) * sizeof(DIv);
+          cc.need_sum += (size_t)cc.need_words[k] * 4;
+          cc.need_max = std::max(cc.need_max, (size_t)cc.need_words[k] * 4);
+        }
+      }
   });
 }
 
@@ -1276,7 +1469,8 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
     Compiled cc;
     if (compile_config(cfgs[i], fld, n_fld, acc, n_acc, *hw, cc, &cache) != WS_OK) continue;
     for (size_t k = 0; k < cc.f.size(); ++k) {
-      dsc += sizeof(DField) + sizeof(DGroup) + cc.acc[k].size() * sizeof(DAcc) + cc.iv[k].size() * sizeof(DIv);
+      dsc += sizeof(DField) + sizeof(DGroup) + (size_t)(cc.acc_off[k + 1] - cc.acc_off[k]) * sizeof(DAcc) +
+             (size_t)(cc.iv_off[k + 1] - cc.iv_off[k]) * sizeof(DIv);
       scr += (size_t)cc.need_words[k] * 4;
       mf = std::max(mf, (size_t)cc.need_words[k] * 4);
     }
@@ -1292,16 +1486,101 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
 // builds field groups and cuts passes.  avail_fn(descriptor bytes) gives the scratch
 // capacity.  Needs no device.
 struct HostDesc {
-  std::vector<DCfg> hcfg;
+  HostVec<DCfg> hcfg;
   HostVec<DAcc> hacc;
   HostVec<DIv> hiv;
   size_t scratch = 0, desc_bytes = 0;
 };
 
+// Field groups of candidate i (fields already in p->hfld): consecutive fields bounded by
+// the shared-memory staging (fields, folded accesses) and by what one pass of scratch
+// holds; appended to `go` with the per-group walk decisions.
+struct GroupOut {
+  std::vector<DGroup> g;
+  std::vector<char> iv_ok, rows_ok;
+  std::vector<int64_t> slots, winstr;
+  std::vector<WarpClasses> cls;
+  int32_t iv_cap = 0;
+};
+
+static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &hw, GroupOut &go) {
+  const int a = p->cfg_cf_begin[i], b = p->cfg_cf_begin[i + 1];
+  int k = a;
+  bool wave_seen = false;
+  while (k < b) {
+    DGroup G;
+    memset(&G, 0, sizeof(G));
+    G.cfg = i;
+    G.f_begin = k;
+    G.first_of_cfg = k == a;
+    G.mw_block = p->hfld[k].mw_block;
+    G.levels = p->hfld[k].level_mask;
+    G.first_wave = (G.levels & 2) && !wave_seen;
+    wave_seen = wave_seen || (G.levels & 2);
+    int64_t need = 0;
+    while (k < b) {
+      const DField &f = p->hfld[k];
+      const int na = f.n_load + f.n_store;
+      if (G.f_count > 0 && (G.f_count >= kMaxGroupFields || G.acc_count + na > kMaxFoldedAccesses ||
+                            need + p->need_words[k] > p->scratch_words || f.level_mask != G.levels))
+        break;
+      G.f_count += 1;
+      G.acc_count += na;
+      G.n_loads += f.n_load;
+      G.n_stores += f.n_store;
+      G.mw_end = std::max(G.mw_end, f.mw_end);
+      need += p->need_words[k];
+      ++k;
+    }
+    // uniform layout: a field's relative address is the shared thread address plus a
+    // per-field constant, so all the group's accesses can be walked as one list
+    G.uniform = 1;
+    G.iv = 1;
+    for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
+      const DField &f = p->hfld[q], &f0 = p->hfld[G.f_begin];
+      if (f.wide || f.esize != f0.esize || f.stride[0] != f0.stride[0] || f.stride[1] != f0.stride[1] ||
+          f.stride[2] != f0.stride[2])
+        G.uniform = 0;
+      if (!f.iv) G.iv = 0;
+      G.n_iv += f.n_iv;
+    }
+    // interval walk: uniform groups whose row segments have contiguous sectors
+    G.iv = G.iv && G.uniform;
+    if (G.iv) go.iv_cap = std::max(go.iv_cap, G.n_iv);
+    // row walk: interval groups whose store counts add up per row segment
+    bool rows = G.iv && cc.rows_geom_ok && (G.levels & 2);
+    int64_t instr_w = 0, instr_yz = 0;
+    for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
+      rows = rows && p->hfld[q].rows_ok;
+      instr_w += p->hfld[q].n_load + p->hfld[q].n_store;
+      instr_yz += p->hfld[q].n_load;
+    }
+    const DCfg &dc = cc.d;
+    go.iv_ok.push_back((char)G.iv);
+    go.rows_ok.push_back((char)rows);
+    // with the block level when the group also serves the representative block
+    go.slots.push_back(dc.rows_slot_end[(G.levels & 1) ? 3 : 2]);
+    {
+      const DField &f0 = p->hfld[G.f_begin], &c0 = p->hfld[a];
+      WarpClasses wc;
+      if (rows && (G.levels & 1)) {
+        if (f0.esize == c0.esize && f0.stride[0] == c0.stride[0] && f0.stride[1] == c0.stride[1] &&
+            f0.stride[2] == c0.stride[2])
+          wc = cc.cls;
+        else
+          block_warp_classes(dc, f0.esize, f0.stride, hw, wc);
+      }
+      go.cls.push_back(wc);
+    }
+    go.winstr.push_back((cc.lvl_blocks[0] * instr_w + (cc.lvl_blocks[1] + cc.lvl_blocks[2]) * instr_yz) * dc.wpb);
+    go.g.push_back(G);
+  }
+}
+
 static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                        const ws_access *acc, int n_acc, const ws_hw *hw,
                        const std::function<size_t(size_t)> &avail_fn, HostDesc &h) {
-  std::vector<DCfg> &hcfg = h.hcfg;
+  HostVec<DCfg> &hcfg = h.hcfg;
   HostVec<DAcc> &hacc = h.hacc;
   HostVec<DIv> &hiv = h.hiv;
   hcfg.resize(n_cfg);
@@ -1309,17 +1588,14 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   std::vector<Compiled> comp;
   std::vector<int> status;
   compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, comp, status);
-  // scratch capacity: what the arena can give after the descriptors
+  // scratch capacity: what the arena can give after the descriptors (a field, its access
+  // and interval lists, at most one field group each)
   size_t dsc = 64 * 1024, total_need = 0, max_field = 0;
   for (int i = 0; i < n_cfg; ++i) {
     if (status[i] != WS_OK) continue;
-    for (size_t k = 0; k < comp[i].f.size(); ++k) {
-      // a field, its access and interval lists, at most one field group
-      dsc += sizeof(DField) + sizeof(DGroup) + comp[i].acc[k].size() * sizeof(DAcc) +
-             comp[i].iv[k].size() * sizeof(DIv);
-      total_need += (size_t)comp[i].need_words[k] * 4;
-      max_field = std::max(max_field, (size_t)comp[i].need_words[k] * 4);
-    }
+    dsc += comp[i].dsc_bytes;
+    total_need += comp[i].need_sum;
+    max_field = std::max(max_field, comp[i].need_max);
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
   const size_t avail = avail_fn(dsc);
@@ -1327,159 +1603,112 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   scratch = std::max<size_t>(scratch, 16);
   h.scratch = scratch;
   h.desc_bytes = dsc;
-  for (int i = 0; i < n_cfg; ++i) {
-    if (status[i] != WS_OK) continue;
-    for (int64_t w : comp[i].need_words)
-      if ((size_t)w * 4 > scratch) status[i] = WS_ENOMEM;
-  }
-  // descriptors: fields in candidate order; candidates sharing a field and a folding
-  // share its access and interval lists on the device (dedup by sorting fold keys)
+  for (int i = 0; i < n_cfg; ++i)
+    if (status[i] == WS_OK && comp[i].need_max > scratch) status[i] = WS_ENOMEM;
+  // descriptors: fields in candidate order; candidates that share a field and a folding
+  // share its access and interval lists on the device (the first such field owns them)
   std::vector<int64_t> cf_off(n_cfg + 1, 0);
   for (int i = 0; i < n_cfg; ++i) cf_off[i + 1] = cf_off[i] + (status[i] == WS_OK ? (int64_t)comp[i].f.size() : 0);
   const int64_t nf = cf_off[n_cfg];
-  std::vector<std::pair<uint64_t, int64_t>> keys((size_t)nf);
-  std::vector<int32_t> cf_cfg((size_t)nf);
-  for (int i = 0; i < n_cfg; ++i)
-    for (int64_t j = cf_off[i]; j < cf_off[i + 1]; ++j) {
-      keys[(size_t)j] = std::make_pair(comp[i].fkey[(size_t)(j - cf_off[i])], j);
-      cf_cfg[(size_t)j] = i;
-    }
-  std::sort(keys.begin(), keys.end());
   std::vector<int32_t> acc_b((size_t)nf), iv_b((size_t)nf);
   std::vector<char> owner((size_t)nf, 0);
   int64_t na = 0, ni = 0;
-  for (size_t r = 0; r < keys.size();) {
-    // a run of equal keys shares one list; kNoShare keys are runs of one
-    size_t e = r + 1;
-    while (e < keys.size() && keys[e].first == keys[r].first && keys[r].first != kNoShare) ++e;
-    const int64_t j0 = keys[r].second;
-    const int i0 = cf_cfg[(size_t)j0];
-    const size_t k0 = (size_t)(j0 - cf_off[i0]);
-    owner[(size_t)j0] = 1;
-    for (size_t q = r; q < e; ++q) {
-      acc_b[(size_t)keys[q].second] = (int32_t)na;
-      iv_b[(size_t)keys[q].second] = (int32_t)ni;
-    }
-    na += (int64_t)comp[i0].acc[k0].size();
-    ni += (int64_t)comp[i0].iv[k0].size();
-    r = e;
+  {
+    std::unordered_map<uint64_t, int64_t> first;   // shared fold key -> owning field
+    for (int i = 0; i < n_cfg; ++i)
+      for (int64_t j = cf_off[i]; j < cf_off[i + 1]; ++j) {
+        const size_t k = (size_t)(j - cf_off[i]);
+        const uint64_t key = comp[i].fkey[k];
+        if (key != kNoShare) {
+          auto it = first.find(key);
+          if (it != first.end()) {
+            acc_b[(size_t)j] = acc_b[(size_t)it->second];
+            iv_b[(size_t)j] = iv_b[(size_t)it->second];
+            continue;
+          }
+          first.emplace(key, j);
+        }
+        owner[(size_t)j] = 1;
+        acc_b[(size_t)j] = (int32_t)na;
+        iv_b[(size_t)j] = (int32_t)ni;
+        na += comp[i].acc_off[k + 1] - comp[i].acc_off[k];
+        ni += comp[i].iv_off[k + 1] - comp[i].iv_off[k];
+      }
   }
   hacc.resize((size_t)na);
   hiv.resize((size_t)ni);
   p->hfld.resize((size_t)nf);
   p->need_words.resize((size_t)nf);
   for (int i = 0; i <= n_cfg; ++i) p->cfg_cf_begin[i] = (int32_t)cf_off[i];
-  auto fill = [&](int t, int nth) {
-    for (int i = t; i < n_cfg; i += nth) {
-      DCfg &d = hcfg[i];
-      if (status[i] == WS_OK) d = comp[i].d;
-      else memset(&d, 0, sizeof(d));
-      d.status = status[i];
-      d.field_begin = (int32_t)cf_off[i];
-      if (status[i] != WS_OK) {
-        d.n_field = 0;
-        continue;
-      }
-      for (size_t k = 0; k < comp[i].f.size(); ++k) {
-        const size_t j = (size_t)cf_off[i] + k;
-        DField f = comp[i].f[k];
-        f.cfg = i;
-        f.acc_begin = acc_b[j];
-        f.iv_begin = iv_b[j];
-        p->hfld[j] = f;
-        p->need_words[j] = comp[i].need_words[k];
-        if (owner[j]) {
-          std::copy(comp[i].acc[k].begin(), comp[i].acc[k].end(), hacc.begin() + acc_b[j]);
-          std::copy(comp[i].iv[k].begin(), comp[i].iv[k].end(), hiv.begin() + iv_b[j]);
+  p->scratch_words = (int64_t)(scratch / 4);
+  // per candidate, in parallel over dynamic chunks: its DCfg, DFields and owned lists,
+  // then its field groups (into the chunk's output); its compiled lists are freed here
+  const int chunk = 64;
+  const int n_chunks = (n_cfg + chunk - 1) / chunk;
+  std::vector<GroupOut> gout((size_t)n_chunks);
+  std::vector<int32_t> grp_count((size_t)n_cfg, 0);
+  std::atomic<int> next(0);
+  auto fill = [&](int) {
+    for (int ch = next.fetch_add(1); ch < n_chunks; ch = next.fetch_add(1)) {
+      GroupOut &go = gout[(size_t)ch];
+      for (int i = ch * chunk; i < std::min(n_cfg, (ch + 1) * chunk); ++i) {
+        DCfg &d = hcfg[i];
+        if (status[i] == WS_OK) d = comp[i].d;
+        else memset(&d, 0, sizeof(d));
+        d.status = status[i];
+        d.field_begin = (int32_t)cf_off[i];
+        if (status[i] != WS_OK) {
+          d.n_field = 0;
+          continue;
         }
+        Compiled &cc = comp[i];
+        for (size_t k = 0; k < cc.f.size(); ++k) {
+          const size_t j = (size_t)cf_off[i] + k;
+          DField f = cc.f[k];
+          f.cfg = i;
+          f.acc_begin = acc_b[j];
+          f.iv_begin = iv_b[j];
+          p->hfld[j] = f;
+          p->need_words[j] = cc.need_words[k];
+          if (owner[j]) {
+            std::copy(cc.acc.begin() + cc.acc_off[k], cc.acc.begin() + cc.acc_off[k + 1], hacc.begin() + acc_b[j]);
+            std::copy(cc.iv.begin() + cc.iv_off[k], cc.iv.begin() + cc.iv_off[k + 1], hiv.begin() + iv_b[j]);
+          }
+        }
+        const size_t before = go.g.size();
+        build_groups(p, i, cc, *hw, go);
+        grp_count[(size_t)i] = (int32_t)(go.g.size() - before);
+        std::vector<DField>().swap(cc.f);
+        std::vector<DAcc>().swap(cc.acc);
+        std::vector<DIv>().swap(cc.iv);
       }
     }
   };
   {
     const int nth = n_cfg >= 256 ? HostPool::get().width() : 1;
-    HostPool::get().run(nth, [&](int t) { fill(t, nth); });
+    HostPool::get().run(nth, fill);
   }
   p->cfg_cf_begin[n_cfg] = (int32_t)p->hfld.size();
-  p->scratch_words = (int64_t)(scratch / 4);
-  // field groups: consecutive fields of a candidate, bounded by the shared-memory
-  // staging (fields, folded accesses) and by what one pass of scratch holds
+  // concatenate the chunks' groups in candidate order
   p->cfg_grp_begin.assign(n_cfg + 1, 0);
-  for (int i = 0; i < n_cfg; ++i) {
-    p->cfg_grp_begin[i] = (int32_t)p->hgrp.size();
-    const int a = p->cfg_cf_begin[i], b = p->cfg_cf_begin[i + 1];
-    int k = a;
-    bool wave_seen = false;
-    while (k < b) {
-      DGroup G;
-      memset(&G, 0, sizeof(G));
-      G.cfg = i;
-      G.f_begin = k;
-      G.first_of_cfg = k == a;
-      G.mw_block = p->hfld[k].mw_block;
-      G.levels = p->hfld[k].level_mask;
-      G.first_wave = (G.levels & 2) && !wave_seen;
-      wave_seen = wave_seen || (G.levels & 2);
-      int64_t need = 0;
-      while (k < b) {
-        const DField &f = p->hfld[k];
-        const int na = f.n_load + f.n_store;
-        if (G.f_count > 0 && (G.f_count >= kMaxGroupFields || G.acc_count + na > kMaxFoldedAccesses ||
-                              need + p->need_words[k] > p->scratch_words || f.level_mask != G.levels))
-          break;
-        G.f_count += 1;
-        G.acc_count += na;
-        G.n_loads += f.n_load;
-        G.n_stores += f.n_store;
-        G.mw_end = std::max(G.mw_end, f.mw_end);
-        need += p->need_words[k];
-        ++k;
-      }
-      // uniform layout: a field's relative address is the shared thread address plus a
-      // per-field constant, so all the group's accesses can be walked as one list
-      G.uniform = 1;
-      G.iv = 1;
-      for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
-        const DField &f = p->hfld[q], &f0 = p->hfld[G.f_begin];
-        if (f.wide || f.esize != f0.esize || f.stride[0] != f0.stride[0] || f.stride[1] != f0.stride[1] ||
-            f.stride[2] != f0.stride[2])
-          G.uniform = 0;
-        if (!f.iv) G.iv = 0;
-        G.n_iv += f.n_iv;
-      }
-      // interval walk: uniform groups whose row segments have contiguous sectors
-      G.iv = G.iv && G.uniform;
-      if (G.iv) p->iv_cap = std::max(p->iv_cap, G.n_iv);
-      // row walk: interval groups whose store counts add up per row segment
-      bool rows = G.iv && comp[i].rows_geom_ok && (G.levels & 2);
-      int64_t instr_w = 0, instr_yz = 0;
-      for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
-        rows = rows && p->hfld[q].rows_ok;
-        instr_w += p->hfld[q].n_load + p->hfld[q].n_store;
-        instr_yz += p->hfld[q].n_load;
-      }
-      const DCfg &dc = comp[i].d;
-      p->grp_iv_ok.push_back((char)G.iv);
-      p->grp_rows_ok.push_back((char)rows);
-      // with the block level when the group also serves the representative block
-      p->grp_slots.push_back(dc.rows_slot_end[(G.levels & 1) ? 3 : 2]);
-      {
-        const DField &f0 = p->hfld[G.f_begin], &c0 = p->hfld[p->cfg_cf_begin[i]];
-        WarpClasses wc;
-        if (rows && (G.levels & 1)) {
-          if (f0.esize == c0.esize && f0.stride[0] == c0.stride[0] && f0.stride[1] == c0.stride[1] &&
-              f0.stride[2] == c0.stride[2])
-            wc = comp[i].cls;
-          else
-            block_warp_classes(dc, f0.esize, f0.stride, *hw, wc);
-        }
-        p->grp_classes.push_back(wc);
-      }
-      p->grp_winstr_rows.push_back(
-          (comp[i].lvl_blocks[0] * instr_w + (comp[i].lvl_blocks[1] + comp[i].lvl_blocks[2]) * instr_yz) * dc.wpb);
-      p->hgrp.push_back(G);
-    }
+  for (int i = 0; i < n_cfg; ++i) p->cfg_grp_begin[i + 1] = p->cfg_grp_begin[i] + grp_count[(size_t)i];
+  const size_t ng = (size_t)p->cfg_grp_begin[n_cfg];
+  p->hgrp.clear();
+  p->hgrp.reserve(ng);
+  p->grp_iv_ok.reserve(ng);
+  p->grp_rows_ok.reserve(ng);
+  p->grp_slots.reserve(ng);
+  p->grp_classes.reserve(ng);
+  p->grp_winstr_rows.reserve(ng);
+  for (GroupOut &go : gout) {
+    p->hgrp.insert(p->hgrp.end(), go.g.begin(), go.g.end());
+    p->grp_iv_ok.insert(p->grp_iv_ok.end(), go.iv_ok.begin(), go.iv_ok.end());
+    p->grp_rows_ok.insert(p->grp_rows_ok.end(), go.rows_ok.begin(), go.rows_ok.end());
+    p->grp_slots.insert(p->grp_slots.end(), go.slots.begin(), go.slots.end());
+    p->grp_classes.insert(p->grp_classes.end(), go.cls.begin(), go.cls.end());
+    p->grp_winstr_rows.insert(p->grp_winstr_rows.end(), go.winstr.begin(), go.winstr.end());
+    p->iv_cap = std::max(p->iv_cap, go.iv_cap);
   }
-  p->cfg_grp_begin[n_cfg] = (int32_t)p->hgrp.size();
   p->layout();
 }
 
@@ -1514,6 +1743,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   default_tuning(p->tune);
 
   HostDesc h;
+  const auto t_begin = std::chrono::steady_clock::now();
   build_host(p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t dsc) {
     size_t avail = ctx->arena->largest_free();
     avail = avail > dsc + (8 << 20) ? avail - dsc - (8 << 20) : 0;
@@ -1521,7 +1751,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     if (scratch_cap) avail = std::min(avail, scratch_cap);
     return avail;
   }, h);
-  std::vector<DCfg> &hcfg = h.hcfg;
+  const auto t_host = std::chrono::steady_clock::now();
+  HostVec<DCfg> &hcfg = h.hcfg;
   HostVec<DAcc> &hacc = h.hacc;
   HostVec<DIv> &hiv = h.hiv;
   const size_t scratch = h.scratch;
@@ -1589,6 +1820,11 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
   if (!upload && (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
   p->scratch_bytes = scratch;
+  {
+    const auto t_end = std::chrono::steady_clock::now();
+    p->ms_create_host = std::chrono::duration<float, std::milli>(t_host - t_begin).count();
+    p->ms_create_device = std::chrono::duration<float, std::milli>(t_end - t_host).count();
+  }
   p->upload_bytes = (int64_t)(hcfg.size() * sizeof(DCfg) + p->hfld.size() * sizeof(DField) +
                               p->hgrp.size() * sizeof(DGroup) + hacc.size() * sizeof(DAcc) +
                               hiv.size() * sizeof(DIv) + seg.size() * sizeof(int32_t));
@@ -1657,6 +1893,8 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
     out->count_items = p->citem_begin_end;
     out->passes = (int64_t)p->passes.size();
     out->upload_bytes = p->upload_bytes;
+    out->ms_create_host = p->ms_create_host;
+    out->ms_create_device = p->ms_create_device;
     std::vector<int64_t> cnt((size_t)p->n_cfg * N_COUNTERS);
     if (p->n_cfg)
       e = cudaMemcpy(cnt.data(), (char *)p->dev(p->d_counters) + p->grab_bytes, cnt.size() * 8, cudaMemcpyDeviceToHost);
