@@ -1126,6 +1126,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int32_t s_gad[2][17];
   __shared__ int32_t s_gwi[2];
   __shared__ long long s_item;
+  __shared__ unsigned long long s_acc[kRowsThreads / 32][3];   // per warp: the item's counts (lane 0 adds)
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
@@ -1139,6 +1140,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   const uint32_t nwarps = blockDim.x >> 5;
   int cur_g = -1, cur_cfg = -1;
 
+  if (threadIdx.x < kRowsThreads / 32) s_acc[threadIdx.x][0] = s_acc[threadIdx.x][1] = s_acc[threadIdx.x][2] = 0ull;
   for (;;) {
     if (threadIdx.x == 0) s_item = a.ritem_lo + (long long)atomicAdd(a.rgrab, 1ull);
     __syncthreads();
@@ -1215,12 +1217,11 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         const int32_t xa = (int32_t)bxa * s_c.B[0], xb = min((int32_t)bxb * s_c.B[0], s_c.N[0]);
         const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
         const int64_t nx = xb - xa;
-        unsigned long long *const ctr = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
         // the block level only fills the block bitmaps: its counts come from enum_kernel
         const bool blk = lv == 3;
         if (lane == 0u && !blk) {
-          if (lv == 0 && s_g.first_wave) atomicAdd(ctr + C_LUPS_WAVE, (unsigned long long)(nx * kv));
-          atomicAdd(ctr + C_ADDR, (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]));
+          if (lv == 0 && s_g.first_wave) s_acc[warp][0] += (unsigned long long)(nx * kv);
+          s_acc[warp][1] += (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]);
         }
         const int64_t el0 = es * (F0.stride[1] * y + F0.stride[2] * z);
         const int64_t ea = el0 + sxe * xa, eb = el0 + sxe * (xb - 1);
@@ -1258,6 +1259,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
         }
         if (lv == 0 || blk) {
+          uint32_t sreq = 0;   // this lane's per-warp store sectors of the row (< 2^27)
           for (int j = L + (int)lane; j < L + S; j += 32) {
             if ((int)s_kmin[j] >= kv) continue;
             const DField &F = s_fk[s_af[j]];
@@ -1273,22 +1275,32 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
             if (cb) atomicOr(bm + cu, cb);
             nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-            if (!blk)
-              atomicAdd(ctr + C_W_SREQ,
-                        (unsigned long long)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb));
+            if (!blk) sreq += (uint32_t)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb);
           }
+          sreq = __reduce_add_sync(FULL, sreq);
+          if (lane == 0u) s_acc[warp][2] += sreq;
         }
       }
     }
 
     bad = __reduce_add_sync(FULL, bad);
     nred = __reduce_add_sync(FULL, nred);
+    unsigned long long *const c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
     if (lane == 0) {
-      unsigned long long *const c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
       if (bad) atomicAdd(c + C_OVERFLOW, (unsigned long long)bad);
       if (nred) atomicAdd(c + C_RED, (unsigned long long)nred);
     }
     __syncthreads();
+    // the item's wave LUPs, address evaluations and store requests, once per CTA
+    if (threadIdx.x < 3) {
+      const int k = threadIdx.x;
+      unsigned long long v = 0;
+      for (int w = 0; w < kRowsThreads / 32; ++w) {
+        v += s_acc[w][k];
+        s_acc[w][k] = 0ull;
+      }
+      if (v) atomicAdd(c + (k == 0 ? C_LUPS_WAVE : k == 1 ? C_ADDR : C_W_SREQ), v);
+    }
   }
 }
 
