@@ -1549,12 +1549,18 @@ __device__ __forceinline__ int rank_seg_of(const RankArgs &a, int64_t x) {
   return lo;
 }
 
-__device__ __forceinline__ double rank_key_of(double v) {
-  return isnan(v) ? __longlong_as_double(0x7ff0000000000000ll) : v;
+// The rank keys as integers in the same order as the doubles they stand for (NaN
+// counts as +inf, -0 as +0): a sign-magnitude bit pattern maps monotonically to two's
+// complement by flipping the magnitude bits of negative values.  Integer compares keep
+// the ranking off the fp64 pipe.
+__device__ __forceinline__ long long rank_ord_of(double v) {
+  long long b = isnan(v) ? 0x7ff0000000000000ll : __double_as_longlong(v);
+  if ((b << 1) == 0) b = 0;
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
 __global__ void __launch_bounds__(kRankTile) rank_count_kernel(RankArgs a) {
-  __shared__ double s_key[kRankTile];
+  __shared__ long long s_key[kRankTile];
   const int64_t i_first = (int64_t)blockIdx.x * kRankTile;
   if (i_first >= a.n) return;
   const int64_t i = i_first + threadIdx.x;
@@ -1562,15 +1568,15 @@ __global__ void __launch_bounds__(kRankTile) rank_count_kernel(RankArgs a) {
   const int64_t j_lo = a.seg[rank_seg_of(a, i_first)], j_hi = a.seg[rank_seg_of(a, i_last) + 1];
   const int64_t t0 = j_lo + (int64_t)blockIdx.y * kRankTile;
   if (t0 >= j_hi) return;
-  if (t0 + threadIdx.x < j_hi) s_key[threadIdx.x] = rank_key_of(a.keys[t0 + threadIdx.x]);
+  if (t0 + threadIdx.x < j_hi) s_key[threadIdx.x] = rank_ord_of(a.keys[t0 + threadIdx.x]);
   __syncthreads();
   if (i >= a.n) return;
   const int my_seg = rank_seg_of(a, i);
   const int64_t a0 = max(t0, (int64_t)a.seg[my_seg]), a1 = min(t0 + kRankTile, (int64_t)a.seg[my_seg + 1]);
-  const double ki = rank_key_of(a.keys[i]);
+  const long long ki = rank_ord_of(a.keys[i]);
   int cnt = 0;
   for (int64_t j = a0; j < a1; ++j) {
-    const double kj = s_key[j - t0];
+    const long long kj = s_key[j - t0];
     cnt += (kj < ki) || (kj == ki && j < i);
   }
   if (cnt) atomicAdd(a.rank + i, cnt);
