@@ -16,7 +16,9 @@ replayed as a CUDA graph, descriptors already resident on the device.  Reported:
              it (all three under roofline.kernels): the representative-block kernel
              (exact per-address path) against the measured int32-add rate, the row walk
              against the measured L2 red.or rate, the counting kernel against the
-             measured HBM copy bandwidth (MEASURED_PEAKS.json)
+             measured HBM copy bandwidth (MEASURED_PEAKS.json); traffic = the DRAM bytes
+             per launch ncu measured for that kernel on this workload, read from
+             profiles/dram_traffic_<workload>.txt while the kernel source is unchanged
   cpu_baseline  the CPU oracle on a bounded sample of the same sweep, all host cores
 
 --impl reference times the CPU oracle itself on bounded samples of the same workload.
@@ -210,7 +212,29 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-def kernel_rooflines(profs, peaks):
+def kernel_source_digest():
+    """sha256 of the kernels' source: DRAM traffic taken by ncu holds only for this source."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2204_14242_gb300", "csrc", "ws_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def recorded_traffic(workload_key):
+    """DRAM bytes per launch of each kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+    one ncu capture of this workload), from profiles/dram_traffic_<workload>.txt when it
+    was taken from the current kernel source; else {}."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload_key}.txt")
+    try:
+        lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return {}
+    kv = {ln[0]: ln[1] for ln in lines if len(ln) >= 2}
+    if kv.get("kernel_source_sha256") != kernel_source_digest():
+        return {}
+    return {k: int(v) for k, v in kv.items() if k.endswith("_kernel")}
+
+
+def kernel_rooflines(profs, peaks, workload_key=None):
     """Each kernel's achieved rate against the device rate that bounds it; the one with
     the largest share of the step is reported at the top level.
 
@@ -238,8 +262,11 @@ def kernel_rooflines(profs, peaks):
     k["count_kernel"] = {"bound": "hbm", "achieved": b / 1e9, "peak": hbm, "unit": f"GB/s ({hbm_src})",
                          "frac": b / 1e9 / hbm, "per_launch": int(last["bitmap_bytes"]), "ms": ms["count_kernel"]}
     top = max(ms, key=ms.get)
+    traffic = recorded_traffic(workload_key) if workload_key else {}
+    for name in k:
+        k[name]["traffic"] = traffic.get(name)
     out = dict(k[top])
-    out.update({"kernel": top, "traffic": None, "share": ms[top] / last["ms_total"], "kernels": k,
+    out.update({"kernel": top, "share": ms[top] / last["ms_total"], "kernels": k,
                 "ms_model": med("ms_model"), "ms_rank": med("ms_rank"), "ms_step_profiled": med("ms_total")})
     return out
 
@@ -372,7 +399,7 @@ def main():
 
     # per-kernel rooflines: CUDA events around each kernel on its own launch stream
     profs = [plan.profile(stream) for _ in range(3)]
-    roofline = kernel_rooflines(profs, peaks)
+    roofline = kernel_rooflines(profs, peaks, args.workload if args.subset == 1 else None)
     launches_per_step = profs[-1]["launches"]
 
     extra = {}
