@@ -81,6 +81,7 @@ struct ws_ctx {
   ws::Arena *arena = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t upload_stream = nullptr;   // descriptor uploads of pipelined one-shot estimates
 };
 
 struct ws_plan {

@@ -223,6 +223,25 @@ def test_edge_cases(ctx):
     assert len(r0) == 0
 
 
+def test_one_shot_estimate_in_parts(ctx):
+    """ws_estimate_batch cuts batches of 4096 or more candidates into parts that compile while
+    earlier parts run:
+    results and the global ranking are bit-identical to one resident plan's, and sampled
+    candidates match the oracle."""
+    hw = W.a100()
+    cfgs = W.stencil_25pt_sweep(N=(160, 128, 96)) + W.mixed_set(3600, seed=31)
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        res, order = p.results()
+    for _ in range(2):
+        r2, o2 = B.ws_estimate_batch(ctx, cfgs, hw)
+        assert r2.tobytes() == res.tobytes()
+        assert list(o2) == list(order)
+    idx = sample(755, 8, 41)   # the 25-point candidates (the mixed ones match the plan above)
+    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
+    assert_match(r2, want, idx, "parts")
+
+
 @pytest.mark.parametrize("seed", [11, 12])
 def test_interval_walk_uniform_groups(ctx, seed):
     """Uniform field groups take the interval walk: both walks against the oracle."""
