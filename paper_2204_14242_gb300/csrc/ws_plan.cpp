@@ -14,6 +14,8 @@
 #include <fstream>
 #include <functional>
 #include <map>
+#include <memory>
+#include <memory_resource>
 #include <unordered_map>
 #include <mutex>
 #include <new>
@@ -191,19 +193,46 @@ static FastDiv make_fastdiv(uint32_t d) {
   return f;
 }
 
+// What one candidate compiles to.  Its arrays come from a memory resource: in plan
+// creation, the monotonic arena of the worker that compiled it (no per-candidate heap
+// traffic, everything released at once).
 struct Compiled {
+  explicit Compiled(std::pmr::memory_resource *r = std::pmr::get_default_resource())
+      : f(r), acc(r), iv(r), acc_off(r), iv_off(r), fkey(r), need_words(r) {}
   DCfg d{};
   WarpClasses cls;                    // block warp classes for the layout of field 0
   int64_t lvl_blocks[3] = {0, 0, 0};  // blocks of the wave, y set and z set
   bool rows_geom_ok = false;          // row slots fit the kernel's 32-bit decode
-  std::vector<DField> f;
-  std::vector<DAcc> acc;            // access lists of all its fields, field k at [acc_off[k], acc_off[k + 1])
-  std::vector<DIv> iv;              // merged load intervals likewise
-  std::vector<int32_t> acc_off, iv_off;
-  std::vector<uint64_t> fkey;       // (field index, folding): equal keys have equal access lists
-  std::vector<int64_t> need_words;  // bitmap words per field
+  std::pmr::vector<DField> f;
+  std::pmr::vector<DAcc> acc;       // access lists of all its fields, field k at [acc_off[k], acc_off[k + 1])
+  std::pmr::vector<DIv> iv;         // merged load intervals likewise
+  std::pmr::vector<int32_t> acc_off, iv_off;
+  std::pmr::vector<uint64_t> fkey;  // (field index, folding): equal keys have equal access lists
+  std::pmr::vector<int64_t> need_words;  // bitmap words per field
   size_t dsc_bytes = 0;             // descriptor bytes of its fields, lists and groups
   size_t need_sum = 0, need_max = 0;  // bitmap bytes of all its fields / of its largest
+};
+
+// Upstream of the compile arenas: large blocks from the host block cache.
+class BlockResource : public std::pmr::memory_resource {
+  void *do_allocate(size_t bytes, size_t align) override {
+    if (bytes >= kHostBlockMin && align <= 4096) return host_block_alloc(bytes);
+    return std::pmr::new_delete_resource()->allocate(bytes, align);
+  }
+  void do_deallocate(void *p, size_t bytes, size_t align) override {
+    if (bytes >= kHostBlockMin && align <= 4096) host_block_free(p);
+    else std::pmr::new_delete_resource()->deallocate(p, bytes, align);
+  }
+  bool do_is_equal(const std::pmr::memory_resource &o) const noexcept override { return this == &o; }
+};
+
+// The candidates of one plan creation: comp[i] lives in the arena of the pool task that
+// compiled it; destroying the arenas releases everything (Compiled holds no other
+// resources, so its destructor is not needed).
+struct CompileArena {
+  BlockResource upstream;
+  std::vector<std::unique_ptr<std::pmr::monotonic_buffer_resource>> res;
+  std::vector<Compiled *> comp;
 };
 
 // What a field compiles to for one folding (independent of domain and block shape):
@@ -639,6 +668,13 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     out.f.reserve(nd);
     out.acc_off.reserve(nd + 1);
     out.iv_off.reserve(nd + 1);
+    // folded accesses and merged runs: at most fold per raw access (no regrowth in the arena)
+    size_t na = 0;
+    for (int fi = 0; fi < c.n_field; ++fi) na += (size_t)std::max(0, fld[c.field_off + fi].n_access) * (size_t)c.fold;
+    if (na <= (size_t)kMaxFoldedAccesses * (size_t)c.n_field) {
+      out.acc.reserve(na * (nd / (size_t)c.n_field));
+      out.iv.reserve(na * (nd / (size_t)c.n_field));
+    }
     out.fkey.reserve(nd);
     out.need_words.reserve(nd);
   }
@@ -1420,8 +1456,8 @@ class HostPool {
 };
 
 static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
-                        int n_acc, const ws_hw &hw, std::vector<Compiled> &comp, std::vector<int> &status) {
-  comp.resize(n_cfg);
+                        int n_acc, const ws_hw &hw, CompileArena &ca, std::vector<int> &status) {
+  ca.comp.assign(n_cfg, nullptr);
   status.assign(n_cfg, WS_OK);
   // chunks of consecutive candidates handed out dynamically; each thread keeps its fold
   // cache across its chunks (neighbouring candidates often share fields)
@@ -1443,13 +1479,18 @@ static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, i
     }
   }
   const int nth = n_cfg >= 64 ? HostPool::get().width() : 1;
+  ca.res.clear();
+  for (int t = 0; t < nth; ++t)
+    ca.res.emplace_back(new std::pmr::monotonic_buffer_resource(kHostBlockMin, &ca.upstream));
   const int chunk = 32;
   std::atomic<int> next(0);
-  HostPool::get().run(nth, [&](int) {
+  HostPool::get().run(nth, [&](int t) {
     FieldCache cache;
+    std::pmr::memory_resource *r = ca.res[(size_t)t].get();
     for (int c = next.fetch_add(1); c * chunk < n_cfg; c = next.fetch_add(1))
       for (int i = c * chunk; i < std::min(n_cfg, (c + 1) * chunk); ++i) {
-        Compiled &cc = comp[i];
+        Compiled &cc = *new (r->allocate(sizeof(Compiled), alignof(Compiled))) Compiled(r);
+        ca.comp[(size_t)i] = &cc;
         status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, cc, &cache, refs.data());
         if (status[i] != WS_OK) continue;
         for (size_t k = 0; k < cc.f.size(); ++k) {
@@ -1588,17 +1629,18 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   HostVec<DIv> &hiv = h.hiv;
   hcfg.resize(n_cfg);
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
-  std::vector<Compiled> comp;
+  CompileArena ca;
   std::vector<int> status;
-  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, comp, status);
+  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, ca, status);
+  const std::vector<Compiled *> &comp = ca.comp;
   // scratch capacity: what the arena can give after the descriptors (a field, its access
   // and interval lists, at most one field group each)
   size_t dsc = 64 * 1024, total_need = 0, max_field = 0;
   for (int i = 0; i < n_cfg; ++i) {
     if (status[i] != WS_OK) continue;
-    dsc += comp[i].dsc_bytes;
-    total_need += comp[i].need_sum;
-    max_field = std::max(max_field, comp[i].need_max);
+    dsc += comp[i]->dsc_bytes;
+    total_need += comp[i]->need_sum;
+    max_field = std::max(max_field, comp[i]->need_max);
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
   const size_t avail = avail_fn(dsc);
@@ -1607,11 +1649,11 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   h.scratch = scratch;
   h.desc_bytes = dsc;
   for (int i = 0; i < n_cfg; ++i)
-    if (status[i] == WS_OK && comp[i].need_max > scratch) status[i] = WS_ENOMEM;
+    if (status[i] == WS_OK && comp[i]->need_max > scratch) status[i] = WS_ENOMEM;
   // descriptors: fields in candidate order; candidates that share a field and a folding
   // share its access and interval lists on the device (the first such field owns them)
   std::vector<int64_t> cf_off(n_cfg + 1, 0);
-  for (int i = 0; i < n_cfg; ++i) cf_off[i + 1] = cf_off[i] + (status[i] == WS_OK ? (int64_t)comp[i].f.size() : 0);
+  for (int i = 0; i < n_cfg; ++i) cf_off[i + 1] = cf_off[i] + (status[i] == WS_OK ? (int64_t)comp[i]->f.size() : 0);
   const int64_t nf = cf_off[n_cfg];
   std::vector<int32_t> acc_b((size_t)nf), iv_b((size_t)nf);
   std::vector<char> owner((size_t)nf, 0);
@@ -1621,7 +1663,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
     for (int i = 0; i < n_cfg; ++i)
       for (int64_t j = cf_off[i]; j < cf_off[i + 1]; ++j) {
         const size_t k = (size_t)(j - cf_off[i]);
-        const uint64_t key = comp[i].fkey[k];
+        const uint64_t key = comp[i]->fkey[k];
         if (key != kNoShare) {
           auto it = first.find(key);
           if (it != first.end()) {
@@ -1634,8 +1676,8 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
         owner[(size_t)j] = 1;
         acc_b[(size_t)j] = (int32_t)na;
         iv_b[(size_t)j] = (int32_t)ni;
-        na += comp[i].acc_off[k + 1] - comp[i].acc_off[k];
-        ni += comp[i].iv_off[k + 1] - comp[i].iv_off[k];
+        na += comp[i]->acc_off[k + 1] - comp[i]->acc_off[k];
+        ni += comp[i]->iv_off[k + 1] - comp[i]->iv_off[k];
       }
   }
   hacc.resize((size_t)na);
@@ -1645,7 +1687,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   for (int i = 0; i <= n_cfg; ++i) p->cfg_cf_begin[i] = (int32_t)cf_off[i];
   p->scratch_words = (int64_t)(scratch / 4);
   // per candidate, in parallel over dynamic chunks: its DCfg, DFields and owned lists,
-  // then its field groups (into the chunk's output); its compiled lists are freed here
+  // then its field groups (into the chunk's output)
   const int chunk = 64;
   const int n_chunks = (n_cfg + chunk - 1) / chunk;
   std::vector<GroupOut> gout((size_t)n_chunks);
@@ -1656,7 +1698,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
       GroupOut &go = gout[(size_t)ch];
       for (int i = ch * chunk; i < std::min(n_cfg, (ch + 1) * chunk); ++i) {
         DCfg &d = hcfg[i];
-        if (status[i] == WS_OK) d = comp[i].d;
+        if (status[i] == WS_OK) d = comp[i]->d;
         else memset(&d, 0, sizeof(d));
         d.status = status[i];
         d.field_begin = (int32_t)cf_off[i];
@@ -1664,7 +1706,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
           d.n_field = 0;
           continue;
         }
-        Compiled &cc = comp[i];
+        Compiled &cc = *comp[i];
         for (size_t k = 0; k < cc.f.size(); ++k) {
           const size_t j = (size_t)cf_off[i] + k;
           DField f = cc.f[k];
@@ -1681,9 +1723,6 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
         const size_t before = go.g.size();
         build_groups(p, i, cc, *hw, go);
         grp_count[(size_t)i] = (int32_t)(go.g.size() - before);
-        std::vector<DField>().swap(cc.f);
-        std::vector<DAcc>().swap(cc.acc);
-        std::vector<DIv>().swap(cc.iv);
       }
     }
   };

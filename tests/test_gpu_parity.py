@@ -225,9 +225,8 @@ def test_edge_cases(ctx):
 
 def test_one_shot_estimate_in_parts(ctx):
     """ws_estimate_batch cuts batches of 4096 or more candidates into parts that compile while
-    earlier parts run:
-    results and the global ranking are bit-identical to one resident plan's, and sampled
-    candidates match the oracle."""
+    earlier parts run: results and the global ranking are bit-identical to one resident
+    plan's, and sampled candidates match the oracle."""
     hw = W.a100()
     cfgs = W.stencil_25pt_sweep(N=(160, 128, 96)) + W.mixed_set(3600, seed=31)
     with B.Plan(ctx, cfgs, hw) as p:
