@@ -82,6 +82,13 @@ struct ws_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   cudaStream_t upload_stream = nullptr;   // descriptor uploads of pipelined one-shot estimates
+  // Scratch kept between one-shot estimates (ws_estimate_batch): the counting kernel leaves
+  // it zeroed, so a later estimate needs no memset.  Held while `oneshot_mu` is; given back
+  // to the arena when a plan or server of the context needs the room.
+  std::mutex oneshot_mu;
+  int64_t oneshot_off = -1;
+  size_t oneshot_bytes = 0;
+  bool oneshot_dirty = false;   // not known to be zero (new, or an execution failed)
 };
 
 struct ws_plan {
@@ -125,6 +132,10 @@ struct ws_plan {
   int grid_rows(int64_t items) const;
   int bank_shift() const;
   int enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof);
+  // Recorded after the descriptor uploads: launches on any stream wait for it (a graph
+  // capture waits on the host instead, once).
+  cudaEvent_t ready = nullptr;
+  int wait_ready(cudaStream_t st);
   int run_plain(cudaStream_t st);
   int execute(int mode, cudaStream_t st);
 };
@@ -135,6 +146,11 @@ using Plan = ::ws_plan;
 int plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
                       int n_acc, const ws_hw *hw, size_t *desc_bytes, size_t *scratch_bytes,
                       size_t *max_field_bytes);
+// ext_scratch value of plan_create_impl: use (and grow) the context's kept one-shot scratch;
+// the caller holds ctx->oneshot_mu.
+constexpr int64_t kCtxScratch = -2;
+// Gives the context's kept one-shot scratch back to the arena unless an estimate holds it.
+void ctx_reclaim(ws_ctx *ctx);
 int plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                      const ws_access *acc, int n_acc, const ws_hw *hw, const int32_t *seg_begin, int n_seg,
                      const ws_tuning *tuning, size_t scratch_cap, ws_plan **out, cudaStream_t upload,

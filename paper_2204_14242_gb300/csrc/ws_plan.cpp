@@ -1248,14 +1248,24 @@ int ws_plan::run_plain(cudaStream_t st) {
   return WS_OK;
 }
 
+int ws_plan::wait_ready(cudaStream_t st) {
+  if (ready) CU(cudaStreamWaitEvent(st, ready, 0));
+  return WS_OK;
+}
+
 int ws_plan::execute(int mode, cudaStream_t st) {
-  if (mode == WS_MODE_PLAIN) return run_plain(st);
-  if (mode == WS_MODE_DIRECT) return enqueue(st, nullptr, nullptr);
-  if (mode != WS_MODE_BATCHED) {
+  if (mode != WS_MODE_PLAIN && mode != WS_MODE_DIRECT && mode != WS_MODE_BATCHED) {
     set_error("unknown mode");
     return WS_EINVAL;
   }
+  if (mode != WS_MODE_BATCHED) {
+    const int rc = wait_ready(st);
+    if (rc != WS_OK) return rc;
+    return mode == WS_MODE_PLAIN ? run_plain(st) : enqueue(st, nullptr, nullptr);
+  }
   if (!graph_exec) {
+    // the capture cannot wait on an event recorded outside it: wait for the uploads here
+    if (ready) CU(cudaEventSynchronize(ready));
     cudaGraph_t graph = nullptr;
     CU(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue(ctx->capture_stream, nullptr, nullptr);
@@ -1527,8 +1537,8 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
 }
 
 // Host half of plan creation: compiles the candidates, deduplicates their access lists,
-// builds field groups and cuts passes.  avail_fn(descriptor bytes) gives the scratch
-// capacity.  Needs no device.
+// builds field groups and cuts passes.  avail_fn(descriptor bytes, bitmap bytes of all
+// fields) gives the scratch capacity.  Needs no device.
 struct HostDesc {
   HostVec<DCfg> hcfg;
   HostVec<DAcc> hacc;
@@ -1623,7 +1633,7 @@ static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &
 
 static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                        const ws_access *acc, int n_acc, const ws_hw *hw,
-                       const std::function<size_t(size_t)> &avail_fn, HostDesc &h) {
+                       const std::function<size_t(size_t, size_t)> &avail_fn, HostDesc &h) {
   HostVec<DCfg> &hcfg = h.hcfg;
   HostVec<DAcc> &hacc = h.hacc;
   HostVec<DIv> &hiv = h.hiv;
@@ -1643,7 +1653,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
     max_field = std::max(max_field, comp[i]->need_max);
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
-  const size_t avail = avail_fn(dsc);
+  const size_t avail = avail_fn(dsc, total_need);
   size_t scratch = std::min(total_need, avail);
   scratch = std::max<size_t>(scratch, 16);
   h.scratch = scratch;
@@ -1786,7 +1796,30 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
 
   HostDesc h;
   const auto t_begin = std::chrono::steady_clock::now();
-  build_host(p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t dsc) {
+  if (ext_scratch == -1) ctx_reclaim(ctx);
+  bool ctx_scratch = false;   // the plan runs in the context's kept scratch
+  build_host(p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t dsc, size_t need) {
+    if (ext_scratch == kCtxScratch) {
+      // grow the kept scratch to this plan's bitmaps when the arena has the room
+      if (ctx->oneshot_bytes < need) {
+        if (ctx->oneshot_off >= 0) ctx->arena->release(ctx->oneshot_off);
+        ctx->oneshot_off = -1;
+        ctx->oneshot_bytes = 0;
+        size_t room = ctx->arena->largest_free();
+        room = room > dsc + (8 << 20) ? room - dsc - (8 << 20) : 0;
+        const size_t want = std::min(need, room) & ~(size_t)255;
+        const int64_t o = want >= 256 ? ctx->arena->alloc(want) : -1;
+        if (o >= 0) {
+          ctx->oneshot_off = o;
+          ctx->oneshot_bytes = want;
+          ctx->oneshot_dirty = true;
+        }
+      }
+      if (ctx->oneshot_off >= 0) {
+        ctx_scratch = true;
+        return ctx->oneshot_bytes;
+      }
+    }
     size_t avail = ctx->arena->largest_free();
     avail = avail > dsc + (8 << 20) ? avail - dsc - (8 << 20) : 0;
     if (ext_scratch >= 0) avail = ext_scratch_bytes;
@@ -1826,8 +1859,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   p->d_keys = p->take(std::max<size_t>((size_t)n_cfg * sizeof(double), 256));
   p->d_order = p->take(std::max<size_t>((size_t)n_cfg * sizeof(int32_t), 256));
   p->d_rank = p->take(std::max<size_t>((size_t)n_cfg * sizeof(int32_t), 256));
-  if (ext_scratch >= 0) {
-    p->d_scratch = ext_scratch;
+  if (ext_scratch >= 0 || ctx_scratch) {
+    p->d_scratch = ctx_scratch ? ctx->oneshot_off : ext_scratch;
     p->ext_scratch = true;
   } else {
     p->d_scratch = p->take(scratch);
@@ -1854,13 +1887,19 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   if (!hacc.empty() && (e = cudaMemcpyAsync(p->dev(p->d_acc), hacc.data(), hacc.size() * sizeof(DAcc), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if (!hiv.empty() && (e = cudaMemcpyAsync(p->dev(p->d_iv), hiv.data(), hiv.size() * sizeof(DIv), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(p->dev(p->d_seg), seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st)) != cudaSuccess) return fail(e);
-  if (!p->ext_scratch && (e = cudaMemsetAsync(p->dev(p->d_scratch), 0, scratch, st)) != cudaSuccess) return fail(e);
+  if ((!p->ext_scratch || (ctx_scratch && ctx->oneshot_dirty)) &&
+      (e = cudaMemsetAsync(p->dev(p->d_scratch), 0, ctx_scratch ? ctx->oneshot_bytes : scratch, st)) != cudaSuccess)
+    return fail(e);
+  if (ctx_scratch) ctx->oneshot_dirty = false;
   if ((rc = p->upload_fields(st)) != WS_OK) {
     p->release_all();
     delete p;
     return rc;
   }
-  if (!upload && (e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+  // launches wait for this event (pageable copies are staged when cudaMemcpyAsync returns,
+  // so the host arrays may go now)
+  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventRecord(p->ready, st)) != cudaSuccess) return fail(e);
   p->scratch_bytes = scratch;
   {
     const auto t_end = std::chrono::steady_clock::now();
@@ -1912,7 +1951,8 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
   const int nev = 3 + 3 * (int)p->passes.size();
   std::vector<cudaEvent_t> ev(nev);
   for (auto &e : ev) CU(cudaEventCreate(&e));
-  int rc = p->enqueue(st, &ev, out);
+  int rc = p->wait_ready(st);
+  if (rc == WS_OK) rc = p->enqueue(st, &ev, out);
   cudaError_t e = cudaStreamSynchronize(st);
   if (rc == WS_OK && e == cudaSuccess) {
     float ms = 0;
@@ -1964,6 +2004,10 @@ extern "C" int ws_plan_destroy(ws_plan *p) {
   if (!p) return WS_EINVAL;
   cudaSetDevice(p->ctx->device);
   cudaStreamSynchronize(p->ctx->stream);
+  if (p->ready) {
+    cudaEventSynchronize(p->ready);
+    cudaEventDestroy(p->ready);
+  }
   p->release_all();
   delete p;
   return WS_OK;
@@ -1982,7 +2026,12 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  int rc = WS_OK;
+  int rc = p->wait_ready(st);
+  if (rc != WS_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
   for (int ch : chunks) {
     for (int th : threads) {
       for (int pm : pass_mbs) {
@@ -2035,6 +2084,7 @@ static constexpr int kPipeMin = 2048, kPipeParts = 3;
 static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out, int32_t *order_out,
                               cudaStream_t st) {
+  ctx_reclaim(ctx);
   const int parts = std::min(kPipeParts, n_cfg / kPipeMin);
   const size_t rb = (size_t)n_cfg * sizeof(ws_result);
   Arena &ar = *ctx->arena;
@@ -2113,14 +2163,27 @@ extern "C" int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, 
     if (rc != WS_ENOMEM) return rc;
     // the parts did not fit together: one plan, which may run in several scratch passes
   }
+  // one plan; it runs in the context's kept scratch unless another estimate holds it
+  std::unique_lock<std::mutex> kept(ctx->oneshot_mu, std::try_to_lock);
   ws_plan *p = nullptr;
-  int rc = ws_plan_create(ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, &p);
+  int rc = plan_create_impl(ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, 0, &p, nullptr,
+                            kept.owns_lock() ? kCtxScratch : -1, 0);
   if (rc != WS_OK) return rc;
   // a one-shot plan would replay its graph once: launch the batched kernels directly
   rc = ws_plan_execute(p, mode == WS_MODE_BATCHED ? WS_MODE_DIRECT : mode, stream);
   if (rc == WS_OK) rc = ws_plan_results(p, out, order_out, stream);
+  // a failed step may leave bits set in the kept scratch
+  if (rc != WS_OK && kept.owns_lock()) ctx->oneshot_dirty = true;
   ws_plan_destroy(p);
   return rc;
+}
+
+void ws::ctx_reclaim(ws_ctx *ctx) {
+  std::unique_lock<std::mutex> kept(ctx->oneshot_mu, std::try_to_lock);
+  if (!kept.owns_lock() || ctx->oneshot_off < 0) return;
+  ctx->arena->release(ctx->oneshot_off);
+  ctx->oneshot_off = -1;
+  ctx->oneshot_bytes = 0;
 }
 
 extern "C" int ws_describe(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
@@ -2198,7 +2261,7 @@ extern "C" int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field 
   if (tuning) p.tune = *tuning;
   default_tuning(p.tune);
   HostDesc h;
-  build_host(&p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t) { return scratch_bytes; }, h);
+  build_host(&p, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, [&](size_t, size_t) { return scratch_bytes; }, h);
   for (const DCfg &d : h.hcfg) out->candidates_ok += d.status == WS_OK;
   out->fields = (int64_t)p.hfld.size();
   out->groups = (int64_t)p.hgrp.size();

@@ -279,6 +279,7 @@ extern "C" int ws_server_create(ws_ctx *ctx, const ws_server_opts *opts, const w
     delete s;
     return WS_ECUDA;
   }
+  ws::ctx_reclaim(ctx);
   size_t budget = s->opts.mem_budget ? s->opts.mem_budget : ctx->arena->largest_free() / 4 * 3;
   budget = std::min(budget, ctx->arena->largest_free());
   budget &= ~(size_t)255;
