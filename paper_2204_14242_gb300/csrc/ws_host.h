@@ -117,6 +117,11 @@ struct ws_plan {
   float ms_create_host = 0, ms_create_device = 0;   // wall times of the creation (host part, device part)
   int64_t d_grp = -1;
   int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
+  // owner of every work item (enumeration and row-walk items: field group; counting
+  // items: (candidate, field)), filled by layout(), uploaded with the fields
+  ws::HostVec<int32_t> own;             // [enumeration items | row-walk items | counting items]
+  int64_t d_own = -1;
+  size_t d_own_bytes = 0;
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
           d_order = -1, d_rank = -1, d_scratch = -1;
   std::vector<int64_t> allocs;

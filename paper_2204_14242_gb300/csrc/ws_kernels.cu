@@ -116,34 +116,6 @@ __device__ int bank_cycles_rel32(uint32_t rel, bool act, uint32_t lane, uint32_t
   return (int)__reduce_add_sync(FULL, (uint32_t)cycles);
 }
 
-// Last (candidate, field) index in [lo, hi) whose first work item is <= item.  Items
-// are handed out in increasing order, so a CTA's next item never lies before the field
-// of its previous one (`hint`): gallop forward from there, then bisect.
-__device__ __forceinline__ int find_cf(const DField *__restrict__ fld, int lo, int hi, int64_t item,
-                                       bool counting, int hint) {
-  auto begin = [&](int i) { return counting ? fld[i].citem_begin : fld[i].item_begin; };
-  if (hint >= lo && hint < hi && begin(hint) <= item) {
-    int step = 1, l = hint, r = hi;
-    for (;;) {
-      const int nx = l + step;
-      if (nx >= hi) break;
-      if (begin(nx) > item) {
-        r = nx;
-        break;
-      }
-      l = nx;
-      step <<= 1;
-    }
-    lo = l;
-    hi = r;
-  }
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (begin(mid) <= item) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
   return (__umulhi(n, f.m) + n) >> f.s;
@@ -292,33 +264,6 @@ __device__ __forceinline__ uint32_t warp_distinct_sectors(uint32_t r, bool act) 
   return cnt;
 }
 
-// Last field group in [lo, hi) whose first work item is <= item; gallops forward from
-// the CTA's previous group (items are handed out in increasing order).
-template <bool ROWS = false>
-__device__ __forceinline__ int find_grp(const DGroup *__restrict__ grp, int lo, int hi, int64_t item, int hint) {
-  auto begin = [&](int g) { return ROWS ? grp[g].ritem_begin : grp[g].item_begin; };
-  if (hint >= lo && hint < hi && begin(hint) <= item) {
-    int step = 1, l = hint, r = hi;
-    for (;;) {
-      const int nx = l + step;
-      if (nx >= hi) break;
-      if (begin(nx) > item) {
-        r = nx;
-        break;
-      }
-      l = nx;
-      step <<= 1;
-    }
-    lo = l;
-    hi = r;
-  }
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (begin(mid) <= item) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
 
 // A uniform field group walks its loads (stores) lane per access when it has at least
 // this many; with fewer, most lanes of such a walk would idle.
@@ -607,7 +552,7 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.item_hi) break;
-    const int gi = find_grp(a.grp, a.grp_lo, a.grp_hi, item, cur_g);
+    const int gi = a.own_enum[item];
     if (gi != cur_g) {
       // stage the group, then the interval walk's lane layout and the thread table
       const bool new_cfg = stage_group(a, gi, cur_cfg, sm);
@@ -1146,7 +1091,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.ritem_hi) break;
-    const int gi = find_grp<true>(a.grp, a.grp_lo, a.grp_hi, item, cur_g);
+    const int gi = a.own_rows[item];
     if (gi != cur_g) {
       stage_group(a, gi, cur_cfg, sm);
       cur_g = gi;
@@ -1340,15 +1285,13 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
   __shared__ uint32_t s_red[16][12];
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
-  int cur = -1;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
   for (;;) {
     if (threadIdx.x == 0) s_item = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.citem_hi) break;
-    const int cf = find_cf(a.fld, a.cf_lo, a.cf_hi, item, true, cur);
-    cur = cf;
+    const int cf = a.own[item];
     const DField &F = a.fld[cf];
     const int64_t bm_bl = F.bm[BM_BL], bm_bs = F.bm[BM_BS], bm_w = F.bm[BM_W], bm_ws = F.bm[BM_WS];
     const int64_t bm_y = F.bm[BM_Y], bm_z = F.bm[BM_Z];

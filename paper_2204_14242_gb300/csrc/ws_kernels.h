@@ -17,6 +17,8 @@ struct EnumArgs {
   int64_t *counters;               // [n_cfg][N_COUNTERS]
   unsigned long long *grab;        // work-stealing counter (zeroed before the launch)
   unsigned long long *rgrab;       //   of the row kernel
+  const int32_t *own_enum;         // field group of every enumeration item (global numbering)
+  const int32_t *own_rows;         // field group of every row-walk item
   int64_t item_lo, item_hi;        // enumeration items of the pass
   int64_t ritem_lo, ritem_hi;      // row-walk items of the pass
   int32_t grp_lo, grp_hi;          // field-group range of the pass
@@ -29,6 +31,7 @@ struct EnumArgs {
 
 struct CountArgs {
   const DField *fld;
+  const int32_t *own;              // (candidate, field) of every counting item (global numbering)
   uint32_t *scratch;
   int64_t *counters;
   unsigned long long *grab;

@@ -1039,9 +1039,40 @@ void ws_plan::layout() {
   item_begin_end = items;
   ritem_begin_end = ritems;
   citem_begin_end = citems;
+  // owners of the items: [enumeration | row walk | counting]
+  own.resize((size_t)(items + ritems + citems));
+  for (int g = 0; g < ng; ++g) {
+    const DGroup &G = hgrp[g];
+    const int64_t e1 = g + 1 < ng ? hgrp[g + 1].item_begin : items;
+    const int64_t r1 = g + 1 < ng ? hgrp[g + 1].ritem_begin : ritems;
+    std::fill(own.begin() + G.item_begin, own.begin() + e1, (int32_t)g);
+    std::fill(own.begin() + items + G.ritem_begin, own.begin() + items + r1, (int32_t)g);
+  }
+  const int nf = (int)hfld.size();
+  for (int f = 0; f < nf; ++f) {
+    const int64_t c1 = f + 1 < nf ? hfld[f + 1].citem_begin : citems;
+    std::fill(own.begin() + items + ritems + hfld[f].citem_begin, own.begin() + items + ritems + c1, (int32_t)f);
+  }
 }
 
 int ws_plan::upload_fields(cudaStream_t st) {
+  const size_t ob = std::max<size_t>(own.size() * sizeof(int32_t), 256);
+  if (ob > d_own_bytes) {
+    // a larger layout (autotuning): the previous array is no longer read once `st` has
+    // passed its last launch, which precedes this call on the same stream
+    if (d_own >= 0) {
+      CU(cudaStreamSynchronize(st));
+      ctx->arena->release(d_own);
+      allocs.erase(std::find(allocs.begin(), allocs.end(), d_own));
+    }
+    d_own = take(ob);
+    d_own_bytes = d_own >= 0 ? ob : 0;
+    if (d_own < 0) {
+      set_error("arena exhausted while laying out a plan");
+      return WS_ENOMEM;
+    }
+  }
+  if (!own.empty()) CU(cudaMemcpyAsync(dev(d_own), own.data(), own.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   if (!hfld.empty()) CU(cudaMemcpyAsync(dev(d_fld), hfld.data(), hfld.size() * sizeof(DField), cudaMemcpyHostToDevice, st));
   if (!hgrp.empty()) CU(cudaMemcpyAsync(dev(d_grp), hgrp.data(), hgrp.size() * sizeof(DGroup), cudaMemcpyHostToDevice, st));
   if (graph_exec) {
@@ -1108,6 +1139,8 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
     ea.grab = (unsigned long long *)dev(d_counters) + 3 * p;
     ea.rgrab = ea.grab + 1;
+    ea.own_enum = (const int32_t *)dev(d_own);
+    ea.own_rows = ea.own_enum + item_begin_end;
     ea.ritem_lo = P.ritem_lo;
     ea.ritem_hi = P.ritem_hi;
     ea.item_lo = P.item_lo;
@@ -1133,6 +1166,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     if ((rc = mark(2 + 3 * (int)p)) != WS_OK) return rc;
     CountArgs ca;
     ca.fld = ea.fld;
+    ca.own = ea.own_rows + ritem_begin_end;
     ca.scratch = ea.scratch;
     ca.counters = ea.counters;
     ca.grab = ea.grab + 2;
@@ -1200,6 +1234,8 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.counters = counters;
       ea.grab = grab;
       ea.rgrab = grab + 1;
+      ea.own_enum = (const int32_t *)dev(d_own);
+      ea.own_rows = ea.own_enum + item_begin_end;
       ea.item_lo = it_lo;
       ea.item_hi = it_hi;
       ea.ritem_lo = rt_lo;
@@ -1217,6 +1253,7 @@ int ws_plan::run_plain(cudaStream_t st) {
       if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
       CountArgs ca;
       ca.fld = ea.fld;
+      ca.own = ea.own_rows + ritem_begin_end;
       ca.scratch = ea.scratch;
       ca.counters = counters;
       ca.grab = grab + 2;
@@ -1653,6 +1690,22 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
     max_field = std::max(max_field, comp[i]->need_max);
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
+  {
+    // owner tables of the work items (4 bytes per item): at most one enumeration item per
+    // chunk of modelled warps and one row-walk item per chunk of row slots per field
+    // group, plus the representative block's items, plus one counting item per chunk of
+    // bitmap words per field
+    size_t items = total_need / ((size_t)std::max(4, p->tune.count_words) * 4) + 1;
+    const size_t cw = (size_t)std::max(1, p->tune.chunk_warps), cr = (size_t)p->chunk_rows();
+    for (int i = 0; i < n_cfg; ++i) {
+      if (status[i] != WS_OK) continue;
+      const DCfg &d = comp[i]->d;
+      for (const DField &f : comp[i]->f)
+        items += 3 + (size_t)d.lev_end[3] / cw + (size_t)d.rows_slot_end[3] / cr +
+                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kBlockPairs;
+    }
+    dsc += 4 * items;
+  }
   const size_t avail = avail_fn(dsc, total_need);
   size_t scratch = std::min(total_need, avail);
   scratch = std::max<size_t>(scratch, 16);
