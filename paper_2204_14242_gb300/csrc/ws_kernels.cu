@@ -1281,16 +1281,18 @@ __device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, con
 // never waits behind the read of its own sector and the written bytes are those of
 // the non-zero positions alone.
 __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
-  __shared__ long long s_item;
+  __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
   __shared__ uint32_t s_red[16][12];
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-  for (;;) {
-    if (threadIdx.x == 0) s_item = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
+  if (threadIdx.x == 0) s_item[0] = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
+  __syncthreads();
+  for (int par = 0;; par ^= 1) {
+    const int64_t item = s_item[par];
     if (item >= a.citem_hi) break;
+    long long nxt = 0;
+    if (threadIdx.x == 0) nxt = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
     const int cf = a.own[item];
     const DField &F = a.fld[cf];
     const int64_t bm_bl = F.bm[BM_BL], bm_bs = F.bm[BM_BS], bm_w = F.bm[BM_W], bm_ws = F.bm[BM_WS];
@@ -1375,6 +1377,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
       for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += s_red[wi][threadIdx.x];
       if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
     }
+    if (threadIdx.x == 0) s_item[par ^ 1] = nxt;
     __syncthreads();
   }
 }
