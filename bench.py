@@ -198,9 +198,17 @@ def cpu_baseline(cfgs, hw, seconds):
     t = time.perf_counter()
     oracle.estimate(sample, hw, threads=ncore)
     dt = time.perf_counter() - t
+    # one core: an evenly spread part of the sample, sized for about a third of the time
+    # above (per-candidate single-core time estimated as dt x cores / sample size)
+    n1 = max(1, min(len(sample), int(seconds / 3 / max(dt * ncore / len(sample), 1e-6))))
+    one = sample[::max(1, len(sample) // n1)][:n1]
+    t = time.perf_counter()
+    oracle.estimate(one, hw, threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": len(sample) / dt, "unit": UNIT, "cores": ncore, "kind": "oracle",
+            "value_1core": len(one) / dt1,
             "sample": f"{len(sample)} candidates (every {stride}-th of {len(cfgs)}), std::set enumerator, "
-                      f"one candidate per thread, {dt:.1f} s"}
+                      f"one candidate per thread, {dt:.1f} s; 1 core: {len(one)} of them in {dt1:.1f} s"}
 
 
 def measured_hbm_gbs():
