@@ -1860,7 +1860,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
         ctx->oneshot_bytes = 0;
         size_t room = ctx->arena->largest_free();
         room = room > dsc + (8 << 20) ? room - dsc - (8 << 20) : 0;
-        const size_t want = std::min(need, room) & ~(size_t)255;
+        const size_t want = std::min((need + 255) & ~(size_t)255, room & ~(size_t)255);   // whole bitmaps: one pass
         const int64_t o = want >= 256 ? ctx->arena->alloc(want) : -1;
         if (o >= 0) {
           ctx->oneshot_off = o;
