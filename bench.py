@@ -420,6 +420,9 @@ def main():
         extra["plain"] = {"value": len(cfgs) / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
                           "identical_to_batched": rp.tobytes() == res.tobytes()}
         extra["batched_over_plain"] = value / world / extra["plain"]["value"]
+    # the resident plan is released first: the server and each one-shot call then have
+    # the arena to themselves
+    plan.close()
     if args.serve_seconds > 0 and rank == 0:
         extra["served"] = serve(B, W, ctx, hw, args.serve_seconds)
         sv = extra["served"]
@@ -429,9 +432,7 @@ def main():
             rate = max(1.0, 0.7 * sv["configs_per_s"] / mean_k)
             extra["served_at_70pct_capacity"] = serve(B, W, ctx, hw, args.serve_seconds, rate_hz=rate)
 
-    # e2e: host buffers in, host results out, every step (the resident plan is released
-    # first so that each one-shot call has the arena to itself)
-    plan.close()
+    # e2e: host buffers in, host results out, every step
     e2e_steps = max(2, min(args.steps, 5))
     h2d = profs[-1]["upload_bytes"]
     d2h = len(cfgs) * (B.RESULT.itemsize + 4)
