@@ -21,7 +21,6 @@ struct EnumArgs {
   const int32_t *own_rows;         // field group of every row-walk item
   int64_t item_lo, item_hi;        // enumeration items of the pass
   int64_t ritem_lo, ritem_hi;      // row-walk items of the pass
-  int32_t grp_lo, grp_hi;          // field-group range of the pass
   int32_t chunk;                   // modelled warps per item
   int32_t chunk_rows;              // row slots per item (row walk)
   int32_t banks, bank_bytes, pair_dist;
@@ -36,7 +35,6 @@ struct CountArgs {
   int64_t *counters;
   unsigned long long *grab;
   int64_t citem_lo, citem_hi;
-  int32_t cf_lo, cf_hi;
   int32_t chunk_words;             // multiple of 4
 };
 

@@ -1145,8 +1145,6 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.ritem_hi = P.ritem_hi;
     ea.item_lo = P.item_lo;
     ea.item_hi = P.item_hi;
-    ea.grp_lo = P.grp_lo;
-    ea.grp_hi = P.grp_hi;
     ea.chunk = tune.chunk_warps;
     ea.chunk_rows = chunk_rows();
     ea.banks = hw.banks;
@@ -1172,8 +1170,6 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ca.grab = ea.grab + 2;
     ca.citem_lo = P.citem_lo;
     ca.citem_hi = P.citem_hi;
-    ca.cf_lo = P.cf_lo;
-    ca.cf_hi = P.cf_hi;
     ca.chunk_words = tune.count_words;
     if (P.citem_hi > P.citem_lo) {
       CU(launch_count(ca, grid_for(512, P.citem_hi - P.citem_lo, true), st));
@@ -1240,8 +1236,6 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.item_hi = it_hi;
       ea.ritem_lo = rt_lo;
       ea.ritem_hi = rt_hi;
-      ea.grp_lo = glo;
-      ea.grp_hi = ghi;
       ea.chunk = tune.chunk_warps;
       ea.chunk_rows = chunk_rows();
       ea.banks = hw.banks;
@@ -1259,8 +1253,6 @@ int ws_plan::run_plain(cudaStream_t st) {
       ca.grab = grab + 2;
       ca.citem_lo = ct_lo;
       ca.citem_hi = ct_hi;
-      ca.cf_lo = cf_lo;
-      ca.cf_hi = cf_hi;
       ca.chunk_words = tune.count_words;
       if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(512, ct_hi - ct_lo, true), st));
     }
