@@ -1275,14 +1275,63 @@ __device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, con
 }
 
 // Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of
-// words); each thread keeps two 16-byte positions of every bitmap in flight.  The
-// bitmaps are sparse: an all-zero position is neither tallied nor written, and a
-// non-zero one is cleared only after its value has arrived, so the clearing store
-// never waits behind the read of its own sector and the written bytes are those of
-// the non-zero positions alone.
-__global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
+// words).  Every thread streams its own 16-byte positions of each bitmap through a ring of
+// kCountStages slots in shared memory with cp.async (kCountStages - 1 positions in flight
+// per bitmap, held in shared memory rather than registers), tallies them, and clears in
+// global memory only the non-zero positions, after their values have arrived (the bitmaps
+// are sparse; a zero store right behind the load of its own sector made the L2 hold every
+// such store behind the pending fill).  No thread reads another thread's slots, so the ring
+// needs no barriers: cp.async.wait_group orders each thread's own copies.
+__device__ __forceinline__ void cp_async16(uint32_t sdst, const void *gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Streams positions q0 + threadIdx.x + k * kCountThreads < q1 of up to four bitmaps (null =
+// absent, reads as zero) through the calling thread's ring slots; f(v, q) consumes them.
+template <int NS, class F>
+__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, int64_t q1, uint32_t ring, F &&f) {
+  const int64_t first = q0 + threadIdx.x;
+  const int64_t K = first < q1 ? (q1 - first + kCountThreads - 1) / kCountThreads : 0;
+  auto slot = [&](int64_t k, int b) -> uint32_t {
+    return ring + (uint32_t)((((int)(k % kCountStages) * NS + b) * kCountThreads + (int)threadIdx.x) * 16);
+  };
+  auto issue = [&](int64_t k) {
+    if (k < K) {
+      const int64_t q = first + k * kCountThreads;
+#pragma unroll
+      for (int b = 0; b < NS; ++b)
+        if (p[b]) cp_async16(slot(k, b), p[b] + q);
+    }
+    cp_async_commit();   // one group per step, empty or not, so that the wait count holds
+  };
+#pragma unroll
+  for (int k = 0; k < kCountStages - 1; ++k) issue(k);
+  for (int64_t k = 0; k < K; ++k) {
+    issue(k + kCountStages - 1);
+    cp_async_wait<kCountStages - 1>();   // step k's copies of this thread have landed
+    uint4 v[NS];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+      v[b] = make_uint4(0u, 0u, 0u, 0u);
+      if (p[b]) asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                             : "=r"(v[b].x), "=r"(v[b].y), "=r"(v[b].z), "=r"(v[b].w)
+                             : "r"(slot(k, b)) : "memory");
+    }
+    f(v, first + k * kCountThreads);
+  }
+  cp_async_wait<0>();
+}
+
+__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
-  __shared__ uint32_t s_red[16][12];
+  __shared__ uint32_t s_red[kCountThreads / 32][12];
+  extern __shared__ __align__(16) unsigned char s_ring[];   // [stage][bitmap][thread] x 16 bytes
+  const uint32_t ring = (uint32_t)__cvta_generic_to_shared(s_ring);
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
@@ -1305,66 +1354,39 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
     const int64_t c1 = min(c0 + (int64_t)a.chunk_words, ntot);
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // block part: words [c0, min(c1, nb)) -- BL, BS
-    const int64_t cb = min(c1, nb);
-    uint4 *const pbl = bm_bl >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bl) : nullptr;
-    uint4 *const pbs = bm_bs >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bs) : nullptr;
-    for (int64_t i = c0 / 4 + threadIdx.x; i < cb / 4; i += blockDim.x) {
-      const uint4 l = pbl ? pbl[i] : zero;
-      const uint4 t = pbs ? pbs[i] : zero;
-      if (nz(l)) {
-        tally_sectors_lines(acc[0], acc[1], l);
-        pbl[i] = zero;
-      }
-      if (nz(t)) {
-        tally_sectors_lines(acc[2], acc[3], t);
-        pbs[i] = zero;
-      }
+    {
+      uint4 *const pb[2] = {bm_bl >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bl) : nullptr,
+                            bm_bs >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bs) : nullptr};
+      count_stream<2>(pb, c0 / 4, min(c1, nb) / 4, ring, [&](const uint4 (&v)[2], int64_t q) {
+        if (nz(v[0])) {
+          tally_sectors_lines(acc[0], acc[1], v[0]);
+          pb[0][q] = zero;
+        }
+        if (nz(v[1])) {
+          tally_sectors_lines(acc[2], acc[3], v[1]);
+          pb[1][q] = zero;
+        }
+      });
     }
     // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS
-    const bool has_w = bm_w >= 0, has_ws = bm_ws >= 0;
-    uint4 *const pw = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_w) : nullptr;
-    uint4 *const py = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_y) : nullptr;
-    uint4 *const pz = has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_z) : nullptr;
-    uint4 *const ps = has_ws ? reinterpret_cast<uint4 *>(a.scratch + bm_ws) : nullptr;
-    const int64_t q1 = (c1 - nb) / 4;
-    for (int64_t q = (max(c0, nb) - nb) / 4 + threadIdx.x; q < q1; q += 2 * (int64_t)blockDim.x) {
-      const int64_t qb = q + blockDim.x;
-      const bool two = qb < q1;
-      uint4 w0 = zero, y0 = zero, z0 = zero, v0 = zero, w1 = zero, y1 = zero, z1 = zero, v1 = zero;
-      if (has_w) {
-        w0 = pw[q];
-        y0 = py[q];
-        z0 = pz[q];
-        if (two) {
-          w1 = pw[qb];
-          y1 = py[qb];
-          z1 = pz[qb];
+    {
+      const bool has_w = bm_w >= 0;
+      uint4 *const pw[4] = {has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_w) : nullptr,
+                            has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_y) : nullptr,
+                            has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_z) : nullptr,
+                            bm_ws >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_ws) : nullptr};
+      count_stream<4>(pw, (max(c0, nb) - nb) / 4, (c1 - nb) / 4, ring, [&](const uint4 (&v)[4], int64_t q) {
+        if (nz(v[0]) | nz(v[1]) | nz(v[2])) {
+          tally_wave(acc, v[0], v[1], v[2]);
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            if (nz(v[b])) pw[b][q] = zero;
         }
-      }
-      if (has_ws) {
-        v0 = ps[q];
-        if (two) v1 = ps[qb];
-      }
-      if (nz(w0) | nz(y0) | nz(z0)) {
-        tally_wave(acc, w0, y0, z0);
-        if (nz(w0)) pw[q] = zero;
-        if (nz(y0)) py[q] = zero;
-        if (nz(z0)) pz[q] = zero;
-      }
-      if (nz(w1) | nz(y1) | nz(z1)) {
-        tally_wave(acc, w1, y1, z1);
-        if (nz(w1)) pw[qb] = zero;
-        if (nz(y1)) py[qb] = zero;
-        if (nz(z1)) pz[qb] = zero;
-      }
-      if (nz(v0)) {
-        tally_sectors_lines(acc[10], acc[11], v0);
-        ps[q] = zero;
-      }
-      if (nz(v1)) {
-        tally_sectors_lines(acc[10], acc[11], v1);
-        ps[qb] = zero;
-      }
+        if (nz(v[3])) {
+          tally_sectors_lines(acc[10], acc[11], v[3]);
+          pw[3][q] = zero;
+        }
+      });
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -1374,7 +1396,7 @@ __global__ void __launch_bounds__(512, 2) count_kernel(CountArgs a) {
     __syncthreads();
     if (threadIdx.x < 12) {
       unsigned long long t = 0;
-      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += s_red[wi][threadIdx.x];
+      for (int wi = 0; wi < kCountThreads / 32; ++wi) t += s_red[wi][threadIdx.x];
       if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
     }
     if (threadIdx.x == 0) s_item[par ^ 1] = nxt;
@@ -1575,7 +1597,7 @@ cudaError_t launch_rows(const EnumArgs &args, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
-  count_kernel<<<grid, 512, 0, st>>>(args);
+  count_kernel<<<grid, kCountThreads, kCountRingBytes, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st) {
@@ -1610,7 +1632,9 @@ cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rows_kernel, kRowsThreads, dyn);
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, 512, 0);
+  cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRingBytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, kCountThreads, kCountRingBytes);
 }
 
 }  // namespace ws

@@ -65,6 +65,9 @@ cudaError_t enum_occupancy(int threads, int iv_cap, int *blocks_per_sm);
 size_t enum_dyn_smem(int iv_cap);
 cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm);
 constexpr int kRowsThreads = 256;
+constexpr int kCountThreads = 256;   // counting kernel: threads per CTA
+constexpr int kCountStages = 4;      //   ring slots per thread and bitmap (cp.async pipeline depth)
+constexpr int kCountRingBytes = kCountStages * 4 * kCountThreads * 16;   // 64 KiB of dynamic shared memory
 constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
 cudaError_t count_occupancy(int *blocks_per_sm);
 

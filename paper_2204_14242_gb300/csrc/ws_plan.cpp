@@ -1172,7 +1172,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ca.citem_hi = P.citem_hi;
     ca.chunk_words = tune.count_words;
     if (P.citem_hi > P.citem_lo) {
-      CU(launch_count(ca, grid_for(512, P.citem_hi - P.citem_lo, true), st));
+      CU(launch_count(ca, grid_for(kCountThreads, P.citem_hi - P.citem_lo, true), st));
       ++launches;
     }
     if ((rc = mark(3 + 3 * (int)p)) != WS_OK) return rc;
@@ -1254,7 +1254,7 @@ int ws_plan::run_plain(cudaStream_t st) {
       ca.citem_lo = ct_lo;
       ca.citem_hi = ct_hi;
       ca.chunk_words = tune.count_words;
-      if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(512, ct_hi - ct_lo, true), st));
+      if (ct_hi > ct_lo) CU(launch_count(ca, grid_for(kCountThreads, ct_hi - ct_lo, true), st));
     }
     ModelArgs ma;
     ma.cfg = (const DCfg *)dev(d_cfg) + i;
@@ -1880,6 +1880,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     // raise the enumeration kernel's shared-memory limit now, outside any capture
     int occ = 0;
     cudaError_t e0 = enum_occupancy(p->tune.enum_threads, p->iv_cap, &occ);
+    if (e0 == cudaSuccess) e0 = count_occupancy(&occ);   // the counting kernel's ring limit likewise
     if (e0 != cudaSuccess) {
       set_error(std::string("enumeration kernel setup: ") + cudaGetErrorString(e0));
       delete p;
