@@ -55,8 +55,7 @@ struct DCfg {
   FastDiv fd_gx, fd_gy, fd_wpb;
   // Row walk of levels 1-3 (wave, y set, z set).  A block row R = by + g[1] * bz of a
   // level holds one run of blocks that are consecutive in x; its threads with the same
-  // (ty, tz) form one grid row of consecutive x.  Slot = (block row, thread row); the
-  // z set has two slots per thread row (its run may be cut in two by the y set).
+  // (ty, tz) form one grid row of consecutive x.  Slot = (block row, thread row).
   // Level 3 of the row walk is the representative block itself (its block bitmaps).
   int32_t rows_R_lo[4], rows_R_cnt[4];
   int64_t rows_slot_end[4];    // cumulative slots: wave, y set, z set, block (< 2^31)

@@ -1072,6 +1072,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int32_t s_gwi[2];
   __shared__ long long s_item;
   __shared__ unsigned long long s_acc[kRowsThreads / 32][3];   // per warp: the item's counts (lane 0 adds)
+  __shared__ unsigned long long s_memo_key[kRowsThreads];       // per thread: last store-sector count
+  __shared__ uint32_t s_memo_val[kRowsThreads];
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
@@ -1096,6 +1098,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       stage_group(a, gi, cur_cfg, sm);
       cur_g = gi;
       cur_cfg = s_g.cfg;
+      s_memo_key[threadIdx.x] = ~0ull;   // store-sector counts hold for one candidate's geometry
     }
     const int64_t kk = item - s_g.ritem_begin;
     uint32_t bad = 0, nred = 0;
@@ -1125,8 +1128,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         }
         const uint32_t pq = fdiv((uint32_t)loc, s_c.fd_rows);
         const uint32_t t = (uint32_t)loc - pq * (uint32_t)s_c.rows_per_blk;
-        const uint32_t R = (uint32_t)s_c.rows_R_lo[lv] + (lv == 2 ? (pq >> 1) : pq);
-        const uint32_t piece = lv == 2 ? (pq & 1u) : 0u;
+        const uint32_t R = (uint32_t)s_c.rows_R_lo[lv] + pq;
         const uint32_t gx = (uint32_t)s_c.g[0], gy = (uint32_t)s_c.g[1];
         const uint32_t bz = fdiv(R, s_c.fd_gy), by = R - bz * gy;
         const int64_t rb0 = (int64_t)R * gx, rb1 = rb0 + gx;
@@ -1142,14 +1144,12 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           ba = max(s_c.y_lo, rb0);
           bb = min(s_c.y_hi, rb1);
         } else {
+          // z set minus the y set: the y set takes [y_lo, y_hi) outside the last block row,
+          // and z_hi <= y_hi (both are the wave shifted back, the z set by a whole slab), so
+          // only the blocks before y_lo remain in the other rows
           ba = max(s_c.z_lo, rb0);
           bb = min(s_c.z_hi, rb1);
-          if (by != gy - 1 && s_c.y_hi > s_c.y_lo) {
-            if (piece == 0u) bb = min(bb, s_c.y_lo);
-            else ba = max(ba, s_c.y_hi);
-          } else if (piece) {
-            continue;
-          }
+          if (by != gy - 1 && s_c.y_hi > s_c.y_lo) bb = min(bb, s_c.y_lo);
         }
         if (ba >= bb) continue;
         const uint32_t bxa = (uint32_t)(ba - rb0), bxb = (uint32_t)(bb - rb0);
@@ -1220,7 +1220,21 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
             if (cb) atomicOr(bm + cu, cb);
             nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-            if (!blk) sreq += (uint32_t)row_store_sectors(el0 + bo, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb);
+            if (!blk) {
+              // the count depends on the row start only modulo 32 bytes, on t only through
+              // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
+              // rows that agree on those reuse this thread's previous count
+              const int64_t A0 = el0 + bo;
+              const unsigned long long key = (unsigned long long)(A0 & 31) |
+                                             ((unsigned long long)((t * (uint32_t)s_c.B[0]) & 31u) << 5) |
+                                             ((unsigned long long)bxa << 10) | ((unsigned long long)bxb << 37);
+              if (s_memo_key[threadIdx.x] != key) {
+                s_memo_val[threadIdx.x] =
+                    (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb);
+                s_memo_key[threadIdx.x] = key;
+              }
+              sreq += s_memo_val[threadIdx.x];
+            }
           }
           sreq = __reduce_add_sync(FULL, sreq);
           if (lane == 0u) s_acc[warp][2] += sreq;

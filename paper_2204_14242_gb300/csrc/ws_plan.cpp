@@ -607,7 +607,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
         d.rows_R_lo[lv] = (int32_t)R0;
         d.rows_R_cnt[lv] = (int32_t)(R1 - R0 + 1);
       }
-      cum += (int64_t)d.rows_R_cnt[lv] * (lv == 2 ? 2 : 1) * d.rows_per_blk;
+      cum += (int64_t)d.rows_R_cnt[lv] * d.rows_per_blk;
       d.rows_slot_end[lv] = cum;
     }
     out.rows_geom_ok = cum < ((int64_t)1 << 31);
