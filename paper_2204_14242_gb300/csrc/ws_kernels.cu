@@ -1616,7 +1616,9 @@ cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
 }
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st) {
   if (args.n <= 0) return cudaSuccess;
-  model_kernel<<<(args.n + 127) / 128, 128, 0, st>>>(args);
+  // one warp per CTA: the model is fp64 (1/64 of the fp32 rate on this part), so the
+  // candidates are spread over as many SMs' fp64 pipes as possible
+  model_kernel<<<(args.n + 31) / 32, 32, 0, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_rank(const RankArgs &args, cudaStream_t st) {
