@@ -1,0 +1,32 @@
+"""Host-side pieces of bench.py that need no GPU: the per-kernel DRAM traffic recorded with
+ncu is reported only for the kernel source it was taken from; the whole-job throughput and
+the roofline arithmetic."""
+import bench
+
+
+def test_recorded_traffic_follows_the_kernel_source(monkeypatch):
+    got = bench.recorded_traffic("stencil_25pt")
+    assert set(got) == {"enum_kernel", "rows_kernel", "count_kernel"}
+    # the counting kernel reads at least the bitmap bytes the sweep holds (1,445,995,168)
+    assert got["count_kernel"] >= 1_445_995_168
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 64)
+    assert bench.recorded_traffic("stencil_25pt") == {}
+    assert bench.recorded_traffic("no_such_workload") == {}
+
+
+def test_kernel_rooflines_pick_the_largest_share():
+    prof = {"ms_enum": 0.1, "ms_rows": 0.4, "ms_count": 0.2, "ms_model": 0.02, "ms_rank": 0.01, "ms_total": 0.73,
+            "block_addresses": 1_000_000, "row_reds": 40_000_000, "bitmap_bytes": 1_000_000_000}
+    peaks = {"int_ops_per_s": 3.0e13, "l2_red_per_s": 2.0e11}
+    r = bench.kernel_rooflines([prof, prof, prof], peaks)
+    assert r["kernel"] == "rows_kernel"
+    assert abs(r["achieved"] - 40e6 / 0.4e-3 / 1e9) < 1e-9          # G red.or / s
+    assert abs(r["frac"] - (40e6 / 0.4e-3) / 2.0e11) < 1e-12
+    c = r["kernels"]["count_kernel"]
+    assert abs(c["achieved"] - 1e9 / 0.2e-3 / 1e9) < 1e-9          # GB / s
+    assert r["traffic"] is None                                     # no workload given
+
+
+def test_job_throughput_counts_all_ranks():
+    assert bench.job_throughput(755, 1, 1.0) == 755_000.0
+    assert bench.job_throughput(755, 4, 2.0) == 4 * 755 / 2e-3
