@@ -45,7 +45,7 @@ UNIT = "configs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)   # about 0.7 s of timed steps: several clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stencil_25pt", choices=["stencil_25pt", "lbm", "mixed", "stencil_7pt"])
