@@ -45,7 +45,9 @@ UNIT = "configs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)   # about 0.7 s of timed steps: several clock samples
+    # default: 1000 timed steps on the GPU (about 0.7 s, so the clock sampler sees the timed
+    # region several times); 3 for the reference arm, whose steps take seconds each
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stencil_25pt", choices=["stencil_25pt", "lbm", "mixed", "stencil_7pt"])
@@ -342,6 +344,8 @@ def _serve(B, srv, reqs, arrays, rate_hz):
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 3 if args.impl == "reference" else 1000
     if args.impl == "reference":
         run_reference(args)
         return
