@@ -1924,6 +1924,9 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   int rc = WS_OK;
   auto fail = [&](cudaError_t e) {
     set_error(std::string("plan upload: ") + cudaGetErrorString(e));
+    // copies already issued may still read the plan's device memory: let them finish
+    cudaStreamSynchronize(st);
+    if (p->ready) cudaEventDestroy(p->ready);
     p->release_all();
     delete p;
     return WS_ECUDA;
