@@ -1941,6 +1941,7 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     return fail(e);
   if (ctx_scratch) ctx->oneshot_dirty = false;
   if ((rc = p->upload_fields(st)) != WS_OK) {
+    cudaStreamSynchronize(st);   // the copies issued above must finish before the memory goes back
     p->release_all();
     delete p;
     return rc;
