@@ -2222,8 +2222,12 @@ extern "C" int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, 
   // a one-shot plan would replay its graph once: launch the batched kernels directly
   rc = ws_plan_execute(p, mode == WS_MODE_BATCHED ? WS_MODE_DIRECT : mode, stream);
   if (rc == WS_OK) rc = ws_plan_results(p, out, order_out, stream);
-  // a failed step may leave bits set in the kept scratch
-  if (rc != WS_OK && kept.owns_lock()) ctx->oneshot_dirty = true;
+  // a failed step may leave bits set in the kept scratch, and its kernels must be done with
+  // it before another estimate takes it
+  if (rc != WS_OK && kept.owns_lock()) {
+    cudaStreamSynchronize(pick_stream(ctx, stream));
+    ctx->oneshot_dirty = true;
+  }
   ws_plan_destroy(p);
   return rc;
 }
