@@ -1958,7 +1958,8 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
   p->upload_bytes = (int64_t)(hcfg.size() * sizeof(DCfg) + p->hfld.size() * sizeof(DField) +
                               p->hgrp.size() * sizeof(DGroup) + hacc.size() * sizeof(DAcc) +
-                              hiv.size() * sizeof(DIv) + seg.size() * sizeof(int32_t));
+                              hiv.size() * sizeof(DIv) + seg.size() * sizeof(int32_t) +
+                              p->own.size() * sizeof(int32_t));
   *out = p;
   return WS_OK;
 }
