@@ -68,6 +68,27 @@ struct DefaultInitAlloc : std::allocator<T> {
 template <class T>
 using HostVec = std::vector<T, DefaultInitAlloc<T>>;
 
+// Page-locked host blocks for the arrays a plan uploads (when a CUDA device is present;
+// plain memory otherwise), from their own process-wide cache.  Copies from them are
+// asynchronous: the arrays live in the plan until it is destroyed.
+void *pinned_block_alloc(size_t bytes);
+void pinned_block_free(void *p);
+
+template <class T>
+struct PinnedAlloc : DefaultInitAlloc<T> {
+  template <class U>
+  struct rebind {
+    using other = PinnedAlloc<U>;
+  };
+  PinnedAlloc() = default;
+  template <class U>
+  PinnedAlloc(const PinnedAlloc<U> &) {}
+  T *allocate(size_t n) { return static_cast<T *>(pinned_block_alloc(n * sizeof(T))); }
+  void deallocate(T *p, size_t) { pinned_block_free(p); }
+};
+template <class T>
+using PinVec = std::vector<T, PinnedAlloc<T>>;
+
 void set_error(const std::string &s);
 const char *last_error();
 
@@ -97,8 +118,8 @@ struct ws_plan {
   ws_hw hw;
   ws::DHw dhw;
   ws_tuning tune;
-  ws::HostVec<ws::DField> hfld;
-  std::vector<ws::DGroup> hgrp;
+  ws::PinVec<ws::DField> hfld;
+  ws::PinVec<ws::DGroup> hgrp;
   std::vector<char> grp_iv_ok;   // group allows the interval walk (used unless tune.walk asks otherwise)
   std::vector<char> grp_rows_ok; // group allows the row walk of levels 1-3
   std::vector<int64_t> grp_slots;        // row slots of the group's candidate
@@ -113,13 +134,17 @@ struct ws_plan {
   size_t scratch_bytes = 0;
   int64_t item_begin_end = 0, ritem_begin_end = 0, citem_begin_end = 0;
   size_t grab_bytes = 0, counters_bytes = 0;
+  // uploaded arrays that the plan owns until it is destroyed (their copies are asynchronous)
+  ws::PinVec<ws::DCfg> up_cfg;
+  ws::PinVec<ws::DAcc> up_acc;
+  ws::PinVec<ws::DIv> up_iv;
   int64_t upload_bytes = 0;
   float ms_create_host = 0, ms_create_device = 0;   // wall times of the creation (host part, device part)
   int64_t d_grp = -1;
   int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
   // owner of every work item (enumeration and row-walk items: field group; counting
   // items: (candidate, field)), filled by layout(), uploaded with the fields
-  ws::HostVec<int32_t> own;             // [enumeration items | row-walk items | counting items]
+  ws::PinVec<int32_t> own;              // [enumeration items | row-walk items | counting items]
   int64_t d_own = -1;
   size_t d_own_bytes = 0;
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,

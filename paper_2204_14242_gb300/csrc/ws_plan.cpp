@@ -152,6 +152,69 @@ void host_block_free(void *p) {
   }
 }
 
+// Page-locked blocks: their own cache, sizes rounded up to 64 KiB below 2 MiB and to 2 MiB
+// above; a cached block serves requests of at least half its size.  cudaHostAlloc is tried
+// once per process: without a usable device the blocks are plain memory.
+namespace {
+struct PinnedCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> free_;
+  std::unordered_map<void *, std::pair<size_t, bool>> size_;   // size, page-locked
+  size_t cached = 0;
+  int state = 0;   // 0 untried, 1 cudaHostAlloc works, -1 it does not
+};
+PinnedCache &pinned_blocks() {
+  static PinnedCache *c = new PinnedCache;
+  return *c;
+}
+}  // namespace
+
+void *pinned_block_alloc(size_t bytes) {
+  const size_t unit = bytes < ((size_t)2 << 20) ? ((size_t)64 << 10) : ((size_t)2 << 20);
+  const size_t need = std::max(unit, (bytes + unit - 1) / unit * unit);
+  PinnedCache &c = pinned_blocks();
+  std::lock_guard<std::mutex> g(c.mu);
+  auto it = c.free_.lower_bound(need);
+  if (it != c.free_.end() && it->first <= 2 * need) {
+    void *p = it->second;
+    c.cached -= it->first;
+    c.free_.erase(it);
+    return p;
+  }
+  void *p = nullptr;
+  bool locked = false;
+  if (c.state >= 0) {
+    if (cudaHostAlloc(&p, need, cudaHostAllocDefault) == cudaSuccess) {
+      c.state = 1;
+      locked = true;
+    } else {
+      cudaGetLastError();   // not sticky: leave no error behind for later calls
+      p = nullptr;
+      c.state = -1;
+    }
+  }
+  if (!p) p = aligned_alloc(4096, need);
+  if (!p) throw std::bad_alloc();
+  c.size_[p] = std::make_pair(need, locked);
+  return p;
+}
+
+void pinned_block_free(void *p) {
+  if (!p) return;
+  PinnedCache &c = pinned_blocks();
+  std::lock_guard<std::mutex> g(c.mu);
+  auto it = c.size_.find(p);
+  if (it == c.size_.end()) return;
+  if (c.cached + it->second.first <= ((size_t)1 << 30)) {
+    c.free_.emplace(it->second.first, p);
+    c.cached += it->second.first;
+  } else {
+    if (it->second.second) cudaFreeHost(p);
+    else free(p);
+    c.size_.erase(it);
+  }
+}
+
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 static int64_t floor_div128(__int128 a, int64_t b) {
@@ -1569,9 +1632,9 @@ int ws::plan_requirements(const ws_config *cfgs, int n_cfg, const ws_field *fld,
 // builds field groups and cuts passes.  avail_fn(descriptor bytes, bitmap bytes of all
 // fields) gives the scratch capacity.  Needs no device.
 struct HostDesc {
-  HostVec<DCfg> hcfg;
-  HostVec<DAcc> hacc;
-  HostVec<DIv> hiv;
+  PinVec<DCfg> hcfg;
+  PinVec<DAcc> hacc;
+  PinVec<DIv> hiv;
   size_t scratch = 0, desc_bytes = 0;
 };
 
@@ -1663,9 +1726,9 @@ static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &
 static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                        const ws_access *acc, int n_acc, const ws_hw *hw,
                        const std::function<size_t(size_t, size_t)> &avail_fn, HostDesc &h) {
-  HostVec<DCfg> &hcfg = h.hcfg;
-  HostVec<DAcc> &hacc = h.hacc;
-  HostVec<DIv> &hiv = h.hiv;
+  PinVec<DCfg> &hcfg = h.hcfg;
+  PinVec<DAcc> &hacc = h.hacc;
+  PinVec<DIv> &hiv = h.hiv;
   hcfg.resize(n_cfg);
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   CompileArena ca;
@@ -1872,9 +1935,9 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     return avail;
   }, h);
   const auto t_host = std::chrono::steady_clock::now();
-  HostVec<DCfg> &hcfg = h.hcfg;
-  HostVec<DAcc> &hacc = h.hacc;
-  HostVec<DIv> &hiv = h.hiv;
+  PinVec<DCfg> &hcfg = h.hcfg;
+  PinVec<DAcc> &hacc = h.hacc;
+  PinVec<DIv> &hiv = h.hiv;
   const size_t scratch = h.scratch;
   {
     // raise the enumeration kernel's shared-memory limit now, outside any capture
@@ -1960,6 +2023,10 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
                               p->hgrp.size() * sizeof(DGroup) + hacc.size() * sizeof(DAcc) +
                               hiv.size() * sizeof(DIv) + seg.size() * sizeof(int32_t) +
                               p->own.size() * sizeof(int32_t));
+  // the copies from these page-locked arrays may still be running: the plan keeps them
+  p->up_cfg = std::move(hcfg);
+  p->up_acc = std::move(hacc);
+  p->up_iv = std::move(hiv);
   *out = p;
   return WS_OK;
 }
