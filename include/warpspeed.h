@@ -150,7 +150,7 @@ typedef struct ws_result {
 /* Tuning of the batched kernels (picked by ws_autotune; zeros = defaults). */
 typedef struct ws_tuning {
   int32_t chunk_warps;     /* modelled warps per enumeration work item                   */
-  int32_t enum_threads;    /* threads per CTA of the enumeration kernel (128..1024)      */
+  int32_t enum_threads;    /* threads per CTA of the enumeration kernel (64..512, x32)   */
   int32_t count_words;     /* bitmap words per counting work item                        */
   int32_t ctas_per_sm;     /* persistent CTAs per SM (0 = occupancy limit)               */
   int32_t pass_mb;         /* bitmap scratch per pass in MiB, e.g. sized to stay in L2 (0 or

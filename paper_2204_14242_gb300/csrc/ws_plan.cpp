@@ -2139,7 +2139,7 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
   ws_tuning win = orig;
   float win_ms = -1.f;
   const int chunks[] = {64, 256, 1024, 4096};
-  const int threads[] = {256, 512};
+  const int threads[] = {128, 256, 512};
   const int pass_mbs[] = {96, 1024, 8192, -1};
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
