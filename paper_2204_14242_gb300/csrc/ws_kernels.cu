@@ -10,10 +10,13 @@
 //                 row is one sector range set with 64-bit red.or; per-warp store sectors
 //                 by floor sums (Sec. 4.4, closed-form counting instead of implicit sets).
 //   count_kernel  popcounts of the bitmaps: unique sectors, unique 128 B lines (nibble
-//                 OR), y / z overlaps by AND / AND-NOT.  Leaves the bitmaps zeroed for
-//                 the next step (only non-zero positions are written).
+//                 OR), y / z overlaps by AND / AND-NOT, streamed through a per-thread
+//                 cp.async ring in shared memory.  Leaves the bitmaps zeroed for the next
+//                 step (only non-zero positions are written).
 //   model_kernel  fp64 capacity model and limiters (Sec. 2, 4.5), one thread per candidate.
 //   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.8).
+// The three persistent kernels take work items from an atomic counter and find each item's
+// field group (or field) in an owner table the host lays out with the items.
 #include <cuda_runtime.h>
 
 #include <mutex>
