@@ -372,12 +372,16 @@ def test_autotune_keeps_results(ctx):
         r1, o1 = p.results()
         best = p.autotune()
         assert best["chunk_warps"] in (64, 256, 1024, 4096) and best["pass_mb"] in (96, 1024, 8192, -1)
+        assert best["enum_threads"] in (128, 256, 512)
         p.execute(B.WS_MODE_BATCHED)
         r2, o2 = p.results()
         prof = p.profile()
     assert r1.tobytes() == r2.tobytes() and o1.tobytes() == o2.tobytes()
     # per pass enumeration, row walk and counting; then model, counting rank and scatter
     assert prof["launches"] == 3 * prof["passes"] + 3 and prof["addresses"] > 0 and prof["ms_enum"] > 0
+    # creation times: the host part (compile, grouping, layout) and the device part
+    assert prof["ms_create_host"] > 0 and prof["ms_create_device"] > 0
+    assert prof["upload_bytes"] > 0
 
 
 def test_server_results_same_alone_and_in_the_mix(ctx):
