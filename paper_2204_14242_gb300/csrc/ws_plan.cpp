@@ -2193,7 +2193,8 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
 // each its own plan; part k + 1 compiles on the host and uploads on the context's upload
 // stream while part k runs on the caller's stream.  Results are per candidate, so the parts
 // give the same results as one plan; the ranking runs once over all results.  Returns
-// WS_ENOMEM without side effects when the parts do not fit the arena together.  Parts of
+// WS_ENOMEM (the caller then runs one plan) when the parts do not fit the arena together or
+// a part's share of it is too small for one of its fields.  Parts of
 // fewer than kPipeMin candidates lose more on the device (launches, tails) than the overlap
 // gains (measured on GB300: 755 candidates in 3 parts 2.0 ms against 1.8 ms in one plan;
 // 20,000 mixed candidates 99 ms against 107 ms).
@@ -2262,6 +2263,10 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
     set_error(std::string("pipelined estimate: ") + cudaGetErrorString(e));
     rc = WS_ECUDA;
   }
+  // a part's share of the arena may be too small for a field that one plan could hold:
+  // then the caller runs the batch as one plan instead
+  for (int i = 0; rc == WS_OK && i < n_cfg; ++i)
+    if (out[i].status == WS_ENOMEM) rc = WS_ENOMEM;
   for (ws_plan *p : plans) ws_plan_destroy(p);
   for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   for (int64_t o : {o_res, o_keys, o_ord, o_rnk, o_seg})
