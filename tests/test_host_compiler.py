@@ -38,6 +38,30 @@ def test_thread_groups_match_the_oracle():
         assert zs == list(grp["z"])
 
 
+def test_z_set_ends_before_the_y_set_ends():
+    """The row walk gives the z set one slot per thread row: outside the last block row the
+    y set removes [y_lo, y_hi) from the z blocks of a row, and z_hi <= y_hi (both sets are
+    the wave shifted back, the z set by a whole slab), so only the z blocks before y_lo can
+    remain.  Checked on random candidates, the sweeps and wave-size overrides, against the
+    brute-force z set."""
+    rng = W.SplitMix64(23)
+    cases = [(random_tiny(rng), W.Hardware(sms=rng.randint(1, 6), max_blocks_sm=rng.randint(1, 4)))
+             for _ in range(300)]
+    cases += [(c, W.a100()) for c in W.stencil_25pt_sweep(N=(96, 64, 48))[::5]]
+    for c, hw in cases:
+        info = B.ws_describe([c], hw)[0]
+        assert info["status"] == 0
+        if info["y_hi"] > info["y_lo"] and info["z_hi"] > info["z_lo"]:
+            assert info["z_hi"] <= info["y_hi"]
+        g = info["grid"]
+        ys = {b for b in range(info["y_lo"], info["y_hi"]) if (b // g[0]) % g[1] != g[1] - 1}
+        last_row = lambda b: (b // g[0]) % g[1] == g[1] - 1
+        # the single-slot reading: z blocks of other rows lie before y_lo (or the y set is empty)
+        single = [b for b in range(info["z_lo"], info["z_hi"])
+                  if last_row(b) or info["y_hi"] <= info["y_lo"] or b < info["y_lo"]]
+        assert single == [b for b in range(info["z_lo"], info["z_hi"]) if b not in ys]
+
+
 def test_bitmaps_contain_every_sector():
     for c, hw in sample_configs():
         finfo = B.ws_describe_fields(c, hw)
