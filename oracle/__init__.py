@@ -13,8 +13,13 @@ Parity status per function (see the tests under ``tests/``):
   * layer-condition overlaps ov_y / ov_z: pinned by brute force and the 7-point closed
     form under the stated reading of the thread sets;
   * capacity model and limiters: pinned at the special cases the paper fixes
-    (R_hit = 1 -> compulsory, R_hit = 0 -> request volume, lowest-limiter = max);
-    the hit-rate coefficients themselves are parity unpinned (not printed in the paper).
+    (R_hit = 1 -> compulsory, R_hit = 0 -> request volume, lowest-limiter = max) and,
+    term by term, against closed forms derived by hand for the 7-point case and a
+    misaligned streaming copy (O_L1, O_y, O_z, O_st, R(O) with b, c != 0, every volume
+    and limiter time; tests/test_model_pins.py, which also plants mistakes in a copy of
+    this oracle and checks that the pins catch them);
+  * the hit-rate coefficients are inputs: the paper prints none, so their values (not
+    the function they enter) are parity unpinned.
 """
 from __future__ import annotations
 
