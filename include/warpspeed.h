@@ -48,7 +48,7 @@ extern "C" {
 #define WS_EOVERFLOW (-5)  /* a counting structure overflowed (never silent)             */
 #define WS_ECUDA (-6)      /* a CUDA runtime call failed                                 */
 #define WS_ENOTFOUND (-7)  /* unknown request id                                         */
-#define WS_ECANCELED (-8)  /* server shut down before the request ran                    */
+#define WS_ECANCELED (-8)  /* server: request withdrawn, or shut down before it ran       */
 
 /* ---- modes of ws_plan_execute / ws_estimate_batch ---------------------------------- */
 #define WS_MODE_PLAIN 0    /* one synchronous launch sequence per candidate               */
@@ -360,7 +360,8 @@ typedef struct ws_server_stats {
   int64_t submitted, completed, rejected, steps, configs_done;
   int64_t bytes_in_use, peak_bytes;
   int32_t inflight_steps, queued;
-} ws_server_stats;
+  int64_t canceled;           /* requests withdrawn by ws_server_cancel                    */
+} ws_server_stats; /* 72 bytes */
 
 int ws_server_create(ws_ctx *ctx, const ws_server_opts *opts, const ws_hw *hw, ws_server **srv);
 /* Copies the request and queues it; returns at once.  A request whose scratch exceeds
@@ -371,6 +372,15 @@ int ws_server_submit(ws_server *srv, const ws_request *req, uint64_t *req_id);
  * results (and ranking, may be NULL) and forgets it.  WS_EAGAIN if not finished. */
 int ws_server_poll(ws_server *srv, uint64_t req_id, ws_result *out, int32_t *order, int64_t timeout_us);
 int ws_server_stats_get(ws_server *srv, ws_server_stats *out);
+/* paused != 0: admit no new device steps (steps already admitted run to the end);
+ * requests keep queueing until the queue is full.  paused == 0: resume admission.
+ * Lets a host drain the GPU for other work, or gather a burst of requests into fewer,
+ * larger steps, without losing queued requests. */
+int ws_server_pause(ws_server *srv, int paused);
+/* Withdraws a request that is still queued: WS_OK, and its next poll returns
+ * WS_ECANCELED (and forgets it).  WS_EAGAIN if it was already admitted into a step
+ * (poll for its result), WS_ENOTFOUND for an unknown or already collected id. */
+int ws_server_cancel(ws_server *srv, uint64_t req_id);
 /* Finishes every admitted step, cancels queued requests, joins the worker. */
 int ws_server_destroy(ws_server *srv);
 

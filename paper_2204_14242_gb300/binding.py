@@ -56,7 +56,7 @@ REQUEST = np.dtype([("cfgs", "<u8"), ("n_cfg", "<i4"), ("n_fld", "<i4"), ("fld",
                     ("n_acc", "<i4"), ("reserved", "<i4")], align=True)
 SERVER_STATS = np.dtype([("submitted", "<i8"), ("completed", "<i8"), ("rejected", "<i8"), ("steps", "<i8"),
                          ("configs_done", "<i8"), ("bytes_in_use", "<i8"), ("peak_bytes", "<i8"),
-                         ("inflight_steps", "<i4"), ("queued", "<i4")], align=True)
+                         ("inflight_steps", "<i4"), ("queued", "<i4"), ("canceled", "<i8")], align=True)
 CFG_INFO = np.dtype([("status", "<i4"), ("grid", "<i4", (3,)), ("threads", "<i4"), ("warps_per_block", "<i4"),
                      ("blocks_per_sm", "<i4"), ("n_field", "<i4"), ("total_blocks", "<i8"), ("rep_block", "<i8"),
                      ("wave_first", "<i8"), ("wave_blocks", "<i8"), ("y_lo", "<i8"), ("y_hi", "<i8"),
@@ -65,7 +65,7 @@ CFG_INFO = np.dtype([("status", "<i4"), ("grid", "<i4", (3,)), ("threads", "<i4"
                      ("scratch_bytes", "<i8")], align=True)
 FIELD_INFO = np.dtype([("lo_sector", "<i8", (2,)), ("words", "<i8", (2,)), ("n_load", "<i4"), ("n_store", "<i4")],
                       align=True)
-assert (CFG_INFO.itemsize, FIELD_INFO.itemsize) == (144, 40)
+assert (CFG_INFO.itemsize, FIELD_INFO.itemsize, SERVER_STATS.itemsize) == (144, 40, 72)
 assert (ACCESS.itemsize, FIELD.itemsize, CONFIG.itemsize, HW.itemsize, RESULT.itemsize) == (24, 56, 64, 176, 312)
 
 WS_OK, WS_EINVAL, WS_ENOMEM, WS_EAGAIN, WS_ETIMEDOUT, WS_EOVERFLOW, WS_ECUDA, WS_ENOTFOUND, WS_ECANCELED = \
@@ -78,7 +78,8 @@ EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_
            "ws_plan_create", "ws_plan_execute", "ws_plan_results", "ws_plan_device_results", "ws_plan_profile",
            "ws_autotune", "ws_plan_destroy", "ws_estimate_batch", "ws_rank", "ws_rank_key", "ws_server_create",
            "ws_server_submit", "ws_server_poll", "ws_server_stats_get", "ws_server_destroy", "ws_describe",
-           "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc", "ws_plan_dry_run"]
+           "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc", "ws_plan_dry_run",
+           "ws_server_pause", "ws_server_cancel"]
 
 
 class WsError(RuntimeError):
@@ -134,6 +135,7 @@ def load(build_if_missing: bool = False):
             "ws_describe_fields": ([P, P, I, P, I, P, P], I), "ws_measure_peaks": ([P, P, P], I),
             "ws_estimate_batch_noalloc": ([I, P, I, P, I, P, I, P, P, P, P], I),
             "ws_plan_dry_run": ([P, I, P, I, P, I, P, P, ctypes.c_size_t, P], I),
+            "ws_server_pause": ([P, I], I), "ws_server_cancel": ([P, ctypes.c_uint64], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -497,6 +499,15 @@ class Server:
         if rc != WS_OK:
             return rc, None, None
         return rc, res, order
+
+    def pause(self, paused: bool = True) -> None:
+        """Stops (or resumes) admitting new device steps; queued requests wait."""
+        _check(load().ws_server_pause(self.handle, int(bool(paused))), "ws_server_pause")
+
+    def cancel(self, rid: int) -> int:
+        """Withdraws a queued request: WS_OK (its poll then returns WS_ECANCELED),
+        WS_EAGAIN if it already runs, WS_ENOTFOUND if unknown."""
+        return load().ws_server_cancel(self.handle, rid)
 
     def stats(self) -> dict:
         s = np.zeros(1, SERVER_STATS)

@@ -37,6 +37,7 @@ static_assert(sizeof(ws_hw) == 176, "ws_hw layout");
 static_assert(sizeof(ws_result) == 312, "ws_result layout");
 static_assert(sizeof(ws_cfg_info) == 144, "ws_cfg_info layout");
 static_assert(sizeof(ws_field_info) == 40, "ws_field_info layout");
+static_assert(sizeof(ws_server_stats) == 72, "ws_server_stats layout");
 
 namespace ws {
 

@@ -74,6 +74,7 @@ struct ws_server {
   std::vector<Slot> slots;
   std::thread worker;
   bool stop = false;
+  bool paused = false;     // admit no new steps (ws_server_pause)
   uint64_t next_id = 1;
   ws_server_stats stats;
 };
@@ -243,7 +244,7 @@ void worker_main(ws_server *s) {
     retire(s);
     if (!s->inflight.empty() || !s->queue.empty()) s->cv_done.notify_all();
     bool launched = false;
-    if (!s->stop)
+    if (!s->stop && !s->paused)
       while (admit(s, lk)) launched = true;
     if (launched) continue;
     if (s->stop) {
@@ -376,6 +377,32 @@ extern "C" int ws_server_poll(ws_server *s, uint64_t id, ws_result *out, int32_t
   s->reqs.erase(it);
   delete r;
   return rc;
+}
+
+extern "C" int ws_server_pause(ws_server *s, int paused) {
+  if (!s) return WS_EINVAL;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv_work.notify_all();
+  return WS_OK;
+}
+
+extern "C" int ws_server_cancel(ws_server *s, uint64_t id) {
+  if (!s) return WS_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return WS_ENOTFOUND;
+  Request *r = it->second;
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q == s->queue.end()) return r->done && r->status == WS_ECANCELED ? WS_OK : WS_EAGAIN;
+  s->queue.erase(q);
+  r->status = WS_ECANCELED;
+  r->done = true;
+  s->stats.canceled += 1;
+  s->cv_done.notify_all();
+  return WS_OK;
 }
 
 extern "C" int ws_server_stats_get(ws_server *s, ws_server_stats *out) {

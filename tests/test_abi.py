@@ -51,6 +51,7 @@ def test_struct_layouts_match_the_header():
     assert int(sizes["ws_tuning"]) == B.TUNING.itemsize
     assert int(sizes["ws_profile"]) == B.PROFILE.itemsize
     assert int(sizes["ws_plan_summary"]) == B.PLAN_SUMMARY.itemsize
+    assert int(sizes["ws_server_stats"]) == B.SERVER_STATS.itemsize
 
 
 def test_host_constants_and_rank_key():
