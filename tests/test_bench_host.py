@@ -4,13 +4,15 @@ the roofline arithmetic."""
 import bench
 
 
-def test_recorded_traffic_follows_the_kernel_source(monkeypatch):
-    got = bench.recorded_traffic("stencil_25pt")
-    assert set(got) == {"enum_kernel", "rows_kernel", "count_kernel"}
-    # the counting kernel reads at least the bitmap bytes the sweep holds (1,445,995,168)
-    assert got["count_kernel"] >= 1_445_995_168
+def test_recorded_traffic_follows_the_kernel_source(monkeypatch, tmp_path):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic_sweep.txt").write_text(
+        "# comment\nkernel_source_sha256 " + "a" * 64 + "\nenum_kernel 968448\nfp_kernel 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_digest", lambda: "a" * 64)
+    assert bench.recorded_traffic("sweep") == {"enum_kernel": 968448, "fp_kernel": 1234}
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 64)
-    assert bench.recorded_traffic("stencil_25pt") == {}
+    assert bench.recorded_traffic("sweep") == {}
     assert bench.recorded_traffic("no_such_workload") == {}
 
 

@@ -2,9 +2,12 @@
 
 Integer counts must match bit for bit; fp64 volumes and times within 1e-12 relative
 (the only differences allowed are exp() rounding between CUDA and the host libm);
-rankings must be identical.  Small cases are checked in full; the full-size sweeps
-run exactly as the benchmark launches them and are checked on sampled candidates
-the oracle computes one by one.
+rankings must be identical.  Small cases are checked in full against the oracle run
+here; the full-size workloads run exactly as the benchmark launches them and are
+checked, candidate by candidate and ranking by ranking, against the oracle results
+stored under tests/golden/ by tests/make_oracle_golden.py (every candidate of the
+25-point and LBM sweeps, a stratified sample of 212 mixed candidates, every candidate
+of the served stream).
 """
 import os
 
@@ -12,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+from make_oracle_golden import SERVER_STREAM, fingerprint
 from paper_2204_14242_gb300 import binding as B
 from paper_2204_14242_gb300 import workloads as W
 from test_oracle_pins import random_tiny
@@ -45,6 +49,40 @@ def assert_match(res, want, idx=None, what=""):
         assert g["limiter"] == w["limiter"], (what, i)
         for k in B.RESULT_DBL:
             assert np.isclose(g[k], w[k], rtol=RTOL, atol=0.0), (what, i, k, g[k], w[k])
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def stored_oracle(name, configs, hw):
+    """Oracle results stored for `name`: (indices, list of result dicts).  The stored
+    fingerprint of the oracle's inputs must match these candidates."""
+    z = np.load(os.path.join(GOLDEN, f"oracle_{name}.npz"))
+    idx = [int(i) for i in z["idx"]]
+    assert str(z["fingerprint"]) == fingerprint([configs[i] for i in idx], hw), f"{name}: generator drifted"
+    ik, dk = [str(k) for k in z["int_keys"]], [str(k) for k in z["dbl_keys"]]
+    out = []
+    for r_i, r_d in zip(z["out_i"], z["out_d"]):
+        d = {k: int(v) for k, v in zip(ik, r_i)}
+        d.update({k: float(v) for k, v in zip(dk, r_d)})
+        out.append(d)
+    return idx, out, z
+
+
+def assert_ranking(order, t_gpu, t_oracle, what=""):
+    """The GPU's order equals the oracle's rank of the oracle's times.  The rank key
+    quantises t_pred to 40 bits; GPU and host exp() may differ by an ulp, which can move a
+    time across a quantisation boundary.  Only then may the orders differ, and the GPU order
+    must still be the same rule applied to its own times."""
+    want = [int(i) for i in oracle.rank(t_oracle)]
+    if [int(i) for i in order] == want:
+        return
+    kg = [oracle.rank_key(float(t)) for t in t_gpu]
+    ko = [oracle.rank_key(float(t)) for t in t_oracle]
+    moved = [i for i in range(len(kg)) if kg[i] != ko[i]]
+    assert moved, (what, "orders differ although every rank key agrees")
+    assert len(moved) <= max(1, len(kg) // 1000), (what, moved)
+    assert [int(i) for i in order] == [int(i) for i in oracle.rank(t_gpu)], what
 
 
 def test_7pt_all_modes(ctx):
@@ -110,48 +148,56 @@ def sample(n_total, k, seed):
 
 
 def test_25pt_sweep_full_size(ctx):
-    """640x512x512 (x = 640), 755 candidates in one batched launch; 16 sampled against the oracle."""
+    """640x512x512 (x = 640), 755 candidates in one batched launch: every candidate and the
+    whole ranking against the stored oracle results."""
     cfgs = W.stencil_25pt_sweep()
     hw = W.a100()
+    idx, want, _ = stored_oracle("stencil_25pt_sweep", cfgs, hw)
+    assert idx == list(range(len(cfgs)))
     with B.Plan(ctx, cfgs, hw) as p:
         p.execute(B.WS_MODE_BATCHED)
         res, order = p.results()
     assert (res["status"] == 0).all()
-    idx = sample(len(cfgs), 16, 3)
-    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
     assert_match(res, want, idx, "25pt")
-    # ranking: the GPU's order sorts its own keys exactly like the oracle's rule
-    keys = [B.ws_rank_key(t) for t in res["t_pred"]]
-    assert list(order) == sorted(range(len(cfgs)), key=lambda i: (keys[i], i))
+    assert_ranking(order, res["t_pred"], [w["t_pred"] for w in want], "25pt")
 
 
 def test_lbm_sweep_full_size(ctx):
-    """256^3, 42 arrays, 755 candidates; 4 sampled against the oracle."""
+    """256^3, 42 arrays, 755 candidates: every candidate and the ranking against the stored
+    oracle results."""
     cfgs = W.lbm_sweep()
     hw = W.a100()
+    idx, want, _ = stored_oracle("lbm_sweep", cfgs, hw)
+    assert idx == list(range(len(cfgs)))
     with B.Plan(ctx, cfgs, hw) as p:
         p.execute(B.WS_MODE_BATCHED)
         res, order = p.results()
     assert (res["status"] == 0).all()
-    idx = sample(len(cfgs), 4, 4)
-    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
     assert_match(res, want, idx, "lbm")
+    assert_ranking(order, res["t_pred"], [w["t_pred"] for w in want], "lbm")
 
 
 def test_mixed_set_full_size(ctx):
-    """20,000 seeded mixed candidates in one plan (several scratch passes); the 12 with
-    the least enumeration work plus 4 random ones checked against the oracle."""
+    """20,000 seeded mixed candidates in one plan, as the benchmark runs them; a stratified
+    sample of 212 (the 12 smallest and 12 largest by enumeration work, the 8 with the widest
+    address range, one from each of 180 strata of the work order) against the stored oracle
+    results, and the ranking of the sample by the oracle's rule."""
     cfgs = W.mixed_set()
     hw = W.a100()
-    info = B.ws_describe(cfgs, hw)
+    idx, want, _ = stored_oracle("mixed_set_sample", cfgs, hw)
+    assert len(idx) >= 200
     with B.Plan(ctx, cfgs, hw) as p:
         p.execute(B.WS_MODE_BATCHED)
         res, order = p.results()
     assert (res["status"] == 0).all()
-    work = info["modelled_warps"] * (info["folded_loads"] + info["folded_stores"])
-    idx = sorted(set(np.argsort(work)[:12].tolist()) | set(sample(len(cfgs), 4, 5)))
-    want = oracle.estimate([cfgs[i] for i in idx], hw, threads=THREADS)
     assert_match(res, want, idx, "mixed")
+    # the global order restricted to the sample is the oracle's order of the sample
+    pos = np.empty(len(cfgs), np.int64)
+    pos[order] = np.arange(len(cfgs))
+    got = [idx[j] for j in sorted(range(len(idx)), key=lambda j: pos[idx[j]])]
+    want_order = [idx[j] for j in oracle.rank([w["t_pred"] for w in want])]
+    if got != want_order:
+        assert_ranking([idx.index(i) for i in got], res["t_pred"][idx], [w["t_pred"] for w in want], "mixed")
 
 
 def random_uniform_tiny(rng: W.SplitMix64):
@@ -249,7 +295,7 @@ def test_interval_walk_uniform_groups(ctx, seed):
     cfgs = [random_uniform_tiny(rng) for _ in range(250)]
     want = oracle.estimate(cfgs, hw, threads=THREADS)
     ranks = list(oracle.rank([w["t_pred"] for w in want]))
-    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ROWS, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
             res, order = p.results()
@@ -258,14 +304,15 @@ def test_interval_walk_uniform_groups(ctx, seed):
 
 
 def test_interval_and_address_walks_identical(ctx):
-    """The row walk, the per-warp interval walk and the per-address walk give
-    bit-identical results on the workload families and the edge cases."""
+    """The footprint kernel (sets in shared memory), the row walk into device bitmaps, the
+    per-warp interval walk and the per-address walk give bit-identical results on the
+    workload families and the edge cases."""
     hw = W.a100()
     rng = W.SplitMix64(77)
     cfgs = (W.stencil_25pt_sweep(N=(160, 128, 96))[::9] + W.lbm_sweep(N=(96, 64, 48))[::37] +
             W.mixed_set(2000)[::50] + edge_configs() + [random_tiny(rng) for _ in range(100)])
     outs, stats = [], []
-    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ROWS, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
             res, order = p.results()
@@ -277,8 +324,8 @@ def test_interval_and_address_walks_identical(ctx):
             # address evaluations and modelled (warp, instruction) pairs are properties of
             # the candidates, however they are walked
             stats.append((prof["addresses"], prof["warp_instr"], prof["block_addresses"]))
-    assert outs[0] == outs[1] == outs[2]
-    assert stats[0] == stats[1] == stats[2], stats
+    assert outs[0] == outs[1] == outs[2] == outs[3]
+    assert stats[0] == stats[1] == stats[2] == stats[3], stats
     assert stats[0][0] > stats[0][2] > 0
 
 
@@ -295,7 +342,7 @@ def test_multidim_address_space(ctx):
     for w in want:
         if w["status"] != 0:
             w["status"] = B.WS_EINVAL
-    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
+    for walk in (B.WS_WALK_INTERVAL, B.WS_WALK_ROWS, B.WS_WALK_SEGMENT, B.WS_WALK_ADDRESS):
         with B.Plan(ctx, cfgs, hw, tuning={"walk": walk}) as p:
             p.execute(B.WS_MODE_BATCHED)
             res, order = p.results()
@@ -386,7 +433,7 @@ def test_autotune_keeps_results(ctx):
 
 def test_server_results_same_alone_and_in_the_mix(ctx):
     hw = W.a100()
-    reqs = W.request_stream(n_requests=24, seed=77, kmin=4, kmax=40)
+    reqs = W.request_stream(**SERVER_STREAM)
     alone = []
     for r in reqs:
         res, order = B.ws_estimate_batch(ctx, r.configs, hw)
@@ -412,6 +459,13 @@ def test_server_results_same_alone_and_in_the_mix(ctx):
         res, order = got[rid]
         assert res.tobytes() == res_a.tobytes()
         assert order.tobytes() == ord_a.tobytes()
-    # and the mix agrees with the oracle on one request
-    want = oracle.estimate(reqs[0].configs[:3], hw, threads=THREADS)
-    assert_match(got[ids[0]][0], want, [0, 1, 2], "server")
+    # every served result and every request's ranking against the stored oracle results
+    flat = [c for r in reqs for c in r.configs]
+    idx, want, z = stored_oracle("request_stream_small", flat, hw)
+    starts = [int(x) for x in z["request_starts"]]
+    assert len(starts) == len(reqs) + 1 and starts[-1] == len(flat)
+    for k, rid in enumerate(ids):
+        res, order = got[rid]
+        w = want[starts[k]:starts[k + 1]]
+        assert_match(res, w, what=f"served request {k}")
+        assert_ranking(order, res["t_pred"], [x["t_pred"] for x in w], f"served request {k}")
