@@ -159,16 +159,12 @@ typedef struct ws_tuning {
                               identical counts.  WS_WALK_INTERVAL (0): closed-form interval
                               counting (Sec. 4.4) wherever it is exact -- whole grid rows of
                               a level as sector ranges, per-warp store sectors by floor sums,
-                              with each field's sets built and counted in shared memory
-                              (address slice by address slice) where its accesses fit there,
-                              else in device-memory bitmaps, else row segments of each warp;
-                              WS_WALK_ROWS (3): the same row walk, always into device-memory
-                              bitmaps; WS_WALK_SEGMENT (2): intervals per row segment of each
-                              modelled warp only; WS_WALK_ADDRESS (1): every address
-                              evaluated.  The walk is fixed when the plan is created.      */
+                              else row segments of each warp; WS_WALK_SEGMENT (2): intervals
+                              per row segment of each modelled warp only; WS_WALK_ADDRESS
+                              (1): every address evaluated.                                */
 } ws_tuning; /* 24 bytes */
 
-enum { WS_WALK_INTERVAL = 0, WS_WALK_ADDRESS = 1, WS_WALK_SEGMENT = 2, WS_WALK_ROWS = 3 };
+enum { WS_WALK_INTERVAL = 0, WS_WALK_ADDRESS = 1, WS_WALK_SEGMENT = 2 };
 
 /* Per-kernel device time of one profiled step (CUDA events on the launch stream). */
 typedef struct ws_profile {
@@ -189,12 +185,7 @@ typedef struct ws_profile {
                                 compilation, list sharing, grouping, pass layout           */
   float ms_create_device;    /* wall time of the rest of the creation: device memory,
                                 descriptor upload, scratch zeroing, stream synchronisation */
-  float ms_footprint;        /* footprint kernel: row walk and counting of the fields whose
-                                sets are built in shared memory                            */
-  int32_t pad;
-  int64_t footprint_items;   /* (field, address slice) items of the footprint kernel       */
-  int64_t smem_ors;          /* 32-bit shared-memory atomicOr issued by the footprint kernel */
-} ws_profile; /* 136 bytes */
+} ws_profile; /* 112 bytes */
 
 typedef struct ws_ctx ws_ctx;
 typedef struct ws_plan ws_plan;
@@ -287,8 +278,7 @@ typedef struct ws_plan_summary {
   int64_t descriptor_bytes;   /* device bytes of descriptors, counters and results */
   int64_t scratch_bytes;      /* bitmap scratch the plan takes */
   int64_t bitmap_bytes;       /* bitmap bytes of all fields (what one pass would need) */
-  int64_t footprint_items;    /* (field, address slice) items of the footprint kernel */
-} ws_plan_summary; /* 104 bytes */
+} ws_plan_summary; /* 96 bytes */
 int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
                     int n_acc, const ws_hw *hw, const ws_tuning *tuning, size_t scratch_bytes,
                     ws_plan_summary *out);

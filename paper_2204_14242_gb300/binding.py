@@ -44,13 +44,12 @@ TUNING = np.dtype([("chunk_warps", "<i4"), ("enum_threads", "<i4"), ("count_word
                    ("ctas_per_sm", "<i4"), ("pass_mb", "<i4"), ("walk", "<i4")], align=True)
 PLAN_SUMMARY = np.dtype([(k, "<i8") for k in (
     "candidates_ok", "fields", "groups", "passes", "enum_items", "row_items", "count_items", "access_entries",
-    "interval_entries", "descriptor_bytes", "scratch_bytes", "bitmap_bytes", "footprint_items")], align=True)
+    "interval_entries", "descriptor_bytes", "scratch_bytes", "bitmap_bytes")], align=True)
 PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4"), ("ms_model", "<f4"),
                     ("ms_rank", "<f4"), ("ms_rows", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),
                     ("upload_bytes", "<i8"), ("row_reds", "<i8"), ("block_addresses", "<i8"),
-                    ("ms_create_host", "<f4"), ("ms_create_device", "<f4"), ("ms_footprint", "<f4"), ("pad", "<i4"),
-                    ("footprint_items", "<i8"), ("smem_ors", "<i8")], align=True)
+                    ("ms_create_host", "<f4"), ("ms_create_device", "<f4")], align=True)
 SERVER_OPTS = np.dtype([("mem_budget", "<u8"), ("max_inflight", "<i4"), ("max_step_cfgs", "<i4"),
                         ("max_queue", "<i4"), ("reserved", "<i4")], align=True)
 REQUEST = np.dtype([("cfgs", "<u8"), ("n_cfg", "<i4"), ("n_fld", "<i4"), ("fld", "<u8"), ("acc", "<u8"),
@@ -72,7 +71,7 @@ assert (ACCESS.itemsize, FIELD.itemsize, CONFIG.itemsize, HW.itemsize, RESULT.it
 WS_OK, WS_EINVAL, WS_ENOMEM, WS_EAGAIN, WS_ETIMEDOUT, WS_EOVERFLOW, WS_ECUDA, WS_ENOTFOUND, WS_ECANCELED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 WS_MODE_PLAIN, WS_MODE_BATCHED, WS_MODE_DIRECT = 0, 1, 2
-WS_WALK_INTERVAL, WS_WALK_ADDRESS, WS_WALK_SEGMENT, WS_WALK_ROWS = 0, 1, 2, 3
+WS_WALK_INTERVAL, WS_WALK_ADDRESS, WS_WALK_SEGMENT = 0, 1, 2
 WS_ADDR_LINEAR, WS_ADDR_MULTIDIM = 0, 1
 
 EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_create", "ws_destroy",

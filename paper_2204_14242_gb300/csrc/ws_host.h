@@ -132,7 +132,7 @@ struct ws_plan {
   std::vector<ws::DPass> passes;
   int64_t scratch_words = 0;
   size_t scratch_bytes = 0;
-  int64_t item_begin_end = 0, ritem_begin_end = 0, citem_begin_end = 0, fitem_begin_end = 0;
+  int64_t item_begin_end = 0, ritem_begin_end = 0, citem_begin_end = 0;
   size_t grab_bytes = 0, counters_bytes = 0;
   // uploaded arrays that the plan owns until it is destroyed (their copies are asynchronous)
   ws::PinVec<ws::DCfg> up_cfg;
@@ -144,7 +144,7 @@ struct ws_plan {
   int32_t iv_cap = 0;  // most merged load intervals of an interval-walk group (dynamic shared memory)
   // owner of every work item (enumeration and row-walk items: field group; counting
   // items: (candidate, field)), filled by layout(), uploaded with the fields
-  ws::PinVec<int32_t> own;              // [enumeration | row-walk | counting items | footprint items x 2]
+  ws::PinVec<int32_t> own;              // [enumeration items | row-walk items | counting items]
   int64_t d_own = -1;
   size_t d_own_bytes = 0;
   int64_t d_cfg = -1, d_fld = -1, d_acc = -1, d_iv = -1, d_seg = -1, d_counters = -1, d_results = -1, d_keys = -1,
@@ -160,7 +160,6 @@ struct ws_plan {
   int upload_fields(cudaStream_t st);
   int grid_for(int threads, int64_t items, bool counting) const;
   int grid_rows(int64_t items) const;
-  int grid_fp(int64_t items) const;
   int bank_shift() const;
   int enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof);
   // Recorded after the descriptor uploads: launches on any stream wait for it (a graph

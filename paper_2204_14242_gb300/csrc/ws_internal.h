@@ -18,7 +18,6 @@ enum Counter {
   C_OVERFLOW,  // bitmap indices outside the bitmap (skipped; the candidate fails)
   C_RED,       // 64-bit red.or issued by the row walk (diagnostic)
   C_ADDR0,     // address evaluations of the representative block (diagnostic)
-  C_SMEM,      // 32-bit shared-memory atomicOr issued by the footprint kernel (diagnostic)
   N_COUNTERS
 };
 
@@ -89,17 +88,6 @@ struct DField {
   int32_t level_mask;     // levels served: 1 the representative block, 2 wave + y / z sets
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
-  // Footprint kernel (fields whose sets it builds in shared memory; no device bitmaps).
-  // Its address space starts at sector fp_lo (the lower of the block and wave origins)
-  // and spans fp_words 32-bit words, cut into fp_slices slices of kFpSliceWords words.
-  int32_t fused;          // the footprint kernel serves this field
-  int32_t count_lups;     // this field's wave rows count the candidate's wave LUPs
-  int32_t fp_slices;
-  int32_t pad2;
-  int64_t fp_lo;
-  int64_t fp_words;
-  int64_t fp_omin, fp_omax;   // byte offsets from a thread's first point spanned by its loads and stores
-  int64_t fitem_begin;    // first footprint-kernel item (one per slice)
 };
 
 // One folded access: byte offset from the thread's first point, and the smallest
@@ -155,7 +143,7 @@ struct DGroup {
   int32_t n_rep;
   uint8_t rep_warp[32];
   uint8_t rep_mult[32];
-  int32_t fused;          // its fields' wave, y / z and block sets are built by the footprint kernel
+  int32_t pad2;
 };
 
 // Classes of representative-block warps with identical per-instruction counts (host).
@@ -170,20 +158,10 @@ struct DPass {
   int64_t item_lo, item_hi;    // enumeration items of the pass
   int64_t ritem_lo, ritem_hi;  // row-walk items of the pass
   int64_t citem_lo, citem_hi;  // counting items of the pass
-  int64_t fitem_lo, fitem_hi;  // footprint-kernel items of the pass
   int32_t cf_lo, cf_hi;        // (candidate, field) index range
   int32_t grp_lo, grp_hi;      // field-group index range
   int64_t words;               // scratch words [0, words) holding the pass's bitmaps
 };
-
-// Footprint kernel limits: a fused field has at most kFpMaxAcc folded accesses and
-// kFpMaxIv merged load runs (staged in shared memory) and at most kFpMaxSlices slices;
-// a slice holds kFpSliceWords words per bitmap (three bitmaps: 180 KiB), i.e. 491,520
-// sectors or 15 MiB of address space.
-constexpr int kFpSliceWords = 15360;
-constexpr int kFpMaxAcc = 1024;
-constexpr int kFpMaxIv = 1024;
-constexpr int kFpMaxSlices = 32;
 
 constexpr int kMaxFoldedAccesses = 2048;   // per field group, staged in shared memory
 constexpr int kMaxGroupFields = 32;

@@ -13,9 +13,6 @@
 //                 OR), y / z overlaps by AND / AND-NOT, streamed through a per-thread
 //                 cp.async ring in shared memory.  Leaves the bitmaps zeroed for the next
 //                 step (only non-zero positions are written).
-//   fp_kernel     the row walk and the counting of one field at a time with its sector
-//                 sets in shared memory (one address slice per work item): the wave, y / z
-//                 and block footprints, their lines and overlaps, without device bitmaps.
 //   model_kernel  fp64 capacity model and limiters (Sec. 2, 4.5), one thread per candidate.
 //   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.8).
 // The three persistent kernels take work items from an atomic counter and find each item's
@@ -600,9 +597,8 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
       const int64_t np = (int64_t)s_g.n_rep * LS;
       const int64_t p0 = kk * (int64_t)a.block_pairs, p1 = min(p0 + (int64_t)a.block_pairs, np);
       const bool fast_banks = a.bank_shift >= 0;
-      // with the row walk (or the footprint kernel) the block sets are built there: count
-      // only, one warp per class
-      const bool count_only = s_g.rows || s_g.fused;
+      // with the row walk the block bitmaps are built there: count only, one warp per class
+      const bool count_only = s_g.rows;
       for (int64_t pp = p0 + warp; pp < p1; pp += nwarps) {
         const uint32_t r = (uint32_t)(pp / LS), j = (uint32_t)(pp - (int64_t)r * LS);
         const uint32_t mw = s_g.rep_warp[r], mult = s_g.rep_mult[r];
@@ -1425,344 +1421,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   }
 }
 
-// ---- footprint kernel -------------------------------------------------------------------
-// The row walk of one field with its sector sets in shared memory.  A work item is one
-// address slice of one fused field; the CTA keeps three bitmaps of the slice (A, B, C) and
-// builds and counts the field's sets in three phases:
-//   1. wave loads -> A, y-set loads -> B, wave stores -> C; count |W|, lines(W), lines(Y),
-//      |W & Y| (ov_y), |WS|, lines(WS); then A = W \ Y, B = C = 0;
-//   2. z-set loads -> B, block loads -> C; count lines(Z), |(W \ Y) & Z| (ov_z), |BL|,
-//      lines(BL); clear;
-//   3. block stores -> A; count |BS|, lines(BS); clear.
-// Each phase filters the row slots of its levels whose byte range (over the field's
-// accesses) meets the slice, in rounds of one slot per thread, and then walks them with P
-// lanes per slot.  A row's own counts (LUPs, address evaluations, per-warp store sectors,
-// out-of-range accesses) are taken in its home slice only: the slice holding its lowest
-// byte.  Nothing outside shared memory is written except the candidate's counters.
-
-// One row slot of the row walk: level (0 wave, 1 y set, 2 z set, 3 the representative
-// block), thread row t, block run [bxa, bxb) of its block row, grid row (y, z) of its
-// first folded point, x range [xa, xb) and valid folded points kv.
-struct FpSlot {
-  int32_t lv, kv, y, z, xa, xb;
-  uint32_t t, bxa, bxb;
-};
-
-// Decodes row slot q of a candidate (the slot numbering of the row walk); false when the
-// slot holds no valid point of its level.
-__device__ __forceinline__ bool fp_decode(const DCfg &c, uint32_t q, FpSlot &o) {
-  int lv;
-  uint32_t loc;
-  if (q < (uint32_t)c.rows_slot_end[0]) {
-    lv = 0; loc = q;
-  } else if (q < (uint32_t)c.rows_slot_end[1]) {
-    lv = 1; loc = q - (uint32_t)c.rows_slot_end[0];
-  } else if (q < (uint32_t)c.rows_slot_end[2]) {
-    lv = 2; loc = q - (uint32_t)c.rows_slot_end[1];
-  } else {
-    lv = 3; loc = q - (uint32_t)c.rows_slot_end[2];
-  }
-  const uint32_t pq = fdiv(loc, c.fd_rows);
-  const uint32_t t = loc - pq * (uint32_t)c.rows_per_blk;
-  const uint32_t R = (uint32_t)c.rows_R_lo[lv] + pq;
-  const uint32_t gx = (uint32_t)c.g[0], gy = (uint32_t)c.g[1];
-  const uint32_t bz = fdiv(R, c.fd_gy), by = R - bz * gy;
-  const int64_t rb0 = (int64_t)R * gx, rb1 = rb0 + gx;
-  int64_t ba, bb;
-  if (lv == 0) {
-    ba = max(c.s, rb0);
-    bb = min(c.s + c.weff, rb1);
-  } else if (lv == 3) {
-    ba = c.rep;
-    bb = c.rep + 1;
-  } else if (lv == 1) {
-    if (by == gy - 1) return false;
-    ba = max(c.y_lo, rb0);
-    bb = min(c.y_hi, rb1);
-  } else {
-    // z set minus the y set (see the row walk)
-    ba = max(c.z_lo, rb0);
-    bb = min(c.z_hi, rb1);
-    if (by != gy - 1 && c.y_hi > c.y_lo) bb = min(bb, c.y_lo);
-  }
-  if (ba >= bb) return false;
-  o.bxa = (uint32_t)(ba - rb0);
-  o.bxb = (uint32_t)(bb - rb0);
-  const uint32_t tz = fdiv(t, c.fd_b1), ty = t - tz * (uint32_t)c.B[1];
-  int32_t y = (int32_t)(by * (uint32_t)c.B[1] + ty), z = (int32_t)(bz * (uint32_t)c.B[2] + tz);
-  if (c.fold_axis == 1) y *= c.fold;
-  if (c.fold_axis == 2) z *= c.fold;
-  if (y >= c.N[1] || z >= c.N[2]) return false;
-  o.xa = (int32_t)o.bxa * c.B[0];
-  o.xb = min((int32_t)o.bxb * c.B[0], c.N[0]);
-  o.kv = c.fold_axis == 1 ? min(c.fold, c.N[1] - y) : c.fold_axis == 2 ? min(c.fold, c.N[2] - z) : 1;
-  o.lv = lv;
-  o.t = t;
-  o.y = y;
-  o.z = z;
-  return true;
-}
-
-// Sets sectors [s0, s1] (relative to the slice) of a shared-memory slice bitmap, clipped
-// to the slice; returns the atomics issued.
-__device__ __forceinline__ uint32_t fp_set(uint32_t *__restrict__ bm, int64_t s0, int64_t s1) {
-  constexpr int64_t kLast = (int64_t)kFpSliceWords * 32 - 1;
-  if (s0 < 0) s0 = 0;
-  if (s1 > kLast) s1 = kLast;
-  if (s0 > s1) return 0u;
-  const uint32_t w0 = (uint32_t)s0 >> 5, w1 = (uint32_t)s1 >> 5;
-  const uint32_t m0 = ~0u << ((uint32_t)s0 & 31u), m1 = ~0u >> (31u - ((uint32_t)s1 & 31u));
-  if (w0 == w1) {
-    atomicOr(bm + w0, m0 & m1);
-    return 1u;
-  }
-  atomicOr(bm + w0, m0);
-  for (uint32_t w = w0 + 1; w < w1; ++w) atomicOr(bm + w, ~0u);
-  atomicOr(bm + w1, m1);
-  return w1 - w0 + 1u;
-}
-
-constexpr size_t kFpDynSmem = (size_t)3 * kFpSliceWords * 4 + (size_t)kFpMaxIv * 12 + (size_t)kFpMaxAcc * 9 +
-                              (size_t)kFpListCap * 4;
-
-__global__ void __launch_bounds__(kFpThreads, 1) fp_kernel(FpArgs a) {
-  extern __shared__ __align__(16) unsigned char s_dyn[];
-  constexpr int SW = kFpSliceWords;
-  uint32_t *const bmA = reinterpret_cast<uint32_t *>(s_dyn);
-  uint32_t *const bmB = bmA + SW;
-  uint32_t *const bmC = bmB + SW;
-  int64_t *const s_ibo = reinterpret_cast<int64_t *>(bmC + SW);   // merged load runs: offset from the origin
-  int64_t *const s_boff = s_ibo + kFpMaxIv;                       // folded accesses (loads, then stores)
-  uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_boff + kFpMaxAcc);
-  uint32_t *const s_list = s_iext + kFpMaxIv;                     // filtered row slots of a round
-  uint8_t *const s_kmin = reinterpret_cast<uint8_t *>(s_list + kFpListCap);
-  __shared__ DCfg s_c;
-  __shared__ DField s_f;
-  __shared__ long long s_item;
-  __shared__ int s_cnt;
-  __shared__ unsigned long long s_memo_key[kFpThreads];   // per thread: last per-warp store-sector count
-  __shared__ uint32_t s_memo_val[kFpThreads];
-  __shared__ unsigned long long s_red[kFpThreads / 32][17];
-
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  {
-    uint4 *const all = reinterpret_cast<uint4 *>(bmA);
-    for (int i = (int)tid; i < 3 * SW / 4; i += kFpThreads) all[i] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  int cur_cfg = -1;
-  for (;;) {
-    if (tid == 0) s_item = a.item_lo + (long long)atomicAdd(a.grab, 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
-    if (item >= a.item_hi) break;
-    const int cf = a.own[2 * item], sl = a.own[2 * item + 1];
-    if (tid == 0) s_f = a.fld[cf];
-    s_memo_key[tid] = ~0ull;   // store-sector counts hold for one candidate's geometry
-    __syncthreads();
-    if (s_f.cfg != cur_cfg) {
-      cur_cfg = s_f.cfg;
-      if (tid == 0) s_c = a.cfg[cur_cfg];
-    }
-    const DField &F = s_f;
-    const int64_t org = F.base - 32 * F.fp_lo;   // origin: byte 0 of the field's footprint space
-    for (int j = (int)tid; j < F.n_iv; j += kFpThreads) {
-      const DIv v = a.iv[F.iv_begin + j];
-      s_ibo[j] = v.boff + org;
-      s_iext[j] = v.ext;
-    }
-    for (int j = (int)tid; j < F.n_load + F.n_store; j += kFpThreads) {
-      const DAcc d = a.acc[F.acc_begin + j];
-      s_boff[j] = d.boff + org;
-      s_kmin[j] = (uint8_t)d.kmin;
-    }
-    __syncthreads();
-    const DCfg &c = s_c;
-    const int mask = F.level_mask;
-    constexpr int64_t SB = (int64_t)SW * 1024;            // bytes of address space per slice
-    const int64_t s_base = (int64_t)sl * SB, sec0 = (int64_t)sl * SW * 32;
-    const int64_t off1 = 32 * (F.lo[1] - F.fp_lo), lim1 = off1 + (F.words[1] << 10);
-    const int64_t off0 = 32 * (F.lo[0] - F.fp_lo), lim0 = off0 + (F.words[0] << 10);
-    const int64_t omin = F.fp_omin + org, omax = F.fp_omax + org;
-    const int64_t es = F.esize, sxe = es * F.stride[0];
-    const int nw = (int)min((int64_t)SW, F.fp_words - (int64_t)sl * SW);   // a multiple of 4
-    const int nslice = F.fp_slices;
-    int P = 1;
-    while (P < 32 && (P < F.n_iv || P < F.n_load || P < F.n_store)) P <<= 1;
-    const int G = 32 / P;
-    uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t bad = 0, nsm = 0;
-    unsigned long long lups = 0, naddr = 0, sreq = 0;
-
-    for (int ph = 1; ph <= 3; ++ph) {
-      uint32_t q_lo, q_hi;
-      if (ph == 1) {
-        q_lo = 0;
-        q_hi = (uint32_t)c.rows_slot_end[F.n_load > 0 ? 1 : 0];
-      } else if (ph == 2) {
-        if (F.n_load == 0) continue;
-        q_lo = (uint32_t)c.rows_slot_end[1];
-        q_hi = (uint32_t)c.rows_slot_end[(mask & 1) ? 3 : 2];
-      } else {
-        if (!(mask & 1) || F.n_store == 0) continue;
-        q_lo = (uint32_t)c.rows_slot_end[2];
-        q_hi = (uint32_t)c.rows_slot_end[3];
-      }
-      if (tid == 0) s_cnt = 0;
-      __syncthreads();
-      for (uint32_t q0 = q_lo; q0 < q_hi; q0 += kFpThreads) {
-        // ---- filter: this round's slots whose bytes meet the slice, or whose home it is
-        const uint32_t q = q0 + tid;
-        bool rel = false;
-        FpSlot g;
-        if (q < q_hi && fp_decode(c, q, g)) {
-          const int64_t el0 = es * (F.stride[1] * (int64_t)g.y + F.stride[2] * (int64_t)g.z);
-          const int64_t ea = el0 + sxe * g.xa, eb = el0 + sxe * (g.xb - 1);
-          const int64_t v0 = min(ea, eb) + omin, v1 = max(ea, eb) + omax;
-          const int64_t hs = v0 < 0 ? 0 : min(v0 / SB, (int64_t)nslice - 1);
-          rel = (v1 >= s_base && v0 < s_base + SB) || hs == sl;
-        }
-        const uint32_t bal = __ballot_sync(FULL, rel);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&s_cnt, __popc(bal));
-        base = __shfl_sync(FULL, base, 0);
-        if (rel) s_list[base + __popc(bal & ((1u << lane) - 1u))] = q;
-        __syncthreads();
-        const int n = s_cnt;
-        __syncthreads();   // every thread has read the count before the next round adds to it
-        if (n <= kFpListCap - kFpThreads && q0 + kFpThreads < q_hi) continue;
-        // ---- walk the listed slots, P lanes per slot
-        for (int i0 = (int)warp * G; i0 < n; i0 += (kFpThreads / 32) * G) {
-          const int i = i0 + (int)lane / P, e0 = (int)lane % P;
-          if (i >= n) continue;
-          FpSlot s;
-          fp_decode(c, s_list[i], s);
-          const int64_t el0 = es * (F.stride[1] * (int64_t)s.y + F.stride[2] * (int64_t)s.z);
-          const int64_t ea = el0 + sxe * s.xa, eb = el0 + sxe * (s.xb - 1);
-          const int64_t lo = min(ea, eb), hi = max(ea, eb);
-          const int64_t v0 = lo + omin;
-          const bool home = (v0 < 0 ? 0 : min(v0 / SB, (int64_t)nslice - 1)) == sl;
-          const int64_t nx = s.xb - s.xa;
-          if (home && e0 == 0 && ph < 3 && s.lv < 3) {
-            if (s.lv == 0) {
-              if (F.count_lups) lups += (unsigned long long)(nx * s.kv);
-              naddr += (unsigned long long)(nx * (F.cnt_load[s.kv] + F.cnt_store[s.kv]));
-            } else {
-              naddr += (unsigned long long)(nx * F.cnt_load[s.kv]);
-            }
-          }
-          if (ph < 3) {
-            // loads: merged runs (raw folded loads when the row has fewer valid folded
-            // points than the fold, each checked against them)
-            uint32_t *const bm = s.lv == 0 ? bmA : s.lv == 3 ? bmC : bmB;
-            const int64_t llo = s.lv == 3 ? off0 : off1, lhi = s.lv == 3 ? lim0 : lim1;
-            const bool fullk = s.kv == c.fold;
-            const int M = fullk ? F.n_iv : F.n_load;
-            for (int e = e0; e < M; e += P) {
-              int64_t bo;
-              uint32_t ext;
-              if (fullk) {
-                bo = s_ibo[e];
-                ext = s_iext[e];
-              } else {
-                if ((int)s_kmin[e] >= s.kv) continue;
-                bo = s_boff[e];
-                ext = 0u;
-              }
-              const int64_t a0 = lo + bo, a1 = hi + bo + (int64_t)ext;
-              if (a0 < llo || a1 >= lhi) {
-                bad += home;
-                continue;
-              }
-              nsm += fp_set(bm, (a0 >> 5) - sec0, (a1 >> 5) - sec0);
-            }
-          }
-          if ((ph == 1 && s.lv == 0) || ph == 3) {
-            uint32_t *const bm = ph == 1 ? bmC : bmA;
-            const int64_t llo = ph == 3 ? off0 : off1, lhi = ph == 3 ? lim0 : lim1;
-            for (int j = e0; j < F.n_store; j += P) {
-              if ((int)s_kmin[F.n_load + j] >= s.kv) continue;
-              const int64_t bo = s_boff[F.n_load + j];
-              const int64_t a0 = lo + bo, a1 = hi + bo;
-              if (a0 < llo || a1 >= lhi) {
-                bad += home;
-                continue;
-              }
-              nsm += fp_set(bm, (a0 >> 5) - sec0, (a1 >> 5) - sec0);
-              if (ph == 1 && home) {
-                // per-warp store sectors of the row; the count depends on the row start only
-                // modulo 32 bytes, on t only through t * B0 modulo 32 and on the block run
-                const int64_t A0 = el0 + bo;
-                const unsigned long long key = (unsigned long long)(A0 & 31) |
-                                               ((unsigned long long)((s.t * (uint32_t)c.B[0]) & 31u) << 5) |
-                                               ((unsigned long long)s.bxa << 10) | ((unsigned long long)s.bxb << 37);
-                if (s_memo_key[tid] != key) {
-                  s_memo_val[tid] = (uint32_t)row_store_sectors(A0, sxe, c.B[0], c.N[0], c.full_end, s.t, s.bxa, s.bxb);
-                  s_memo_key[tid] = key;
-                }
-                sreq += s_memo_val[tid];
-              }
-            }
-          }
-        }
-        __syncthreads();
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
-      }
-      // ---- count the slice (words [0, nw)) and clear what the next phase reuses
-      uint4 *const A4 = reinterpret_cast<uint4 *>(bmA);
-      uint4 *const B4 = reinterpret_cast<uint4 *>(bmB);
-      uint4 *const C4 = reinterpret_cast<uint4 *>(bmC);
-      const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
-      for (int i = (int)tid; i < nw / 4; i += kFpThreads) {
-        const uint4 va = A4[i], vb = B4[i], vc = C4[i];
-        if (ph == 1) {
-          tally_wave(acc, va, vb, z4);                 // |W|, lines(W), lines(Y), |W & Y|
-          tally_sectors_lines(acc[10], acc[11], vc);   // wave stores
-          A4[i] = make_uint4(va.x & ~vb.x, va.y & ~vb.y, va.z & ~vb.z, va.w & ~vb.w);
-          B4[i] = z4;
-          C4[i] = z4;
-        } else if (ph == 2) {
-          acc[7] += lines_of(vb.x) + lines_of(vb.y) + lines_of(vb.z) + lines_of(vb.w);
-          acc[9] += __popc(va.x & vb.x) + __popc(va.y & vb.y) + __popc(va.z & vb.z) + __popc(va.w & vb.w);
-          tally_sectors_lines(acc[0], acc[1], vc);     // block loads
-          A4[i] = z4;
-          B4[i] = z4;
-          C4[i] = z4;
-        } else {
-          tally_sectors_lines(acc[2], acc[3], va);     // block stores
-          A4[i] = z4;
-        }
-      }
-      __syncthreads();
-    }
-    // ---- the item's counts: one add per counter
-    unsigned long long v[17];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = acc[k];
-    v[12] = lups;
-    v[13] = naddr;
-    v[14] = sreq;
-    v[15] = bad;
-    v[16] = nsm;
-#pragma unroll
-    for (int k = 0; k < 17; ++k) {
-      unsigned long long x = v[k];
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-      if (lane == 0) s_red[warp][k] = x;
-    }
-    __syncthreads();
-    if (tid < 17) {
-      unsigned long long t = 0;
-      for (int w = 0; w < kFpThreads / 32; ++w) t += s_red[w][tid];
-      const int dst = tid < 12 ? kCountDst[tid]
-                               : tid == 12 ? C_LUPS_WAVE : tid == 13 ? C_ADDR : tid == 14 ? C_W_SREQ
-                                                                         : tid == 15 ? C_OVERFLOW : C_SMEM;
-      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)F.cfg * N_COUNTERS + dst), t);
-    }
-  }
-}
-
 // R(O) = a * exp(-b * exp(-c * O)), Sec. 4.5
 __device__ __forceinline__ double rhat_dev(const double h[3], double O) {
   return __dmul_rn(h[0], exp(-__dmul_rn(h[1], exp(-__dmul_rn(h[2], O)))));
@@ -1991,14 +1649,6 @@ cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm) {
   cudaError_t e = enum_allow_smem(dyn);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rows_kernel, kRowsThreads, dyn);
-}
-cudaError_t fp_setup() {
-  return cudaFuncSetAttribute(fp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFpDynSmem);
-}
-cudaError_t launch_fp(const FpArgs &args, int grid, cudaStream_t st) {
-  if (args.item_hi <= args.item_lo) return cudaSuccess;
-  fp_kernel<<<grid, kFpThreads, kFpDynSmem, st>>>(args);
-  return cudaGetLastError();
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRingBytes);

@@ -38,21 +38,6 @@ struct CountArgs {
   int32_t chunk_words;             // multiple of 4
 };
 
-// Footprint kernel: one work item = one address slice of one fused field.  The CTA walks
-// the field's grid rows (wave, y set, z set, representative block), sets each row's
-// merged load runs and stores as sector ranges in shared-memory bitmaps of the slice, and
-// counts them there (sectors, lines, overlaps): no device-memory bitmap is touched.
-struct FpArgs {
-  const DCfg *cfg;
-  const DField *fld;
-  const DAcc *acc;
-  const DIv *iv;
-  int64_t *counters;
-  unsigned long long *grab;
-  const int32_t *own;              // two per item: fused field, slice
-  int64_t item_lo, item_hi;
-};
-
 struct ModelArgs {
   const DCfg *cfg;
   const int64_t *counters;
@@ -85,9 +70,5 @@ constexpr int kCountStages = 4;      //   ring slots per thread and bitmap (cp.a
 constexpr int kCountRingBytes = kCountStages * 4 * kCountThreads * 16;   // 64 KiB of dynamic shared memory
 constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
 cudaError_t count_occupancy(int *blocks_per_sm);
-constexpr int kFpThreads = 512;      // footprint kernel: threads per CTA (one CTA per SM)
-constexpr int kFpListCap = 2048;     //   row slots filtered per round
-cudaError_t launch_fp(const FpArgs &args, int grid, cudaStream_t st);
-cudaError_t fp_setup();              // raises the kernel's shared-memory limit (call outside capture)
 
 }  // namespace ws

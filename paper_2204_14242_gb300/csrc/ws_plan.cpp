@@ -571,7 +571,7 @@ static const uint64_t kNoShare = ~(uint64_t)0;   // a list that no other descrip
 // per-(field, folding) part across candidates that share fields.
 static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, const ws_access *acc, int n_acc,
                           const ws_hw &hw, Compiled &out, FieldCache *cache = nullptr,
-                          const uint8_t *field_refs = nullptr, bool allow_fuse = true) {
+                          const uint8_t *field_refs = nullptr) {
   DCfg &d = out.d;
   memset(&d, 0, sizeof(d));
   for (int k = 0; k < 3; ++k) {
@@ -833,42 +833,9 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       df.cnt_store[kv] = ff->cnt_store[kv];
     }
     for (int k = 0; k < N_BITMAPS; ++k) df.bm[k] = -1;
-    // footprint kernel: the field's address space from the lower of its block and wave
-    // origins, cut into slices of kFpSliceWords words; the offsets its loads (merged
-    // runs) and stores span from a thread's first point
-    {
-      const int64_t lo_u = (mask & 1) ? std::min(df.lo[0], df.lo[1]) : df.lo[1];
-      int64_t hi_u = df.lo[1] + 32 * df.words[1];
-      if (mask & 1) hi_u = std::max(hi_u, df.lo[0] + 32 * df.words[0]);
-      const int64_t fw = (ceil_div(hi_u - lo_u, 32) + 3) & ~(int64_t)3;
-      df.fp_lo = lo_u;
-      df.fp_words = fw;
-      df.fp_slices = (int32_t)std::min<int64_t>(ceil_div(fw, kFpSliceWords), INT32_MAX);
-      int64_t omin = 0, omax = 0;
-      bool any = false;
-      for (const DIv &v : ff->iv) {
-        omin = any ? std::min(omin, v.boff) : v.boff;
-        omax = any ? std::max(omax, v.boff + (int64_t)v.ext) : v.boff + (int64_t)v.ext;
-        any = true;
-      }
-      for (size_t j = (size_t)ff->n_load; j < ff->da.size(); ++j) {
-        omin = any ? std::min(omin, ff->da[j].boff) : ff->da[j].boff;
-        omax = any ? std::max(omax, ff->da[j].boff) : ff->da[j].boff;
-        any = true;
-      }
-      df.fp_omin = omin;
-      df.fp_omax = omax;
-      df.fused = (allow_fuse && (mask & 2) && df.iv && df.rows_ok && out.rows_geom_ok && (has_l || has_s) &&
-                  df.n_load + df.n_store <= kFpMaxAcc && df.n_iv <= kFpMaxIv && fw > 0 &&
-                  ceil_div(fw, kFpSliceWords) <= kFpMaxSlices)
-                     ? 1
-                     : 0;
-    }
     int64_t need = 0;
-    if (!df.fused) {
-      if (has_l) need += df.words[0] + 3 * df.words[1];
-      if (has_s) need += df.words[0] + df.words[1];
-    }
+    if (has_l) need += df.words[0] + 3 * df.words[1];
+    if (has_s) need += df.words[0] + df.words[1];
     out.f.push_back(df);
     out.acc.insert(out.acc.end(), ff->da.begin(), ff->da.end());
     out.iv.insert(out.iv.end(), ff->iv.begin(), ff->iv.end());
@@ -1043,7 +1010,7 @@ static void default_tuning(ws_tuning &t) {
   t.count_words = std::max(256, t.count_words / 4 * 4);
   t.chunk_warps = std::max(1, t.chunk_warps);
   if (t.pass_mb < 0) t.pass_mb = -1;
-  if (t.walk != WS_WALK_ADDRESS && t.walk != WS_WALK_SEGMENT && t.walk != WS_WALK_ROWS) t.walk = WS_WALK_INTERVAL;
+  if (t.walk != WS_WALK_ADDRESS && t.walk != WS_WALK_SEGMENT) t.walk = WS_WALK_INTERVAL;
 }
 
 // Numbers work items and cuts passes for the current tuning.
@@ -1059,14 +1026,14 @@ void ws_plan::layout() {
   }
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
-  int64_t items = 0, ritems = 0, citems = 0, fitems = 0, used = 0;
+  int64_t items = 0, ritems = 0, citems = 0, used = 0;
   for (size_t g = 0; g < hgrp.size(); ++g) {
     DGroup &G = hgrp[g];
     G.iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
-    G.rows = grp_rows_ok[g] && (tune.walk == WS_WALK_INTERVAL || tune.walk == WS_WALK_ROWS);
-    // the row walk (or the footprint kernel) builds the block sets, so the block path
-    // counts one warp per class; otherwise it inserts every warp
-    const bool classes = (G.rows || G.fused) && (G.levels & 1) && grp_classes[g].n > 0;
+    G.rows = grp_rows_ok[g] && tune.walk == WS_WALK_INTERVAL;
+    // the row walk builds the block bitmaps, so the block path counts one warp per
+    // class; otherwise it inserts every warp
+    const bool classes = G.rows && (G.levels & 1) && grp_classes[g].n > 0;
     const int wpb = (int)G.mw_block;
     G.n_rep = classes ? grp_classes[g].n : wpb;
     for (int r = 0; r < G.n_rep; ++r) {
@@ -1085,14 +1052,12 @@ void ws_plan::layout() {
       cur.item_hi = items;
       cur.ritem_hi = ritems;
       cur.citem_hi = citems;
-      cur.fitem_hi = fitems;
       cur.words = used;
       passes.push_back(cur);
       memset(&cur, 0, sizeof(cur));
       cur.item_lo = items;
       cur.ritem_lo = ritems;
       cur.citem_lo = citems;
-      cur.fitem_lo = fitems;
       cur.cf_lo = G.f_begin;
       cur.grp_lo = g;
       used = 0;
@@ -1102,15 +1067,6 @@ void ws_plan::layout() {
       int64_t o = used;
       const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
       for (int b = 0; b < N_BITMAPS; ++b) f.bm[b] = -1;
-      f.fitem_begin = fitems;
-      f.count_lups = G.fused && G.first_wave && k == 0;
-      if (G.fused) {
-        // sets in shared memory: one footprint-kernel item per address slice, no bitmaps
-        f.item_begin = items;
-        f.citem_begin = citems;
-        fitems += f.fp_slices;
-        continue;
-      }
       if (has_l) {
         f.bm[BM_BL] = o; o += f.words[0];
         f.bm[BM_W] = o; o += f.words[1];
@@ -1135,22 +1091,20 @@ void ws_plan::layout() {
                                 : 0;
     items += G.n0_items;
     if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
-    else if ((G.levels & 2) && !G.fused) items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
+    else if (G.levels & 2) items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
   }
   cur.cf_hi = (int)hfld.size();
   cur.grp_hi = ng;
   cur.item_hi = items;
   cur.ritem_hi = ritems;
   cur.citem_hi = citems;
-  cur.fitem_hi = fitems;
   cur.words = used;
   if (ng > 0) passes.push_back(cur);
   item_begin_end = items;
   ritem_begin_end = ritems;
   citem_begin_end = citems;
-  fitem_begin_end = fitems;
-  // owners of the items: [enumeration | row walk | counting | footprint (field, slice)]
-  own.resize((size_t)(items + ritems + citems + 2 * fitems));
+  // owners of the items: [enumeration | row walk | counting]
+  own.resize((size_t)(items + ritems + citems));
   for (int g = 0; g < ng; ++g) {
     const DGroup &G = hgrp[g];
     const int64_t e1 = g + 1 < ng ? hgrp[g + 1].item_begin : items;
@@ -1162,14 +1116,6 @@ void ws_plan::layout() {
   for (int f = 0; f < nf; ++f) {
     const int64_t c1 = f + 1 < nf ? hfld[f + 1].citem_begin : citems;
     std::fill(own.begin() + items + ritems + hfld[f].citem_begin, own.begin() + items + ritems + c1, (int32_t)f);
-  }
-  int32_t *const fown = own.data() + items + ritems + citems;
-  for (int f = 0; f < nf; ++f) {
-    if (!hfld[f].fused) continue;
-    for (int32_t sl = 0; sl < hfld[f].fp_slices; ++sl) {
-      fown[2 * (hfld[f].fitem_begin + sl)] = f;
-      fown[2 * (hfld[f].fitem_begin + sl) + 1] = sl;
-    }
   }
 }
 
@@ -1221,11 +1167,6 @@ int ws_plan::grid_rows(int64_t items) const {
   return (int)g;
 }
 
-// One CTA per SM (its shared-memory bitmaps take the SM).
-int ws_plan::grid_fp(int64_t items) const {
-  return (int)std::min<int64_t>((int64_t)ctx->sm_count, std::max<int64_t>(items, 1));
-}
-
 int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
   int occ = 1;
   if (counting) count_occupancy(&occ);
@@ -1238,8 +1179,8 @@ int ws_plan::grid_for(int threads, int64_t items, bool counting) const {
 }
 
 // Enqueues one batched step (all passes, model, rank) on `st`; `ev` (may be null)
-// receives events [start, per pass (after enumeration, after row walk, after the footprint
-// kernel, after counting), after model, after rank].
+// receives events [start, per pass (after enumeration, after row walk, after counting),
+// after model, after rank].
 int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *prof) {
   auto mark = [&](int k) -> int {
     if (ev) CU(cudaEventRecord((*ev)[k], st));
@@ -1260,7 +1201,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.iv_cap = iv_cap;
     ea.scratch = (uint32_t *)dev(d_scratch);
     ea.counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
-    ea.grab = (unsigned long long *)dev(d_counters) + 4 * p;
+    ea.grab = (unsigned long long *)dev(d_counters) + 3 * p;
     ea.rgrab = ea.grab + 1;
     ea.own_enum = (const int32_t *)dev(d_own);
     ea.own_rows = ea.own_enum + item_begin_end;
@@ -1279,27 +1220,12 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
       CU(launch_enum(ea, grid_for(tune.enum_threads, P.item_hi - P.item_lo, false), tune.enum_threads, st));
       ++launches;
     }
-    if ((rc = mark(1 + 4 * (int)p)) != WS_OK) return rc;
+    if ((rc = mark(1 + 3 * (int)p)) != WS_OK) return rc;
     if (P.ritem_hi > P.ritem_lo) {
       CU(launch_rows(ea, grid_rows(P.ritem_hi - P.ritem_lo), st));
       ++launches;
     }
-    if ((rc = mark(2 + 4 * (int)p)) != WS_OK) return rc;
-    if (P.fitem_hi > P.fitem_lo) {
-      FpArgs fa;
-      fa.cfg = ea.cfg;
-      fa.fld = ea.fld;
-      fa.acc = ea.acc;
-      fa.iv = ea.iv;
-      fa.counters = ea.counters;
-      fa.grab = ea.grab + 3;
-      fa.own = ea.own_rows + ritem_begin_end + citem_begin_end;
-      fa.item_lo = P.fitem_lo;
-      fa.item_hi = P.fitem_hi;
-      CU(launch_fp(fa, grid_fp(P.fitem_hi - P.fitem_lo), st));
-      ++launches;
-    }
-    if ((rc = mark(3 + 4 * (int)p)) != WS_OK) return rc;
+    if ((rc = mark(2 + 3 * (int)p)) != WS_OK) return rc;
     CountArgs ca;
     ca.fld = ea.fld;
     ca.own = ea.own_rows + ritem_begin_end;
@@ -1313,7 +1239,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
       CU(launch_count(ca, grid_for(kCountThreads, P.citem_hi - P.citem_lo, true), st));
       ++launches;
     }
-    if ((rc = mark(4 + 4 * (int)p)) != WS_OK) return rc;
+    if ((rc = mark(3 + 3 * (int)p)) != WS_OK) return rc;
   }
   ModelArgs ma;
   ma.cfg = (const DCfg *)dev(d_cfg);
@@ -1324,7 +1250,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
   ma.hw = dhw;
   CU(launch_model(ma, st));
   launches += n_cfg > 0;
-  if ((rc = mark(1 + 4 * (int)passes.size())) != WS_OK) return rc;
+  if ((rc = mark(1 + 3 * (int)passes.size())) != WS_OK) return rc;
   RankArgs ra;
   ra.keys = (const double *)dev(d_keys);
   ra.seg = (const int32_t *)dev(d_seg);
@@ -1334,7 +1260,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
   ra.n_seg = n_seg;
   CU(launch_rank(ra, st));
   launches += n_cfg > 0 ? 2 : 0;   // counting rank + scatter
-  if ((rc = mark(2 + 4 * (int)passes.size())) != WS_OK) return rc;
+  if ((rc = mark(2 + 3 * (int)passes.size())) != WS_OK) return rc;
   if (prof) prof->launches = launches;
   return WS_OK;
 }
@@ -1356,8 +1282,7 @@ int ws_plan::run_plain(cudaStream_t st) {
       const int cf_lo = hgrp[glo].f_begin, cf_hi = hgrp[ghi - 1].f_begin + hgrp[ghi - 1].f_count;
       const int64_t ct_lo = hfld[cf_lo].citem_begin, ct_hi = cf_hi < nf ? hfld[cf_hi].citem_begin : citem_begin_end;
       const int64_t rt_lo = hgrp[glo].ritem_begin, rt_hi = ghi < ng ? hgrp[ghi].ritem_begin : ritem_begin_end;
-      const int64_t ft_lo = hfld[cf_lo].fitem_begin, ft_hi = cf_hi < nf ? hfld[cf_hi].fitem_begin : fitem_begin_end;
-      CU(cudaMemsetAsync(grab, 0, 4 * sizeof(unsigned long long), st));
+      CU(cudaMemsetAsync(grab, 0, 3 * sizeof(unsigned long long), st));
       EnumArgs ea;
       ea.cfg = (const DCfg *)dev(d_cfg);
       ea.fld = (const DField *)dev(d_fld);
@@ -1384,19 +1309,6 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.block_pairs = kBlockPairs;
       if (it_hi > it_lo) CU(launch_enum(ea, grid_for(tune.enum_threads, it_hi - it_lo, false), tune.enum_threads, st));
       if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
-      if (ft_hi > ft_lo) {
-        FpArgs fa;
-        fa.cfg = ea.cfg;
-        fa.fld = ea.fld;
-        fa.acc = ea.acc;
-        fa.iv = ea.iv;
-        fa.counters = counters;
-        fa.grab = grab + 3;
-        fa.own = ea.own_rows + ritem_begin_end + citem_begin_end;
-        fa.item_lo = ft_lo;
-        fa.item_hi = ft_hi;
-        CU(launch_fp(fa, grid_fp(ft_hi - ft_lo), st));
-      }
       CountArgs ca;
       ca.fld = ea.fld;
       ca.own = ea.own_rows + ritem_begin_end;
@@ -1647,7 +1559,7 @@ class HostPool {
 };
 
 static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
-                        int n_acc, const ws_hw &hw, bool allow_fuse, CompileArena &ca, std::vector<int> &status) {
+                        int n_acc, const ws_hw &hw, CompileArena &ca, std::vector<int> &status) {
   ca.comp.assign(n_cfg, nullptr);
   status.assign(n_cfg, WS_OK);
   // chunks of consecutive candidates handed out dynamically; each thread keeps its fold
@@ -1682,7 +1594,7 @@ static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, i
       for (int i = c * chunk; i < std::min(n_cfg, (c + 1) * chunk); ++i) {
         Compiled &cc = *new (r->allocate(sizeof(Compiled), alignof(Compiled))) Compiled(r);
         ca.comp[(size_t)i] = &cc;
-        status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, cc, &cache, refs.data(), allow_fuse);
+        status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, cc, &cache, refs.data());
         if (status[i] != WS_OK) continue;
         for (size_t k = 0; k < cc.f.size(); ++k) {
           cc.dsc_bytes += sizeof(DField) + sizeof(DGroup) + (size_t)(cc.acc_off[k + 1] - cc.acc_off[k]) * sizeof(DAcc) +
@@ -1757,8 +1669,7 @@ static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &
       const DField &f = p->hfld[k];
       const int na = f.n_load + f.n_store;
       if (G.f_count > 0 && (G.f_count >= kMaxGroupFields || G.acc_count + na > kMaxFoldedAccesses ||
-                            need + p->need_words[k] > p->scratch_words || f.level_mask != G.levels ||
-                            f.fused != p->hfld[G.f_begin].fused))
+                            need + p->need_words[k] > p->scratch_words || f.level_mask != G.levels))
         break;
       G.f_count += 1;
       G.acc_count += na;
@@ -1783,10 +1694,8 @@ static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &
     // interval walk: uniform groups whose row segments have contiguous sectors
     G.iv = G.iv && G.uniform;
     if (G.iv) go.iv_cap = std::max(go.iv_cap, G.n_iv);
-    // fields served by the footprint kernel form groups of their own; for the others, the
     // row walk: interval groups whose store counts add up per row segment
-    G.fused = p->hfld[G.f_begin].fused;
-    bool rows = !G.fused && G.iv && cc.rows_geom_ok && (G.levels & 2);
+    bool rows = G.iv && cc.rows_geom_ok && (G.levels & 2);
     int64_t instr_w = 0, instr_yz = 0;
     for (int q = G.f_begin; q < G.f_begin + G.f_count; ++q) {
       rows = rows && p->hfld[q].rows_ok;
@@ -1801,7 +1710,7 @@ static void build_groups(const Plan *p, int i, const Compiled &cc, const ws_hw &
     {
       const DField &f0 = p->hfld[G.f_begin], &c0 = p->hfld[a];
       WarpClasses wc;
-      if ((rows || (G.fused && G.uniform)) && (G.levels & 1)) {
+      if (rows && (G.levels & 1)) {
         if (f0.esize == c0.esize && f0.stride[0] == c0.stride[0] && f0.stride[1] == c0.stride[1] &&
             f0.stride[2] == c0.stride[2])
           wc = cc.cls;
@@ -1825,7 +1734,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   CompileArena ca;
   std::vector<int> status;
-  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, p->tune.walk == WS_WALK_INTERVAL, ca, status);
+  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, ca, status);
   const std::vector<Compiled *> &comp = ca.comp;
   // scratch capacity: what the arena can give after the descriptors (a field, its access
   // and interval lists, at most one field group each)
@@ -1849,8 +1758,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
       const DCfg &d = comp[i]->d;
       for (const DField &f : comp[i]->f)
         items += 3 + (size_t)d.lev_end[3] / cw + (size_t)d.rows_slot_end[3] / cr +
-                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kBlockPairs +
-                 (f.fused ? 2 * (size_t)f.fp_slices : 0);
+                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kBlockPairs;
     }
     dsc += 4 * items;
   }
@@ -2037,7 +1945,6 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
     int occ = 0;
     cudaError_t e0 = enum_occupancy(p->tune.enum_threads, p->iv_cap, &occ);
     if (e0 == cudaSuccess) e0 = count_occupancy(&occ);   // the counting kernel's ring limit likewise
-    if (e0 == cudaSuccess) e0 = fp_setup();              // and the footprint kernel's bitmaps
     if (e0 != cudaSuccess) {
       set_error(std::string("enumeration kernel setup: ") + cudaGetErrorString(e0));
       delete p;
@@ -2046,10 +1953,10 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
 
   // device buffers
-  // four work-stealing counters per pass (enumeration, row walk, footprint, counting); any tuning
+  // three work-stealing counters per pass (enumeration, row walk, counting); any tuning
   // makes at most one pass per
   // (candidate, field), so size for that (retuning may change the pass count)
-  p->grab_bytes = 32 * (p->hfld.size() + 1);
+  p->grab_bytes = 24 * (p->hfld.size() + 1);
   p->counters_bytes = p->grab_bytes + (size_t)n_cfg * N_COUNTERS * 8;
   p->d_cfg = p->take(std::max<size_t>(hcfg.size() * sizeof(DCfg), 256));
   p->d_grp = p->take(std::max<size_t>(p->hgrp.size() * sizeof(DGroup), 256));
@@ -2160,7 +2067,7 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
   CU(cudaSetDevice(p->ctx->device));
   cudaStream_t st = pick_stream(p->ctx, stream);
   memset(out, 0, sizeof(*out));
-  const int nev = 3 + 4 * (int)p->passes.size();
+  const int nev = 3 + 3 * (int)p->passes.size();
   std::vector<cudaEvent_t> ev(nev);
   for (auto &e : ev) CU(cudaEventCreate(&e));
   int rc = p->wait_ready(st);
@@ -2170,24 +2077,21 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
     float ms = 0;
     const int np = (int)p->passes.size();
     for (int k = 0; k < np; ++k) {
-      cudaEventElapsedTime(&ms, ev[4 * k], ev[1 + 4 * k]);
+      cudaEventElapsedTime(&ms, ev[3 * k], ev[1 + 3 * k]);
       out->ms_enum += ms;
-      cudaEventElapsedTime(&ms, ev[1 + 4 * k], ev[2 + 4 * k]);
+      cudaEventElapsedTime(&ms, ev[1 + 3 * k], ev[2 + 3 * k]);
       out->ms_rows += ms;
-      cudaEventElapsedTime(&ms, ev[2 + 4 * k], ev[3 + 4 * k]);
-      out->ms_footprint += ms;
-      cudaEventElapsedTime(&ms, ev[3 + 4 * k], ev[4 + 4 * k]);
+      cudaEventElapsedTime(&ms, ev[2 + 3 * k], ev[3 + 3 * k]);
       out->ms_count += ms;
     }
-    cudaEventElapsedTime(&ms, ev[4 * np], ev[1 + 4 * np]);
+    cudaEventElapsedTime(&ms, ev[3 * np], ev[1 + 3 * np]);
     out->ms_model = ms;
-    cudaEventElapsedTime(&ms, ev[1 + 4 * np], ev[2 + 4 * np]);
+    cudaEventElapsedTime(&ms, ev[1 + 3 * np], ev[2 + 3 * np]);
     out->ms_rank = ms;
-    cudaEventElapsedTime(&ms, ev[0], ev[2 + 4 * np]);
+    cudaEventElapsedTime(&ms, ev[0], ev[2 + 3 * np]);
     out->ms_total = ms;
     out->enum_items = p->item_begin_end + p->ritem_begin_end;
     out->count_items = p->citem_begin_end;
-    out->footprint_items = p->fitem_begin_end;
     out->passes = (int64_t)p->passes.size();
     out->upload_bytes = p->upload_bytes;
     out->ms_create_host = p->ms_create_host;
@@ -2200,12 +2104,11 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
       out->warp_instr += cnt[(size_t)i * N_COUNTERS + C_WINSTR];
       out->row_reds += cnt[(size_t)i * N_COUNTERS + C_RED];
       out->block_addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR0];
-      out->smem_ors += cnt[(size_t)i * N_COUNTERS + C_SMEM];
     }
     // the row walk visits no modelled warps at levels 1-3: their (warp, instruction)
     // pairs are known from the block counts
     for (size_t g = 0; g < p->hgrp.size(); ++g)
-      if (p->hgrp[g].rows || p->hgrp[g].fused) out->warp_instr += p->grp_winstr_rows[g];
+      if (p->hgrp[g].rows) out->warp_instr += p->grp_winstr_rows[g];
     int64_t bm = 0;
     for (size_t k = 0; k < p->hfld.size(); ++k) bm += p->need_words[k] * 4;
     out->bitmap_bytes = bm;
@@ -2494,7 +2397,6 @@ extern "C" int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field 
   out->enum_items = p.item_begin_end;
   out->row_items = p.ritem_begin_end;
   out->count_items = p.citem_begin_end;
-  out->footprint_items = p.fitem_begin_end;
   out->access_entries = (int64_t)h.hacc.size();
   out->interval_entries = (int64_t)h.hiv.size();
   out->descriptor_bytes = (int64_t)h.desc_bytes;

@@ -132,19 +132,13 @@ def test_plan_dry_run_host_pipeline():
     assert one["candidates_ok"] == len(sweep) and one["fields"] == 2 * len(sweep) and one["passes"] == 1
     # candidates sharing a field and a folding share its lists on the device
     assert two["access_entries"] == one["access_entries"] and two["fields"] == 2 * one["fields"]
-    # by default every field's sets are built in shared memory: no bitmaps, no row-walk or
-    # counting items, one footprint item per address slice of each field
-    assert one["bitmap_bytes"] == 0 and one["row_items"] == 0 and one["count_items"] == 0
-    assert one["footprint_items"] >= one["fields"]
-    rows = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_ROWS})
-    assert rows["footprint_items"] == 0 and rows["scratch_bytes"] == rows["bitmap_bytes"] > 0
-    small = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_ROWS}, scratch_bytes=rows["bitmap_bytes"] // 7)
-    assert small["passes"] > 1 and small["count_items"] == rows["count_items"]
+    assert one["scratch_bytes"] == one["bitmap_bytes"]
+    small = B.ws_plan_dry_run(sweep, hw, scratch_bytes=one["bitmap_bytes"] // 7)
+    assert small["passes"] > 1 and small["count_items"] == one["count_items"]
     seg = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_SEGMENT})
     adr = B.ws_plan_dry_run(sweep, hw, tuning={"walk": B.WS_WALK_ADDRESS})
-    assert rows["row_items"] > 0 and seg["row_items"] == 0 and adr["row_items"] == 0
-    assert seg["footprint_items"] == adr["footprint_items"] == 0
-    assert seg["enum_items"] == adr["enum_items"] > rows["enum_items"] == one["enum_items"]
+    assert one["row_items"] > 0 and seg["row_items"] == 0 and adr["row_items"] == 0
+    assert seg["enum_items"] == adr["enum_items"] > one["enum_items"]
     # multi-dimensional candidates: a block and a wave descriptor per field; the wave
     # lists (virtual strides of the candidate) are never shared
     md = lambda c: dataclasses.replace(c, address_mode=B.WS_ADDR_MULTIDIM)
