@@ -174,8 +174,7 @@ typedef struct ws_profile {
   int64_t enum_items, count_items;
   int64_t warp_instr;        /* modelled (warp, access) pairs evaluated                  */
   int64_t addresses;         /* valid (thread, access) address evaluations               */
-  int64_t bitmap_bytes;      /* bitmap bytes the counting kernel reads (it writes back only
-                                the non-zero 16-byte positions, as zeros)                  */
+  int64_t bitmap_bytes;      /* bitmap and page-flag bytes the plan's fields occupy        */
   int64_t passes;            /* scratch passes the plan needed                            */
   int64_t upload_bytes;      /* descriptor bytes the plan copied host -> device           */
   int64_t row_reds;          /* 64-bit red.or issued by the row walk                      */
@@ -185,7 +184,9 @@ typedef struct ws_profile {
                                 compilation, list sharing, grouping, pass layout           */
   float ms_create_device;    /* wall time of the rest of the creation: device memory,
                                 descriptor upload, scratch zeroing, stream synchronisation */
-} ws_profile; /* 112 bytes */
+  int64_t count_bytes;       /* bitmap bytes the counting kernel read: the pages the row walk
+                                flagged as written (every word for the other walks)        */
+} ws_profile; /* 120 bytes */
 
 typedef struct ws_ctx ws_ctx;
 typedef struct ws_plan ws_plan;

@@ -49,7 +49,7 @@ PROFILE = np.dtype([("ms_total", "<f4"), ("ms_enum", "<f4"), ("ms_count", "<f4")
                     ("ms_rank", "<f4"), ("ms_rows", "<f4"), ("launches", "<i4"), ("enum_items", "<i8"), ("count_items", "<i8"),
                     ("warp_instr", "<i8"), ("addresses", "<i8"), ("bitmap_bytes", "<i8"), ("passes", "<i8"),
                     ("upload_bytes", "<i8"), ("row_reds", "<i8"), ("block_addresses", "<i8"),
-                    ("ms_create_host", "<f4"), ("ms_create_device", "<f4")], align=True)
+                    ("ms_create_host", "<f4"), ("ms_create_device", "<f4"), ("count_bytes", "<i8")], align=True)
 SERVER_OPTS = np.dtype([("mem_budget", "<u8"), ("max_inflight", "<i4"), ("max_step_cfgs", "<i4"),
                         ("max_queue", "<i4"), ("reserved", "<i4")], align=True)
 REQUEST = np.dtype([("cfgs", "<u8"), ("n_cfg", "<i4"), ("n_fld", "<i4"), ("fld", "<u8"), ("acc", "<u8"),

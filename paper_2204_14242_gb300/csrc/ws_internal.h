@@ -18,12 +18,29 @@ enum Counter {
   C_OVERFLOW,  // bitmap indices outside the bitmap (skipped; the candidate fails)
   C_RED,       // 64-bit red.or issued by the row walk (diagnostic)
   C_ADDR0,     // address evaluations of the representative block (diagnostic)
+  C_CBYTES,    // bitmap bytes the counting kernel read (flagged pages only for row-walk fields)
   N_COUNTERS
 };
 
 // Bitmaps of one field, in order: block loads, block stores, wave loads, y-set loads,
 // z-set loads, wave stores.  Bit i of a bitmap stands for sector (lo + i).
 enum Bitmap { BM_BL, BM_BS, BM_W, BM_Y, BM_Z, BM_WS, N_BITMAPS };
+
+// Page flags of the row walk: a page is kPageWords bitmap words (8,192 sectors, 256 KiB of
+// address space).  The row walk sets a flag byte for every page it writes into; the
+// counting kernel reads only flagged pages and clears their flags.  Flag bytes of a field:
+// [BL pages | BS pages | W | Y | Z | WS pages], block bitmaps with ceil(words[0] / 256)
+// pages each, the others ceil(words[1] / 256).
+constexpr int kPageWords = 256;
+constexpr int kPageShiftBytes = 18;   // byte offset in a bitmap's address space -> page
+
+__host__ __device__ inline int64_t page_count(int64_t words) { return (words + kPageWords - 1) / kPageWords; }
+__host__ __device__ inline int64_t page_flag_off(int b, int64_t words0, int64_t words1) {
+  return b < 2 ? b * page_count(words0) : 2 * page_count(words0) + (b - 2) * page_count(words1);
+}
+__host__ __device__ inline int64_t page_flag_words(int64_t words0, int64_t words1) {
+  return (2 * page_count(words0) + 4 * page_count(words1) + 3) / 4;
+}
 
 // Division by an invariant 32-bit divisor d >= 1 by multiply and shift (Granlund and
 // Montgomery 1994): with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1,
@@ -70,6 +87,7 @@ struct DField {
   int64_t lo[2];          // first sector of the block bitmaps [0] / wave bitmaps [1]
   int64_t words[2];       // 32-bit words per block bitmap [0] / wave bitmap [1]
   int64_t bm[N_BITMAPS];  // word offset of each bitmap in the pass scratch, -1 = absent
+  int64_t pg;             // word offset of the page flags (row-walk fields), -1 = count every word
   int64_t item_begin;     // first enumeration work item (global numbering)
   int64_t citem_begin;    // first counting work item
   int64_t mw_end;         // modelled warps this field visits (loads: all levels, stores: block + wave)

@@ -315,6 +315,12 @@ __device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, u
   cb = m1;
 }
 
+// Flags the pages [p0, p1] of one bitmap as written (plain byte stores; the flag array
+// starts zeroed and only ever receives ones until the counting kernel clears it).
+__device__ __forceinline__ void flag_pages(uint8_t *__restrict__ fl, uint32_t p0, uint32_t p1) {
+  for (uint32_t p = p0; p <= p1; ++p) fl[p] = 1;
+}
+
 // Byte range [lo, hi] (relative to the bitmap origin) of one row segment of a
 // modelled warp under byte offset bo and extent ext.  Thread addresses are kept as
 // their low 32 bits; `mn` is the warp's smallest full thread address, and every valid
@@ -1205,6 +1211,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
           if (cb) atomicOr(bm + cu, cb);
           nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+          flag_pages(reinterpret_cast<uint8_t *>(a.scratch + F.pg) + page_flag_off(bsel, F.words[0], F.words[1]),
+                     (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
         }
         if (lv == 0 || blk) {
           uint32_t sreq = 0;   // this lane's per-warp store sectors of the row (< 2^27)
@@ -1217,12 +1225,15 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
               ++bad;
               continue;
             }
-            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[blk ? BM_BS : BM_WS]);
+            const int sb = blk ? BM_BS : BM_WS;
+            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[sb]);
             uint32_t cu = 0xffffffffu;
             unsigned long long cb = 0ull;
             put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
             if (cb) atomicOr(bm + cu, cb);
             nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+            flag_pages(reinterpret_cast<uint8_t *>(a.scratch + F.pg) + page_flag_off(sb, F.words[0], F.words[1]),
+                       (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
             if (!blk) {
               // the count depends on the row start only modulo 32 bytes, on t only through
               // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
@@ -1309,9 +1320,11 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Streams positions q0 + threadIdx.x + k * kCountThreads < q1 of up to four bitmaps (null =
-// absent, reads as zero) through the calling thread's ring slots; f(v, q) consumes them.
-template <int NS, class F>
-__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, int64_t q1, uint32_t ring, F &&f) {
+// absent, reads as zero) through the calling thread's ring slots; only positions for which
+// on(b, q) holds are copied (the others read as zero); f(v, q) consumes them.
+template <int NS, class A, class F>
+__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, int64_t q1, uint32_t ring, A &&on,
+                                             F &&f) {
   const int64_t first = q0 + threadIdx.x;
   const int64_t K = first < q1 ? (q1 - first + kCountThreads - 1) / kCountThreads : 0;
   auto slot = [&](int64_t k, int b) -> uint32_t {
@@ -1322,7 +1335,7 @@ __device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, 
       const int64_t q = first + k * kCountThreads;
 #pragma unroll
       for (int b = 0; b < NS; ++b)
-        if (p[b]) cp_async16(slot(k, b), p[b] + q);
+        if (p[b] && on(b, q)) cp_async16(slot(k, b), p[b] + q);
     }
     cp_async_commit();   // one group per step, empty or not, so that the wait count holds
   };
@@ -1331,22 +1344,26 @@ __device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, 
   for (int64_t k = 0; k < K; ++k) {
     issue(k + kCountStages - 1);
     cp_async_wait<kCountStages - 1>();   // step k's copies of this thread have landed
+    const int64_t q = first + k * kCountThreads;
     uint4 v[NS];
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
       v[b] = make_uint4(0u, 0u, 0u, 0u);
-      if (p[b]) asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-                             : "=r"(v[b].x), "=r"(v[b].y), "=r"(v[b].z), "=r"(v[b].w)
-                             : "r"(slot(k, b)) : "memory");
+      if (p[b] && on(b, q)) asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                                         : "=r"(v[b].x), "=r"(v[b].y), "=r"(v[b].z), "=r"(v[b].w)
+                                         : "r"(slot(k, b)) : "memory");
     }
-    f(v, first + k * kCountThreads);
+    f(v, q);
   }
   cp_async_wait<0>();
 }
 
+constexpr int kCountMaxPages = kCountMaxWords / kPageWords;
+
 __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
-  __shared__ uint32_t s_red[kCountThreads / 32][12];
+  __shared__ uint32_t s_red[kCountThreads / 32][13];
+  __shared__ uint8_t s_fl[4][kCountMaxPages];   // page flags of the item's chunk, per bitmap of its part
   extern __shared__ __align__(16) unsigned char s_ring[];   // [stage][bitmap][thread] x 16 bytes
   const uint32_t ring = (uint32_t)__cvta_generic_to_shared(s_ring);
   const uint32_t lane = threadIdx.x & 31u;
@@ -1361,20 +1378,45 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
     if (threadIdx.x == 0) nxt = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
     const int cf = a.own[item];
     const DField &F = a.fld[cf];
-    const int64_t bm_bl = F.bm[BM_BL], bm_bs = F.bm[BM_BS], bm_w = F.bm[BM_W], bm_ws = F.bm[BM_WS];
-    const int64_t bm_y = F.bm[BM_Y], bm_z = F.bm[BM_Z];
     const int cfg = F.cfg;
-    const bool has_blk = bm_bl >= 0 || bm_bs >= 0;
-    const int64_t nb = has_blk ? F.words[0] : 0;
-    const int64_t ntot = nb + F.words[1];
-    const int64_t c0 = (item - F.citem_begin) * (int64_t)a.chunk_words;
-    const int64_t c1 = min(c0 + (int64_t)a.chunk_words, ntot);
+    // the field's items: chunks of its block bitmaps' words, then of its wave bitmaps'
+    const int64_t cw = a.chunk_words;
+    const int64_t kb = (F.words[0] + cw - 1) / cw;
+    const int64_t k = item - F.citem_begin;
+    const bool blk = k < kb;
+    const int64_t c0 = (blk ? k : k - kb) * cw;
+    const int64_t c1 = min(c0 + cw, blk ? F.words[0] : F.words[1]);
+    const int NB = blk ? 2 : 4;
+    const int b0 = blk ? BM_BL : BM_W;   // BL, BS | W, Y, Z, WS are consecutive bitmap indices
+    // page flags of the chunk (row-walk fields): copied to shared memory, then cleared
+    const bool paged = F.pg >= 0;
+    const int64_t pg0 = c0 / kPageWords;
+    const int npg = (int)((c1 - c0 + kPageWords - 1) / kPageWords);
+    uint8_t *const fl = paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) : nullptr;
+    uint32_t rd = 0;   // bitmap bytes this thread's share of the item reads
+    if (paged) {
+      for (int i = threadIdx.x; i < NB * npg; i += kCountThreads) {
+        const int b = i / npg, j = i - b * npg;
+        uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
+        const uint8_t v = *f;
+        s_fl[b][j] = v;
+        if (v) {
+          *f = 0;
+          if (F.bm[b0 + b] >= 0) rd += 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
+        }
+      }
+      __syncthreads();
+    } else if (threadIdx.x == 0) {
+      for (int b = 0; b < NB; ++b)
+        if (F.bm[b0 + b] >= 0) rd += 4u * (uint32_t)(c1 - c0);
+    }
+    // position q (16 bytes) of bitmap b of the part is read iff its page is flagged
+    auto on = [&](int b, int64_t q) -> bool { return !paged || s_fl[b][(q >> 6) - pg0] != 0; };
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    // block part: words [c0, min(c1, nb)) -- BL, BS
-    {
-      uint4 *const pb[2] = {bm_bl >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bl) : nullptr,
-                            bm_bs >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_bs) : nullptr};
-      count_stream<2>(pb, c0 / 4, min(c1, nb) / 4, ring, [&](const uint4 (&v)[2], int64_t q) {
+    if (blk) {
+      uint4 *const pb[2] = {F.bm[BM_BL] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BL]) : nullptr,
+                            F.bm[BM_BS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BS]) : nullptr};
+      count_stream<2>(pb, c0 / 4, c1 / 4, ring, on, [&](const uint4 (&v)[2], int64_t q) {
         if (nz(v[0])) {
           tally_sectors_lines(acc[0], acc[1], v[0]);
           pb[0][q] = zero;
@@ -1384,15 +1426,13 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
           pb[1][q] = zero;
         }
       });
-    }
-    // wave part: words [max(c0, nb), c1) - nb -- W, Y, Z, WS
-    {
-      const bool has_w = bm_w >= 0;
-      uint4 *const pw[4] = {has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_w) : nullptr,
-                            has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_y) : nullptr,
-                            has_w ? reinterpret_cast<uint4 *>(a.scratch + bm_z) : nullptr,
-                            bm_ws >= 0 ? reinterpret_cast<uint4 *>(a.scratch + bm_ws) : nullptr};
-      count_stream<4>(pw, (max(c0, nb) - nb) / 4, (c1 - nb) / 4, ring, [&](const uint4 (&v)[4], int64_t q) {
+    } else {
+      const bool has_w = F.bm[BM_W] >= 0;
+      uint4 *const pw[4] = {has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_W]) : nullptr,
+                            has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr,
+                            has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr,
+                            F.bm[BM_WS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr};
+      count_stream<4>(pw, c0 / 4, c1 / 4, ring, on, [&](const uint4 (&v)[4], int64_t q) {
         if (nz(v[0]) | nz(v[1]) | nz(v[2])) {
           tally_wave(acc, v[0], v[1], v[2]);
 #pragma unroll
@@ -1406,15 +1446,20 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
       });
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      uint32_t v = __reduce_add_sync(FULL, acc[k]);
-      if (lane == 0) s_red[warp][k] = v;
+    for (int kk = 0; kk < 12; ++kk) {
+      uint32_t v = __reduce_add_sync(FULL, acc[kk]);
+      if (lane == 0) s_red[warp][kk] = v;
+    }
+    {
+      const uint32_t v = __reduce_add_sync(FULL, rd);
+      if (lane == 0) s_red[warp][12] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 12) {
+    if (threadIdx.x < 13) {
       unsigned long long t = 0;
       for (int wi = 0; wi < kCountThreads / 32; ++wi) t += s_red[wi][threadIdx.x];
-      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + kCountDst[threadIdx.x]), t);
+      const int dst = threadIdx.x < 12 ? kCountDst[threadIdx.x] : C_CBYTES;
+      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + dst), t);
     }
     if (threadIdx.x == 0) s_item[par ^ 1] = nxt;
     __syncthreads();

@@ -35,7 +35,7 @@ struct CountArgs {
   int64_t *counters;
   unsigned long long *grab;
   int64_t citem_lo, citem_hi;
-  int32_t chunk_words;             // multiple of 4
+  int32_t chunk_words;             // a multiple of kPageWords, at most kCountMaxWords
 };
 
 struct ModelArgs {
@@ -68,6 +68,7 @@ constexpr int kRowsThreads = 256;
 constexpr int kCountThreads = 256;   // counting kernel: threads per CTA
 constexpr int kCountStages = 4;      //   ring slots per thread and bitmap (cp.async pipeline depth)
 constexpr int kCountRingBytes = kCountStages * 4 * kCountThreads * 16;   // 64 KiB of dynamic shared memory
+constexpr int kCountMaxWords = 65536;   // most bitmap words of one counting item
 constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
 cudaError_t count_occupancy(int *blocks_per_sm);
 

@@ -836,6 +836,7 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     int64_t need = 0;
     if (has_l) need += df.words[0] + 3 * df.words[1];
     if (has_s) need += df.words[0] + df.words[1];
+    need += page_flag_words(df.words[0], df.words[1]);   // used when the field takes the row walk
     out.f.push_back(df);
     out.acc.insert(out.acc.end(), ff->da.begin(), ff->da.end());
     out.iv.insert(out.iv.end(), ff->iv.begin(), ff->iv.end());
@@ -1007,7 +1008,7 @@ static void default_tuning(ws_tuning &t) {
   if (t.enum_threads <= 0) t.enum_threads = 256;
   if (t.count_words <= 0) t.count_words = 16384;   // 64 KiB of words per counting item (measured: 8 K and 256 K slower)
   t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
-  t.count_words = std::max(256, t.count_words / 4 * 4);
+  t.count_words = std::min(kCountMaxWords, std::max(kPageWords, t.count_words / kPageWords * kPageWords));
   t.chunk_warps = std::max(1, t.chunk_warps);
   if (t.pass_mb < 0) t.pass_mb = -1;
   if (t.walk != WS_WALK_ADDRESS && t.walk != WS_WALK_SEGMENT) t.walk = WS_WALK_INTERVAL;
@@ -1077,10 +1078,18 @@ void ws_plan::layout() {
         f.bm[BM_BS] = o; o += f.words[0];
         f.bm[BM_WS] = o; o += f.words[1];
       }
+      // the row walk flags the pages it writes, so the counting reads only those
+      f.pg = -1;
+      if (G.rows) {
+        f.pg = o;
+        o += page_flag_words(f.words[0], f.words[1]);
+      }
       used = o;
       f.item_begin = items;
       f.citem_begin = citems;
-      citems += ceil_div(f.words[0] + f.words[1], tune.count_words);
+      // counting items: chunks of the block bitmaps' words, then of the wave bitmaps' words
+      // (each chunk a whole number of pages of one part)
+      citems += ceil_div(f.words[0], tune.count_words) + ceil_div(f.words[1], tune.count_words);
     }
     // enumeration items: the representative block (exact path) in chunks of (modelled
     // warp, instruction) pairs; then chunks of the remaining modelled warps, or, for the
@@ -2104,6 +2113,7 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
       out->warp_instr += cnt[(size_t)i * N_COUNTERS + C_WINSTR];
       out->row_reds += cnt[(size_t)i * N_COUNTERS + C_RED];
       out->block_addresses += cnt[(size_t)i * N_COUNTERS + C_ADDR0];
+      out->count_bytes += cnt[(size_t)i * N_COUNTERS + C_CBYTES];
     }
     // the row walk visits no modelled warps at levels 1-3: their (warp, instruction)
     // pairs are known from the block counts

@@ -428,6 +428,8 @@ def test_autotune_keeps_results(ctx):
     # creation times: the host part (compile, grouping, layout) and the device part
     assert prof["ms_create_host"] > 0 and prof["ms_create_device"] > 0
     assert prof["upload_bytes"] > 0
+    # the counting reads only the bitmap pages the row walk wrote into
+    assert 0 < prof["count_bytes"] < prof["bitmap_bytes"]
 
 
 def test_server_results_same_alone_and_in_the_mix(ctx):
