@@ -38,8 +38,10 @@ __host__ __device__ inline int64_t page_count(int64_t words) { return (words + k
 __host__ __device__ inline int64_t page_flag_off(int b, int64_t words0, int64_t words1) {
   return b < 2 ? b * page_count(words0) : 2 * page_count(words0) + (b - 2) * page_count(words1);
 }
+// Words the flags take, a multiple of 4 so that the bitmaps after them stay 16-byte
+// aligned (the counting kernel moves bitmaps in 16-byte units).
 __host__ __device__ inline int64_t page_flag_words(int64_t words0, int64_t words1) {
-  return (2 * page_count(words0) + 4 * page_count(words1) + 3) / 4;
+  return (2 * page_count(words0) + 4 * page_count(words1) + 15) / 16 * 4;
 }
 
 // Division by an invariant 32-bit divisor d >= 1 by multiply and shift (Granlund and
