@@ -315,10 +315,12 @@ __device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, u
   cb = m1;
 }
 
-// Flags the pages [p0, p1] of one bitmap as written (plain byte stores; the flag array
-// starts zeroed and only ever receives ones until the counting kernel clears it).
+// Flags the pages [p0, p1] of one bitmap as written.  The flag array starts zeroed and only
+// ever receives ones until the counting kernel clears it; a flag already seen set (a load
+// that mostly hits L1) is not stored again.
 __device__ __forceinline__ void flag_pages(uint8_t *__restrict__ fl, uint32_t p0, uint32_t p1) {
-  for (uint32_t p = p0; p <= p1; ++p) fl[p] = 1;
+  for (uint32_t p = p0; p <= p1; ++p)
+    if (!fl[p]) fl[p] = 1;
 }
 
 // Byte range [lo, hi] (relative to the bitmap origin) of one row segment of a
@@ -1319,23 +1321,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Streams positions q0 + threadIdx.x + k * kCountThreads < q1 of up to four bitmaps (null =
-// absent, reads as zero) through the calling thread's ring slots; only positions for which
-// on(b, q) holds are copied (the others read as zero); f(v, q) consumes them.
-template <int NS, class A, class F>
-__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, int64_t q1, uint32_t ring, A &&on,
+// Streams the item's positions (16-byte units of up to four bitmaps; null = absent, reads
+// as zero) through the calling thread's ring slots: index i = threadIdx.x + k * kCountThreads
+// < n maps to position qof(i) (< 0: none); only positions for which on(b, q) holds are copied
+// (the others read as zero); f(v, q) consumes them.
+template <int NS, class Q, class A, class F>
+__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t n, uint32_t ring, Q &&qof, A &&on,
                                              F &&f) {
-  const int64_t first = q0 + threadIdx.x;
-  const int64_t K = first < q1 ? (q1 - first + kCountThreads - 1) / kCountThreads : 0;
+  const int64_t first = threadIdx.x;
+  const int64_t K = first < n ? (n - first + kCountThreads - 1) / kCountThreads : 0;
   auto slot = [&](int64_t k, int b) -> uint32_t {
     return ring + (uint32_t)((((int)(k % kCountStages) * NS + b) * kCountThreads + (int)threadIdx.x) * 16);
   };
   auto issue = [&](int64_t k) {
     if (k < K) {
-      const int64_t q = first + k * kCountThreads;
+      const int64_t q = qof(first + k * kCountThreads);
+      if (q >= 0) {
 #pragma unroll
-      for (int b = 0; b < NS; ++b)
-        if (p[b] && on(b, q)) cp_async16(slot(k, b), p[b] + q);
+        for (int b = 0; b < NS; ++b)
+          if (p[b] && on(b, q)) cp_async16(slot(k, b), p[b] + q);
+      }
     }
     cp_async_commit();   // one group per step, empty or not, so that the wait count holds
   };
@@ -1344,7 +1349,8 @@ __device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t q0, 
   for (int64_t k = 0; k < K; ++k) {
     issue(k + kCountStages - 1);
     cp_async_wait<kCountStages - 1>();   // step k's copies of this thread have landed
-    const int64_t q = first + k * kCountThreads;
+    const int64_t q = qof(first + k * kCountThreads);
+    if (q < 0) continue;
     uint4 v[NS];
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
@@ -1364,6 +1370,8 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
   __shared__ uint32_t s_red[kCountThreads / 32][13];
   __shared__ uint8_t s_fl[4][kCountMaxPages];   // page flags of the item's chunk, per bitmap of its part
+  __shared__ uint16_t s_pl[kCountMaxPages];      // the chunk's pages that some bitmap flagged
+  __shared__ int s_npl;
   extern __shared__ __align__(16) unsigned char s_ring[];   // [stage][bitmap][thread] x 16 bytes
   const uint32_t ring = (uint32_t)__cvta_generic_to_shared(s_ring);
   const uint32_t lane = threadIdx.x & 31u;
@@ -1406,17 +1414,40 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
         }
       }
       __syncthreads();
+      // the pages some bitmap flagged, in order (one warp compacts them)
+      if (warp == 0) {
+        int cnt = 0;
+        for (int j0 = 0; j0 < npg; j0 += 32) {
+          const int j = j0 + (int)lane;
+          bool act = false;
+          if (j < npg)
+            for (int b = 0; b < NB; ++b) act = act || (s_fl[b][j] != 0 && F.bm[b0 + b] >= 0);
+          const uint32_t m = __ballot_sync(FULL, act);
+          if (act) s_pl[cnt + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
+          cnt += __popc(m);
+        }
+        if (lane == 0) s_npl = cnt;
+      }
+      __syncthreads();
     } else if (threadIdx.x == 0) {
       for (int b = 0; b < NB; ++b)
         if (F.bm[b0 + b] >= 0) rd += 4u * (uint32_t)(c1 - c0);
     }
-    // position q (16 bytes) of bitmap b of the part is read iff its page is flagged
+    // positions of the item: every position of the chunk, or those of its flagged pages;
+    // position q (16 bytes) of bitmap b is read iff that bitmap flagged its page
+    const int64_t qa = c0 / 4, qb = c1 / 4;
+    const int64_t npos = paged ? (int64_t)s_npl * (kPageWords / 4) : qb - qa;
+    auto qof = [&](int64_t i) -> int64_t {
+      if (!paged) return qa + i;
+      const int64_t q = (pg0 + s_pl[i >> 6]) * (kPageWords / 4) + (i & 63);
+      return q < qb ? q : -1;
+    };
     auto on = [&](int b, int64_t q) -> bool { return !paged || s_fl[b][(q >> 6) - pg0] != 0; };
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (blk) {
       uint4 *const pb[2] = {F.bm[BM_BL] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BL]) : nullptr,
                             F.bm[BM_BS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BS]) : nullptr};
-      count_stream<2>(pb, c0 / 4, c1 / 4, ring, on, [&](const uint4 (&v)[2], int64_t q) {
+      count_stream<2>(pb, npos, ring, qof, on, [&](const uint4 (&v)[2], int64_t q) {
         if (nz(v[0])) {
           tally_sectors_lines(acc[0], acc[1], v[0]);
           pb[0][q] = zero;
@@ -1432,7 +1463,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
                             has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr,
                             has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr,
                             F.bm[BM_WS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr};
-      count_stream<4>(pw, c0 / 4, c1 / 4, ring, on, [&](const uint4 (&v)[4], int64_t q) {
+      count_stream<4>(pw, npos, ring, qof, on, [&](const uint4 (&v)[4], int64_t q) {
         if (nz(v[0]) | nz(v[1]) | nz(v[2])) {
           tally_wave(acc, v[0], v[1], v[2]);
 #pragma unroll
