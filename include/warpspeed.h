@@ -336,6 +336,17 @@ double ws_rank_key(double t);
  * roofline denominators of the benchmark. */
 int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_red_per_s);
 
+/* The same two rates plus the rate of the row walk's own access pattern: every thread
+ * sets runs of three consecutive 64-bit words (one sector range) with 64-bit red.or, at
+ * far-apart places of a 64 MiB buffer (L2 resident). */
+typedef struct ws_peaks {
+  double int_ops_per_s;        /* 32-bit integer adds per second                          */
+  double l2_red_per_s;         /* 32-bit red.or per second on distinct random words        */
+  double l2_red64_run_per_s;   /* 64-bit red.or per second in runs of 3 adjacent words    */
+  double reserved;
+} ws_peaks; /* 32 bytes */
+int ws_measure_peaks2(ws_ctx *ctx, ws_peaks *out);
+
 /* ---- continuous-batching server ---------------------------------------------------- */
 typedef struct ws_server_opts {
   size_t mem_budget;        /* bytes of the arena the server may hold (0 = whole arena)  */

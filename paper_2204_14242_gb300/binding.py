@@ -79,7 +79,7 @@ EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_
            "ws_autotune", "ws_plan_destroy", "ws_estimate_batch", "ws_rank", "ws_rank_key", "ws_server_create",
            "ws_server_submit", "ws_server_poll", "ws_server_stats_get", "ws_server_destroy", "ws_describe",
            "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc", "ws_plan_dry_run",
-           "ws_server_pause", "ws_server_cancel"]
+           "ws_server_pause", "ws_server_cancel", "ws_measure_peaks2"]
 
 
 class WsError(RuntimeError):
@@ -136,6 +136,7 @@ def load(build_if_missing: bool = False):
             "ws_estimate_batch_noalloc": ([I, P, I, P, I, P, I, P, P, P, P], I),
             "ws_plan_dry_run": ([P, I, P, I, P, I, P, P, ctypes.c_size_t, P], I),
             "ws_server_pause": ([P, I], I), "ws_server_cancel": ([P, ctypes.c_uint64], I),
+            "ws_measure_peaks2": ([P, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -308,9 +309,9 @@ class Context:
 
 
 def ws_measure_peaks(ctx: Context) -> dict:
-    a, b = ctypes.c_double(), ctypes.c_double()
-    _check(load().ws_measure_peaks(ctx.handle, ctypes.byref(a), ctypes.byref(b)), "ws_measure_peaks")
-    return {"int_ops_per_s": a.value, "l2_red_per_s": b.value}
+    pk = (ctypes.c_double * 4)()
+    _check(load().ws_measure_peaks2(ctx.handle, pk), "ws_measure_peaks2")
+    return {"int_ops_per_s": pk[0], "l2_red_per_s": pk[1], "l2_red64_run_per_s": pk[2]}
 
 
 def ws_create(device: int = 0, arena_bytes: int = 4 << 30) -> Context:

@@ -1364,7 +1364,7 @@ __device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t n, u
   cp_async_wait<0>();
 }
 
-constexpr int kCountMaxPages = kCountMaxWords / kPageWords;
+constexpr int kCountMaxPages = kPagedChunkWords / kPageWords;
 
 __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
@@ -1388,7 +1388,8 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
     const DField &F = a.fld[cf];
     const int cfg = F.cfg;
     // the field's items: chunks of its block bitmaps' words, then of its wave bitmaps'
-    const int64_t cw = a.chunk_words;
+    const bool paged = F.pg >= 0;
+    const int64_t cw = paged ? kPagedChunkWords : a.chunk_words;
     const int64_t kb = (F.words[0] + cw - 1) / cw;
     const int64_t k = item - F.citem_begin;
     const bool blk = k < kb;
@@ -1397,7 +1398,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
     const int NB = blk ? 2 : 4;
     const int b0 = blk ? BM_BL : BM_W;   // BL, BS | W, Y, Z, WS are consecutive bitmap indices
     // page flags of the chunk (row-walk fields): copied to shared memory, then cleared
-    const bool paged = F.pg >= 0;
     const int64_t pg0 = c0 / kPageWords;
     const int npg = (int)((c1 - c0 + kPageWords - 1) / kPageWords);
     uint8_t *const fl = paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) : nullptr;

@@ -44,10 +44,36 @@ __global__ void l2_red_kernel(uint32_t *buf, uint32_t words_mask, int iters) {
   }
 }
 
+// The row walk's pattern: every lane sets a run of kRun consecutive 64-bit units (one
+// sector range) at its own place, 64-bit red.or per unit; lanes of a warp are far apart.
+constexpr int kRun = 3;
+__global__ void l2_red64_runs_kernel(unsigned long long *buf, uint32_t units_mask, int iters) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t idx = tid * 2654435761u;
+  for (int i = 0; i < iters; ++i) {
+    const uint32_t u0 = idx & units_mask & ~7u;
+#pragma unroll
+    for (int r = 0; r < kRun; ++r) atomicOr(buf + u0 + r, 1ull << ((i + r) & 63));
+    idx += 0x9e3779b9u;
+  }
+}
+
 }  // namespace
 
 extern "C" int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_red_per_s) {
-  if (!ctx || !int_ops_per_s || !l2_red_per_s) return WS_EINVAL;
+  ws_peaks pk;
+  const int rc = ws_measure_peaks2(ctx, &pk);
+  if (rc == WS_OK) {
+    if (int_ops_per_s) *int_ops_per_s = pk.int_ops_per_s;
+    if (l2_red_per_s) *l2_red_per_s = pk.l2_red_per_s;
+  }
+  return rc;
+}
+
+extern "C" int ws_measure_peaks2(ws_ctx *ctx, ws_peaks *pk) {
+  if (!ctx || !pk) return WS_EINVAL;
+  memset(pk, 0, sizeof(*pk));
+  double *int_ops_per_s = &pk->int_ops_per_s, *l2_red_per_s = &pk->l2_red_per_s;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return WS_ECUDA;
   const size_t red_words = (size_t)16 << 20;  // 64 MiB: inside L2
   int64_t o_out = ctx->arena->alloc(256), o_buf = ctx->arena->alloc(red_words * 4);
@@ -63,8 +89,8 @@ extern "C" int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_r
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int blocks = ctx->sm_count * 8, threads = 256;
-  float best_int = 1e30f, best_red = 1e30f;
-  const int int_iters = 4096, red_iters = 256;
+  float best_int = 1e30f, best_red = 1e30f, best_run = 1e30f;
+  const int int_iters = 4096, red_iters = 256, run_iters = 128;
   cudaMemsetAsync(buf, 0, red_words * 4, st);
   for (int r = 0; r < 4; ++r) {
     float ms = 0;
@@ -80,6 +106,14 @@ extern "C" int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_r
     cudaEventSynchronize(e1);
     cudaEventElapsedTime(&ms, e0, e1);
     if (r > 0) best_red = ms < best_red ? ms : best_red;
+    cudaEventRecord(e0, st);
+    // units u0 .. u0 + kRun - 1 with u0 a multiple of 8 below red_words / 2 - 8: inside the buffer
+    l2_red64_runs_kernel<<<blocks, threads, 0, st>>>((unsigned long long *)buf, (uint32_t)(red_words / 2 - 8),
+                                                      run_iters);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best_run = ms < best_run ? ms : best_run;
   }
   cudaError_t e = cudaGetLastError();
   cudaEventDestroy(e0);
@@ -93,5 +127,6 @@ extern "C" int ws_measure_peaks(ws_ctx *ctx, double *int_ops_per_s, double *l2_r
   const double n_threads = (double)blocks * threads;
   *int_ops_per_s = n_threads * int_iters * (double)(kChains * kUnroll + kChains) / (best_int * 1e-3);
   *l2_red_per_s = n_threads * red_iters / (best_red * 1e-3);
+  pk->l2_red64_run_per_s = n_threads * run_iters * kRun / (best_run * 1e-3);
   return WS_OK;
 }

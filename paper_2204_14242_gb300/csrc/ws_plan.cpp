@@ -1006,7 +1006,7 @@ static void default_tuning(ws_tuning &t) {
   if (t.chunk_warps <= 0) t.chunk_warps = 4096;
   if (t.pass_mb == 0) t.pass_mb = -1;
   if (t.enum_threads <= 0) t.enum_threads = 256;
-  if (t.count_words <= 0) t.count_words = 65536;   // 256 KiB of words (256 pages) per counting item
+  if (t.count_words <= 0) t.count_words = 16384;   // 64 KiB of words per counting item (fields without page flags)
   t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
   t.count_words = std::min(kCountMaxWords, std::max(kPageWords, t.count_words / kPageWords * kPageWords));
   t.chunk_warps = std::max(1, t.chunk_warps);
@@ -1088,8 +1088,10 @@ void ws_plan::layout() {
       f.item_begin = items;
       f.citem_begin = citems;
       // counting items: chunks of the block bitmaps' words, then of the wave bitmaps' words
-      // (each chunk a whole number of pages of one part)
-      citems += ceil_div(f.words[0], tune.count_words) + ceil_div(f.words[1], tune.count_words);
+      // (each chunk a whole number of pages of one part; larger chunks when only flagged
+      // pages are read)
+      const int64_t cw = f.pg >= 0 ? kPagedChunkWords : tune.count_words;
+      citems += ceil_div(f.words[0], cw) + ceil_div(f.words[1], cw);
     }
     // enumeration items: the representative block (exact path) in chunks of (modelled
     // warp, instruction) pairs; then chunks of the remaining modelled warps, or, for the

@@ -52,6 +52,7 @@ def test_struct_layouts_match_the_header():
     assert int(sizes["ws_profile"]) == B.PROFILE.itemsize
     assert int(sizes["ws_plan_summary"]) == B.PLAN_SUMMARY.itemsize
     assert int(sizes["ws_server_stats"]) == B.SERVER_STATS.itemsize
+    assert int(sizes["ws_peaks"]) == 4 * 8
 
 
 def test_host_constants_and_rank_key():
