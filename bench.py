@@ -1,25 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 estimator (one JSON line on stdout, rank 0).
 
-Default workload: the 3D 25-point star (radius 4) sweep, fp64, 640x512x512 with
-x = 640 contiguous, 151 block shapes x 5 folding variants = 755 candidates.  One
-step estimates every candidate (block and wave enumeration, bitmap counting, model,
-ranking) with the batched form: one persistent enumeration launch per scratch pass,
-replayed as a CUDA graph, descriptors already resident on the device.  Reported:
-  value      candidates/s of that step (device time, CUDA events, L2 flushed between
-             steps), summed over ranks (weak scaling: every rank runs the full sweep)
-  e2e        the same metric through ws_estimate_batch with host buffers (descriptor
-             compile, host->device copies, kernels, device->host results) per step
-  plain      candidates/s of the plain form (one synchronous launch sequence per candidate)
-  served     the Poisson request stream through the continuous-batching server (p50/p99)
-  roofline   the kernel with the largest share of the step, against the rate that bounds
-             it (all three under roofline.kernels): the representative-block kernel
-             (exact per-address path) against the measured int32-add rate, the row walk
-             against the measured L2 red.or rate, the counting kernel against the
-             measured HBM copy bandwidth (MEASURED_PEAKS.json); traffic = the DRAM bytes
-             per launch ncu measured for that kernel on this workload, read from
-             profiles/dram_traffic_<workload>.txt while the kernel source is unchanged
-  cpu_baseline  the CPU oracle on a bounded sample of the same sweep, all host cores
+Headline workload: the batched mixed set, 20,000 seeded candidates (star or box stencils
+of radius 1-4 with 5-125 offsets, 1-27 fp32 or fp64 arrays, domains 64..1024 per axis,
+random block shapes and foldings), the largest configuration that runs on one GPU.  One
+step estimates every candidate (representative-block enumeration, row walk, counting,
+model, ranking) in the batched form: descriptors resident on the device, the step's
+launches replayed as one CUDA graph.  Reported:
+  value       candidates/s of that step (device time, CUDA events, L2 flushed between steps),
+              summed over ranks (weak scaling: every rank runs the whole set)
+  e2e         the same metric through ws_estimate_batch with host buffers in and out
+  plain       the same candidates as one synchronous launch sequence per candidate
+  roofline    the kernel with the largest share of the step against the rate that bounds
+              it; every kernel under roofline.kernels:
+                enum_kernel   representative block, exact per address: addresses / s vs the
+                              measured int32-add rate (ALU)
+                rows_kernel   row walk: 64-bit red.or / s vs the measured rate of the same
+                              pattern (runs of adjacent 64-bit words, L2 atomics)
+                count_kernel  bitmap bytes read / s (only the pages the row walk flagged) vs
+                              the measured HBM copy bandwidth (MEASURED_PEAKS.json)
+  workloads   the 25-point sweep (755 candidates) and the LBM sweep (755 candidates) with
+              their own batched, end-to-end and plain numbers and rooflines
+  served      a Poisson request stream through the continuous-batching server: first its
+              capacity (the whole stream submitted at once), then 200 requests/s, then the
+              rate that offers 70 % of the measured capacity; p50 / p99 latency, utilisation
+  cpu_baseline  the CPU oracle on a bounded sample of the headline set, all host cores
 
 --impl reference times the CPU oracle itself on bounded samples of the same workload.
 """
@@ -45,14 +50,17 @@ UNIT = "configs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # default: 1000 timed steps on the GPU (about 0.7 s, so the clock sampler sees the timed
-    # region several times); 3 for the reference arm, whose steps take seconds each
+    # default: 30 timed steps of the headline set on the GPU (about 1.5 s); 3 for the
+    # reference arm, whose steps take seconds each
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stencil_25pt", choices=["stencil_25pt", "lbm", "mixed", "stencil_7pt"])
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "stencil_25pt", "lbm", "stencil_7pt"])
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests per served run (0 = no serving)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the 25-point and LBM sub-records")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--arena-gb", type=float, default=48.0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -62,19 +70,21 @@ def parse():
     return ap.parse_args()
 
 
+WORKLOADS = {
+    "mixed": ("20,000 seeded mixed stencils (seed 20221): star or box, radius 1-4, 5-125 offsets, 1-27 fp32/fp64 "
+              "arrays, domains 64..1024 per axis, random block shapes and foldings"),
+    "stencil_25pt": ("3D 25-point star r=4 sweep, fp64, 640x512x512 (x=640 contiguous), 151 block shapes x "
+                     "{none,2y,4y,2z,4z} folding = 755 candidates"),
+    "lbm": "LBM-shaped: 27 D3Q27 + 15 D3Q15 fp64 arrays, 256^3, 755 candidates",
+    "stencil_7pt": "3D 7-point star 128^3 block 32x4x1 wave 8",
+}
+
+
 def workload(name):
     from paper_2204_14242_gb300 import workloads as W
-    if name == "stencil_25pt":
-        return W.stencil_25pt_sweep(), {"workload": "3D 25-point star r=4 sweep, fp64, 640x512x512 (x=640 contiguous), "
-                                                   "151 block shapes x {none,2y,4y,2z,4z} folding = 755 candidates",
-                                        "candidates": 755, "modelled_gpu": "A100-SXM4-40G (Table 1)"}
-    if name == "lbm":
-        return W.lbm_sweep(), {"workload": "LBM-shaped: 27 D3Q27 + 15 D3Q15 fp64 arrays, 256^3, 755 candidates",
-                               "candidates": 755, "modelled_gpu": "A100-SXM4-40G (Table 1)"}
-    if name == "mixed":
-        return W.mixed_set(), {"workload": "20000 seeded mixed stencils (seed 20221)", "candidates": 20000,
-                               "modelled_gpu": "A100-SXM4-40G (Table 1)"}
-    return [W.stencil_7pt_128()], {"workload": "3D 7-point star 128^3 block 32x4x1 wave 8", "candidates": 1}
+    cfgs = {"mixed": W.mixed_set, "stencil_25pt": W.stencil_25pt_sweep, "lbm": W.lbm_sweep,
+            "stencil_7pt": lambda: [W.stencil_7pt_128()]}[name]()
+    return cfgs, {"workload": WORKLOADS[name], "candidates": len(cfgs), "modelled_gpu": "A100-SXM4-40G (Table 1)"}
 
 
 def cores():
@@ -102,15 +112,16 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device):
+    def __init__(self, device, period_ms=50):
         self.device = device
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
@@ -130,24 +141,28 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.reader.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            p = [x.strip() for x in l.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, p[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines):
+    """Median SM clock, its maximum and the throttle reasons seen, from nvidia-smi CSV lines."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for l in lines:
+        p = [x.strip() for x in l.split(",")]
+        if len(p) < 9:
+            continue
+        try:
+            sm.append(float(p[1]))
+            mx.append(float(p[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, p[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---- reference arm: the CPU oracle --------------------------------------------------------
@@ -164,6 +179,7 @@ def run_reference(args):
     stride = max(1, len(cfgs) // (per_step * max(1, args.steps + args.warmup)))
     pool = cfgs[::stride]
     k = 0
+
     def step():
         nonlocal k
         batch = [pool[(k + i) % len(pool)] for i in range(per_step)]
@@ -176,7 +192,7 @@ def run_reference(args):
     times = [step() for _ in range(args.steps)]
     sec = sum(times) / len(times)
     value = per_step / sec
-    sample = f"{per_step} candidates per step, every {stride}-th of the {len(cfgs)}-candidate sweep, rotating"
+    sample = f"{per_step} candidates per step, every {stride}-th of the {len(cfgs)}-candidate set, rotating"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
@@ -251,8 +267,10 @@ def kernel_rooflines(profs, peaks, workload_key=None):
     enum_kernel  representative block, exact per-address path: addresses evaluated
                  (valid threads x issued accesses of the block) / s vs int32 adds / s
     rows_kernel  row walk: 64-bit red.or inserts (one per bitmap unit a sector range
-                 covers) / s vs the measured L2 red.or rate on distinct words
-    count_kernel bitmap bytes read / s vs the measured HBM copy bandwidth
+                 covers) / s vs the measured rate of that pattern (runs of adjacent 64-bit
+                 words at far-apart places), and the 32-bit random-word rate for context
+    count_kernel bitmap bytes read (the pages the row walk flagged; every word of fields
+                 the other walks fill) / s vs the measured HBM copy bandwidth
     """
     med = lambda k: statistics.median(p[k] for p in profs)
     last = profs[-1]
@@ -264,36 +282,101 @@ def kernel_rooflines(profs, peaks, workload_key=None):
     k["enum_kernel"] = {"bound": "alu", "achieved": a / 1e9, "peak": peaks["int_ops_per_s"] / 1e9,
                         "unit": "G addresses/s vs G int32-add/s (measured)", "frac": a / peaks["int_ops_per_s"],
                         "per_launch": block_addresses, "ms": ms["enum_kernel"]}
+    run_peak = peaks.get("l2_red64_run_per_s") or peaks["l2_red_per_s"]
     r = last["row_reds"] / (ms["rows_kernel"] * 1e-3) if ms["rows_kernel"] > 0 else 0.0
-    k["rows_kernel"] = {"bound": "l2_atomic", "achieved": r / 1e9, "peak": peaks["l2_red_per_s"] / 1e9,
-                        "unit": "G red.or/s (measured)", "frac": r / peaks["l2_red_per_s"],
+    k["rows_kernel"] = {"bound": "l2_atomic", "achieved": r / 1e9, "peak": run_peak / 1e9,
+                        "unit": "G 64-bit red.or/s vs the same run pattern (measured)", "frac": r / run_peak,
+                        "peak_random_32bit": peaks["l2_red_per_s"] / 1e9,
                         "per_launch": int(last["row_reds"]), "ms": ms["rows_kernel"]}
-    b = last["bitmap_bytes"] / (ms["count_kernel"] * 1e-3) if ms["count_kernel"] > 0 else 0.0
+    cb = int(last.get("count_bytes") or 0)
+    b = cb / (ms["count_kernel"] * 1e-3) if ms["count_kernel"] > 0 else 0.0
     k["count_kernel"] = {"bound": "hbm", "achieved": b / 1e9, "peak": hbm, "unit": f"GB/s ({hbm_src})",
-                         "frac": b / 1e9 / hbm, "per_launch": int(last["bitmap_bytes"]), "ms": ms["count_kernel"]}
+                         "frac": b / 1e9 / hbm, "per_launch": cb, "bitmap_bytes": int(last["bitmap_bytes"]),
+                         "ms": ms["count_kernel"]}
     top = max(ms, key=ms.get)
     traffic = recorded_traffic(workload_key) if workload_key else {}
     for name in k:
         k[name]["traffic"] = traffic.get(name)
     out = dict(k[top])
-    out.update({"kernel": top, "share": ms[top] / last["ms_total"], "kernels": k,
-                "ms_model": med("ms_model"), "ms_rank": med("ms_rank"), "ms_step_profiled": med("ms_total")})
+    out.update({"kernel": top, "share": ms[top] / med("ms_total"), "kernels": k,
+                "ms_model": med("ms_model"), "ms_rank": med("ms_rank"), "ms_step_profiled": med("ms_total"),
+                "passes": int(last["passes"])})
     return out
 
 
-def serve(B, W, ctx, hw, seconds, seed=20222, rate_hz=200.0):
-    """Poisson request stream through the server; latency from arrival to completed poll."""
-    n_req = max(1, int(seconds * rate_hz))
-    reqs = W.request_stream(n_requests=n_req, seed=seed, rate_hz=rate_hz)
-    arrays = [B.marshal(r.configs) for r in reqs]
-    srv = B.Server(ctx, hw, mem_budget=int(24 << 30), max_inflight=4, max_step_cfgs=4096)
-    try:
-        return _serve(B, srv, reqs, arrays, rate_hz)
-    finally:
-        srv.close()
+def unique_sectors(res):
+    return int(res["blk_load_sectors"].sum() + res["blk_store_sectors"].sum() + res["wave_load_sectors"].sum()
+               + res["wave_store_sectors"].sum())
 
 
-def _serve(B, srv, reqs, arrays, rate_hz):
+# ---- one workload: batched steps, per-kernel profile, plain form, end to end ---------------
+def measure(B, torch, ctx, cfgs, hw, stream, flush, args, steps, plain=True, autotune=True, dist=None,
+            device=None, clocks=None):
+    """Times `steps` batched steps of `cfgs` (L2 flushed between steps, CUDA events on the
+    launch stream), profiles the kernels, runs the plain form and the end-to-end call."""
+    arrays = B.marshal(cfgs)
+    plan = B.Plan(ctx, arrays=arrays, hw=hw)
+    plan.profile(stream)              # first direct step: also warms up the kernels
+    tuning = plan.autotune(stream) if autotune else None
+    for _ in range(max(args.warmup, 3)):
+        with torch.cuda.stream(stream):
+            flush.random_(0, 255)
+        plan.execute(B.WS_MODE_BATCHED, stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t_wall = time.perf_counter()
+    for s, e in evs:
+        with torch.cuda.stream(stream):
+            flush.random_(0, 255)          # L2 flush outside the timed events
+        s.record(stream)
+        plan.execute(B.WS_MODE_BATCHED, stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    ms = [s.elapsed_time(e) for s, e in evs]
+    ms_step = step_time_over_ranks(sum(ms) / len(ms), dist, device)
+    res, order = plan.results(stream)
+    profs = [plan.profile(stream) for _ in range(3)]
+    out = {"ms_per_step": ms_step, "res": res, "order": order, "profs": profs, "tuning": tuning, "clocks": clk,
+           "timed_wall_s": t_wall, "launches_per_step": profs[-1]["launches"]}
+    if plain:
+        t = time.perf_counter()
+        plan.execute(B.WS_MODE_PLAIN, stream)
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t
+        rp, op = plan.results(stream)
+        out["plain"] = {"value": len(cfgs) / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
+                        "identical_to_batched": rp.tobytes() == res.tobytes() and op.tobytes() == order.tobytes()}
+    h2d = profs[-1]["upload_bytes"]
+    plan.close()
+    # end to end: host buffers in, host results out, every step
+    e2e_steps = 3
+    B.ws_estimate_batch(ctx, hw=hw, mode=B.WS_MODE_BATCHED, stream=stream, arrays=arrays)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        r2, o2 = B.ws_estimate_batch(ctx, hw=hw, mode=B.WS_MODE_BATCHED, stream=stream, arrays=arrays)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if r2.tobytes() != res.tobytes() or o2.tobytes() != order.tobytes():
+        raise SystemExit("e2e results differ from the resident plan's")
+    out["e2e"] = {"value": len(cfgs) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(len(cfgs) * (B.RESULT.itemsize + 4)), "ms_per_step": e2e_s * 1e3}
+    return out
+
+
+# ---- serving --------------------------------------------------------------------------------
+def serve_stream(B, srv, reqs, arrays, times):
+    """Submits request i at time times[i] (seconds from the start; all 0 = at once) and polls
+    until every request is back; latency = completed poll minus scheduled arrival."""
     lat = {}
     done = threading.Event()
     submitted = {}
@@ -318,34 +401,85 @@ def _serve(B, srv, reqs, arrays, rate_hz):
     th = threading.Thread(target=poller, daemon=True)
     th.start()
     t0 = time.perf_counter()
-    for r, arr in zip(reqs, arrays):
-        target = t0 + r.arrival_s
+    for t_rel, arr in zip(times, arrays):
+        target = t0 + t_rel
         while True:
             d = target - time.perf_counter()
             if d <= 0:
                 break
             time.sleep(min(d, 0.001))
-        rid = srv.submit(arrays=arr)
+        while True:
+            try:
+                rid = srv.submit(arrays=arr)
+                break
+            except B.WsError as e:          # queue full: retry shortly (counts in the latency)
+                if e.code != B.WS_EAGAIN:
+                    raise
+                time.sleep(0.0005)
         with lock:
             submitted[rid] = target
     done.set()
     th.join()
     t1 = time.perf_counter()
-    stats = srv.stats()
     ls = sorted(v[0] for v in lat.values())
     ok = sum(1 for v in lat.values() if v[1] == 0)
     cfg_done = sum(v[2] for v in lat.values())
     q = lambda p: ls[min(len(ls) - 1, int(math.ceil(p * len(ls))) - 1)] * 1e3
-    offered = sum(len(r.configs) for r in reqs) / max(reqs[-1].arrival_s, 1e-9)
-    return {"requests": len(reqs), "ok": ok, "p50_ms": q(0.50), "p99_ms": q(0.99), "configs_per_s": cfg_done / (t1 - t0),
-            "offered_configs_per_s": offered, "steps": stats["steps"], "peak_scratch_bytes": stats["peak_bytes"],
-            "rate_hz": rate_hz, "seconds": t1 - t0}
+    return {"requests": len(arrays), "ok": ok, "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "configs_per_s": cfg_done / (t1 - t0), "seconds": t1 - t0, "configs": cfg_done}
+
+
+def serving(B, W, ctx, hw, n_req, rate_hz, seed=20222):
+    """Capacity first (every request submitted at once), then the stream at `rate_hz` and at
+    the rate that offers 70 % of the measured capacity; utilisation = offered / capacity."""
+    reqs = W.request_stream(n_requests=n_req, seed=seed, rate_hz=rate_hz)
+    arrays = [B.marshal(r.configs) for r in reqs]
+    n_cfg = sum(len(r.configs) for r in reqs)
+    mean_k = n_cfg / len(reqs)
+    out = {"stream": f"{len(reqs)} requests (seed {seed}), {n_cfg} candidates, mean {mean_k:.1f} per request, "
+                     "each a mixed-style stencil with 16-512 (shape, folding) candidates"}
+    srv = B.Server(ctx, hw, mem_budget=int(24 << 30), max_inflight=8, max_step_cfgs=4096, max_queue=1 << 16)
+    try:
+        cap = serve_stream(B, srv, reqs, arrays, [0.0] * len(reqs))
+        capacity = cap["configs_per_s"]
+        out["capacity"] = dict(cap, note="whole stream submitted at once: served candidates/s at saturation")
+        runs = [("at_200_req_s", rate_hz, [r.arrival_s for r in reqs])]
+        rho_rate = 0.7 * capacity / mean_k
+        scale = rate_hz / rho_rate
+        runs.append(("at_70pct_capacity", rho_rate, [r.arrival_s * scale for r in reqs]))
+        for name, rate, times in runs:
+            r = serve_stream(B, srv, reqs, arrays, times)
+            offered = n_cfg / max(times[-1], 1e-9)
+            r.update({"rate_hz": rate, "offered_configs_per_s": offered, "utilisation": offered / capacity})
+            out[name] = r
+        out["stats"] = srv.stats()
+    finally:
+        srv.close()
+    return out
+
+
+def record(B, meas, n_cfg, world, profs_key=None, peaks=None):
+    res = meas["res"]
+    ms = meas["ms_per_step"]
+    rec = {"value": job_throughput(n_cfg, world, ms), "unit": UNIT, "ms_per_step": ms,
+           "unique_sectors_per_s": world * unique_sectors(res) / (ms * 1e-3), "e2e": meas["e2e"],
+           "roofline": kernel_rooflines(meas["profs"], peaks, profs_key)}
+    pr = meas["profs"][-1]
+    if pr.get("count_bytes"):
+        # bitmap bits the counting read per unique sector (and y / z line bits) it counted
+        yz = int(res["y_lines"].sum() + res["z_lines"].sum()) * 4
+        rec["count_bits_per_set_sector"] = 8.0 * pr["count_bytes"] / max(1, unique_sectors(res) + yz)
+        rec["bitmap_bits_per_set_sector"] = 8.0 * pr["bitmap_bytes"] / max(1, unique_sectors(res) + yz)
+    if "plain" in meas:
+        rec["plain"] = meas["plain"]
+        rec["batched_over_plain"] = rec["value"] / world / meas["plain"]["value"]
+    return rec
 
 
 def main():
     args = parse()
     if args.steps is None:
-        args.steps = 3 if args.impl == "reference" else 1000
+        args.steps = 3 if args.impl == "reference" else 30
     if args.impl == "reference":
         run_reference(args)
         return
@@ -369,102 +503,56 @@ def main():
         cfg_meta = dict(cfg_meta, candidates=len(cfgs), subset=f"every {args.subset}-th candidate")
     hw = W.a100()
     ctx = B.Context(local, int(args.arena_gb * (1 << 30)))
-    peaks = B.ws_measure_peaks(ctx)    # before the plan takes the arena
+    peaks = B.ws_measure_peaks(ctx)    # before the plans take the arena
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
-    arrays = B.marshal(cfgs)
-    plan = B.Plan(ctx, arrays=arrays, hw=hw)
-    prof0 = plan.profile(stream)   # first direct step: also warms up the kernels
-    tuning = plan.autotune(stream) if args.autotune else None
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    for _ in range(max(args.warmup, 3)):
-        with torch.cuda.stream(stream):
-            flush.random_(0, 255)
-        plan.execute(B.WS_MODE_BATCHED, stream)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
     clocks = Clocks(local)
-    clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for s, e in evs:
-        with torch.cuda.stream(stream):
-            flush.random_(0, 255)          # L2 flush outside the timed events
-        s.record(stream)
-        plan.execute(B.WS_MODE_BATCHED, stream)
-        e.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = [s.elapsed_time(e) for s, e in evs]
-    ms_step = step_time_over_ranks(sum(ms) / len(ms), dist, f"cuda:{local}")
-    res, order = plan.results(stream)
-    value = job_throughput(len(cfgs), world, ms_step)
-    unique_sectors = int(res["blk_load_sectors"].sum() + res["blk_store_sectors"].sum() + res["wave_load_sectors"].sum()
-                         + res["wave_store_sectors"].sum())
-    sectors_per_s = world * unique_sectors / (ms_step * 1e-3)
+    head = measure(B, torch, ctx, cfgs, hw, stream, flush, args, args.steps,
+                   plain=not args.no_plain and rank == 0, autotune=args.autotune, dist=dist,
+                   device=f"cuda:{local}", clocks=clocks)
+    headline = record(B, head, len(cfgs), world, args.workload if args.subset == 1 else None, peaks)
 
-    # per-kernel rooflines: CUDA events around each kernel on its own launch stream
-    profs = [plan.profile(stream) for _ in range(3)]
-    roofline = kernel_rooflines(profs, peaks, args.workload if args.subset == 1 else None)
-    launches_per_step = profs[-1]["launches"]
+    subs = {}
+    if not args.no_sub and rank == 0 and args.subset == 1:
+        for name in ("stencil_25pt", "lbm"):
+            if name == args.workload:
+                continue
+            c2, meta2 = workload(name)
+            m = measure(B, torch, ctx, c2, hw, stream, flush, args, max(10, args.steps),
+                        plain=not args.no_plain, autotune=args.autotune)
+            subs[name] = dict(record(B, m, len(c2), 1, name, peaks), config=dict(meta2, tuning=m["tuning"]))
 
-    extra = {}
-    if not args.no_plain and rank == 0 and len(cfgs) <= 4096:
-        t = time.perf_counter()
-        plan.execute(B.WS_MODE_PLAIN, stream)
-        torch.cuda.synchronize()
-        plain_s = time.perf_counter() - t
-        rp, op = plan.results(stream)
-        extra["plain"] = {"value": len(cfgs) / plain_s, "unit": UNIT, "ms_per_step": plain_s * 1e3,
-                          "identical_to_batched": rp.tobytes() == res.tobytes()}
-        extra["batched_over_plain"] = value / world / extra["plain"]["value"]
-    # the resident plan is released first: the server and each one-shot call then have
-    # the arena to themselves
-    plan.close()
-    if args.serve_seconds > 0 and rank == 0:
-        extra["served"] = serve(B, W, ctx, hw, args.serve_seconds)
-        sv = extra["served"]
-        if sv["offered_configs_per_s"] > sv["configs_per_s"]:
-            # over capacity at the specified rate: also serve at ~70 % of the measured capacity
-            mean_k = sv["offered_configs_per_s"] / 200.0
-            rate = max(1.0, 0.7 * sv["configs_per_s"] / mean_k)
-            extra["served_at_70pct_capacity"] = serve(B, W, ctx, hw, args.serve_seconds, rate_hz=rate)
-
-    # e2e: host buffers in, host results out, every step
-    e2e_steps = max(2, min(args.steps, 5))
-    h2d = profs[-1]["upload_bytes"]
-    d2h = len(cfgs) * (B.RESULT.itemsize + 4)
-    B.ws_estimate_batch(ctx, hw=hw, mode=B.WS_MODE_BATCHED, stream=stream, arrays=arrays)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        r2, o2 = B.ws_estimate_batch(ctx, hw=hw, mode=B.WS_MODE_BATCHED, stream=stream, arrays=arrays)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    if r2.tobytes() != res.tobytes() or o2.tobytes() != order.tobytes():
-        raise SystemExit("e2e results differ from the resident plan's")
+    served = None
+    if args.serve_requests > 0 and rank == 0:
+        served = serving(B, W, ctx, hw, args.serve_requests, args.serve_rate)
 
     out = None
     if rank == 0:
         base = cpu_baseline(cfgs, hw, args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+        clk = head["clocks"]
+        if clk:
+            # time x median SM clock of the timed region (cycles per step at that clock)
+            clk["timed_wall_s"] = head["timed_wall_s"]
+            clk["mcycles_per_step"] = head["ms_per_step"] * clk["sm_mhz"] * 1e-3
+        out = {"metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
                "config": dict(cfg_meta, parallelism=f"replicas x{world} (independent candidates, no collective)",
                               l2="flushed between steps (256 MiB write)", mode="batched: persistent + CUDA graph",
-                              tuning=tuning),
-               "unique_sectors_per_s": sectors_per_s,
-               "e2e": {"value": len(cfgs) / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                       "d2h_bytes_per_step": int(d2h)},
-               "roofline": roofline,
-               "gpu_launches": launches_per_step * args.steps,
-               "clocks": clk, "cpu_baseline": base}
-        out.update(extra)
+                              tuning=head["tuning"]),
+               "unique_sectors_per_s": headline["unique_sectors_per_s"],
+               "e2e": headline["e2e"],
+               "roofline": headline["roofline"],
+               "gpu_launches": head["launches_per_step"] * args.steps,
+               "clocks": clk, "cpu_baseline": base, "peaks": peaks}
+        for k in ("plain", "batched_over_plain", "count_bits_per_set_sector", "bitmap_bits_per_set_sector"):
+            if k in headline:
+                out[k] = headline[k]
+        if subs:
+            out["workloads"] = subs
+        if served:
+            out["served"] = served
         print(json.dumps(out))
     ctx.close()
     if dist is not None:

@@ -18,7 +18,8 @@ def test_recorded_traffic_follows_the_kernel_source(monkeypatch, tmp_path):
 
 def test_kernel_rooflines_pick_the_largest_share():
     prof = {"ms_enum": 0.1, "ms_rows": 0.4, "ms_count": 0.2, "ms_model": 0.02, "ms_rank": 0.01, "ms_total": 0.73,
-            "block_addresses": 1_000_000, "row_reds": 40_000_000, "bitmap_bytes": 1_000_000_000}
+            "block_addresses": 1_000_000, "row_reds": 40_000_000, "bitmap_bytes": 4_000_000_000,
+            "count_bytes": 1_000_000_000, "passes": 1}
     peaks = {"int_ops_per_s": 3.0e13, "l2_red_per_s": 2.0e11}
     r = bench.kernel_rooflines([prof, prof, prof], peaks)
     assert r["kernel"] == "rows_kernel"
@@ -32,3 +33,21 @@ def test_kernel_rooflines_pick_the_largest_share():
 def test_job_throughput_counts_all_ranks():
     assert bench.job_throughput(755, 1, 1.0) == 755_000.0
     assert bench.job_throughput(755, 4, 2.0) == 4 * 755 / 2e-3
+
+
+def test_rows_roofline_uses_the_run_pattern_peak_when_measured():
+    prof = {"ms_enum": 0.1, "ms_rows": 0.4, "ms_count": 0.2, "ms_model": 0.02, "ms_rank": 0.01, "ms_total": 0.73,
+            "block_addresses": 1, "row_reds": 40_000_000, "bitmap_bytes": 1, "count_bytes": 1, "passes": 1}
+    peaks = {"int_ops_per_s": 3.0e13, "l2_red_per_s": 2.0e11, "l2_red64_run_per_s": 4.0e11}
+    r = bench.kernel_rooflines([prof], peaks)["kernels"]["rows_kernel"]
+    assert abs(r["frac"] - (40e6 / 0.4e-3) / 4.0e11) < 1e-12 and r["peak_random_32bit"] == 200.0
+
+
+def test_clock_summary():
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage"]
+    c = bench.summarize_clocks(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.summarize_clocks([]) is None
