@@ -309,17 +309,20 @@ int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_fi
  * ws_estimate_batch (host buffers; results and ranking of the whole batch), same
  * kernels launched directly on `stream` (NULL = legacy default stream), but every
  * device buffer comes from one fixed array of WS_NOALLOC_SCRATCH_BYTES inside the
- * library: no cudaMalloc, cudaFree, stream creation or library allocator is called.
- *   - The first call on a device (that device is made current) looks up the array's
- *     device address with cudaGetSymbolAddress; make that first call before any
- *     stream capture.
+ * library, and the call creates no CUDA resource: no cudaMalloc, cudaFree,
+ * cudaHostAlloc, stream or event (ws_resource_counts_get does not move).  Its host
+ * memory is plain heap memory (descriptor compilation and pageable upload arrays).
+ *   - The first call on a device looks up the array's device address there with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.  The
+ *     caller's current device is restored before the call returns.
  *   - A batch whose descriptors plus its largest field's bitmaps plus 8 MiB of
- *     headroom exceed the array returns WS_ENOMEM (ws_last_error says by how much);
- *     larger batches otherwise run in several bitmap passes.
- *   - All calls on a device share the array and each call clears the bitmaps it
- *     uses; calls whose device work overlaps (other host threads, other streams)
- *     race on it and must be serialised by the caller.  Calls from several host
- *     threads are serialised on the host, but not across processes. */
+ *     headroom exceed the array returns WS_ENOMEM (ws_last_error says so) before any
+ *     kernel runs; larger batches otherwise run in several bitmap passes.
+ *   - Every call on a device uses the same array and clears the bitmaps it uses first.
+ *     Two calls whose device work overlapped would race on it, so calls on one device
+ *     are serialised in this process: each holds a per-device lock for its whole
+ *     duration and returns only after its device work has finished.  Work the caller
+ *     enqueues on other streams never touches the array.  Each process has its own. */
 int ws_estimate_batch_noalloc(int device, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out,
                               int32_t *order_out, void *stream);
@@ -346,6 +349,16 @@ typedef struct ws_peaks {
   double reserved;
 } ws_peaks; /* 32 bytes */
 int ws_measure_peaks2(ws_ctx *ctx, ws_peaks *out);
+
+/* CUDA resources this library has created in this process so far, for callers that must
+ * check that a code path creates none (see ws_estimate_batch_noalloc). */
+typedef struct ws_resource_counts {
+  int64_t device_allocs;       /* cudaMalloc (context arenas the library allocates)       */
+  int64_t pinned_host_allocs;  /* cudaHostAlloc (upload staging, server result buffers)   */
+  int64_t streams;             /* cudaStreamCreate* (contexts, server slots)              */
+  int64_t events;              /* cudaEventCreate* (plan readiness, profiling, parts)     */
+} ws_resource_counts; /* 32 bytes */
+int ws_resource_counts_get(ws_resource_counts *out);
 
 /* ---- continuous-batching server ---------------------------------------------------- */
 typedef struct ws_server_opts {

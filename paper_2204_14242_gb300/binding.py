@@ -79,7 +79,7 @@ EXPORTS = ["ws_version", "ws_status_string", "ws_last_error", "ws_hw_a100", "ws_
            "ws_autotune", "ws_plan_destroy", "ws_estimate_batch", "ws_rank", "ws_rank_key", "ws_server_create",
            "ws_server_submit", "ws_server_poll", "ws_server_stats_get", "ws_server_destroy", "ws_describe",
            "ws_describe_fields", "ws_measure_peaks", "ws_estimate_batch_noalloc", "ws_plan_dry_run",
-           "ws_server_pause", "ws_server_cancel", "ws_measure_peaks2"]
+           "ws_server_pause", "ws_server_cancel", "ws_measure_peaks2", "ws_resource_counts_get"]
 
 
 class WsError(RuntimeError):
@@ -136,7 +136,7 @@ def load(build_if_missing: bool = False):
             "ws_estimate_batch_noalloc": ([I, P, I, P, I, P, I, P, P, P, P], I),
             "ws_plan_dry_run": ([P, I, P, I, P, I, P, P, ctypes.c_size_t, P], I),
             "ws_server_pause": ([P, I], I), "ws_server_cancel": ([P, ctypes.c_uint64], I),
-            "ws_measure_peaks2": ([P, P], I),
+            "ws_measure_peaks2": ([P, P], I), "ws_resource_counts_get": ([P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -445,6 +445,13 @@ def ws_estimate_batch_noalloc(device: int = 0, configs=None, hw=None, stream=Non
                                          h.ctypes.data, _ptr(res), _ptr(order), _stream_handle(stream)),
            "ws_estimate_batch_noalloc")
     return res, order
+
+
+def ws_resource_counts() -> dict:
+    """CUDA resources the library has created in this process so far."""
+    c = (ctypes.c_int64 * 4)()
+    _check(load().ws_resource_counts_get(c), "ws_resource_counts_get")
+    return {"device_allocs": c[0], "pinned_host_allocs": c[1], "streams": c[2], "events": c[3]}
 
 
 def ws_rank(ctx: Context, results: np.ndarray, stream=None) -> np.ndarray:

@@ -92,6 +92,20 @@ using PinVec = std::vector<T, PinnedAlloc<T>>;
 void set_error(const std::string &s);
 const char *last_error();
 
+// Resources the library creates (for ws_resource_counts_get): device allocations,
+// page-locked host allocations, streams and events.
+enum ResourceKind { RES_DEVICE_ALLOC, RES_PINNED_ALLOC, RES_STREAM, RES_EVENT, N_RES };
+void count_resource(ResourceKind k);
+
+// While alive on a thread, the page-locked block allocator of that thread never calls
+// cudaHostAlloc: a request the cache cannot serve gets plain (pageable) memory, which is
+// freed, not cached, when released.
+struct NoPinnedScope {
+  NoPinnedScope();
+  ~NoPinnedScope();
+  bool prev;
+};
+
 }  // namespace ws
 
 struct ws_ctx {
@@ -110,6 +124,9 @@ struct ws_ctx {
   int64_t oneshot_off = -1;
   size_t oneshot_bytes = 0;
   bool oneshot_dirty = false;   // not known to be zero (new, or an execution failed)
+  // Plans of this context create no readiness event (their uploads and launches share one
+  // stream; used by the entry point that may create no CUDA resources).
+  bool no_events = false;
 };
 
 struct ws_plan {

@@ -8,9 +8,11 @@
 // every device buffer of one estimation -- compiled descriptors, counters, sector
 // bitmaps, results and ranking -- is carved from the fixed array below, which the CUDA
 // runtime reserves when this library's device code is loaded and keeps until the
-// process exits.  No cudaMalloc, cudaMallocAsync, cudaFree, stream creation or
-// library allocator is called; the only host allocations are the descriptor
-// compiler's temporary host containers.
+// process exits.  The call creates no CUDA resource: no cudaMalloc, cudaMallocAsync,
+// cudaFree, cudaHostAlloc, stream or event (ws_resource_counts_get shows it).  Its host
+// memory is plain heap memory: the descriptor compiler's containers and the pageable
+// arrays the descriptors are uploaded from (page-locked blocks are used only when an
+// earlier plan left one in the library's cache).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -27,16 +29,16 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[WS_NOALLOC_SCRATCH_BYTES];
 
 struct NoallocDevice {
+  std::mutex mu;           // serialises the calls on this device (they share the array)
   bool ready = false;
   ws_ctx ctx;              // wraps the fixed scratch; owns no stream and no allocation
   ws::Arena *arena = nullptr;
 };
 
-std::mutex g_mu;
 NoallocDevice g_dev[64];
 
 // Once per device, with that device current: device address of the scratch array and
-// the SM count.  Returns WS_OK or WS_ECUDA.
+// the SM count.  Returns WS_OK or WS_ECUDA.  Called with the device's lock held.
 int setup(int device) {
   NoallocDevice &d = g_dev[device];
   if (d.ready) return WS_OK;
@@ -57,9 +59,21 @@ int setup(int device) {
   d.ctx.sm_count = sms;
   d.ctx.owns_arena = false;
   d.ctx.arena = d.arena;
+  d.ctx.no_events = true;   // uploads and launches share the caller's stream
   d.ready = true;
   return WS_OK;
 }
+
+// Puts the caller's current device back on every return path.
+struct CurrentDevice {
+  int prev = -1;
+  CurrentDevice() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~CurrentDevice() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
@@ -67,7 +81,9 @@ extern "C" int ws_estimate_batch_noalloc(int device, const ws_config *cfgs, int 
                                          int n_fld, const ws_access *acc, int n_acc, const ws_hw *hw,
                                          ws_result *out, int32_t *order_out, void *stream) {
   if (device < 0 || device >= 64 || !hw || n_cfg < 0 || (n_cfg > 0 && (!cfgs || !out))) return WS_EINVAL;
-  std::lock_guard<std::mutex> g(g_mu);
+  const CurrentDevice keep;
+  NoallocDevice &d = g_dev[device];
+  std::lock_guard<std::mutex> g(d.mu);
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) {
     ws::set_error(std::string("cudaSetDevice: ") + cudaGetErrorString(e));
@@ -75,25 +91,30 @@ extern "C" int ws_estimate_batch_noalloc(int device, const ws_config *cfgs, int 
   }
   int rc = setup(device);
   if (rc != WS_OK) return rc;
-  // size check before any device work: descriptors, the largest field's bitmaps (the
-  // batch runs in as many passes as needed) and the plan's 8 MiB of headroom must fit
-  // the fixed scratch
-  size_t desc = 0, scratch = 0, max_field = 0;
-  ws::plan_requirements(cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, &desc, &scratch, &max_field);
-  if (desc + max_field + ((size_t)8 << 20) > (size_t)WS_NOALLOC_SCRATCH_BYTES) {
-    ws::set_error("request needs " + std::to_string(desc + max_field) + " bytes of device scratch; the no-alloc "
-                  "entry point has a fixed " + std::to_string((size_t)WS_NOALLOC_SCRATCH_BYTES) + " bytes");
-    return WS_ENOMEM;
-  }
-  NoallocDevice &d = g_dev[device];
   d.ctx.stream = (cudaStream_t)stream;          // the caller's stream (NULL = legacy default)
   d.ctx.capture_stream = (cudaStream_t)stream;  // unused: this path launches directly
+  const ws::NoPinnedScope pageable;             // upload arrays from plain host memory
   ws_plan *p = nullptr;
-  // the plan clears its bitmap scratch before use, so leftovers of earlier calls
+  // one compile: the plan takes the descriptors from the array, then its bitmaps (in as
+  // many passes as needed) and clears them before use, so leftovers of earlier calls
   // (including failed ones) never leak into this one
   rc = ws::plan_create_impl(&d.ctx, cfgs, n_cfg, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, 0, &p, nullptr,
                             -1, 0);
+  const std::string too_big = "the batch's descriptors and largest field do not fit the no-alloc entry point's fixed " +
+                              std::to_string((size_t)WS_NOALLOC_SCRATCH_BYTES) + " bytes of device scratch";
+  if (rc == WS_ENOMEM) {
+    ws::set_error(too_big);
+    return rc;
+  }
   if (rc != WS_OK) return rc;
+  // a field whose bitmaps alone exceed what the array has left for scratch: refuse the
+  // batch before any kernel runs
+  for (int i = 0; i < n_cfg; ++i)
+    if (p->up_cfg[(size_t)i].status == WS_ENOMEM) {
+      ws_plan_destroy(p);
+      ws::set_error(too_big);
+      return WS_ENOMEM;
+    }
   rc = p->execute(WS_MODE_DIRECT, (cudaStream_t)stream);
   if (rc == WS_OK) rc = ws_plan_results(p, out, order_out, stream);
   ws_plan_destroy(p);

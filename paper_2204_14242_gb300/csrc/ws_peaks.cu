@@ -88,6 +88,8 @@ extern "C" int ws_measure_peaks2(ws_ctx *ctx, ws_peaks *pk) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  ws::count_resource(ws::RES_EVENT);
+  ws::count_resource(ws::RES_EVENT);
   const int blocks = ctx->sm_count * 8, threads = 256;
   float best_int = 1e30f, best_red = 1e30f, best_run = 1e30f;
   const int int_iters = 4096, red_iters = 256, run_iters = 128;

@@ -157,10 +157,15 @@ void host_block_free(void *p) {
 // above; a cached block serves requests of at least half its size.  cudaHostAlloc is tried
 // once per process: without a usable device the blocks are plain memory.
 namespace {
+struct PinnedBlock {
+  size_t size;
+  bool locked;     // page-locked (cudaHostAlloc)
+  bool cacheable;  // returned to the cache when released (else freed)
+};
 struct PinnedCache {
   std::mutex mu;
   std::multimap<size_t, void *> free_;
-  std::unordered_map<void *, std::pair<size_t, bool>> size_;   // size, page-locked
+  std::unordered_map<void *, PinnedBlock> size_;
   size_t cached = 0;
   int state = 0;   // 0 untried, 1 cudaHostAlloc works, -1 it does not
 };
@@ -168,7 +173,14 @@ PinnedCache &pinned_blocks() {
   static PinnedCache *c = new PinnedCache;
   return *c;
 }
+thread_local bool t_no_pinned = false;
+std::atomic<int64_t> g_resources[N_RES];
 }  // namespace
+
+void count_resource(ResourceKind k) { g_resources[k].fetch_add(1, std::memory_order_relaxed); }
+
+NoPinnedScope::NoPinnedScope() : prev(t_no_pinned) { t_no_pinned = true; }
+NoPinnedScope::~NoPinnedScope() { t_no_pinned = prev; }
 
 void *pinned_block_alloc(size_t bytes) {
   const size_t unit = bytes < ((size_t)2 << 20) ? ((size_t)64 << 10) : ((size_t)2 << 20);
@@ -184,10 +196,11 @@ void *pinned_block_alloc(size_t bytes) {
   }
   void *p = nullptr;
   bool locked = false;
-  if (c.state >= 0) {
+  if (c.state >= 0 && !t_no_pinned) {
     if (cudaHostAlloc(&p, need, cudaHostAllocDefault) == cudaSuccess) {
       c.state = 1;
       locked = true;
+      count_resource(RES_PINNED_ALLOC);
     } else {
       cudaGetLastError();   // not sticky: leave no error behind for later calls
       p = nullptr;
@@ -196,7 +209,7 @@ void *pinned_block_alloc(size_t bytes) {
   }
   if (!p) p = aligned_alloc(4096, need);
   if (!p) throw std::bad_alloc();
-  c.size_[p] = std::make_pair(need, locked);
+  c.size_[p] = PinnedBlock{need, locked, !t_no_pinned};
   return p;
 }
 
@@ -206,11 +219,11 @@ void pinned_block_free(void *p) {
   std::lock_guard<std::mutex> g(c.mu);
   auto it = c.size_.find(p);
   if (it == c.size_.end()) return;
-  if (c.cached + it->second.first <= ((size_t)1 << 30)) {
-    c.free_.emplace(it->second.first, p);
-    c.cached += it->second.first;
+  if (it->second.cacheable && c.cached + it->second.size <= ((size_t)1 << 30)) {
+    c.free_.emplace(it->second.size, p);
+    c.cached += it->second.size;
   } else {
-    if (it->second.second) cudaFreeHost(p);
+    if (it->second.locked) cudaFreeHost(p);
     else free(p);
     c.size_.erase(it);
   }
@@ -1448,7 +1461,8 @@ extern "C" int ws_create(ws_ctx **out, int device, void *arena, size_t arena_byt
   c->l2_bytes = prop.l2CacheSize;
   char *base = (char *)arena;
   if (!base) {
-    if (cudaMalloc((void **)&base, arena_bytes) != cudaSuccess) {
+    if (cudaMalloc((void **)&base, arena_bytes) == cudaSuccess) count_resource(RES_DEVICE_ALLOC);
+    else {
       delete c;
       set_error("cudaMalloc of the arena failed");
       return WS_ENOMEM;
@@ -1464,7 +1478,17 @@ extern "C" int ws_create(ws_ctx **out, int device, void *arena, size_t arena_byt
     delete c;
     return WS_ECUDA;
   }
+  for (int k = 0; k < 3; ++k) count_resource(RES_STREAM);
   *out = c;
+  return WS_OK;
+}
+
+extern "C" int ws_resource_counts_get(ws_resource_counts *out) {
+  if (!out) return WS_EINVAL;
+  out->device_allocs = g_resources[RES_DEVICE_ALLOC].load();
+  out->pinned_host_allocs = g_resources[RES_PINNED_ALLOC].load();
+  out->streams = g_resources[RES_STREAM].load();
+  out->events = g_resources[RES_EVENT].load();
   return WS_OK;
 }
 
@@ -2023,8 +2047,11 @@ int ws::plan_create_impl(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws
   }
   // launches wait for this event (pageable copies are staged when cudaMemcpyAsync returns,
   // so the host arrays may go now)
-  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  if ((e = cudaEventRecord(p->ready, st)) != cudaSuccess) return fail(e);
+  if (!ctx->no_events) {
+    if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    count_resource(RES_EVENT);
+    if ((e = cudaEventRecord(p->ready, st)) != cudaSuccess) return fail(e);
+  }
   p->scratch_bytes = scratch;
   {
     const auto t_end = std::chrono::steady_clock::now();
@@ -2080,7 +2107,10 @@ extern "C" int ws_plan_profile(ws_plan *p, void *stream, ws_profile *out) {
   memset(out, 0, sizeof(*out));
   const int nev = 3 + 3 * (int)p->passes.size();
   std::vector<cudaEvent_t> ev(nev);
-  for (auto &e : ev) CU(cudaEventCreate(&e));
+  for (auto &e : ev) {
+    CU(cudaEventCreate(&e));
+    count_resource(RES_EVENT);
+  }
   int rc = p->wait_ready(st);
   if (rc == WS_OK) rc = p->enqueue(st, &ev, out);
   cudaError_t e = cudaStreamSynchronize(st);
@@ -2157,6 +2187,8 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
+  count_resource(RES_EVENT);
+  count_resource(RES_EVENT);
   int rc = p->wait_ready(st);
   if (rc != WS_OK) {
     cudaEventDestroy(e0);
@@ -2207,7 +2239,7 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
 // stream while part k runs on the caller's stream.  Results are per candidate, so the parts
 // give the same results as one plan; the ranking runs once over all results.  Returns
 // WS_ENOMEM (the caller then runs one plan) when the parts do not fit the arena together or
-// a part's share of it is too small for one of its fields.  Parts of
+// a part's share of it is too small for a field that the whole arena could hold.  Parts of
 // fewer than kPipeMin candidates lose more on the device (launches, tails) than the overlap
 // gains (measured on GB300: 755 candidates in 3 parts 2.0 ms against 1.8 ms in one plan;
 // 20,000 mixed candidates 99 ms against 107 ms).
@@ -2244,6 +2276,7 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
     cudaEvent_t ev;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) break;
+    count_resource(RES_EVENT);
     evs.push_back(ev);
     e = cudaEventRecord(ev, ctx->upload_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
@@ -2276,14 +2309,24 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
     set_error(std::string("pipelined estimate: ") + cudaGetErrorString(e));
     rc = WS_ECUDA;
   }
-  // a part's share of the arena may be too small for a field that one plan could hold:
-  // then the caller runs the batch as one plan instead
+  std::vector<int> short_of_room;   // candidates a part had too little scratch for
   for (int i = 0; rc == WS_OK && i < n_cfg; ++i)
-    if (out[i].status == WS_ENOMEM) rc = WS_ENOMEM;
+    if (out[i].status == WS_ENOMEM) short_of_room.push_back(i);
   for (ws_plan *p : plans) ws_plan_destroy(p);
   for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   for (int64_t o : {o_res, o_keys, o_ord, o_rnk, o_seg})
     if (o >= 0) ar.release(o);
+  // a part's share of the arena may be too small for a field that one plan could hold:
+  // then the caller runs the batch as one plan instead.  A field too large for the whole
+  // arena keeps its WS_ENOMEM (one plan would refuse it as well).
+  if (!short_of_room.empty()) {
+    const size_t room = ar.largest_free();
+    for (int i : short_of_room) {
+      size_t dsc = 0, scr = 0, mf = 0;
+      plan_requirements(cfgs + i, 1, fld, n_fld, acc, n_acc, hw, &dsc, &scr, &mf);
+      if (mf + ((size_t)8 << 20) <= room) return WS_ENOMEM;
+    }
+  }
   return rc;
 }
 

@@ -100,7 +100,9 @@ bool ensure_slot_capacity(Slot &sl, size_t n) {
   sl.h_ord = nullptr;
   size_t c = std::max<size_t>(n, 1024);
   if (cudaHostAlloc((void **)&sl.h_res, c * sizeof(ws_result), cudaHostAllocDefault) != cudaSuccess) return false;
+  ws::count_resource(ws::RES_PINNED_ALLOC);
   if (cudaHostAlloc((void **)&sl.h_ord, c * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) return false;
+  ws::count_resource(ws::RES_PINNED_ALLOC);
   sl.cap = c;
   return true;
 }
@@ -300,8 +302,10 @@ extern "C" int ws_server_create(ws_ctx *ctx, const ws_server_opts *opts, const w
   }
   s->slots.resize(s->opts.max_inflight);
   for (Slot &sl : s->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        !ensure_slot_capacity(sl, (size_t)s->opts.max_step_cfgs)) {
+    const bool made = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (made) ws::count_resource(ws::RES_STREAM);
+    else sl.stream = nullptr;
+    if (!made || !ensure_slot_capacity(sl, (size_t)s->opts.max_step_cfgs)) {
       for (Slot &x : s->slots) {
         if (x.stream) cudaStreamDestroy(x.stream);
         if (x.h_res) cudaFreeHost(x.h_res);

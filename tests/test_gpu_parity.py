@@ -470,3 +470,47 @@ def test_server_results_same_alone_and_in_the_mix(ctx):
         w = want[starts[k]:starts[k + 1]]
         assert_match(res, w, what=f"served request {k}")
         assert_ranking(order, res["t_pred"], [x["t_pred"] for x in w], f"served request {k}")
+
+
+def big_field_candidate(fold):
+    """One field read by the 25-point star and written in place, 1024^3 fp64, blocks of
+    4x1x64 threads folded along z: its bitmaps take tens of MiB (41 MiB folded twice,
+    161 MiB eight times)."""
+    N = (1024, 1024, 1024)
+    f = W.Field(8, [W.Access(*o) for o in W.star_offsets(4)] + [W.Access(0, 0, 0, 1)], strides=W.dense_strides(N))
+    return W.Config(N=N, B=(4, 1, 64), fields=[f], fold_axis=2, fold=fold, flops_per_lup=25.0)
+
+
+def test_pipelined_estimate_falls_back_to_one_plan(ctx):
+    """ws_estimate_batch cuts 4096 or more candidates into parts that share the arena.  A
+    field that fits the whole arena but not a part's share makes the call run the batch as
+    one plan: results and order byte-identical to a resident plan's.  A field too large for
+    the whole arena gets WS_ENOMEM in its own result while the others are estimated."""
+    hw = W.a100()
+    rng = W.SplitMix64(515)
+    small = [random_tiny(rng) for _ in range(4200)]
+    big = big_field_candidate(2)
+    need = B.ws_plan_dry_run([big], hw)["bitmap_bytes"]
+    cfgs = small[:2000] + [big] + small[2000:]
+    with B.Plan(ctx, cfgs, hw) as p:
+        p.execute(B.WS_MODE_BATCHED)
+        ref, ref_order = p.results()
+    assert (ref["status"] == 0).all()
+    # the parts take a third of the free arena each: less than the big field needs
+    arena = int(need * 1.6) + (48 << 20)
+    tight = B.Context(0, arena)
+    try:
+        res, order = B.ws_estimate_batch(tight, cfgs, hw)
+        assert res.tobytes() == ref.tobytes() and order.tobytes() == ref_order.tobytes()
+        # a field larger than this whole arena: its own WS_ENOMEM, the rest as one plan gives
+        huge = big_field_candidate(8)
+        assert B.ws_plan_dry_run([huge], hw)["bitmap_bytes"] > arena
+        cfgs2 = small[:2000] + [huge] + small[2000:]
+        res2, order2 = B.ws_estimate_batch(tight, cfgs2, hw)
+    finally:
+        tight.close()
+    assert res2[2000]["status"] == B.WS_ENOMEM
+    keep = np.ones(len(cfgs2), bool)
+    keep[2000] = False
+    assert res2[keep].tobytes() == ref[keep].tobytes()
+    assert int(order2[-1]) == 2000          # an unestimated candidate ranks last

@@ -4,8 +4,10 @@ Some applications embed the estimator where device memory belongs to someone els
 fixed pool of a serving runtime, a captured steady state that must not allocate); they
 call this entry point, which takes all device scratch from a fixed 32 MiB array inside
 the library.  This file checks it through the C ABI against ws_estimate_batch, twice in
-a row, that the second call leaves the device's free memory untouched, and that an
-oversized batch is refused with WS_ENOMEM.  It is named to be collected last.
+a row; that those calls create no CUDA resource at all (no device or page-locked host
+allocation, stream or event: the library's own resource counters stay put, and so does
+the device's free memory); that the caller's current device is left as it was; and that
+an oversized batch is refused with WS_ENOMEM.  It is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -42,16 +44,21 @@ def test_noalloc_matches_estimate_batch_twice():
     with B.Context(0, 2 << 30) as ctx:
         ref, ref_order = B.ws_estimate_batch(ctx, hw=hw, arrays=arrays)
     assert (ref["status"] == 0).all()
+    torch.cuda.synchronize()
+    counts_before = B.ws_resource_counts()
     res1, order1 = B.ws_estimate_batch_noalloc(0, hw=hw, arrays=arrays)
     torch.cuda.synchronize()
     free_before, _ = torch.cuda.mem_get_info(0)
     res2, order2 = B.ws_estimate_batch_noalloc(0, hw=hw, arrays=arrays)
     torch.cuda.synchronize()
     free_after, _ = torch.cuda.mem_get_info(0)
+    counts_after = B.ws_resource_counts()
     for res, order in ((res1, order1), (res2, order2)):
         same(res, ref)
         assert list(order) == list(ref_order)
     assert free_after == free_before
+    assert counts_after == counts_before, (counts_before, counts_after)
+    assert torch.cuda.current_device() == 0
 
 
 def test_noalloc_on_a_torch_stream_and_oversized_batch():
