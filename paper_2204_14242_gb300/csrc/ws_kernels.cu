@@ -1377,7 +1377,10 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-  if (threadIdx.x == 0) s_item[0] = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
+  if (threadIdx.x == 0) {
+    s_item[0] = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
+    s_npl = 0;
+  }
   __syncthreads();
   for (int par = 0;; par ^= 1) {
     const int64_t item = s_item[par];
@@ -1403,30 +1406,23 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
     uint8_t *const fl = paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) : nullptr;
     uint32_t rd = 0;   // bitmap bytes this thread's share of the item reads
     if (paged) {
-      for (int i = threadIdx.x; i < NB * npg; i += kCountThreads) {
-        const int b = i / npg, j = i - b * npg;
-        uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
-        const uint8_t v = *f;
-        s_fl[b][j] = v;
-        if (v) {
-          *f = 0;
-          if (F.bm[b0 + b] >= 0) rd += 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
+      // a thread per page: its flags into shared memory (cleared in device memory), and the
+      // page into the list when a present bitmap flagged it (list order does not matter)
+      for (int j = threadIdx.x; j < npg; j += kCountThreads) {
+        bool act = false;
+        for (int b = 0; b < NB; ++b) {
+          uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
+          const uint8_t v = *f;
+          s_fl[b][j] = v;
+          if (v) {
+            *f = 0;
+            if (F.bm[b0 + b] >= 0) {
+              act = true;
+              rd += 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
+            }
+          }
         }
-      }
-      __syncthreads();
-      // the pages some bitmap flagged, in order (one warp compacts them)
-      if (warp == 0) {
-        int cnt = 0;
-        for (int j0 = 0; j0 < npg; j0 += 32) {
-          const int j = j0 + (int)lane;
-          bool act = false;
-          if (j < npg)
-            for (int b = 0; b < NB; ++b) act = act || (s_fl[b][j] != 0 && F.bm[b0 + b] >= 0);
-          const uint32_t m = __ballot_sync(FULL, act);
-          if (act) s_pl[cnt + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
-          cnt += __popc(m);
-        }
-        if (lane == 0) s_npl = cnt;
+        if (act) s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
       }
       __syncthreads();
     } else if (threadIdx.x == 0) {
@@ -1492,7 +1488,10 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
       const int dst = threadIdx.x < 12 ? kCountDst[threadIdx.x] : C_CBYTES;
       if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + dst), t);
     }
-    if (threadIdx.x == 0) s_item[par ^ 1] = nxt;
+    if (threadIdx.x == 0) {
+      s_item[par ^ 1] = nxt;
+      s_npl = 0;
+    }
     __syncthreads();
   }
 }
