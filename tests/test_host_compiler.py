@@ -42,8 +42,10 @@ def test_z_set_ends_before_the_y_set_ends():
     """The row walk gives the z set one slot per thread row: outside the last block row the
     y set removes [y_lo, y_hi) from the z blocks of a row, and z_hi <= y_hi (both sets are
     the wave shifted back, the z set by a whole slab), so only the z blocks before y_lo can
-    remain.  Checked on random candidates, the sweeps and wave-size overrides, against the
-    brute-force z set."""
+    remain.  Checked on random candidates, the sweeps and wave-size overrides: the single
+    slot per row, read off the compiler's ranges, must give the y and z block sets that
+    tests/brute_force.py enumerates on its own (wave shifted back by a block row / slab,
+    blocks outside the grid dropped, minus the wave and, for z, minus the y set)."""
     rng = W.SplitMix64(23)
     cases = [(random_tiny(rng), W.Hardware(sms=rng.randint(1, 6), max_blocks_sm=rng.randint(1, 4)))
              for _ in range(300)]
@@ -54,12 +56,14 @@ def test_z_set_ends_before_the_y_set_ends():
         if info["y_hi"] > info["y_lo"] and info["z_hi"] > info["z_lo"]:
             assert info["z_hi"] <= info["y_hi"]
         g = info["grid"]
-        ys = {b for b in range(info["y_lo"], info["y_hi"]) if (b // g[0]) % g[1] != g[1] - 1}
+        grp = brute_force.thread_groups(c, hw)          # independent enumeration of the sets
         last_row = lambda b: (b // g[0]) % g[1] == g[1] - 1
+        ys = [b for b in range(info["y_lo"], info["y_hi"]) if not last_row(b)]
+        assert ys == [int(b) for b in grp["y"]]
         # the single-slot reading: z blocks of other rows lie before y_lo (or the y set is empty)
         single = [b for b in range(info["z_lo"], info["z_hi"])
                   if last_row(b) or info["y_hi"] <= info["y_lo"] or b < info["y_lo"]]
-        assert single == [b for b in range(info["z_lo"], info["z_hi"]) if b not in ys]
+        assert single == [int(b) for b in grp["z"]]
 
 
 def test_bitmaps_contain_every_sector():
