@@ -1125,9 +1125,6 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       const int Mfull = s_ioff[s_g.f_count];
       const DField &F0 = s_fk[0];
       const int64_t es = F0.esize, sxe = es * F0.stride[0];
-      // rows of the layout follow each other in memory (row stride = row length, x ascending)
-      const int64_t rowb = es * F0.stride[1];
-      const bool contig = sxe > 0 && rowb == sxe * (int64_t)s_c.N[0];
       for (int64_t slot = q0 + warp; slot < q1; slot += nwarps) {
         int lv;
         int64_t loc;
@@ -1168,21 +1165,14 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         if (ba >= bb) continue;
         const uint32_t bxa = (uint32_t)(ba - rb0), bxb = (uint32_t)(bb - rb0);
         const uint32_t tz = fdiv(t, s_c.fd_b1), ty = t - tz * (uint32_t)s_c.B[1];
-        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
-        // A block run spanning the whole grid row, in a row-contiguous layout without y
-        // folding: the thread rows ty of one tz are consecutive rows at consecutive addresses,
-        // so the slot with ty = 0 takes all of them as one range per access run.  Exact in
-        // sectors: across the row ends the addresses still step by at most 32 bytes.
-        const bool merge = contig && faxis != 1 && bxa == 0 && bxb == gx;
-        if (merge && ty != 0) continue;
         int32_t y = (int32_t)(by * (uint32_t)s_c.B[1] + ty), z = (int32_t)(bz * (uint32_t)s_c.B[2] + tz);
+        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
         if (faxis == 1) y *= fold;
         if (faxis == 2) z *= fold;
         if (y >= s_c.N[1] || z >= s_c.N[2]) continue;
-        const int32_t nrows = merge ? min(s_c.B[1], s_c.N[1] - y) : 1;   // grid rows of the slot
         const int32_t xa = (int32_t)bxa * s_c.B[0], xb = min((int32_t)bxb * s_c.B[0], s_c.N[0]);
         const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
-        const int64_t nx = (int64_t)(xb - xa) * nrows;
+        const int64_t nx = xb - xa;
         // the block level only fills the block bitmaps: its counts come from enum_kernel
         const bool blk = lv == 3;
         if (lane == 0u && !blk) {
@@ -1191,7 +1181,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         }
         const int64_t el0 = es * (F0.stride[1] * y + F0.stride[2] * z);
         const int64_t ea = el0 + sxe * xa, eb = el0 + sxe * (xb - 1);
-        const int64_t lo = min(ea, eb), hi = max(ea, eb) + (int64_t)(nrows - 1) * rowb;
+        const int64_t lo = min(ea, eb), hi = max(ea, eb);
         const bool fullk = kv == fold;
         const int M = fullk ? Mfull : L;
         const int bsel = lv == 0 ? BM_W : lv == 1 ? BM_Y : lv == 2 ? BM_Z : BM_BL;
@@ -1227,7 +1217,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
                      (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
         }
         if (lv == 0 || blk) {
-          unsigned long long sreq = 0;   // this lane's per-warp store sectors of the slot's rows
+          uint32_t sreq = 0;   // this lane's per-warp store sectors of the row (< 2^27)
           for (int j = L + (int)lane; j < L + S; j += 32) {
             if ((int)s_kmin[j] >= kv) continue;
             const DField &F = s_fk[s_af[j]];
@@ -1247,27 +1237,22 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             flag_pages(reinterpret_cast<uint8_t *>(a.scratch + F.pg) + page_flag_off(sb, F.words[0], F.words[1]),
                        (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
             if (!blk) {
-              // per grid row of the slot: the count depends on the row start only modulo 32
-              // bytes, on its thread row t only through t * B0 modulo 32 (where the row's
-              // first warp ends) and on the block run, so rows that agree on those reuse this
-              // thread's previous count
-              for (int32_t r = 0; r < nrows; ++r) {
-                const int64_t A0 = el0 + (int64_t)r * rowb + bo;
-                const uint32_t tr = t + (uint32_t)r;
-                const unsigned long long key = (unsigned long long)(A0 & 31) |
-                                               ((unsigned long long)((tr * (uint32_t)s_c.B[0]) & 31u) << 5) |
-                                               ((unsigned long long)bxa << 10) | ((unsigned long long)bxb << 37);
-                if (s_memo_key[threadIdx.x] != key) {
-                  s_memo_val[threadIdx.x] =
-                      (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, tr, bxa, bxb);
-                  s_memo_key[threadIdx.x] = key;
-                }
-                sreq += s_memo_val[threadIdx.x];
+              // the count depends on the row start only modulo 32 bytes, on t only through
+              // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
+              // rows that agree on those reuse this thread's previous count
+              const int64_t A0 = el0 + bo;
+              const unsigned long long key = (unsigned long long)(A0 & 31) |
+                                             ((unsigned long long)((t * (uint32_t)s_c.B[0]) & 31u) << 5) |
+                                             ((unsigned long long)bxa << 10) | ((unsigned long long)bxb << 37);
+              if (s_memo_key[threadIdx.x] != key) {
+                s_memo_val[threadIdx.x] =
+                    (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb);
+                s_memo_key[threadIdx.x] = key;
               }
+              sreq += s_memo_val[threadIdx.x];
             }
           }
-#pragma unroll
-          for (int o = 16; o >= 1; o >>= 1) sreq += __shfl_xor_sync(FULL, sreq, o);
+          sreq = __reduce_add_sync(FULL, sreq);
           if (lane == 0u) s_acc[warp][2] += sreq;
         }
       }
