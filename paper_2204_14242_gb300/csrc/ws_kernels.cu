@@ -1304,76 +1304,28 @@ __device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, con
   acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
 }
 
-// Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of
-// words).  Every thread streams its own 16-byte positions of each bitmap through a ring of
-// kCountStages slots in shared memory with cp.async (kCountStages - 1 positions in flight
-// per bitmap, held in shared memory rather than registers), tallies them, and clears in
-// global memory only the non-zero positions, after their values have arrived (the bitmaps
-// are sparse; a zero store right behind the load of its own sector made the L2 hold every
-// such store behind the pending fill).  No thread reads another thread's slots, so the ring
-// needs no barriers: cp.async.wait_group orders each thread's own copies.
-__device__ __forceinline__ void cp_async16(uint32_t sdst, const void *gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sdst), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Streams the item's positions (16-byte units of up to four bitmaps; null = absent, reads
-// as zero) through the calling thread's ring slots: index i = threadIdx.x + k * kCountThreads
-// < n maps to position qof(i) (< 0: none); only positions for which on(b, q) holds are copied
-// (the others read as zero); f(v, q) consumes them.
-template <int NS, class Q, class A, class F>
-__device__ __forceinline__ void count_stream(uint4 *const (&p)[NS], int64_t n, uint32_t ring, Q &&qof, A &&on,
-                                             F &&f) {
-  const int64_t first = threadIdx.x;
-  const int64_t K = first < n ? (n - first + kCountThreads - 1) / kCountThreads : 0;
-  auto slot = [&](int64_t k, int b) -> uint32_t {
-    return ring + (uint32_t)((((int)(k % kCountStages) * NS + b) * kCountThreads + (int)threadIdx.x) * 16);
-  };
-  auto issue = [&](int64_t k) {
-    if (k < K) {
-      const int64_t q = qof(first + k * kCountThreads);
-      if (q >= 0) {
-#pragma unroll
-        for (int b = 0; b < NS; ++b)
-          if (p[b] && on(b, q)) cp_async16(slot(k, b), p[b] + q);
-      }
-    }
-    cp_async_commit();   // one group per step, empty or not, so that the wait count holds
-  };
-#pragma unroll
-  for (int k = 0; k < kCountStages - 1; ++k) issue(k);
-  for (int64_t k = 0; k < K; ++k) {
-    issue(k + kCountStages - 1);
-    cp_async_wait<kCountStages - 1>();   // step k's copies of this thread have landed
-    const int64_t q = qof(first + k * kCountThreads);
-    if (q < 0) continue;
-    uint4 v[NS];
-#pragma unroll
-    for (int b = 0; b < NS; ++b) {
-      v[b] = make_uint4(0u, 0u, 0u, 0u);
-      if (p[b] && on(b, q)) asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-                                         : "=r"(v[b].x), "=r"(v[b].y), "=r"(v[b].z), "=r"(v[b].w)
-                                         : "r"(slot(k, b)) : "memory");
-    }
-    f(v, q);
-  }
-  cp_async_wait<0>();
-}
-
+// Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of the
+// words of its block bitmaps or of its wave bitmaps).  The chunk is cut into pages of
+// kPageWords words; for a field the row walk filled, only the pages it flagged are read
+// (and their flags cleared), otherwise every page.  One warp takes one page at a time:
+// each lane loads two 16-byte positions of every bitmap of the part that has the page
+// flagged (all loads in flight together), tallies sectors, lines and overlaps, and clears
+// the non-zero positions, so the bitmaps are left zeroed for the next step.
 constexpr int kCountMaxPages = kPagedChunkWords / kPageWords;
 
-__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
+__device__ __forceinline__ uint4 ld_v4(const uint4 *p) {
+  uint4 v;
+  asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
   __shared__ uint32_t s_red[kCountThreads / 32][13];
-  __shared__ uint8_t s_fl[4][kCountMaxPages];   // page flags of the item's chunk, per bitmap of its part
-  __shared__ uint16_t s_pl[kCountMaxPages];      // the chunk's pages that some bitmap flagged
+  __shared__ uint32_t s_fl[kCountMaxPages];      // per page: byte b = 1 when bitmap b of the part is read
+  __shared__ uint16_t s_pl[kCountMaxPages];      // the chunk's pages to read (any order)
   __shared__ int s_npl;
-  extern __shared__ __align__(16) unsigned char s_ring[];   // [stage][bitmap][thread] x 16 bytes
-  const uint32_t ring = (uint32_t)__cvta_generic_to_shared(s_ring);
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
@@ -1400,77 +1352,78 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(CountArgs a) {
     const int64_t c1 = min(c0 + cw, blk ? F.words[0] : F.words[1]);
     const int NB = blk ? 2 : 4;
     const int b0 = blk ? BM_BL : BM_W;   // BL, BS | W, Y, Z, WS are consecutive bitmap indices
-    // page flags of the chunk (row-walk fields): copied to shared memory, then cleared
     const int64_t pg0 = c0 / kPageWords;
     const int npg = (int)((c1 - c0 + kPageWords - 1) / kPageWords);
     uint8_t *const fl = paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) : nullptr;
-    uint32_t rd = 0;   // bitmap bytes this thread's share of the item reads
-    if (paged) {
-      // a thread per page: its flags into shared memory (cleared in device memory), and the
-      // page into the list when a present bitmap flagged it (list order does not matter)
-      for (int j = threadIdx.x; j < npg; j += kCountThreads) {
-        bool act = false;
-        for (int b = 0; b < NB; ++b) {
+    uint4 *bp[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      bp[b] = (b < NB && F.bm[b0 + b] >= 0) ? reinterpret_cast<uint4 *>(a.scratch + F.bm[b0 + b]) : nullptr;
+    uint32_t rd = 0;   // bitmap bytes this thread's pages take
+    // a thread per page: which bitmaps to read (flags cleared in device memory as they are
+    // taken); pages with none are dropped
+    for (int j = threadIdx.x; j < npg; j += kCountThreads) {
+      uint32_t m = 0;
+      const uint32_t pbytes = 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b >= NB) continue;
+        bool on = bp[b] != nullptr;
+        if (paged) {
           uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
           const uint8_t v = *f;
-          s_fl[b][j] = v;
-          if (v) {
-            *f = 0;
-            if (F.bm[b0 + b] >= 0) {
-              act = true;
-              rd += 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
-            }
+          if (v) *f = 0;
+          on = on && v != 0;
+        }
+        if (on) {
+          m |= 1u << (8 * b);
+          rd += pbytes;
+        }
+      }
+      s_fl[j] = m;
+      if (m) s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
+    }
+    __syncthreads();
+    uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int npl = s_npl;
+    for (int i = warp; i < npl; i += kCountThreads / 32) {
+      const int j = s_pl[i];
+      const uint32_t m = s_fl[j];
+      const int64_t q0 = (c0 + (int64_t)j * kPageWords) / 4;                    // first position of the page
+      const int np = (int)min((int64_t)(kPageWords / 4), c1 / 4 - q0);          // its positions (<= 64)
+      uint4 v[4][2];
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = (int)lane + 32 * h;
+          v[b][h] = ((m >> (8 * b)) & 1u) && r < np ? ld_v4(bp[b] + q0 + r) : zero;
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t q = q0 + (int)lane + 32 * h;
+        if (blk) {
+          if (nz(v[0][h])) {
+            tally_sectors_lines(acc[0], acc[1], v[0][h]);
+            bp[0][q] = zero;
+          }
+          if (nz(v[1][h])) {
+            tally_sectors_lines(acc[2], acc[3], v[1][h]);
+            bp[1][q] = zero;
+          }
+        } else {
+          if (nz(v[0][h]) | nz(v[1][h]) | nz(v[2][h])) {
+            tally_wave(acc, v[0][h], v[1][h], v[2][h]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              if (nz(v[b][h])) bp[b][q] = zero;
+          }
+          if (nz(v[3][h])) {
+            tally_sectors_lines(acc[10], acc[11], v[3][h]);
+            bp[3][q] = zero;
           }
         }
-        if (act) s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
       }
-      __syncthreads();
-    } else if (threadIdx.x == 0) {
-      for (int b = 0; b < NB; ++b)
-        if (F.bm[b0 + b] >= 0) rd += 4u * (uint32_t)(c1 - c0);
-    }
-    // positions of the item: every position of the chunk, or those of its flagged pages;
-    // position q (16 bytes) of bitmap b is read iff that bitmap flagged its page
-    const int64_t qa = c0 / 4, qb = c1 / 4;
-    const int64_t npos = paged ? (int64_t)s_npl * (kPageWords / 4) : qb - qa;
-    auto qof = [&](int64_t i) -> int64_t {
-      if (!paged) return qa + i;
-      const int64_t q = (pg0 + s_pl[i >> 6]) * (kPageWords / 4) + (i & 63);
-      return q < qb ? q : -1;
-    };
-    auto on = [&](int b, int64_t q) -> bool { return !paged || s_fl[b][(q >> 6) - pg0] != 0; };
-    uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (blk) {
-      uint4 *const pb[2] = {F.bm[BM_BL] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BL]) : nullptr,
-                            F.bm[BM_BS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_BS]) : nullptr};
-      count_stream<2>(pb, npos, ring, qof, on, [&](const uint4 (&v)[2], int64_t q) {
-        if (nz(v[0])) {
-          tally_sectors_lines(acc[0], acc[1], v[0]);
-          pb[0][q] = zero;
-        }
-        if (nz(v[1])) {
-          tally_sectors_lines(acc[2], acc[3], v[1]);
-          pb[1][q] = zero;
-        }
-      });
-    } else {
-      const bool has_w = F.bm[BM_W] >= 0;
-      uint4 *const pw[4] = {has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_W]) : nullptr,
-                            has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Y]) : nullptr,
-                            has_w ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_Z]) : nullptr,
-                            F.bm[BM_WS] >= 0 ? reinterpret_cast<uint4 *>(a.scratch + F.bm[BM_WS]) : nullptr};
-      count_stream<4>(pw, npos, ring, qof, on, [&](const uint4 (&v)[4], int64_t q) {
-        if (nz(v[0]) | nz(v[1]) | nz(v[2])) {
-          tally_wave(acc, v[0], v[1], v[2]);
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            if (nz(v[b])) pw[b][q] = zero;
-        }
-        if (nz(v[3])) {
-          tally_sectors_lines(acc[10], acc[11], v[3]);
-          pw[3][q] = zero;
-        }
-      });
     }
 #pragma unroll
     for (int kk = 0; kk < 12; ++kk) {
@@ -1689,7 +1642,7 @@ cudaError_t launch_rows(const EnumArgs &args, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_count(const CountArgs &args, int grid, cudaStream_t st) {
-  count_kernel<<<grid, kCountThreads, kCountRingBytes, st>>>(args);
+  count_kernel<<<grid, kCountThreads, 0, st>>>(args);
   return cudaGetLastError();
 }
 cudaError_t launch_model(const ModelArgs &args, cudaStream_t st) {
@@ -1726,9 +1679,7 @@ cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rows_kernel, kRowsThreads, dyn);
 }
 cudaError_t count_occupancy(int *blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCountRingBytes);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, kCountThreads, kCountRingBytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, count_kernel, kCountThreads, 0);
 }
 
 }  // namespace ws

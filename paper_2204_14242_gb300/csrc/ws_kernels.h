@@ -66,8 +66,6 @@ size_t enum_dyn_smem(int iv_cap);
 cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm);
 constexpr int kRowsThreads = 256;
 constexpr int kCountThreads = 256;   // counting kernel: threads per CTA
-constexpr int kCountStages = 4;      //   ring slots per thread and bitmap (cp.async pipeline depth)
-constexpr int kCountRingBytes = kCountStages * 4 * kCountThreads * 16;   // 64 KiB of dynamic shared memory
 constexpr int kCountMaxWords = 65536;   // most bitmap words of one counting item of a field without page flags
 constexpr int kPagedChunkWords = 262144;   // bitmap words of one counting item of a field with page flags (1024 pages)
 constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
