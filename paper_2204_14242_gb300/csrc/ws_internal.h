@@ -29,21 +29,19 @@ enum Bitmap { BM_BL, BM_BS, BM_W, BM_Y, BM_Z, BM_WS, N_BITMAPS };
 // Page flags of the row walk: a page is kPageWords bitmap words (8,192 sectors, 256 KiB of
 // address space).  The row walk sets a flag byte for every page it writes into; the
 // counting kernel reads only flagged pages and clears their flags.  Flag bytes of a field:
-// [BL pages | BS pages | W | Y | Z | WS pages], each bitmap's run of flags padded to a
-// multiple of 16 bytes (the counting kernel reads them 16 at a time): block bitmaps with
-// ceil(words[0] / 256) pages each, the others ceil(words[1] / 256).
+// [BL pages | BS pages | W | Y | Z | WS pages], block bitmaps with ceil(words[0] / 256)
+// pages each, the others ceil(words[1] / 256).
 constexpr int kPageWords = 256;
 constexpr int kPageShiftBytes = 18;   // byte offset in a bitmap's address space -> page
 
 __host__ __device__ inline int64_t page_count(int64_t words) { return (words + kPageWords - 1) / kPageWords; }
-__host__ __device__ inline int64_t page_flags16(int64_t words) { return (page_count(words) + 15) / 16 * 16; }
 __host__ __device__ inline int64_t page_flag_off(int b, int64_t words0, int64_t words1) {
-  return b < 2 ? b * page_flags16(words0) : 2 * page_flags16(words0) + (b - 2) * page_flags16(words1);
+  return b < 2 ? b * page_count(words0) : 2 * page_count(words0) + (b - 2) * page_count(words1);
 }
-// Words the flags take: a multiple of 4, so the bitmaps after them stay 16-byte aligned
-// (the counting kernel moves bitmaps in 16-byte units).
+// Words the flags take, a multiple of 4 so that the bitmaps after them stay 16-byte
+// aligned (the counting kernel moves bitmaps in 16-byte units).
 __host__ __device__ inline int64_t page_flag_words(int64_t words0, int64_t words1) {
-  return (2 * page_flags16(words0) + 4 * page_flags16(words1)) / 4;
+  return (2 * page_count(words0) + 4 * page_count(words1) + 15) / 16 * 4;
 }
 
 // Division by an invariant 32-bit divisor d >= 1 by multiply and shift (Granlund and

@@ -1360,39 +1360,28 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
     for (int b = 0; b < 4; ++b)
       bp[b] = (b < NB && F.bm[b0 + b] >= 0) ? reinterpret_cast<uint4 *>(a.scratch + F.bm[b0 + b]) : nullptr;
     uint32_t rd = 0;   // bitmap bytes this thread's pages take
-    // a thread per 16 pages: which bitmaps to read (16 flags of a bitmap in one load, then
-    // cleared in device memory); pages with none are dropped.  Chunks start at a multiple
-    // of 16 pages, so a group never straddles two chunks; flags past the part's last page
-    // are padding and never set.
-    for (int j0 = 16 * (int)threadIdx.x; j0 < npg; j0 += 16 * kCountThreads) {
-      uint4 f4[4];
+    // a thread per page: which bitmaps to read (flags cleared in device memory as they are
+    // taken); pages with none are dropped
+    for (int j = threadIdx.x; j < npg; j += kCountThreads) {
+      uint32_t m = 0;
+      const uint32_t pbytes = 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        f4[b] = make_uint4(0u, 0u, 0u, 0u);
-        if (b < NB && bp[b] != nullptr) {
-          if (paged) {
-            uint4 *const f = reinterpret_cast<uint4 *>(fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j0);
-            f4[b] = *f;
-            if (nz(f4[b])) *f = make_uint4(0u, 0u, 0u, 0u);
-          } else {
-            f4[b] = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-          }
+        if (b >= NB) continue;
+        bool on = bp[b] != nullptr;
+        if (paged) {
+          uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
+          const uint8_t v = *f;
+          if (v) *f = 0;
+          on = on && v != 0;
+        }
+        if (on) {
+          m |= 1u << (8 * b);
+          rd += pbytes;
         }
       }
-      for (int jj = 0; jj < 16 && j0 + jj < npg; ++jj) {
-        uint32_t m = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const uint32_t w = jj < 4 ? f4[b].x : jj < 8 ? f4[b].y : jj < 12 ? f4[b].z : f4[b].w;
-          if ((w >> (8 * (jj & 3))) & 0xffu) m |= 1u << (8 * b);
-        }
-        const int j = j0 + jj;
-        s_fl[j] = m;
-        if (m) {
-          s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
-          rd += (uint32_t)__popc(m) * 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
-        }
-      }
+      s_fl[j] = m;
+      if (m) s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
     }
     __syncthreads();
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
