@@ -1069,6 +1069,25 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
 // load run (raw loads when the row has fewer valid folded points than the fold) is one
 // sector range of the row; wave stores also add their per-warp sector counts in closed
 // form (row_store_sectors).
+// Magic numbers of FastDiv for a divisor fixed per work item (once per thread and item).
+__device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = d <= 1u ? 0u : 32u - __clz(d - 1u);
+  f.m = (uint32_t)((((unsigned long long)1 << 32) * (((unsigned long long)1 << f.s) - d)) / d + 1ull);
+  f.pad = 0u;
+  return f;
+}
+
+// One decoded row slot of a warp's batch: the byte range of its row (relative to the field
+// base; the fields of a row-walk group share element size and strides), the start of the
+// row, its thread row, block run, level and valid folded points.
+struct RowSlot {
+  int64_t lo, hi, el0;
+  uint32_t t, bxa, bxb;
+  uint8_t lv, kv, pad[2];
+};
+
 __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ DCfg s_c;
   __shared__ DGroup s_g;
@@ -1082,9 +1101,18 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int32_t s_gad[2][17];
   __shared__ int32_t s_gwi[2];
   __shared__ long long s_item;
-  __shared__ unsigned long long s_acc[kRowsThreads / 32][3];   // per warp: the item's counts (lane 0 adds)
   __shared__ unsigned long long s_memo_key[kRowsThreads];       // per thread: last store-sector count
   __shared__ uint32_t s_memo_val[kRowsThreads];
+  // per field of the staged group: bitmap word offsets, page-flag byte offsets, bitmap byte
+  // sizes (block, wave), wave minus block origin and the stores' origin adjustment (block, wave)
+  __shared__ int64_t s_fbm[kMaxGroupFields][N_BITMAPS];
+  __shared__ int64_t s_fpg[kMaxGroupFields][N_BITMAPS];
+  __shared__ int64_t s_flim[kMaxGroupFields][2];
+  __shared__ int64_t s_fblk[kMaxGroupFields];
+  __shared__ int64_t s_forg[kMaxGroupFields][2];
+  __shared__ RowSlot s_rs[kRowsThreads / 32][32];                 // per warp: its batch of decoded slots
+  __shared__ uint8_t s_ord[kRowsThreads / 32][2][32];             // full-fold slots, slots with stores
+  __shared__ unsigned long long s_acc[kRowsThreads / 32][5];     // per warp: the item's counts
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
@@ -1096,9 +1124,9 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t nwarps = blockDim.x >> 5;
+  const uint32_t below = (1u << lane) - 1u;
   int cur_g = -1, cur_cfg = -1;
 
-  if (threadIdx.x < kRowsThreads / 32) s_acc[threadIdx.x][0] = s_acc[threadIdx.x][1] = s_acc[threadIdx.x][2] = 0ull;
   for (;;) {
     if (threadIdx.x == 0) s_item = a.ritem_lo + (long long)atomicAdd(a.rgrab, 1ull);
     __syncthreads();
@@ -1110,22 +1138,42 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       cur_g = gi;
       cur_cfg = s_g.cfg;
       s_memo_key[threadIdx.x] = ~0ull;   // store-sector counts hold for one candidate's geometry
+      for (int i = threadIdx.x; i < s_g.f_count * N_BITMAPS; i += blockDim.x) {
+        const int k = i / N_BITMAPS, b = i - k * N_BITMAPS;
+        const DField &F = s_fk[k];
+        s_fbm[k][b] = F.bm[b];
+        s_fpg[k][b] = 4 * F.pg + page_flag_off(b, F.words[0], F.words[1]);
+        if (b < 2) {
+          s_flim[k][b] = F.words[b] << 10;
+          s_forg[k][b] = F.base - 32 * F.lo[b];
+        }
+        if (b == 0) s_fblk[k] = 32 * (F.lo[1] - F.lo[0]);
+      }
+      __syncthreads();
     }
     const int64_t kk = item - s_g.ritem_begin;
+    // ---- row walk of levels 1-3 and the block: every slot is one grid row of a level
+    // (block run x thread row); each merged load run (raw loads when the row has fewer
+    // valid folded points than the fold) is one sector range of the row, and stores also
+    // add their per-warp sector counts in closed form.  A warp decodes 32 slots at once,
+    // one per lane, then spreads the (slot, run) and (slot, store) pairs over its lanes.
+    const int64_t q0 = kk * (int64_t)a.chunk_rows;
+    const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[(s_g.levels & 1) ? 3 : 2]);
+    const int L = s_loff[s_g.f_count];
+    const int S = s_soff[s_g.f_count] - L;
+    const int Mfull = s_ioff[s_g.f_count];
+    const FastDiv fdM = make_fastdiv_dev((uint32_t)max(Mfull, 1)), fdS = make_fastdiv_dev((uint32_t)max(S, 1));
+    const DField &F0 = s_fk[0];
+    const int64_t es = F0.esize, sxe = es * F0.stride[0];
+    const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
     uint32_t bad = 0, nred = 0;
-    {
-      // ---- row walk of levels 1-3: one grid row (block run x thread row) per warp; each
-      // merged load run (raw loads when the row has fewer valid folded points than the
-      // fold) is one sector range of the row, stores also add their per-warp sector
-      // counts in closed form
-      const int64_t q0 = kk * (int64_t)a.chunk_rows;
-      const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[(s_g.levels & 1) ? 3 : 2]);
-      const int L = s_loff[s_g.f_count];
-      const int S = s_soff[s_g.f_count] - L;
-      const int Mfull = s_ioff[s_g.f_count];
-      const DField &F0 = s_fk[0];
-      const int64_t es = F0.esize, sxe = es * F0.stride[0];
-      for (int64_t slot = q0 + warp; slot < q1; slot += nwarps) {
+    unsigned long long lups = 0, naddr = 0, sreq = 0;
+    for (int64_t b0 = q0 + (int64_t)warp * 32; b0 < q1; b0 += (int64_t)nwarps * 32) {
+      // ---- decode: lane l takes slot b0 + l
+      const int64_t slot = b0 + lane;
+      bool ok = false;
+      RowSlot r;
+      if (slot < q1) {
         int lv;
         int64_t loc;
         if (slot < s_c.rows_slot_end[0]) {
@@ -1144,6 +1192,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         const uint32_t bz = fdiv(R, s_c.fd_gy), by = R - bz * gy;
         const int64_t rb0 = (int64_t)R * gx, rb1 = rb0 + gx;
         int64_t ba, bb;
+        bool in = true;
         if (lv == 0) {
           ba = max(s_c.s, rb0);
           bb = min(s_c.s + s_c.weff, rb1);
@@ -1151,7 +1200,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           ba = s_c.rep;
           bb = s_c.rep + 1;
         } else if (lv == 1) {
-          if (by == gy - 1) continue;
+          in = by != gy - 1;
           ba = max(s_c.y_lo, rb0);
           bb = min(s_c.y_hi, rb1);
         } else {
@@ -1162,119 +1211,154 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           bb = min(s_c.z_hi, rb1);
           if (by != gy - 1 && s_c.y_hi > s_c.y_lo) bb = min(bb, s_c.y_lo);
         }
-        if (ba >= bb) continue;
-        const uint32_t bxa = (uint32_t)(ba - rb0), bxb = (uint32_t)(bb - rb0);
         const uint32_t tz = fdiv(t, s_c.fd_b1), ty = t - tz * (uint32_t)s_c.B[1];
         int32_t y = (int32_t)(by * (uint32_t)s_c.B[1] + ty), z = (int32_t)(bz * (uint32_t)s_c.B[2] + tz);
-        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
         if (faxis == 1) y *= fold;
         if (faxis == 2) z *= fold;
-        if (y >= s_c.N[1] || z >= s_c.N[2]) continue;
-        const int32_t xa = (int32_t)bxa * s_c.B[0], xb = min((int32_t)bxb * s_c.B[0], s_c.N[0]);
-        const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
-        const int64_t nx = xb - xa;
-        // the block level only fills the block bitmaps: its counts come from enum_kernel
-        const bool blk = lv == 3;
-        if (lane == 0u && !blk) {
-          if (lv == 0 && s_g.first_wave) s_acc[warp][0] += (unsigned long long)(nx * kv);
-          s_acc[warp][1] += (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]);
-        }
-        const int64_t el0 = es * (F0.stride[1] * y + F0.stride[2] * z);
-        const int64_t ea = el0 + sxe * xa, eb = el0 + sxe * (xb - 1);
-        const int64_t lo = min(ea, eb), hi = max(ea, eb);
-        const bool fullk = kv == fold;
-        const int M = fullk ? Mfull : L;
-        const int bsel = lv == 0 ? BM_W : lv == 1 ? BM_Y : lv == 2 ? BM_Z : BM_BL;
-        const int lvi = blk ? 0 : 1;   // bitmap origin / size index
-        for (int e = (int)lane; e < M; e += 32) {
-          int k;
-          int64_t bo;
-          uint32_t ext;
-          if (fullk) {
-            k = s_iaf[e];
-            bo = s_ibo[e];
-            ext = s_iext[e];
-          } else {
-            if ((int)s_kmin[e] >= kv) continue;
-            k = s_af[e];
-            bo = s_boff[e] + s_fk[k].base - 32 * s_fk[k].lo[1];
-            ext = 0u;
+        if (in && ba < bb && y < s_c.N[1] && z < s_c.N[2]) {
+          ok = true;
+          r.bxa = (uint32_t)(ba - rb0);
+          r.bxb = (uint32_t)(bb - rb0);
+          const int32_t xa = (int32_t)r.bxa * s_c.B[0], xb = min((int32_t)r.bxb * s_c.B[0], s_c.N[0]);
+          const int kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+          const int64_t nx = xb - xa;
+          // the block level only fills the block bitmaps: its counts come from enum_kernel
+          if (lv != 3) {
+            if (lv == 0 && s_g.first_wave) lups += (unsigned long long)(nx * kv);
+            naddr += (unsigned long long)(nx * s_gad[lv == 0 ? 0 : 1][kv]);
           }
-          const DField &F = s_fk[k];
-          if (blk) bo += 32 * (F.lo[1] - F.lo[0]);   // staged offsets are relative to the wave origin
-          const int64_t a0 = lo + bo, a1 = hi + bo + (int64_t)ext;
-          if (a0 < 0 || a1 >= (F.words[lvi] << 10)) {
+          r.el0 = es * (F0.stride[1] * y + F0.stride[2] * z);
+          const int64_t ea = r.el0 + sxe * xa, eb = r.el0 + sxe * (xb - 1);
+          r.lo = min(ea, eb);
+          r.hi = max(ea, eb);
+          r.t = t;
+          r.lv = (uint8_t)lv;
+          r.kv = (uint8_t)kv;
+          s_rs[warp][lane] = r;
+        }
+      }
+      const bool full = ok && r.kv == fold;
+      const bool st = ok && (r.lv == 0 || r.lv == 3) && S > 0;
+      const uint32_t fullm = __ballot_sync(FULL, full), stm = __ballot_sync(FULL, st);
+      const uint32_t partm = __ballot_sync(FULL, ok && !full);
+      if (full) s_ord[warp][0][__popc(fullm & below)] = (uint8_t)lane;
+      if (st) s_ord[warp][1][__popc(stm & below)] = (uint8_t)lane;
+      __syncwarp();
+      // ---- loads of the full-fold slots: (slot, merged run) pairs over the lanes
+      const int nfull = __popc(fullm);
+      for (int f = (int)lane; f < nfull * Mfull; f += 32) {
+        const int i = (int)fdiv((uint32_t)f, fdM), e = f - i * Mfull;
+        const RowSlot &q = s_rs[warp][s_ord[warp][0][i]];
+        const int k = s_iaf[e];
+        const bool blk = q.lv == 3;
+        const int64_t bo = s_ibo[e] + (blk ? s_fblk[k] : 0);   // staged offsets are relative to the wave origin
+        const int64_t a0 = q.lo + bo, a1 = q.hi + bo + (int64_t)s_iext[e];
+        if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
+          ++bad;
+          continue;
+        }
+        const int bsel = q.lv == 0 ? BM_W : q.lv == 1 ? BM_Y : q.lv == 2 ? BM_Z : BM_BL;
+        unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
+        uint32_t cu = 0xffffffffu;
+        unsigned long long cb = 0ull;
+        put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+        if (cb) atomicOr(bm + cu, cb);
+        nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+        flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
+                   (uint32_t)(a1 >> kPageShiftBytes));
+      }
+      // ---- loads of rows with fewer valid folded points than the fold (domain edge): the
+      // raw folded loads, each issued iff a valid point needs it
+      for (uint32_t pm = partm; pm; pm &= pm - 1u) {
+        const RowSlot &q = s_rs[warp][__ffs(pm) - 1];
+        const bool blk = q.lv == 3;
+        const int bsel = q.lv == 0 ? BM_W : q.lv == 1 ? BM_Y : q.lv == 2 ? BM_Z : BM_BL;
+        for (int e = (int)lane; e < L; e += 32) {
+          if ((int)s_kmin[e] >= q.kv) continue;
+          const int k = s_af[e];
+          const int64_t bo = s_boff[e] + s_forg[k][blk ? 0 : 1];
+          const int64_t a0 = q.lo + bo, a1 = q.hi + bo;
+          if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
             ++bad;
             continue;
           }
-          unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[bsel]);
+          unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
           uint32_t cu = 0xffffffffu;
           unsigned long long cb = 0ull;
           put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
           if (cb) atomicOr(bm + cu, cb);
           nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-          flag_pages(reinterpret_cast<uint8_t *>(a.scratch + F.pg) + page_flag_off(bsel, F.words[0], F.words[1]),
-                     (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
-        }
-        if (lv == 0 || blk) {
-          uint32_t sreq = 0;   // this lane's per-warp store sectors of the row (< 2^27)
-          for (int j = L + (int)lane; j < L + S; j += 32) {
-            if ((int)s_kmin[j] >= kv) continue;
-            const DField &F = s_fk[s_af[j]];
-            const int64_t bo = s_boff[j] + F.base - 32 * F.lo[lvi];
-            const int64_t a0 = lo + bo, a1 = hi + bo;
-            if (a0 < 0 || a1 >= (F.words[lvi] << 10)) {
-              ++bad;
-              continue;
-            }
-            const int sb = blk ? BM_BS : BM_WS;
-            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + F.bm[sb]);
-            uint32_t cu = 0xffffffffu;
-            unsigned long long cb = 0ull;
-            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-            if (cb) atomicOr(bm + cu, cb);
-            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-            flag_pages(reinterpret_cast<uint8_t *>(a.scratch + F.pg) + page_flag_off(sb, F.words[0], F.words[1]),
-                       (uint32_t)(a0 >> kPageShiftBytes), (uint32_t)(a1 >> kPageShiftBytes));
-            if (!blk) {
-              // the count depends on the row start only modulo 32 bytes, on t only through
-              // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
-              // rows that agree on those reuse this thread's previous count
-              const int64_t A0 = el0 + bo;
-              const unsigned long long key = (unsigned long long)(A0 & 31) |
-                                             ((unsigned long long)((t * (uint32_t)s_c.B[0]) & 31u) << 5) |
-                                             ((unsigned long long)bxa << 10) | ((unsigned long long)bxb << 37);
-              if (s_memo_key[threadIdx.x] != key) {
-                s_memo_val[threadIdx.x] =
-                    (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, t, bxa, bxb);
-                s_memo_key[threadIdx.x] = key;
-              }
-              sreq += s_memo_val[threadIdx.x];
-            }
-          }
-          sreq = __reduce_add_sync(FULL, sreq);
-          if (lane == 0u) s_acc[warp][2] += sreq;
+          flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
+                     (uint32_t)(a1 >> kPageShiftBytes));
         }
       }
+      // ---- stores of wave and block rows: (slot, store) pairs over the lanes; wave rows
+      // add their per-warp store sectors
+      const int nst = __popc(stm);
+      for (int f = (int)lane; f < nst * S; f += 32) {
+        const int i = (int)fdiv((uint32_t)f, fdS), j = L + (f - i * S);
+        const RowSlot &q = s_rs[warp][s_ord[warp][1][i]];
+        if ((int)s_kmin[j] >= q.kv) continue;
+        const bool blk = q.lv == 3;
+        const int k = s_af[j];
+        const int64_t bo = s_boff[j] + s_forg[k][blk ? 0 : 1];
+        const int64_t a0 = q.lo + bo, a1 = q.hi + bo;
+        if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
+          ++bad;
+          continue;
+        }
+        const int sb = blk ? BM_BS : BM_WS;
+        unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][sb]);
+        uint32_t cu = 0xffffffffu;
+        unsigned long long cb = 0ull;
+        put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+        if (cb) atomicOr(bm + cu, cb);
+        nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+        flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][sb], (uint32_t)(a0 >> kPageShiftBytes),
+                   (uint32_t)(a1 >> kPageShiftBytes));
+        if (!blk) {
+          // the count depends on the row start only modulo 32 bytes, on t only through
+          // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
+          // rows that agree on those reuse this thread's previous count
+          const int64_t A0 = q.el0 + bo;
+          const unsigned long long key = (unsigned long long)(A0 & 31) |
+                                         ((unsigned long long)((q.t * (uint32_t)s_c.B[0]) & 31u) << 5) |
+                                         ((unsigned long long)q.bxa << 10) | ((unsigned long long)q.bxb << 37);
+          if (s_memo_key[threadIdx.x] != key) {
+            s_memo_val[threadIdx.x] =
+                (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, q.t, q.bxa, q.bxb);
+            s_memo_key[threadIdx.x] = key;
+          }
+          sreq += s_memo_val[threadIdx.x];
+        }
+      }
+      __syncwarp();   // the batch's slots are read before the next batch overwrites them
     }
 
+    // the item's counts: per warp, then once per CTA
     bad = __reduce_add_sync(FULL, bad);
     nred = __reduce_add_sync(FULL, nred);
-    unsigned long long *const c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      lups += __shfl_xor_sync(FULL, lups, o);
+      naddr += __shfl_xor_sync(FULL, naddr, o);
+      sreq += __shfl_xor_sync(FULL, sreq, o);
+    }
     if (lane == 0) {
-      if (bad) atomicAdd(c + C_OVERFLOW, (unsigned long long)bad);
-      if (nred) atomicAdd(c + C_RED, (unsigned long long)nred);
+      s_acc[warp][0] = lups;
+      s_acc[warp][1] = naddr;
+      s_acc[warp][2] = sreq;
+      s_acc[warp][3] = bad;
+      s_acc[warp][4] = nred;
     }
     __syncthreads();
-    // the item's wave LUPs, address evaluations and store requests, once per CTA
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 5) {
       const int k = threadIdx.x;
       unsigned long long v = 0;
-      for (int w = 0; w < kRowsThreads / 32; ++w) {
-        v += s_acc[w][k];
-        s_acc[w][k] = 0ull;
-      }
-      if (v) atomicAdd(c + (k == 0 ? C_LUPS_WAVE : k == 1 ? C_ADDR : C_W_SREQ), v);
+      for (int w = 0; w < kRowsThreads / 32; ++w) v += s_acc[w][k];
+      unsigned long long *const c = (unsigned long long *)(a.counters + (int64_t)s_g.cfg * N_COUNTERS);
+      const int dst = k == 0 ? C_LUPS_WAVE : k == 1 ? C_ADDR : k == 2 ? C_W_SREQ : k == 3 ? C_OVERFLOW : C_RED;
+      if (v) atomicAdd(c + dst, v);
     }
   }
 }
