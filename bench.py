@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the 25-point and LBM sub-records")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--arena-gb", type=float, default=48.0)
+    ap.add_argument("--arena-gb", type=float, default=200.0,
+                    help="device arena of the context (the bitmap scratch of the headline set fits one pass)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tuning instead of autotuning the plan before timing")
     ap.add_argument("--subset", type=int, default=1,
