@@ -248,17 +248,28 @@ def kernel_source_digest():
 
 def recorded_traffic(workload_key):
     """DRAM bytes per launch of each kernel (dram__bytes_read.sum + dram__bytes_write.sum,
-    one ncu capture of this workload), from profiles/dram_traffic_<workload>.txt when it
-    was taken from the current kernel source; else {}."""
+    one ncu capture), from profiles/dram_traffic_<workload>.txt when it was taken from the
+    current kernel source; else {}.  A line `<kernel> <bytes> <units>` holds a capture of a
+    smaller case with that many of the kernel's algorithmic units (64-bit bitmap words
+    written, bitmap bytes read, block addresses): the full launch's traffic is scaled by
+    its own units.  Returns kernel -> (bytes, units or None)."""
     path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload_key}.txt")
     try:
         lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
     except OSError:
         return {}
-    kv = {ln[0]: ln[1] for ln in lines if len(ln) >= 2}
-    if kv.get("kernel_source_sha256") != kernel_source_digest():
+    kv = {ln[0]: ln[1:] for ln in lines if len(ln) >= 2}
+    if kv.get("kernel_source_sha256", [None])[0] != kernel_source_digest():
         return {}
-    return {k: int(v) for k, v in kv.items() if k.endswith("_kernel")}
+    return {k: (int(v[0]), int(v[1]) if len(v) > 1 else None) for k, v in kv.items() if k.endswith("_kernel")}
+
+
+def scaled_traffic(rec, units):
+    """Traffic of a full launch with `units` algorithmic units, from a recorded capture."""
+    if not rec:
+        return None
+    b, u = rec
+    return int(round(b * units / u)) if u else b
 
 
 def kernel_rooflines(profs, peaks, workload_key=None):
@@ -297,7 +308,7 @@ def kernel_rooflines(profs, peaks, workload_key=None):
     top = max(ms, key=ms.get)
     traffic = recorded_traffic(workload_key) if workload_key else {}
     for name in k:
-        k[name]["traffic"] = traffic.get(name)
+        k[name]["traffic"] = scaled_traffic(traffic.get(name), k[name]["per_launch"])
     out = dict(k[top])
     out.update({"kernel": top, "share": ms[top] / med("ms_total"), "kernels": k,
                 "ms_model": med("ms_model"), "ms_rank": med("ms_rank"), "ms_step_profiled": med("ms_total"),

@@ -7,10 +7,15 @@ import bench
 def test_recorded_traffic_follows_the_kernel_source(monkeypatch, tmp_path):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "dram_traffic_sweep.txt").write_text(
-        "# comment\nkernel_source_sha256 " + "a" * 64 + "\nenum_kernel 968448\nfp_kernel 1234\n")
+        "# comment\nkernel_source_sha256 " + "a" * 64 + "\nenum_kernel 968448\nrows_kernel 2000 500\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "a" * 64)
-    assert bench.recorded_traffic("sweep") == {"enum_kernel": 968448, "fp_kernel": 1234}
+    got = bench.recorded_traffic("sweep")
+    assert got == {"enum_kernel": (968448, None), "rows_kernel": (2000, 500)}
+    # a capture of a smaller case scales with the full launch's units; a full-size one does not
+    assert bench.scaled_traffic(got["rows_kernel"], 5000) == 20000
+    assert bench.scaled_traffic(got["enum_kernel"], 123) == 968448
+    assert bench.scaled_traffic(None, 1) is None
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 64)
     assert bench.recorded_traffic("sweep") == {}
     assert bench.recorded_traffic("no_such_workload") == {}
