@@ -1113,6 +1113,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ RowSlot s_rs[kRowsThreads / 32][32];                 // per warp: its batch of decoded slots
   __shared__ uint8_t s_ord[kRowsThreads / 32][2][32];             // full-fold slots, slots with stores
   __shared__ unsigned long long s_acc[kRowsThreads / 32][5];     // per warp: the item's counts
+  __shared__ int s_batch;                                         // next batch of 32 slots of the item
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
@@ -1128,7 +1129,10 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   int cur_g = -1, cur_cfg = -1;
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = a.ritem_lo + (long long)atomicAdd(a.rgrab, 1ull);
+    if (threadIdx.x == 0) {
+      s_item = a.ritem_lo + (long long)atomicAdd(a.rgrab, 1ull);
+      s_batch = 0;
+    }
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.ritem_hi) break;
@@ -1168,7 +1172,12 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
     const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
     uint32_t bad = 0, nred = 0;
     unsigned long long lups = 0, naddr = 0, sreq = 0;
-    for (int64_t b0 = q0 + (int64_t)warp * 32; b0 < q1; b0 += (int64_t)nwarps * 32) {
+    // the warps take the item's batches of 32 slots as they finish the previous one
+    for (;;) {
+      int bi = 0;
+      if (lane == 0) bi = atomicAdd(&s_batch, 1);
+      const int64_t b0 = q0 + 32 * (int64_t)__shfl_sync(FULL, bi, 0);
+      if (b0 >= q1) break;
       // ---- decode: lane l takes slot b0 + l
       const int64_t slot = b0 + lane;
       bool ok = false;
