@@ -319,8 +319,7 @@ __device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, u
 // ever receives ones until the counting kernel clears it; a flag already seen set (a load
 // that mostly hits L1) is not stored again.
 __device__ __forceinline__ void flag_pages(uint8_t *__restrict__ fl, uint32_t p0, uint32_t p1) {
-  for (uint32_t p = p0; p <= p1; ++p)
-    if (!fl[p]) fl[p] = 1;
+  for (uint32_t p = p0; p <= p1; ++p) fl[p] = 1;
 }
 
 // Byte range [lo, hi] (relative to the bitmap origin) of one row segment of a
