@@ -81,6 +81,7 @@ struct DCfg {
   int32_t rows_per_blk;        // B[1] * B[2]
   int32_t full_end;            // blocks in x that lie entirely inside N[0]
   FastDiv fd_rows, fd_b1;
+  FastDiv fd_b2, fd_fold;      // for locating the row of a covering run
 };
 
 struct DField {
@@ -122,11 +123,20 @@ struct DAcc {
 // most 32 B apart, so that for a row segment of threads whose addresses step by at
 // most 32 B the union of all their sectors is the single sector range
 // [(lowest thread address + boff) / 32, (highest thread address + boff + ext) / 32].
+//
+// Covering run: when every offset of the run lies in one grid row (dy, dz, dc) with x
+// offsets dx_lo..dx_hi, and an earlier run of the field (in a fixed order) with the same dc
+// and x offsets covering dx_lo..dx_hi lies (ddy, ddz) grid rows back, the range of (row r,
+// this run) is contained in the range of (row r + (ddy, ddz), that run) whenever that row
+// belongs to the same level with an x range covering r's (and all its folded points are
+// valid), so the row walk skips it.  Containment is transitive and the order is strict, so
+// a skipped range is always covered by one that is set.  ddy == kNoCover: no covering run.
 struct DIv {
   int64_t boff;           // smallest byte offset of the run
   uint32_t ext;           // largest minus smallest byte offset
-  int32_t pad;
+  int16_t ddy, ddz;       // grid rows to the covering run's row (kNoCover: none)
 };
+constexpr int16_t kNoCover = -32768;
 
 struct DHw {
   double clock_hz, l1_bytes, l2_bytes, bw_l2, bw_dram, fp_peak;

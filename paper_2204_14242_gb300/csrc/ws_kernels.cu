@@ -445,6 +445,7 @@ struct StageSmem {
   int32_t *gwi;                  // access instructions, [0] levels 0-1, [1] 2-3
   int64_t *ibo;                  // merged load runs: offset relative to the field's bitmap origin
   uint32_t *iext;                //   extent
+  int32_t *idd;                  //   grid rows to the covering run's row (ddy | ddz << 16)
   uint8_t *iaf;                  //   field
 };
 
@@ -499,6 +500,7 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
     const DIv v = a.iv[F.iv_begin + (j - m.ioff[k])];
     m.ibo[j] = v.boff + F.base - 32 * F.lo[1];
     m.iext[j] = v.ext;
+    m.idd[j] = (int32_t)(uint16_t)v.ddy | ((int32_t)(uint16_t)v.ddz << 16);
     m.iaf[j] = (uint8_t)k;
   }
   // raw folded accesses; uniform groups fold each field's constant into the 32-bit
@@ -548,9 +550,10 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
   uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
-  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
+  int32_t *const s_idd = reinterpret_cast<int32_t *>(s_dyn + 12 * iv_cap16);
+  uint8_t *const s_iaf = s_dyn + 16 * iv_cap16;
   const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, s_b32, s_kmin, s_gad, s_gwi,
-                     s_ibo, s_iext, s_iaf};
+                     s_ibo, s_iext, s_idd, s_iaf};
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -1084,8 +1087,46 @@ __device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
 struct RowSlot {
   int64_t lo, hi, el0;
   uint32_t t, bxa, bxb;
+  int32_t y, z;           // grid row of the slot's first folded point
   uint8_t lv, kv, pad[2];
 };
+
+// True when grid row (ys, zs) is a thread row of level lv whose block run covers
+// [bxa, bxb) and whose folded points are all inside the domain: the same level rules as the
+// row walk's slot decoding (wave, y set without the last block row, z set before the y set
+// outside the last block row, the representative block).
+__device__ __forceinline__ bool row_covers(const DCfg &c, int lv, int32_t ys, int32_t zs, uint32_t bxa, uint32_t bxb) {
+  if (ys < 0 || zs < 0 || ys >= c.N[1] || zs >= c.N[2]) return false;
+  uint32_t yt = (uint32_t)ys, zt = (uint32_t)zs;
+  if (c.fold_axis == 1) {
+    yt = fdiv(yt, c.fd_fold);
+    if ((int32_t)yt * c.fold != ys || c.N[1] - ys < c.fold) return false;
+  } else if (c.fold_axis == 2) {
+    zt = fdiv(zt, c.fd_fold);
+    if ((int32_t)zt * c.fold != zs || c.N[2] - zs < c.fold) return false;
+  }
+  const uint32_t by = fdiv(yt, c.fd_b1), bz = fdiv(zt, c.fd_b2);
+  const uint32_t gx = (uint32_t)c.g[0], gy = (uint32_t)c.g[1];
+  const int64_t R = (int64_t)by + (int64_t)gy * bz, rb0 = R * gx, rb1 = rb0 + gx;
+  int64_t ba, bb;
+  if (lv == 0) {
+    ba = max(c.s, rb0);
+    bb = min(c.s + c.weff, rb1);
+  } else if (lv == 3) {
+    if (c.rep < rb0 || c.rep >= rb1) return false;
+    ba = c.rep;
+    bb = c.rep + 1;
+  } else if (lv == 1) {
+    if (by == gy - 1) return false;
+    ba = max(c.y_lo, rb0);
+    bb = min(c.y_hi, rb1);
+  } else {
+    ba = max(c.z_lo, rb0);
+    bb = min(c.z_hi, rb1);
+    if (by != gy - 1 && c.y_hi > c.y_lo) bb = min(bb, c.y_lo);
+  }
+  return ba < bb && ba - rb0 <= (int64_t)bxa && bb - rb0 >= (int64_t)bxb;
+}
 
 __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ DCfg s_c;
@@ -1117,9 +1158,10 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
   uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
-  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
+  int32_t *const s_idd = reinterpret_cast<int32_t *>(s_dyn + 12 * iv_cap16);
+  uint8_t *const s_iaf = s_dyn + 16 * iv_cap16;
   const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, nullptr, s_kmin, s_gad, s_gwi,
-                     s_ibo, s_iext, s_iaf};
+                     s_ibo, s_iext, s_idd, s_iaf};
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -1240,6 +1282,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           r.lo = min(ea, eb);
           r.hi = max(ea, eb);
           r.t = t;
+          r.y = y;
+          r.z = z;
           r.lv = (uint8_t)lv;
           r.kv = (uint8_t)kv;
           s_rs[warp][lane] = r;
@@ -1257,6 +1301,11 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       for (int f = (int)lane; f < nfull * Mfull; f += 32) {
         const int i = (int)fdiv((uint32_t)f, fdM), e = f - i * Mfull;
         const RowSlot &q = s_rs[warp][s_ord[warp][0][i]];
+        // a range that an earlier run of the field sets, containing it, from another row of
+        // the level is skipped
+        const int32_t dd = s_idd[e];
+        const int ddy = (int16_t)(dd & 0xffff), ddz = (int16_t)(dd >> 16);
+        if (ddy != kNoCover && row_covers(s_c, q.lv, q.y + ddy, q.z + ddz, q.bxa, q.bxb)) continue;
         const int k = s_iaf[e];
         const bool blk = q.lv == 3;
         const int64_t bo = s_ibo[e] + (blk ? s_fblk[k] : 0);   // staged offsets are relative to the wave origin
@@ -1700,7 +1749,7 @@ __global__ void keys_kernel(const ws_result *__restrict__ res, int n, double *__
 }
 
 // ---- launchers ---------------------------------------------------------------------
-size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 1); }
+size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 4 + 1); }
 
 // Raises the dynamic shared-memory limit of the enumeration and row kernels (once per
 // device and size).

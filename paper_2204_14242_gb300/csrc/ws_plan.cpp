@@ -410,22 +410,67 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
   out.n_store = (int32_t)sk.size();
   // merged load intervals: sorted load offsets cut wherever two neighbours are more than
   // 32 B apart (a chain of byte addresses with steps of at most 32 B touches every
-  // sector between its ends)
+  // sector between its ends); for each, the grid row of its offsets and its covering run
   {
-    static thread_local std::vector<int64_t> b;
+    struct Ld {
+      int64_t b, o[4];   // byte offset; dx dy dz dc
+    };
+    static thread_local std::vector<Ld> b;
     b.resize((size_t)out.n_load);
-    for (int i = 0; i < out.n_load; ++i) b[(size_t)i] = out.da[(size_t)i].boff;
-    std::sort(b.begin(), b.end());
+    for (int i = 0; i < out.n_load; ++i) {
+      b[(size_t)i].b = out.da[(size_t)i].boff;
+      off_unkey(lk[(size_t)i], b[(size_t)i].o);
+    }
+    std::sort(b.begin(), b.end(), [](const Ld &p, const Ld &q) { return p.b < q.b; });
+    struct RunRow {
+      bool one_row;
+      int64_t dy, dz, dc, dxlo, dxhi;
+    };
+    static thread_local std::vector<RunRow> rr;
+    rr.clear();
     out.iv.clear();
     for (size_t i = 0; i < b.size();) {
       size_t j = i;
-      while (j + 1 < b.size() && b[j + 1] - b[j] <= 32) ++j;
+      while (j + 1 < b.size() && b[j + 1].b - b[j].b <= 32) ++j;
       DIv v;
-      v.boff = b[i];
-      v.ext = (uint32_t)(b[j] - b[i]);
-      v.pad = 0;
+      v.boff = b[i].b;
+      v.ext = (uint32_t)(b[j].b - b[i].b);
+      v.ddy = kNoCover;
+      v.ddz = 0;
       out.iv.push_back(v);
+      RunRow r{true, b[i].o[1], b[i].o[2], b[i].o[3], b[i].o[0], b[i].o[0]};
+      for (size_t q = i; q <= j; ++q) {
+        r.one_row = r.one_row && b[q].o[1] == r.dy && b[q].o[2] == r.dz && b[q].o[3] == r.dc;
+        r.dxlo = std::min(r.dxlo, b[q].o[0]);
+        r.dxhi = std::max(r.dxhi, b[q].o[0]);
+      }
+      rr.push_back(r);
       i = j + 1;
+    }
+    // covering runs: order runs by (|dy| + |dz|, dz, dy); a run may be covered by an earlier
+    // one of the same dc whose x offsets contain its own, at a row displacement a thread row
+    // can make (a multiple of the fold along the folding axis); the nearest one is taken
+    const size_t nr = rr.size() <= 512 ? rr.size() : 0;   // bounded host work: no covering beyond 512 runs
+    auto rank = [&](size_t e) { return std::make_tuple(std::llabs(rr[e].dy) + std::llabs(rr[e].dz), rr[e].dz, rr[e].dy, e); };
+    for (size_t e = 0; e < nr; ++e) {
+      if (!rr[e].one_row) continue;
+      int64_t best = -1, best_d = 0;
+      for (size_t f = 0; f < nr; ++f) {
+        if (f == e || !rr[f].one_row || !(rank(f) < rank(e)) || rr[f].dc != rr[e].dc) continue;
+        if (rr[f].dxlo > rr[e].dxlo || rr[f].dxhi < rr[e].dxhi) continue;
+        const int64_t ddy = rr[e].dy - rr[f].dy, ddz = rr[e].dz - rr[f].dz;
+        if ((fold_axis == 1 && ddy % fold != 0) || (fold_axis == 2 && ddz % fold != 0)) continue;
+        if (std::llabs(ddy) >= 32767 || std::llabs(ddz) >= 32767) continue;
+        const int64_t d = std::llabs(ddy) + std::llabs(ddz);
+        if (best < 0 || d < best_d) {
+          best = (int64_t)f;
+          best_d = d;
+        }
+      }
+      if (best >= 0) {
+        out.iv[e].ddy = (int16_t)(rr[e].dy - rr[(size_t)best].dy);
+        out.iv[e].ddz = (int16_t)(rr[e].dz - rr[(size_t)best].dz);
+      }
     }
   }
   // issued accesses of a thread with kv valid folded points: those with kmin < kv
@@ -674,6 +719,8 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     d.full_end = (int32_t)(c.N[0] / c.B[0]);
     d.fd_rows = make_fastdiv((uint32_t)d.rows_per_blk);
     d.fd_b1 = make_fastdiv((uint32_t)c.B[1]);
+    d.fd_b2 = make_fastdiv((uint32_t)c.B[2]);
+    d.fd_fold = make_fastdiv((uint32_t)c.fold);
     const int64_t rng[4][2] = {{s, s + weff}, {y_lo, y_hi}, {z_lo, z_hi}, {rep, rep + 1}};
     int64_t cum = 0;
     for (int lv = 0; lv < 4; ++lv) {
