@@ -10,9 +10,9 @@
 //                 row is one sector range set with 64-bit red.or; per-warp store sectors
 //                 by floor sums (Sec. 4.4, closed-form counting instead of implicit sets).
 //   count_kernel  popcounts of the bitmaps: unique sectors, unique 128 B lines (nibble
-//                 OR), y / z overlaps by AND / AND-NOT, streamed through a per-thread
-//                 cp.async ring in shared memory.  Leaves the bitmaps zeroed for the next
-//                 step (only non-zero positions are written).
+//                 OR), y / z overlaps by AND / AND-NOT, reading only the pages the row
+//                 walk flagged, one warp per page.  Leaves the bitmaps and flags zeroed for
+//                 the next step (only non-zero positions are written).
 //   model_kernel  fp64 capacity model and limiters (Sec. 2, 4.5), one thread per candidate.
 //   rank_count_kernel, rank_scatter_kernel   stable counting rank per segment (Sec. 5.8).
 // The three persistent kernels take work items from an atomic counter and find each item's
@@ -316,8 +316,8 @@ __device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, u
 }
 
 // Flags the pages [p0, p1] of one bitmap as written.  The flag array starts zeroed and only
-// ever receives ones until the counting kernel clears it; a flag already seen set (a load
-// that mostly hits L1) is not stored again.
+// ever receives ones until the counting kernel clears it, so plain byte stores suffice (the
+// same value from any number of writers; reading a flag first to skip the store was slower).
 __device__ __forceinline__ void flag_pages(uint8_t *__restrict__ fl, uint32_t p0, uint32_t p1) {
   for (uint32_t p = p0; p <= p1; ++p) fl[p] = 1;
 }
