@@ -107,6 +107,8 @@ struct DField {
   int32_t n_iv;           // merged load intervals
   int32_t rows_ok;        // stores: the row segments of one warp never share a sector
   int32_t level_mask;     // levels served: 1 the representative block, 2 wave + y / z sets
+  int32_t n_iv_unc;       // merged load intervals without a covering run (they come first)
+  int16_t cov_dy, cov_dz; // largest |row displacement| from an interval to its covering run
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };

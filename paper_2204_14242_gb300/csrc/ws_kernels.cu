@@ -445,8 +445,12 @@ struct StageSmem {
   int32_t *gwi;                  // access instructions, [0] levels 0-1, [1] 2-3
   int64_t *ibo;                  // merged load runs: offset relative to the field's bitmap origin
   uint32_t *iext;                //   extent
-  int32_t *idd;                  //   grid rows to the covering run's row (ddy | ddz << 16)
   uint8_t *iaf;                  //   field
+  // row walk only (else null): the runs without a covering run of all fields first, then the
+  // others; idst[0][k] / idst[1][k] = first staged slot of field k's runs of each kind;
+  // cov = {runs without a covering run, largest |ddy|, largest |ddz| of the others}
+  int32_t (*idst)[kMaxGroupFields];
+  int32_t *cov;
 };
 
 // Stages group gi (and its candidate when it differs from cur_cfg); ends with a barrier.
@@ -478,6 +482,27 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
       o += G.iv ? m.fk[k].n_iv : 0;
     }
     m.ioff[G.f_count] = o;
+    if (m.cov) {
+      int u = 0, dy = 0, dz = 0;
+      for (int k = 0; k < G.f_count; ++k)
+        if (G.iv) {
+          m.idst[0][k] = u;
+          u += m.fk[k].n_iv_unc;
+          if (m.fk[k].n_iv_unc < m.fk[k].n_iv) {
+            dy = max(dy, (int)m.fk[k].cov_dy);
+            dz = max(dz, (int)m.fk[k].cov_dz);
+          }
+        }
+      int c = u;
+      for (int k = 0; k < G.f_count; ++k)
+        if (G.iv) {
+          m.idst[1][k] = c;
+          c += m.fk[k].n_iv - m.fk[k].n_iv_unc;
+        }
+      m.cov[0] = u;
+      m.cov[1] = dy;
+      m.cov[2] = dz;
+    }
   }
   for (int t = threadIdx.x; t < 34; t += blockDim.x) {
     // issued accesses per thread (by valid folded points) and access instructions,
@@ -497,11 +522,12 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
     int k = 0;
     while (m.ioff[k + 1] <= j) ++k;
     const DField &F = m.fk[k];
-    const DIv v = a.iv[F.iv_begin + (j - m.ioff[k])];
-    m.ibo[j] = v.boff + F.base - 32 * F.lo[1];
-    m.iext[j] = v.ext;
-    m.idd[j] = (int32_t)(uint16_t)v.ddy | ((int32_t)(uint16_t)v.ddz << 16);
-    m.iaf[j] = (uint8_t)k;
+    const int jj = j - m.ioff[k];
+    const DIv v = a.iv[F.iv_begin + jj];
+    const int d = !m.cov ? j : jj < F.n_iv_unc ? m.idst[0][k] + jj : m.idst[1][k] + (jj - F.n_iv_unc);
+    m.ibo[d] = v.boff + F.base - 32 * F.lo[1];
+    m.iext[d] = v.ext;
+    m.iaf[d] = (uint8_t)k;
   }
   // raw folded accesses; uniform groups fold each field's constant into the 32-bit
   // offsets, so that address = shared thread address + offset for every field
@@ -550,10 +576,9 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
   uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
-  int32_t *const s_idd = reinterpret_cast<int32_t *>(s_dyn + 12 * iv_cap16);
-  uint8_t *const s_iaf = s_dyn + 16 * iv_cap16;
+  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
   const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, s_b32, s_kmin, s_gad, s_gwi,
-                     s_ibo, s_iext, s_idd, s_iaf};
+                     s_ibo, s_iext, s_iaf, nullptr, nullptr};
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -1081,7 +1106,7 @@ __device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
   return f;
 }
 
-// One decoded row slot of a warp's batch: the byte range of its row (relative to the field
+// One decoded row slot (a lane's): the byte range of its row (relative to the field
 // base; the fields of a row-walk group share element size and strides), the start of the
 // row, its thread row, block run, level and valid folded points.
 struct RowSlot {
@@ -1091,41 +1116,38 @@ struct RowSlot {
   uint8_t lv, kv, pad[2];
 };
 
-// True when grid row (ys, zs) is a thread row of level lv whose block run covers
-// [bxa, bxb) and whose folded points are all inside the domain: the same level rules as the
-// row walk's slot decoding (wave, y set without the last block row, z set before the y set
-// outside the last block row, the representative block).
-__device__ __forceinline__ bool row_covers(const DCfg &c, int lv, int32_t ys, int32_t zs, uint32_t bxa, uint32_t bxb) {
-  if (ys < 0 || zs < 0 || ys >= c.N[1] || zs >= c.N[2]) return false;
-  uint32_t yt = (uint32_t)ys, zt = (uint32_t)zs;
+// True when every grid row displaced from row (y, z) of level lv by at most dy rows in y
+// and dz in z (multiples of the fold along the folding axis) is a thread row of the same
+// level whose block run contains [bxa, bxb) and whose folded points are all inside the
+// domain.  The displaced rows' block rows lie between those of the two extreme corners
+// (R = by + gy * bz grows with by and bz), so the level's block interval is checked at
+// those two; the z set is checked against its tighter bound (before the y set) throughout.
+// Then every run whose covering run lies within that displacement may be skipped at this
+// row: the covering run sets a containing range from the displaced row, which the walk
+// visits with a containing block run (and if it skips that run there in turn, a run even
+// earlier in the covering order covers both).
+__device__ __forceinline__ bool row_interior(const DCfg &c, int lv, int32_t y, int32_t z, uint32_t bxa, uint32_t bxb,
+                                             int32_t dy, int32_t dz) {
+  const int32_t fy = c.fold_axis == 1 ? c.fold : 1, fz = c.fold_axis == 2 ? c.fold : 1;
+  if (y < dy || z < dz || y + dy + fy > c.N[1] || z + dz + fz > c.N[2]) return false;
+  uint32_t y0 = (uint32_t)(y - dy), y1 = (uint32_t)(y + dy), z0 = (uint32_t)(z - dz), z1 = (uint32_t)(z + dz);
   if (c.fold_axis == 1) {
-    yt = fdiv(yt, c.fd_fold);
-    if ((int32_t)yt * c.fold != ys || c.N[1] - ys < c.fold) return false;
+    y0 = fdiv(y0, c.fd_fold);
+    y1 = fdiv(y1, c.fd_fold);
   } else if (c.fold_axis == 2) {
-    zt = fdiv(zt, c.fd_fold);
-    if ((int32_t)zt * c.fold != zs || c.N[2] - zs < c.fold) return false;
+    z0 = fdiv(z0, c.fd_fold);
+    z1 = fdiv(z1, c.fd_fold);
   }
-  const uint32_t by = fdiv(yt, c.fd_b1), bz = fdiv(zt, c.fd_b2);
-  const uint32_t gx = (uint32_t)c.g[0], gy = (uint32_t)c.g[1];
-  const int64_t R = (int64_t)by + (int64_t)gy * bz, rb0 = R * gx, rb1 = rb0 + gx;
-  int64_t ba, bb;
-  if (lv == 0) {
-    ba = max(c.s, rb0);
-    bb = min(c.s + c.weff, rb1);
-  } else if (lv == 3) {
-    if (c.rep < rb0 || c.rep >= rb1) return false;
-    ba = c.rep;
-    bb = c.rep + 1;
-  } else if (lv == 1) {
-    if (by == gy - 1) return false;
-    ba = max(c.y_lo, rb0);
-    bb = min(c.y_hi, rb1);
-  } else {
-    ba = max(c.z_lo, rb0);
-    bb = min(c.z_hi, rb1);
-    if (by != gy - 1 && c.y_hi > c.y_lo) bb = min(bb, c.y_lo);
-  }
-  return ba < bb && ba - rb0 <= (int64_t)bxa && bb - rb0 >= (int64_t)bxb;
+  const uint32_t by0 = fdiv(y0, c.fd_b1), by1 = fdiv(y1, c.fd_b1);
+  const uint32_t bz0 = fdiv(z0, c.fd_b2), bz1 = fdiv(z1, c.fd_b2);
+  if (lv == 3) return by0 == by1 && bz0 == bz1;   // the representative block's own thread rows
+  const int64_t gx = c.g[0], gy = c.g[1];
+  const int64_t lo = ((int64_t)by0 + gy * (int64_t)bz0) * gx + bxa;
+  const int64_t hi = ((int64_t)by1 + gy * (int64_t)bz1) * gx + bxb;
+  if (lv == 0) return c.s <= lo && hi <= c.s + c.weff;
+  if (lv == 1) return (int64_t)by1 != gy - 1 && c.y_lo <= lo && hi <= c.y_hi;
+  const int64_t up = c.y_hi > c.y_lo ? min(c.z_hi, c.y_lo) : c.z_hi;
+  return c.z_lo <= lo && hi <= up;
 }
 
 __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
@@ -1135,6 +1157,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int32_t s_loff[kMaxGroupFields + 1];
   __shared__ int32_t s_soff[kMaxGroupFields + 1];
   __shared__ int32_t s_ioff[kMaxGroupFields + 1];
+  __shared__ int32_t s_idst[2][kMaxGroupFields];
+  __shared__ int32_t s_cov[3];
   __shared__ uint8_t s_af[kMaxFoldedAccesses];
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
   __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
@@ -1150,23 +1174,18 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int64_t s_flim[kMaxGroupFields][2];
   __shared__ int64_t s_fblk[kMaxGroupFields];
   __shared__ int64_t s_forg[kMaxGroupFields][2];
-  __shared__ RowSlot s_rs[kRowsThreads / 32][32];                 // per warp: its batch of decoded slots
-  __shared__ uint8_t s_ord[kRowsThreads / 32][2][32];             // full-fold slots, slots with stores
   __shared__ unsigned long long s_acc[kRowsThreads / 32][5];     // per warp: the item's counts
   __shared__ int s_batch;                                         // next batch of 32 slots of the item
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int iv_cap16 = (a.iv_cap + 15) & ~15;
   int64_t *const s_ibo = reinterpret_cast<int64_t *>(s_dyn);
   uint32_t *const s_iext = reinterpret_cast<uint32_t *>(s_dyn + 8 * iv_cap16);
-  int32_t *const s_idd = reinterpret_cast<int32_t *>(s_dyn + 12 * iv_cap16);
-  uint8_t *const s_iaf = s_dyn + 16 * iv_cap16;
+  uint8_t *const s_iaf = s_dyn + 12 * iv_cap16;
   const StageSmem sm{&s_c, &s_g, s_fk, s_loff, s_soff, s_ioff, s_af, s_boff, nullptr, s_kmin, s_gad, s_gwi,
-                     s_ibo, s_iext, s_idd, s_iaf};
+                     s_ibo, s_iext, s_iaf, s_idst, s_cov};
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
-  const uint32_t nwarps = blockDim.x >> 5;
-  const uint32_t below = (1u << lane) - 1u;
   int cur_g = -1, cur_cfg = -1;
 
   for (;;) {
@@ -1200,14 +1219,17 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
     // ---- row walk of levels 1-3 and the block: every slot is one grid row of a level
     // (block run x thread row); each merged load run (raw loads when the row has fewer
     // valid folded points than the fold) is one sector range of the row, and stores also
-    // add their per-warp sector counts in closed form.  A warp decodes 32 slots at once,
-    // one per lane, then spreads the (slot, run) and (slot, store) pairs over its lanes.
+    // add their per-warp sector counts in closed form.  A warp takes 32 slots at once, one
+    // per lane, and each lane walks the runs and stores of its own row.
     const int64_t q0 = kk * (int64_t)a.chunk_rows;
     const int64_t q1 = min(q0 + (int64_t)a.chunk_rows, s_c.rows_slot_end[(s_g.levels & 1) ? 3 : 2]);
     const int L = s_loff[s_g.f_count];
     const int S = s_soff[s_g.f_count] - L;
     const int Mfull = s_ioff[s_g.f_count];
-    const FastDiv fdM = make_fastdiv_dev((uint32_t)max(Mfull, 1)), fdS = make_fastdiv_dev((uint32_t)max(S, 1));
+    // runs [0, Mu) have no covering run; at rows inside their level (row_interior) only those
+    // are taken, when they are at most half of all runs (otherwise the test of each row costs
+    // more than the runs it saves: all runs are taken everywhere)
+    const int Mu = 2 * s_cov[0] <= Mfull ? s_cov[0] : Mfull;
     const DField &F0 = s_fk[0];
     const int64_t es = F0.esize, sxe = es * F0.stride[0];
     const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
@@ -1286,110 +1308,119 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           r.z = z;
           r.lv = (uint8_t)lv;
           r.kv = (uint8_t)kv;
-          s_rs[warp][lane] = r;
         }
       }
       const bool full = ok && r.kv == fold;
-      const bool st = ok && (r.lv == 0 || r.lv == 3) && S > 0;
-      const uint32_t fullm = __ballot_sync(FULL, full), stm = __ballot_sync(FULL, st);
-      const uint32_t partm = __ballot_sync(FULL, ok && !full);
-      if (full) s_ord[warp][0][__popc(fullm & below)] = (uint8_t)lane;
-      if (st) s_ord[warp][1][__popc(stm & below)] = (uint8_t)lane;
-      __syncwarp();
-      // ---- loads of the full-fold slots: (slot, merged run) pairs over the lanes
-      const int nfull = __popc(fullm);
-      for (int f = (int)lane; f < nfull * Mfull; f += 32) {
-        const int i = (int)fdiv((uint32_t)f, fdM), e = f - i * Mfull;
-        const RowSlot &q = s_rs[warp][s_ord[warp][0][i]];
-        // a range that an earlier run of the field sets, containing it, from another row of
-        // the level is skipped
-        const int32_t dd = s_idd[e];
-        const int ddy = (int16_t)(dd & 0xffff), ddz = (int16_t)(dd >> 16);
-        if (ddy != kNoCover && row_covers(s_c, q.lv, q.y + ddy, q.z + ddz, q.bxa, q.bxb)) continue;
-        const int k = s_iaf[e];
-        const bool blk = q.lv == 3;
-        const int64_t bo = s_ibo[e] + (blk ? s_fblk[k] : 0);   // staged offsets are relative to the wave origin
-        const int64_t a0 = q.lo + bo, a1 = q.hi + bo + (int64_t)s_iext[e];
-        if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
-          ++bad;
-          continue;
-        }
-        const int bsel = q.lv == 0 ? BM_W : q.lv == 1 ? BM_Y : q.lv == 2 ? BM_Z : BM_BL;
-        unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
-        uint32_t cu = 0xffffffffu;
+      const bool inner = full && Mu < Mfull && row_interior(s_c, r.lv, r.y, r.z, r.bxa, r.bxb, s_cov[1], s_cov[2]);
+      const bool blk = r.lv == 3;
+      const int bsel = r.lv == 0 ? BM_W : r.lv == 1 ? BM_Y : r.lv == 2 ? BM_Z : BM_BL;
+      // ---- loads of a full-fold row: its merged runs, [0, Mu) when it lies inside its level.
+      // The lanes walk the same run at the same time (broadcast shared-memory reads); a lane
+      // keeps its field's bitmap pointers, merges consecutive runs that end in one 64-bit
+      // unit into one red.or, and stores a page flag only when the page range moves.
+      if (__any_sync(FULL, full)) {
+        const int me = !full ? 0 : inner ? Mu : Mfull;
+        int kc = -1;
+        unsigned long long *bm = nullptr;
+        uint8_t *fl = nullptr;
+        int64_t lim = 0, fb = 0;
+        uint32_t cu = 0xffffffffu, pl0 = 1u, pl1 = 0u;
         unsigned long long cb = 0ull;
-        put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-        if (cb) atomicOr(bm + cu, cb);
-        nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-        flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
-                   (uint32_t)(a1 >> kPageShiftBytes));
-      }
-      // ---- loads of rows with fewer valid folded points than the fold (domain edge): the
-      // raw folded loads, each issued iff a valid point needs it
-      for (uint32_t pm = partm; pm; pm &= pm - 1u) {
-        const RowSlot &q = s_rs[warp][__ffs(pm) - 1];
-        const bool blk = q.lv == 3;
-        const int bsel = q.lv == 0 ? BM_W : q.lv == 1 ? BM_Y : q.lv == 2 ? BM_Z : BM_BL;
-        for (int e = (int)lane; e < L; e += 32) {
-          if ((int)s_kmin[e] >= q.kv) continue;
-          const int k = s_af[e];
-          const int64_t bo = s_boff[e] + s_forg[k][blk ? 0 : 1];
-          const int64_t a0 = q.lo + bo, a1 = q.hi + bo;
-          if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
+        for (int e = 0; e < me; ++e) {
+          const int k = s_iaf[e];
+          if (k != kc) {
+            if (cb) atomicOr(bm + cu, cb);
+            cu = 0xffffffffu;
+            cb = 0ull;
+            kc = k;
+            bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
+            fl = reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel];
+            lim = s_flim[k][blk ? 0 : 1];
+            fb = blk ? s_fblk[k] : 0;   // staged offsets are relative to the wave origin
+            pl0 = 1u;
+            pl1 = 0u;
+          }
+          const int64_t bo = s_ibo[e] + fb;
+          const int64_t a0 = r.lo + bo, a1 = r.hi + bo + (int64_t)s_iext[e];
+          if (a0 < 0 || a1 >= lim) {
             ++bad;
             continue;
           }
-          unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
-          uint32_t cu = 0xffffffffu;
-          unsigned long long cb = 0ull;
           put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-          if (cb) atomicOr(bm + cu, cb);
           nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-          flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
-                     (uint32_t)(a1 >> kPageShiftBytes));
-        }
-      }
-      // ---- stores of wave and block rows: (slot, store) pairs over the lanes; wave rows
-      // add their per-warp store sectors
-      const int nst = __popc(stm);
-      for (int f = (int)lane; f < nst * S; f += 32) {
-        const int i = (int)fdiv((uint32_t)f, fdS), j = L + (f - i * S);
-        const RowSlot &q = s_rs[warp][s_ord[warp][1][i]];
-        if ((int)s_kmin[j] >= q.kv) continue;
-        const bool blk = q.lv == 3;
-        const int k = s_af[j];
-        const int64_t bo = s_boff[j] + s_forg[k][blk ? 0 : 1];
-        const int64_t a0 = q.lo + bo, a1 = q.hi + bo;
-        if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
-          ++bad;
-          continue;
-        }
-        const int sb = blk ? BM_BS : BM_WS;
-        unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][sb]);
-        uint32_t cu = 0xffffffffu;
-        unsigned long long cb = 0ull;
-        put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-        if (cb) atomicOr(bm + cu, cb);
-        nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
-        flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][sb], (uint32_t)(a0 >> kPageShiftBytes),
-                   (uint32_t)(a1 >> kPageShiftBytes));
-        if (!blk) {
-          // the count depends on the row start only modulo 32 bytes, on t only through
-          // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
-          // rows that agree on those reuse this thread's previous count
-          const int64_t A0 = q.el0 + bo;
-          const unsigned long long key = (unsigned long long)(A0 & 31) |
-                                         ((unsigned long long)((q.t * (uint32_t)s_c.B[0]) & 31u) << 5) |
-                                         ((unsigned long long)q.bxa << 10) | ((unsigned long long)q.bxb << 37);
-          if (s_memo_key[threadIdx.x] != key) {
-            s_memo_val[threadIdx.x] =
-                (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, q.t, q.bxa, q.bxb);
-            s_memo_key[threadIdx.x] = key;
+          const uint32_t p0 = (uint32_t)(a0 >> kPageShiftBytes), p1 = (uint32_t)(a1 >> kPageShiftBytes);
+          if (p0 < pl0 || p1 > pl1) {
+            flag_pages(fl, p0, p1);
+            pl0 = p0;
+            pl1 = p1;
           }
-          sreq += s_memo_val[threadIdx.x];
+        }
+        if (cb) atomicOr(bm + cu, cb);
+      }
+      // ---- loads of rows with fewer valid folded points than the fold (domain edge): the
+      // raw folded loads, each issued iff a valid point needs it
+      if (__any_sync(FULL, ok && !full)) {
+        if (ok && !full) {
+          for (int e = 0; e < L; ++e) {
+            if ((int)s_kmin[e] >= r.kv) continue;
+            const int k = s_af[e];
+            const int64_t bo = s_boff[e] + s_forg[k][blk ? 0 : 1];
+            const int64_t a0 = r.lo + bo, a1 = r.hi + bo;
+            if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
+              ++bad;
+              continue;
+            }
+            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
+            uint32_t cu = 0xffffffffu;
+            unsigned long long cb = 0ull;
+            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+            if (cb) atomicOr(bm + cu, cb);
+            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+            flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
+                       (uint32_t)(a1 >> kPageShiftBytes));
+          }
         }
       }
-      __syncwarp();   // the batch's slots are read before the next batch overwrites them
+      // ---- stores of wave and block rows; wave rows add their per-warp store sectors
+      const bool st = ok && (r.lv == 0 || r.lv == 3) && S > 0;
+      if (__any_sync(FULL, st)) {
+        if (st) {
+          const int sb = blk ? BM_BS : BM_WS;
+          for (int j = L; j < L + S; ++j) {
+            if ((int)s_kmin[j] >= r.kv) continue;
+            const int k = s_af[j];
+            const int64_t bo = s_boff[j] + s_forg[k][blk ? 0 : 1];
+            const int64_t a0 = r.lo + bo, a1 = r.hi + bo;
+            if (a0 < 0 || a1 >= s_flim[k][blk ? 0 : 1]) {
+              ++bad;
+              continue;
+            }
+            unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][sb]);
+            uint32_t cu = 0xffffffffu;
+            unsigned long long cb = 0ull;
+            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+            if (cb) atomicOr(bm + cu, cb);
+            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+            flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][sb], (uint32_t)(a0 >> kPageShiftBytes),
+                       (uint32_t)(a1 >> kPageShiftBytes));
+            if (!blk) {
+              // the count depends on the row start only modulo 32 bytes, on t only through
+              // t * B0 modulo 32 (where the row's first warp ends) and on the block run, so
+              // rows that agree on those reuse this thread's previous count
+              const int64_t A0 = r.el0 + bo;
+              const unsigned long long key = (unsigned long long)(A0 & 31) |
+                                             ((unsigned long long)((r.t * (uint32_t)s_c.B[0]) & 31u) << 5) |
+                                             ((unsigned long long)r.bxa << 10) | ((unsigned long long)r.bxb << 37);
+              if (s_memo_key[threadIdx.x] != key) {
+                s_memo_val[threadIdx.x] =
+                    (uint32_t)row_store_sectors(A0, sxe, s_c.B[0], s_c.N[0], s_c.full_end, r.t, r.bxa, r.bxb);
+                s_memo_key[threadIdx.x] = key;
+              }
+              sreq += s_memo_val[threadIdx.x];
+            }
+          }
+        }
+      }
     }
 
     // the item's counts: per warp, then once per CTA
@@ -1749,7 +1780,7 @@ __global__ void keys_kernel(const ws_result *__restrict__ res, int n, double *__
 }
 
 // ---- launchers ---------------------------------------------------------------------
-size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 4 + 1); }
+size_t enum_dyn_smem(int iv_cap) { return (size_t)((iv_cap + 15) & ~15) * (8 + 4 + 1); }
 
 // Raises the dynamic shared-memory limit of the enumeration and row kernels (once per
 // device and size).

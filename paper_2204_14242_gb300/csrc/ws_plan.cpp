@@ -318,7 +318,9 @@ struct CompileArena {
 struct FieldFold {
   int status = WS_OK;
   std::vector<DAcc> da;
-  std::vector<DIv> iv;
+  std::vector<DIv> iv;     // merged load runs: those without a covering run first
+  int32_t n_iv_unc = 0;     // runs without a covering run
+  int16_t cov_dy = 0, cov_dz = 0;   // largest |row displacement| to a covering run
   int32_t n_load = 0, n_store = 0;
   __int128 omin = 0, omax = 0;
   int16_t cnt_load[17], cnt_store[17];
@@ -470,6 +472,19 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
       if (best >= 0) {
         out.iv[e].ddy = (int16_t)(rr[e].dy - rr[(size_t)best].dy);
         out.iv[e].ddz = (int16_t)(rr[e].dz - rr[(size_t)best].dz);
+      }
+    }
+    // runs without a covering run first: the row walk takes only those at rows whose
+    // displaced rows all lie inside the level (and all runs elsewhere)
+    std::stable_partition(out.iv.begin(), out.iv.end(), [](const DIv &v) { return v.ddy == kNoCover; });
+    out.n_iv_unc = 0;
+    out.cov_dy = out.cov_dz = 0;
+    for (const DIv &v : out.iv) {
+      if (v.ddy == kNoCover) {
+        ++out.n_iv_unc;
+      } else {
+        out.cov_dy = std::max<int16_t>(out.cov_dy, (int16_t)std::abs(v.ddy));
+        out.cov_dz = std::max<int16_t>(out.cov_dz, (int16_t)std::abs(v.ddz));
       }
     }
   }
@@ -868,6 +883,9 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.iv = (!df.wide && df.words[1] < ((int64_t)1 << 21) && std::llabs(F.stride[0]) * F.elem_bytes <= 32) ? 1 : 0;
     df.iv_begin = 0;
     df.n_iv = (int32_t)ff->iv.size();
+    df.n_iv_unc = ff->n_iv_unc;
+    df.cov_dy = ff->cov_dy;
+    df.cov_dz = ff->cov_dz;
     // per-instruction store sectors of the row walk add up the row segments of a warp,
     // exact when no two rows of one warp can touch a common sector: their starts lie
     // further apart than a row's byte span plus 31
