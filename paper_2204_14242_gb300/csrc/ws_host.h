@@ -142,9 +142,9 @@ struct ws_plan {
   std::vector<int64_t> grp_slots;        // row slots of the group's candidate
   std::vector<ws::WarpClasses> grp_classes;  // block warp classes per group (used with the row walk)
   std::vector<int64_t> grp_winstr_rows;  // modelled (warp, instruction) pairs of levels 1-3
-  // row slots per row-walk item: eight 32-slot batches for a CTA's eight warps (measured
-  // best on the three workloads; independent of the enumeration's chunk of modelled warps)
-  int32_t chunk_rows() const { return 256; }
+  // row slots per row-walk item (set by layout(): 256, 512 or 1024)
+  int32_t rows_chunk = 256;
+  int32_t chunk_rows() const { return rows_chunk; }
   std::vector<int32_t> cfg_grp_begin;
   ws::HostVec<int64_t> need_words;
   std::vector<int32_t> cfg_cf_begin;

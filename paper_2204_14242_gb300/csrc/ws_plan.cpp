@@ -1122,6 +1122,19 @@ void ws_plan::layout() {
       G.rep_mult[r] = classes ? grp_classes[g].mult[r] : (uint8_t)1;
     }
   }
+  // row slots per row-walk item: 256 (one 32-slot batch for each of a CTA's eight warps),
+  // doubled up to 1024 while every resident row-walk CTA (four per SM; a dry run without a
+  // device assumes 152 SMs) still gets at least 32 items.  Larger items cost less per slot
+  // (the mixed set's row walk 12.8 -> 12.0 ms at 1024), the small sweeps need the finer
+  // split to balance (LBM 1.33 -> 1.51 ms at 1024)
+  {
+    int64_t slots = 0;
+    for (size_t g = 0; g < hgrp.size(); ++g)
+      if (hgrp[g].rows) slots += grp_slots[g];
+    const int64_t ctas = 4 * (int64_t)(ctx ? ctx->sm_count : 152);
+    rows_chunk = 256;
+    while (rows_chunk < 1024 && slots / (2 * rows_chunk) >= 32 * ctas) rows_chunk *= 2;
+  }
   DPass cur;
   memset(&cur, 0, sizeof(cur));
   const int ng = (int)hgrp.size();
@@ -1854,7 +1867,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
     // group, plus the representative block's items, plus one counting item per chunk of
     // bitmap words per field
     size_t items = total_need / ((size_t)std::max(4, p->tune.count_words) * 4) + 1;
-    const size_t cw = (size_t)std::max(1, p->tune.chunk_warps), cr = (size_t)p->chunk_rows();
+    const size_t cw = (size_t)std::max(1, p->tune.chunk_warps), cr = 256;   // the smallest row-walk item
     for (int i = 0; i < n_cfg; ++i) {
       if (status[i] != WS_OK) continue;
       const DCfg &d = comp[i]->d;
