@@ -1476,15 +1476,15 @@ __device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, con
   acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
 }
 
-// Read-and-clear counting of the bitmaps of one pass.  Work item = (field, chunk of the
-// words of its block bitmaps or of its wave bitmaps).  The chunk is cut into pages of
+// Read-and-clear counting of the bitmaps of one pass.  Counting unit = (field, chunk of the
+// words of its block bitmaps or of its wave bitmaps); work item = consecutive units of one
+// candidate (at most kCountMaxPages pages, kCountItemUnits units), so that a CTA places the
+// many small block parts of a large batch together.  Chunks are cut into pages of
 // kPageWords words; for a field the row walk filled, only the pages it flagged are read
-// (and their flags cleared), otherwise every page.  One warp takes one page at a time:
-// each lane loads two 16-byte positions of every bitmap of the part that has the page
-// flagged (all loads in flight together), tallies sectors, lines and overlaps, and clears
-// the non-zero positions, so the bitmaps are left zeroed for the next step.
-constexpr int kCountMaxPages = kPagedChunkWords / kPageWords;
-
+// (and their flags cleared), otherwise every page.  One warp takes one page at a time: each
+// lane loads two 16-byte positions of every bitmap of the part that has the page flagged
+// (all loads in flight together), tallies sectors, lines and overlaps, and clears the
+// non-zero positions, so the bitmaps are left zeroed for the next step.
 __device__ __forceinline__ uint4 ld_v4(const uint4 *p) {
   uint4 v;
   asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];\n"
@@ -1495,9 +1495,17 @@ __device__ __forceinline__ uint4 ld_v4(const uint4 *p) {
 __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
   __shared__ long long s_item[2];   // this item and the next one (fetched while this one is counted)
   __shared__ uint32_t s_red[kCountThreads / 32][13];
-  __shared__ uint32_t s_fl[kCountMaxPages];      // per page: byte b = 1 when bitmap b of the part is read
-  __shared__ uint16_t s_pl[kCountMaxPages];      // the chunk's pages to read (any order)
+  __shared__ uint32_t s_pl[kCountMaxPages];        // pages to read: bitmap mask | unit << 4 | page << 12
   __shared__ int s_npl;
+  // the item's units: bitmap positions (16-byte units), their flags, first item page
+  __shared__ uint4 *s_ubp[kCountItemUnits][4];
+  __shared__ uint8_t *s_ufl[kCountItemUnits][4];
+  __shared__ int64_t s_uq0[kCountItemUnits];       // first 16-byte position of the chunk
+  __shared__ int64_t s_uq1[kCountItemUnits];       // end position of the chunk
+  __shared__ int32_t s_uw[kCountItemUnits];        // words of the chunk
+  __shared__ int32_t s_upg[kCountItemUnits + 1];   // first item page of each unit, then the end
+  __shared__ uint8_t s_unb[kCountItemUnits];       // bitmaps of the part (2 block, 4 wave)
+  __shared__ int s_cfg;
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
@@ -1511,65 +1519,92 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
     if (item >= a.citem_hi) break;
     long long nxt = 0;
     if (threadIdx.x == 0) nxt = a.citem_lo + (long long)atomicAdd(a.grab, 1ull);
-    const int cf = a.own[item];
-    const DField &F = a.fld[cf];
-    const int cfg = F.cfg;
-    // the field's items: chunks of its block bitmaps' words, then of its wave bitmaps'
-    const bool paged = F.pg >= 0;
-    const int64_t cw = paged ? kPagedChunkWords : a.chunk_words;
-    const int64_t kb = (F.words[0] + cw - 1) / cw;
-    const int64_t k = item - F.citem_begin;
-    const bool blk = k < kb;
-    const int64_t c0 = (blk ? k : k - kb) * cw;
-    const int64_t c1 = min(c0 + cw, blk ? F.words[0] : F.words[1]);
-    const int NB = blk ? 2 : 4;
-    const int b0 = blk ? BM_BL : BM_W;   // BL, BS | W, Y, Z, WS are consecutive bitmap indices
-    const int64_t pg0 = c0 / kPageWords;
-    const int npg = (int)((c1 - c0 + kPageWords - 1) / kPageWords);
-    uint8_t *const fl = paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) : nullptr;
-    uint4 *bp[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-      bp[b] = (b < NB && F.bm[b0 + b] >= 0) ? reinterpret_cast<uint4 *>(a.scratch + F.bm[b0 + b]) : nullptr;
-    uint32_t rd = 0;   // bitmap bytes this thread's pages take
-    // a thread per page: which bitmaps to read (flags cleared in device memory as they are
-    // taken); pages with none are dropped
-    for (int j = threadIdx.x; j < npg; j += kCountThreads) {
-      uint32_t m = 0;
-      const uint32_t pbytes = 4u * (uint32_t)min((int64_t)kPageWords, c1 - c0 - (int64_t)j * kPageWords);
+    const int u0 = a.item_unit[item], nu = a.item_unit[item + 1] - u0;
+    // ---- a thread per unit: where its chunk's bitmaps and flags lie
+    if (threadIdx.x < nu) {
+      const int t = threadIdx.x;
+      const int cf = a.units[2 * (u0 + t)];
+      const int64_t k = a.units[2 * (u0 + t) + 1];
+      const DField &F = a.fld[cf];
+      const bool paged = F.pg >= 0;
+      const int64_t cw = paged ? kPagedChunkWords : a.chunk_words;
+      const int64_t kb = (F.words[0] + cw - 1) / cw;
+      const bool blk = k < kb;
+      const int64_t c0 = (blk ? k : k - kb) * cw;
+      const int64_t c1 = min(c0 + cw, blk ? F.words[0] : F.words[1]);
+      const int NB = blk ? 2 : 4;
+      const int b0 = blk ? BM_BL : BM_W;   // BL, BS | W, Y, Z, WS are consecutive bitmap indices
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        if (b >= NB) continue;
-        bool on = bp[b] != nullptr;
-        if (paged) {
-          uint8_t *const f = fl + page_flag_off(b0 + b, F.words[0], F.words[1]) + pg0 + j;
-          const uint8_t v = *f;
-          if (v) *f = 0;
-          on = on && v != 0;
+        const bool has = b < NB && F.bm[b0 + b] >= 0;
+        s_ubp[t][b] = has ? reinterpret_cast<uint4 *>(a.scratch + F.bm[b0 + b]) : nullptr;
+        s_ufl[t][b] = has && paged ? reinterpret_cast<uint8_t *>(a.scratch + F.pg) +
+                                         page_flag_off(b0 + b, F.words[0], F.words[1]) + c0 / kPageWords
+                                   : nullptr;
+      }
+      s_uq0[t] = c0 / 4;
+      s_uq1[t] = c1 / 4;
+      s_uw[t] = (int32_t)(c1 - c0);
+      s_upg[t + 1] = (int32_t)((c1 - c0 + kPageWords - 1) / kPageWords);
+      s_unb[t] = (uint8_t)NB;
+      if (t == 0) {
+        s_cfg = F.cfg;
+        s_upg[0] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int t = 0; t < nu; ++t) s_upg[t + 1] += s_upg[t];
+    __syncthreads();
+    const int npg = s_upg[nu];
+    uint32_t rd = 0;   // bitmap bytes of the pages this thread lists
+    // ---- a thread per page: which bitmaps to read (flags cleared in device memory as they
+    // are taken); pages with none are dropped
+    for (int j = threadIdx.x; j < npg; j += kCountThreads) {
+      int lo = 0, hi = nu - 1;   // the unit holding page j: s_upg[u] <= j < s_upg[u + 1]
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_upg[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      const int u = lo, lp = j - s_upg[u];
+      const uint32_t pbytes = 4u * (uint32_t)min(kPageWords, s_uw[u] - lp * kPageWords);
+      uint32_t m = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (s_ubp[u][b] == nullptr) continue;
+        bool on = true;
+        uint8_t *const fl = s_ufl[u][b];
+        if (fl != nullptr) {
+          const uint8_t v = fl[lp];
+          if (v) fl[lp] = 0;
+          on = v != 0;
         }
         if (on) {
-          m |= 1u << (8 * b);
+          m |= 1u << b;
           rd += pbytes;
         }
       }
-      s_fl[j] = m;
-      if (m) s_pl[atomicAdd(&s_npl, 1)] = (uint16_t)j;
+      if (m) s_pl[atomicAdd(&s_npl, 1)] = m | ((uint32_t)u << 4) | ((uint32_t)lp << 12);
     }
     __syncthreads();
     uint32_t acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int npl = s_npl;
     for (int i = warp; i < npl; i += kCountThreads / 32) {
-      const int j = s_pl[i];
-      const uint32_t m = s_fl[j];
-      const int64_t q0 = (c0 + (int64_t)j * kPageWords) / 4;                    // first position of the page
-      const int np = (int)min((int64_t)(kPageWords / 4), c1 / 4 - q0);          // its positions (<= 64)
+      const uint32_t ent = s_pl[i];
+      const uint32_t m = ent & 15u;
+      const int u = (int)((ent >> 4) & 255u), lp = (int)(ent >> 12);
+      const bool blk = s_unb[u] == 2;
+      uint4 *const *const bp = s_ubp[u];
+      const int64_t q0 = s_uq0[u] + (int64_t)lp * (kPageWords / 4);           // first position of the page
+      const int np = (int)min((int64_t)(kPageWords / 4), s_uq1[u] - q0);      // its positions (<= 64)
       uint4 v[4][2];
 #pragma unroll
       for (int b = 0; b < 4; ++b)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = (int)lane + 32 * h;
-          v[b][h] = ((m >> (8 * b)) & 1u) && r < np ? ld_v4(bp[b] + q0 + r) : zero;
+          v[b][h] = ((m >> b) & 1u) && r < np ? ld_v4(bp[b] + q0 + r) : zero;
         }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -1611,7 +1646,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
       unsigned long long t = 0;
       for (int wi = 0; wi < kCountThreads / 32; ++wi) t += s_red[wi][threadIdx.x];
       const int dst = threadIdx.x < 12 ? kCountDst[threadIdx.x] : C_CBYTES;
-      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)cfg * N_COUNTERS + dst), t);
+      if (t) atomicAdd((unsigned long long *)(a.counters + (int64_t)s_cfg * N_COUNTERS + dst), t);
     }
     if (threadIdx.x == 0) {
       s_item[par ^ 1] = nxt;

@@ -30,7 +30,9 @@ struct EnumArgs {
 
 struct CountArgs {
   const DField *fld;
-  const int32_t *own;              // (candidate, field) of every counting item (global numbering)
+  const int32_t *item_unit;        // first counting unit of every counting item, then the end
+  const int32_t *units;            // counting units: (field, chunk) pairs; chunks of the block
+                                   // bitmaps' words first, then of the wave bitmaps' words
   uint32_t *scratch;
   int64_t *counters;
   unsigned long long *grab;
@@ -66,8 +68,10 @@ size_t enum_dyn_smem(int iv_cap);
 cudaError_t rows_occupancy(int iv_cap, int *blocks_per_sm);
 constexpr int kRowsThreads = 256;
 constexpr int kCountThreads = 256;   // counting kernel: threads per CTA
-constexpr int kCountMaxWords = 65536;   // most bitmap words of one counting item of a field without page flags
-constexpr int kPagedChunkWords = 262144;   // bitmap words of one counting item of a field with page flags (1024 pages)
+constexpr int kCountMaxWords = 65536;   // most bitmap words of one counting unit of a field without page flags
+constexpr int kPagedChunkWords = 262144;   // bitmap words of one counting unit of a field with page flags (1024 pages)
+constexpr int kCountMaxPages = 1024;   // most pages of one counting item (one unit or several packed)
+constexpr int kCountItemUnits = 64;    // most counting units packed into one counting item
 constexpr int kBlockPairs = 128;   // (modelled warp, instruction) pairs per representative-block item
 cudaError_t count_occupancy(int *blocks_per_sm);
 

@@ -1107,7 +1107,15 @@ void ws_plan::layout() {
   }
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
-  int64_t items = 0, ritems = 0, citems = 0, used = 0;
+  int64_t items = 0, ritems = 0, used = 0;
+  // counting units (field, chunk) as pairs, and the first unit of every counting item; an
+  // item packs consecutive units of one candidate and pass (at most kCountMaxPages pages
+  // and kCountItemUnits units), so that the many small block parts of a large batch do not
+  // each pay for a whole item
+  std::vector<int32_t> cunits, citem_unit;
+  bool c_open = false;
+  int c_cfg = -1;
+  int64_t c_pages = 0, c_units = 0;
   for (size_t g = 0; g < hgrp.size(); ++g) {
     DGroup &G = hgrp[g];
     G.iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
@@ -1145,13 +1153,14 @@ void ws_plan::layout() {
       cur.grp_hi = g;
       cur.item_hi = items;
       cur.ritem_hi = ritems;
-      cur.citem_hi = citems;
+      c_open = false;
+      cur.citem_hi = (int64_t)citem_unit.size();
       cur.words = used;
       passes.push_back(cur);
       memset(&cur, 0, sizeof(cur));
       cur.item_lo = items;
       cur.ritem_lo = ritems;
-      cur.citem_lo = citems;
+      cur.citem_lo = (int64_t)citem_unit.size();
       cur.cf_lo = G.f_begin;
       cur.grp_lo = g;
       used = 0;
@@ -1179,12 +1188,27 @@ void ws_plan::layout() {
       }
       used = o;
       f.item_begin = items;
-      f.citem_begin = citems;
-      // counting items: chunks of the block bitmaps' words, then of the wave bitmaps' words
+      // counting units: chunks of the block bitmaps' words, then of the wave bitmaps' words
       // (each chunk a whole number of pages of one part; larger chunks when only flagged
       // pages are read)
       const int64_t cw = f.pg >= 0 ? kPagedChunkWords : tune.count_words;
-      citems += ceil_div(f.words[0], cw) + ceil_div(f.words[1], cw);
+      const int64_t kb = ceil_div(f.words[0], cw), kw = ceil_div(f.words[1], cw);
+      if (c_open && f.cfg != c_cfg) c_open = false;
+      f.citem_begin = (int64_t)citem_unit.size() - (c_open ? 1 : 0);
+      for (int64_t u = 0; u < kb + kw; ++u) {
+        const int64_t c0 = (u < kb ? u : u - kb) * cw, w = u < kb ? f.words[0] : f.words[1];
+        const int64_t pages = ceil_div(std::min(cw, w - c0), (int64_t)kPageWords);
+        if (!c_open || c_pages + pages > kCountMaxPages || c_units == kCountItemUnits) {
+          citem_unit.push_back((int32_t)(cunits.size() / 2));
+          c_open = true;
+          c_pages = c_units = 0;
+        }
+        c_cfg = f.cfg;
+        cunits.push_back(G.f_begin + k);
+        cunits.push_back((int32_t)u);
+        c_pages += pages;
+        ++c_units;
+      }
     }
     // enumeration items: the representative block (exact path) in chunks of (modelled
     // warp, instruction) pairs; then chunks of the remaining modelled warps, or, for the
@@ -1201,14 +1225,16 @@ void ws_plan::layout() {
   cur.grp_hi = ng;
   cur.item_hi = items;
   cur.ritem_hi = ritems;
+  const int64_t citems = (int64_t)citem_unit.size();
   cur.citem_hi = citems;
   cur.words = used;
   if (ng > 0) passes.push_back(cur);
   item_begin_end = items;
   ritem_begin_end = ritems;
   citem_begin_end = citems;
-  // owners of the items: [enumeration | row walk | counting]
-  own.resize((size_t)(items + ritems + citems));
+  // owners of the items: [enumeration | row walk], then the counting items' first units
+  // (with an end), then the counting units as (field, chunk) pairs
+  own.resize((size_t)(items + ritems + citems + 1) + cunits.size());
   for (int g = 0; g < ng; ++g) {
     const DGroup &G = hgrp[g];
     const int64_t e1 = g + 1 < ng ? hgrp[g + 1].item_begin : items;
@@ -1216,11 +1242,9 @@ void ws_plan::layout() {
     std::fill(own.begin() + G.item_begin, own.begin() + e1, (int32_t)g);
     std::fill(own.begin() + items + G.ritem_begin, own.begin() + items + r1, (int32_t)g);
   }
-  const int nf = (int)hfld.size();
-  for (int f = 0; f < nf; ++f) {
-    const int64_t c1 = f + 1 < nf ? hfld[f + 1].citem_begin : citems;
-    std::fill(own.begin() + items + ritems + hfld[f].citem_begin, own.begin() + items + ritems + c1, (int32_t)f);
-  }
+  std::copy(citem_unit.begin(), citem_unit.end(), own.begin() + items + ritems);
+  own[(size_t)(items + ritems + citems)] = (int32_t)(cunits.size() / 2);
+  std::copy(cunits.begin(), cunits.end(), own.begin() + items + ritems + citems + 1);
 }
 
 int ws_plan::upload_fields(cudaStream_t st) {
@@ -1332,7 +1356,8 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     if ((rc = mark(2 + 3 * (int)p)) != WS_OK) return rc;
     CountArgs ca;
     ca.fld = ea.fld;
-    ca.own = ea.own_rows + ritem_begin_end;
+    ca.item_unit = ea.own_rows + ritem_begin_end;
+    ca.units = ca.item_unit + citem_begin_end + 1;
     ca.scratch = ea.scratch;
     ca.counters = ea.counters;
     ca.grab = ea.grab + 2;
@@ -1415,7 +1440,8 @@ int ws_plan::run_plain(cudaStream_t st) {
       if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
       CountArgs ca;
       ca.fld = ea.fld;
-      ca.own = ea.own_rows + ritem_begin_end;
+      ca.item_unit = ea.own_rows + ritem_begin_end;
+      ca.units = ca.item_unit + citem_begin_end + 1;
       ca.scratch = ea.scratch;
       ca.counters = counters;
       ca.grab = grab + 2;
