@@ -288,31 +288,39 @@ __device__ __forceinline__ void set_sector_range(unsigned long long *__restrict_
 
 // Adds sectors [s0, s1] to a lane's pending 64-bit unit (cu, cb), flushing it with one
 // red.or when the range leaves that unit; units the range covers entirely are written
-// directly.  The caller flushes the last pending unit.
-__device__ __forceinline__ void put_range(unsigned long long *__restrict__ bm, uint32_t &cu, unsigned long long &cb,
-                                          uint32_t s0, uint32_t s1) {
+// directly.  The caller flushes the last pending unit.  Returns the red.or issued.
+__device__ __forceinline__ uint32_t put_range(unsigned long long *__restrict__ bm, uint32_t &cu,
+                                              unsigned long long &cb, uint32_t s0, uint32_t s1) {
   const uint32_t u0 = s0 >> 6, u1 = s1 >> 6;
   const unsigned long long m0 = ~0ull << (s0 & 63u);
   const unsigned long long m1 = ~0ull >> (63u - (s1 & 63u));
+  uint32_t n = 0;
   if (u0 == u1) {
     if (u0 == cu) {
       cb |= m0 & m1;
-      return;
+      return 0;
     }
-    if (cb) atomicOr(bm + cu, cb);
+    if (cb) {
+      atomicOr(bm + cu, cb);
+      n = 1;
+    }
     cu = u0;
     cb = m0 & m1;
-    return;
+    return n;
   }
   if (u0 == cu) {
     atomicOr(bm + u0, cb | m0);
   } else {
-    if (cb) atomicOr(bm + cu, cb);
+    if (cb) {
+      atomicOr(bm + cu, cb);
+      n = 1;
+    }
     atomicOr(bm + u0, m0);
   }
   for (uint32_t u = u0 + 1; u < u1; ++u) atomicOr(bm + u, ~0ull);
   cu = u1;
   cb = m1;
+  return n + (u1 - u0);
 }
 
 // Flags the pages [p0, p1] of one bitmap as written.  The flag array starts zeroed and only
@@ -1329,7 +1337,10 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
         for (int e = 0; e < me; ++e) {
           const int k = s_iaf[e];
           if (k != kc) {
-            if (cb) atomicOr(bm + cu, cb);
+            if (cb) {
+              atomicOr(bm + cu, cb);
+              ++nred;
+            }
             cu = 0xffffffffu;
             cb = 0ull;
             kc = k;
@@ -1346,8 +1357,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             ++bad;
             continue;
           }
-          put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-          nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
+          nred += put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
           const uint32_t p0 = (uint32_t)(a0 >> kPageShiftBytes), p1 = (uint32_t)(a1 >> kPageShiftBytes);
           if (p0 < pl0 || p1 > pl1) {
             flag_pages(fl, p0, p1);
@@ -1355,7 +1365,10 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             pl1 = p1;
           }
         }
-        if (cb) atomicOr(bm + cu, cb);
+        if (cb) {
+          atomicOr(bm + cu, cb);
+          ++nred;
+        }
       }
       // ---- loads of rows with fewer valid folded points than the fold (domain edge): the
       // raw folded loads, each issued iff a valid point needs it
@@ -1373,9 +1386,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][bsel]);
             uint32_t cu = 0xffffffffu;
             unsigned long long cb = 0ull;
-            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+            nred += put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5)) + (cb ? 1u : 0u);
             if (cb) atomicOr(bm + cu, cb);
-            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
             flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][bsel], (uint32_t)(a0 >> kPageShiftBytes),
                        (uint32_t)(a1 >> kPageShiftBytes));
           }
@@ -1398,9 +1410,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             unsigned long long *const bm = reinterpret_cast<unsigned long long *>(a.scratch + s_fbm[k][sb]);
             uint32_t cu = 0xffffffffu;
             unsigned long long cb = 0ull;
-            put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
+            nred += put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5)) + (cb ? 1u : 0u);
             if (cb) atomicOr(bm + cu, cb);
-            nred += (uint32_t)(a1 >> 11) - (uint32_t)(a0 >> 11) + 1u;
             flag_pages(reinterpret_cast<uint8_t *>(a.scratch) + s_fpg[k][sb], (uint32_t)(a0 >> kPageShiftBytes),
                        (uint32_t)(a1 >> kPageShiftBytes));
             if (!blk) {
