@@ -467,7 +467,14 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
   if (threadIdx.x == 0) *m.g = a.grp[gi];
   __syncthreads();
   const DGroup &G = *m.g;
-  for (int k = threadIdx.x; k < G.f_count; k += blockDim.x) m.fk[k] = a.fld[G.f_begin + k];
+  {
+    // the group's fields, copied as 8-byte words by all threads
+    static_assert(sizeof(DField) % 8 == 0, "DField is copied as 8-byte words");
+    const int nw = G.f_count * (int)(sizeof(DField) / 8);
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.fld + G.f_begin);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(m.fk);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+  }
   const bool new_cfg = G.cfg != cur_cfg;
   if (new_cfg && threadIdx.x == 0) *m.c = a.cfg[G.cfg];
   __syncthreads();
@@ -525,8 +532,10 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
     if (kv == 0) m.gwi[lv] = wi;
   }
   __syncthreads();
-  // merged load runs, offsets relative to each field's bitmap origin
-  for (int j = threadIdx.x; j < m.ioff[G.f_count]; j += blockDim.x) {
+  // merged load runs, offsets relative to each field's bitmap origin (the enumeration kernel
+  // uses them only for groups without the row walk)
+  const int n_runs = (m.cov != nullptr || !G.rows) ? m.ioff[G.f_count] : 0;
+  for (int j = threadIdx.x; j < n_runs; j += blockDim.x) {
     int k = 0;
     while (m.ioff[k + 1] <= j) ++k;
     const DField &F = m.fk[k];
