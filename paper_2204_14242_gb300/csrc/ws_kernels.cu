@@ -644,43 +644,65 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
     if (blk) {
       // ---- representative block (Sec. 4.2, 4.3): every (warp, instruction) exactly --
       // distinct sectors per instruction (L1 requests / write-through stores), the block
-      // footprint bitmaps, and half-warp bank cycles
+      // footprint bitmaps, and half-warp bank cycles.  Each warp takes a contiguous run of
+      // the item's (class warp, instruction) pairs, instruction fastest, and keeps the class
+      // warp's thread coordinates and the field's address base while they stay the same.
       const uint32_t LS = (uint32_t)s_soff[s_g.f_count], L = (uint32_t)s_loff[s_g.f_count];
-      const int64_t np = (int64_t)s_g.n_rep * LS;
-      const int64_t p0 = kk * (int64_t)a.block_pairs, p1 = min(p0 + (int64_t)a.block_pairs, np);
+      const uint32_t np = (uint32_t)s_g.n_rep * LS;
+      const uint32_t p0 = (uint32_t)kk * (uint32_t)a.block_pairs, p1 = min(p0 + (uint32_t)a.block_pairs, np);
+      const uint32_t per = (p1 - p0 + nwarps - 1) / nwarps;
+      const uint32_t q0 = min(p0 + warp * per, p1), q1 = min(q0 + per, p1);
       const bool fast_banks = a.bank_shift >= 0;
       // with the row walk the block bitmaps are built there: count only, one warp per class
       const bool count_only = s_g.rows;
-      for (int64_t pp = p0 + warp; pp < p1; pp += nwarps) {
-        const uint32_t r = (uint32_t)(pp / LS), j = (uint32_t)(pp - (int64_t)r * LS);
-        const uint32_t mw = s_g.rep_warp[r], mult = s_g.rep_mult[r];
-        const uint32_t b = (uint32_t)s_c.rep;
-        const uint32_t bt = fdiv(b, s_c.fd_gx);
-        const uint32_t bx = b - bt * (uint32_t)s_c.g[0];
-        const uint32_t bz = fdiv(bt, s_c.fd_gy);
-        const uint32_t by = bt - bz * (uint32_t)s_c.g[1];
-        const uint32_t tid = mw * 32u + lane;
-        const bool exists = tid < (uint32_t)s_c.T;
-        const uint32_t tc = exists ? s_tc[tid] : 0u;
-        const int32_t x = (int32_t)bx * s_c.B[0] + (int32_t)(tc & 1023u);
-        int32_t y = (int32_t)by * s_c.B[1] + (int32_t)((tc >> 10) & 1023u);
-        int32_t z = (int32_t)bz * s_c.B[2] + (int32_t)(tc >> 20);
-        const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
-        if (faxis == 1) y *= fold;
-        if (faxis == 2) z *= fold;
-        const bool valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
-        int kv = 0;
-        if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+      const uint32_t b = (uint32_t)s_c.rep;
+      const uint32_t bt = fdiv(b, s_c.fd_gx);
+      const uint32_t bx = b - bt * (uint32_t)s_c.g[0];
+      const uint32_t bz = fdiv(bt, s_c.fd_gy);
+      const uint32_t by = bt - bz * (uint32_t)s_c.g[1];
+      const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
+      uint32_t r = q0 / max(LS, 1u), j = q0 - r * LS;
+      int cur_r = -1, cur_k = -1;
+      uint32_t mult = 0;
+      int32_t x = 0, y = 0, z = 0;
+      int kv = 0;
+      bool valid = false;
+      int64_t rbase = 0, rlim = 0;
+      for (uint32_t pp = q0; pp < q1; ++pp) {
+        if ((int)r != cur_r) {
+          cur_r = (int)r;
+          cur_k = -1;
+          const uint32_t mw = s_g.rep_warp[r];
+          mult = s_g.rep_mult[r];
+          const uint32_t tid = mw * 32u + lane;
+          const bool exists = tid < (uint32_t)s_c.T;
+          const uint32_t tc = exists ? s_tc[tid] : 0u;
+          x = (int32_t)bx * s_c.B[0] + (int32_t)(tc & 1023u);
+          y = (int32_t)by * s_c.B[1] + (int32_t)((tc >> 10) & 1023u);
+          z = (int32_t)bz * s_c.B[2] + (int32_t)(tc >> 20);
+          if (faxis == 1) y *= fold;
+          if (faxis == 2) z *= fold;
+          valid = exists && x < s_c.N[0] && y < s_c.N[1] && z < s_c.N[2];
+          kv = 0;
+          if (valid) kv = faxis == 1 ? min(fold, s_c.N[1] - y) : faxis == 2 ? min(fold, s_c.N[2] - z) : 1;
+        }
         if (j == 0u) {
           if (s_g.first_of_cfg) acc_lb += mult * __reduce_add_sync(FULL, (uint32_t)kv);
           acc_addr += mult * __reduce_add_sync(FULL, (uint32_t)s_gad[0][kv]);
           acc_wi += mult * (uint32_t)s_gwi[0];
         }
-        const DField &F = s_fk[s_af[j]];
+        const int k = s_af[j];
+        if (k != cur_k) {
+          cur_k = k;
+          const DField &F = s_fk[k];
+          const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
+          rbase = F.base + (int64_t)F.esize * lin - 32 * F.lo[0];
+          rlim = F.words[0] << 10;
+        }
+        const DField &F = s_fk[k];
         const bool act = valid && (int)s_kmin[j] < kv;
-        const int64_t lin = F.stride[0] * x + F.stride[1] * y + F.stride[2] * z;
-        const int64_t rr = F.base + (int64_t)F.esize * lin - 32 * F.lo[0] + s_boff[j];
-        const bool inside = rr >= 0 && rr < (F.words[0] << 10);
+        const int64_t rr = rbase + s_boff[j];
+        const bool inside = rr >= 0 && rr < rlim;
         uint32_t nsec;
         if (count_only) nsec = warp_distinct_sectors((uint32_t)rr, act && inside);
         else nsec = bitmap_insert(a.scratch + F.bm[j < L ? BM_BL : BM_BS], rr, act, lane, F.words[0], bad);
@@ -691,6 +713,10 @@ __global__ void __launch_bounds__(512, 2) enum_kernel(EnumArgs a) {
                                                (uint32_t)(a.banks - 1), (uint32_t)a.pair_dist);
         else
           acc_bank += mult * bank_cycles_warp(rr + 32 * F.lo[0], act, lane, a.banks, a.bank_bytes, a.pair_dist);
+        if (++j == LS) {
+          j = 0;
+          ++r;
+        }
       }
     }
     for (uint32_t mw = mw0 + warp; mw < mw1; mw += nwarps) {
