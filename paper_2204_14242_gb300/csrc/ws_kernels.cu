@@ -101,6 +101,22 @@ __device__ int bank_cycles_rel32(uint32_t rel, bool act, uint32_t lane, uint32_t
                                  uint32_t pair_dist) {
   const uint32_t word = rel >> bshift, bank = word & bmask;
   const uint32_t actm = __ballot_sync(FULL, act);
+  {
+    // every lane active and each half warp's words ascending by 0 or 1 from lane to lane:
+    // its unique words are the consecutive words first .. last, which fall in distinct
+    // banks round-robin, so a group spanning less than the pairing distance costs
+    // ceil(count / banks) cycles
+    const uint32_t prev = __shfl_up_sync(FULL, word, 1);
+    const bool step = (lane & 15u) == 0u || word - prev <= 1u;
+    if (__all_sync(FULL, act && step)) {
+      const uint32_t w0 = __shfl_sync(FULL, word, lane & 16u), w1 = __shfl_sync(FULL, word, (lane & 16u) | 15u);
+      if (((w1 - w0) << bshift) < pair_dist) {
+        const uint32_t nb = bmask + 1u, n = w1 - w0 + 1u;
+        const uint32_t c = (n + nb - 1u) / nb;
+        return (int)(__shfl_sync(FULL, c, 0) + __shfl_sync(FULL, c, 16));
+      }
+    }
+  }
   const uint32_t halfm = lane < 16 ? 0x0000ffffu : 0xffff0000u;
   const uint32_t same = __match_any_sync(FULL, word) & actm & halfm;
   const bool uniq = act && lane == (uint32_t)(__ffs(same) - 1);
@@ -256,6 +272,14 @@ __device__ __forceinline__ void lpa_walk_count(const uint32_t *__restrict__ tbas
 
 // Exact distinct sectors of one instruction whose lanes hold relative addresses r.
 __device__ __forceinline__ uint32_t warp_distinct_sectors(uint32_t r, bool act) {
+  {
+    // every lane active and sectors not decreasing from lane to lane: equal sectors are
+    // neighbours, so the distinct ones are the lanes that start a new sector
+    const uint32_t sec = r >> 5, prev = __shfl_up_sync(FULL, sec, 1);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (__all_sync(FULL, act && (lane == 0u || sec >= prev)))
+      return (uint32_t)__popc(__ballot_sync(FULL, lane == 0u || sec != prev));
+  }
   const uint32_t word = r >> 10, bit = 1u << ((r >> 5) & 31u);
   uint32_t pending = __ballot_sync(FULL, act), cnt = 0;
   while (pending) {
