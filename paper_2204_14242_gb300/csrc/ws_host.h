@@ -142,8 +142,14 @@ struct ws_plan {
   std::vector<int64_t> grp_slots;        // row slots of the group's candidate
   std::vector<ws::WarpClasses> grp_classes;  // block warp classes per group (used with the row walk)
   std::vector<int64_t> grp_winstr_rows;  // modelled (warp, instruction) pairs of levels 1-3
-  // row slots per row-walk item (set by layout(): 256, 512 or 1024)
+  // work-item sizes set by layout(): row slots per row-walk item (256, 512 or 1024),
+  // (warp, instruction) pairs per representative-block item, counting units per counting
+  // item.  plain_layout selects the finest ones (256, kPlainBlockPairs, 1) for the plain
+  // form, whose launches serve one candidate at a time.
+  bool plain_layout = false;
   int32_t rows_chunk = 256;
+  int32_t block_pairs = 128;
+  int32_t count_pack = 1;
   int32_t chunk_rows() const { return rows_chunk; }
   std::vector<int32_t> cfg_grp_begin;
   ws::HostVec<int64_t> need_words;
@@ -186,6 +192,7 @@ struct ws_plan {
   cudaEvent_t ready = nullptr;
   int wait_ready(cudaStream_t st);
   int run_plain(cudaStream_t st);
+  int run_plain_launches(cudaStream_t st);
   int execute(int mode, cudaStream_t st);
 };
 

@@ -72,6 +72,7 @@ constexpr int kCountMaxWords = 65536;   // most bitmap words of one counting uni
 constexpr int kPagedChunkWords = 262144;   // bitmap words of one counting unit of a field with page flags (1024 pages)
 constexpr int kCountMaxPages = 1024;   // most pages of one counting item (one unit or several packed)
 constexpr int kCountItemUnits = 64;    // most counting units packed into one counting item
+constexpr int kPlainBlockPairs = 128;   // the same in the plain form (one candidate per launch)
 constexpr int kBlockPairs = 512;   // (modelled warp, instruction) pairs per representative-block item (mixed set: 4.4 ms of enumeration against 5.5 with 128)
 cudaError_t count_occupancy(int *blocks_per_sm);
 

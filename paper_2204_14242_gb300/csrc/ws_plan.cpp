@@ -1141,8 +1141,10 @@ void ws_plan::layout() {
       if (hgrp[g].rows) slots += grp_slots[g];
     const int64_t ctas = 4 * (int64_t)(ctx ? ctx->sm_count : 152);
     rows_chunk = 256;
-    while (rows_chunk < 1024 && slots / (2 * rows_chunk) >= 32 * ctas) rows_chunk *= 2;
+    while (!plain_layout && rows_chunk < 1024 && slots / (2 * rows_chunk) >= 32 * ctas) rows_chunk *= 2;
   }
+  block_pairs = plain_layout ? kPlainBlockPairs : kBlockPairs;
+  count_pack = plain_layout ? 1 : kCountItemUnits;
   DPass cur;
   memset(&cur, 0, sizeof(cur));
   const int ng = (int)hgrp.size();
@@ -1198,7 +1200,7 @@ void ws_plan::layout() {
       for (int64_t u = 0; u < kb + kw; ++u) {
         const int64_t c0 = (u < kb ? u : u - kb) * cw, w = u < kb ? f.words[0] : f.words[1];
         const int64_t pages = ceil_div(std::min(cw, w - c0), (int64_t)kPageWords);
-        if (!c_open || c_pages + pages > kCountMaxPages || c_units == kCountItemUnits) {
+        if (!c_open || c_pages + pages > kCountMaxPages || c_units == count_pack) {
           citem_unit.push_back((int32_t)(cunits.size() / 2));
           c_open = true;
           c_pages = c_units = 0;
@@ -1215,7 +1217,7 @@ void ws_plan::layout() {
     // row walk, chunks of row slots as items of the row kernel
     G.item_begin = items;
     G.ritem_begin = ritems;
-    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div((int64_t)G.n_rep * G.acc_count, kBlockPairs))
+    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div((int64_t)G.n_rep * G.acc_count, block_pairs))
                                 : 0;
     items += G.n0_items;
     if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
@@ -1343,7 +1345,7 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
     ea.bank_bytes = hw.bank_bytes;
     ea.pair_dist = hw.pair_dist_bytes;
     ea.bank_shift = bank_shift();
-    ea.block_pairs = kBlockPairs;
+    ea.block_pairs = block_pairs;
     if (P.item_hi > P.item_lo) {
       CU(launch_enum(ea, grid_for(tune.enum_threads, P.item_hi - P.item_lo, false), tune.enum_threads, st));
       ++launches;
@@ -1397,6 +1399,27 @@ int ws_plan::enqueue(cudaStream_t st, std::vector<cudaEvent_t> *ev, ws_profile *
 // Plain form: for every candidate, its own enumeration / counting / model launches,
 // then a synchronisation; the ranking runs once at the end.
 int ws_plan::run_plain(cudaStream_t st) {
+  // the plain form launches each candidate's kernels by themselves: the finest work items
+  // spread one candidate over CTAs (the larger items of a big batch pay off only when the
+  // whole batch shares the launches)
+  plain_layout = true;
+  layout();
+  int rc = upload_fields(st);
+  if (rc == WS_OK) rc = run_plain_launches(st);
+  plain_layout = false;
+  layout();
+  const int rc2 = upload_fields(st);
+  // the uploads read the host arrays, which the next layout rewrites
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == WS_OK) rc = rc2;
+  if (rc == WS_OK && e != cudaSuccess) {
+    set_error(cudaGetErrorString(e));
+    rc = WS_ECUDA;
+  }
+  return rc;
+}
+
+int ws_plan::run_plain_launches(cudaStream_t st) {
   CU(cudaMemsetAsync(dev(d_counters), 0, counters_bytes, st));
   int64_t *counters = (int64_t *)((char *)dev(d_counters) + grab_bytes);
   unsigned long long *grab = (unsigned long long *)dev(d_counters);
@@ -1435,7 +1458,7 @@ int ws_plan::run_plain(cudaStream_t st) {
       ea.bank_bytes = hw.bank_bytes;
       ea.pair_dist = hw.pair_dist_bytes;
       ea.bank_shift = bank_shift();
-      ea.block_pairs = kBlockPairs;
+      ea.block_pairs = block_pairs;
       if (it_hi > it_lo) CU(launch_enum(ea, grid_for(tune.enum_threads, it_hi - it_lo, false), tune.enum_threads, st));
       if (rt_hi > rt_lo) CU(launch_rows(ea, grid_rows(rt_hi - rt_lo), st));
       CountArgs ca;
@@ -1899,9 +1922,11 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
       const DCfg &d = comp[i]->d;
       for (const DField &f : comp[i]->f)
         items += 3 + (size_t)d.lev_end[3] / cw + (size_t)d.rows_slot_end[3] / cr +
-                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kBlockPairs;
+                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kPlainBlockPairs;
     }
-    dsc += 4 * items;
+    // an item or counting unit takes at most three table entries (a counting unit: its
+    // (field, chunk) pair and its item's first unit)
+    dsc += 4 * 3 * items;
   }
   const size_t avail = avail_fn(dsc, total_need);
   size_t scratch = std::min(total_need, avail);
@@ -2345,7 +2370,7 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
 // stream while part k runs on the caller's stream.  Results are per candidate, so the parts
 // give the same results as one plan; the ranking runs once over all results.  Returns
 // WS_ENOMEM (the caller then runs one plan) when the parts do not fit the arena together or
-// a part's share of it is too small for a field that the whole arena could hold.  Parts of
+// the parts' scratch is too small for a field that the whole arena could hold.  Parts of
 // fewer than kPipeMin candidates lose more on the device (launches, tails) than the overlap
 // gains (measured on GB300: 755 candidates in 3 parts 2.0 ms against 1.8 ms in one plan;
 // 20,000 mixed candidates 99 ms against 107 ms).
@@ -2354,7 +2379,12 @@ static constexpr int kPipeMin = 2048, kPipeParts = 3;
 static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out, int32_t *order_out,
                               cudaStream_t st) {
-  ctx_reclaim(ctx);
+  // The parts run one after another on `st`, and the counting kernel leaves the bitmaps
+  // zeroed, so they share one scratch: the context's kept one, allocated (three fifths of
+  // the free arena) and zeroed by the first estimate that needs it, reused as it is by the
+  // next ones.  When another estimate holds it, each part takes its own share.
+  std::unique_lock<std::mutex> kept(ctx->oneshot_mu, std::try_to_lock);
+  if (!kept.owns_lock()) ctx_reclaim(ctx);
   const int parts = std::min(kPipeParts, n_cfg / kPipeMin);
   const size_t rb = (size_t)n_cfg * sizeof(ws_result);
   Arena &ar = *ctx->arena;
@@ -2366,9 +2396,33 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
   cudaError_t e = cudaSuccess;
   if (o_res < 0 || o_keys < 0 || o_ord < 0 || o_rnk < 0 || o_seg < 0) rc = WS_ENOMEM;
   char *b = ar.base;
-  // the parts share what the arena holds for scratch
-  const size_t cap = rc == WS_OK ? std::max<size_t>(ar.largest_free() / (size_t)(parts + 1), 16) : 0;
-  if (rc == WS_OK) {
+  int64_t shared = -1;
+  size_t shared_bytes = 0;
+  if (rc == WS_OK && kept.owns_lock()) {
+    if (ctx->oneshot_off < 0 || ctx->oneshot_bytes < ((size_t)1 << 30)) {
+      if (ctx->oneshot_off >= 0) ar.release(ctx->oneshot_off);
+      ctx->oneshot_off = -1;
+      ctx->oneshot_bytes = 0;
+      const size_t want = (ar.largest_free() / 5 * 3) & ~(size_t)255;
+      const int64_t o = want >= ((size_t)64 << 20) ? ar.alloc(want) : -1;
+      if (o >= 0) {
+        ctx->oneshot_off = o;
+        ctx->oneshot_bytes = want;
+        ctx->oneshot_dirty = true;
+      }
+    }
+    if (ctx->oneshot_off >= 0) {
+      shared = ctx->oneshot_off;
+      shared_bytes = ctx->oneshot_bytes;
+      if (ctx->oneshot_dirty) {
+        e = cudaMemsetAsync(b + shared, 0, shared_bytes, ctx->upload_stream);
+        if (e == cudaSuccess) ctx->oneshot_dirty = false;
+      }
+    }
+  }
+  // without the shared scratch the parts share what the arena holds
+  const size_t cap = rc == WS_OK && shared < 0 ? std::max<size_t>(ar.largest_free() / (size_t)(parts + 1), 16) : 0;
+  if (rc == WS_OK && e == cudaSuccess) {
     const int32_t seg[2] = {0, n_cfg};
     e = cudaMemcpyAsync(b + o_seg, seg, sizeof(seg), cudaMemcpyHostToDevice, ctx->upload_stream);
   }
@@ -2376,7 +2430,7 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
     const int lo = (int)((int64_t)n_cfg * k / parts), hi = (int)((int64_t)n_cfg * (k + 1) / parts);
     ws_plan *p = nullptr;
     rc = plan_create_impl(ctx, cfgs + lo, hi - lo, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, cap, &p,
-                          ctx->upload_stream, -1, 0);
+                          ctx->upload_stream, shared, shared_bytes);
     if (rc != WS_OK) break;
     plans.push_back(p);
     cudaEvent_t ev;
@@ -2415,6 +2469,8 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
     set_error(std::string("pipelined estimate: ") + cudaGetErrorString(e));
     rc = WS_ECUDA;
   }
+  // a failed step may leave bits set in the shared scratch (its kernels are done: synchronised above)
+  if (shared >= 0 && rc != WS_OK) ctx->oneshot_dirty = true;
   std::vector<int> short_of_room;   // candidates a part had too little scratch for
   for (int i = 0; rc == WS_OK && i < n_cfg; ++i)
     if (out[i].status == WS_ENOMEM) short_of_room.push_back(i);
@@ -2426,6 +2482,12 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
   // then the caller runs the batch as one plan instead.  A field too large for the whole
   // arena keeps its WS_ENOMEM (one plan would refuse it as well).
   if (!short_of_room.empty()) {
+    // the one plan may use the room the shared scratch takes now
+    if (shared >= 0) {
+      ar.release(ctx->oneshot_off);
+      ctx->oneshot_off = -1;
+      ctx->oneshot_bytes = 0;
+    }
     const size_t room = ar.largest_free();
     for (int i : short_of_room) {
       size_t dsc = 0, scr = 0, mf = 0;
