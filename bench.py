@@ -50,8 +50,8 @@ UNIT = "configs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # default: 30 timed steps of the headline set on the GPU (about 1.5 s); 3 for the
-    # reference arm, whose steps take seconds each
+    # default: 100 timed steps of the headline set on the GPU (about 2.2 s, some 40 clock
+    # samples); 3 for the reference arm, whose steps take seconds each
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -491,7 +491,7 @@ def record(B, meas, n_cfg, world, profs_key=None, peaks=None):
 def main():
     args = parse()
     if args.steps is None:
-        args.steps = 3 if args.impl == "reference" else 30
+        args.steps = 3 if args.impl == "reference" else 100
     if args.impl == "reference":
         run_reference(args)
         return
