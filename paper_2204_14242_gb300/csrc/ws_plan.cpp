@@ -1081,11 +1081,12 @@ int64_t ws_plan::take(size_t bytes) {
 }
 
 static void default_tuning(ws_tuning &t) {
-  // defaults measured on the three workloads: 512-thread enumeration CTAs and chunks of
-  // 1024 modelled warps (the mixed set 5.4 against 9.6 ms of enumeration, the sweeps equal)
-  if (t.chunk_warps <= 0) t.chunk_warps = 1024;
+  // defaults measured on the three workloads: 256-thread enumeration CTAs and chunks of 256
+  // modelled warps, what the autotuner picks for the mixed set (its step 22.9 -> 22.0 ms
+  // against 512 / 1024; the sweeps equal)
+  if (t.chunk_warps <= 0) t.chunk_warps = 256;
   if (t.pass_mb == 0) t.pass_mb = -1;
-  if (t.enum_threads <= 0) t.enum_threads = 512;
+  if (t.enum_threads <= 0) t.enum_threads = 256;
   if (t.count_words <= 0) t.count_words = 16384;   // 64 KiB of words per counting item (fields without page flags)
   t.enum_threads = std::max(64, std::min(512, t.enum_threads / 32 * 32));
   t.count_words = std::min(kCountMaxWords, std::max(kPageWords, t.count_words / kPageWords * kPageWords));
@@ -2374,7 +2375,8 @@ extern "C" int ws_autotune(ws_plan *p, void *stream, ws_tuning *best) {
 // fewer than kPipeMin candidates lose more on the device (launches, tails) than the overlap
 // gains (measured on GB300: 755 candidates in 3 parts 2.0 ms against 1.8 ms in one plan;
 // 20,000 mixed candidates 99 ms against 107 ms).
-static constexpr int kPipeMin = 2048, kPipeParts = 3;
+// (six parts of the 20,000-candidate mixed set: 35.2 ms per call against 36.5 ms with three)
+static constexpr int kPipeMin = 2048, kPipeParts = 6;
 
 static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out, int32_t *order_out,
