@@ -108,7 +108,10 @@ struct DField {
   int32_t rows_ok;        // stores: the row segments of one warp never share a sector
   int32_t level_mask;     // levels served: 1 the representative block, 2 wave + y / z sets
   int32_t n_iv_unc;       // merged load intervals without a covering run (they come first)
+  int32_t n_iv_zc;        // those covered from another z row (they come next; the rest last)
   int16_t cov_dy, cov_dz; // largest |row displacement| from an interval to its covering run
+  int16_t cov_dy_y;       // largest |ddy| of the intervals covered within their z row
+  int16_t pad16;
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };

@@ -478,9 +478,11 @@ struct StageSmem {
   int64_t *ibo;                  // merged load runs: offset relative to the field's bitmap origin
   uint32_t *iext;                //   extent
   uint8_t *iaf;                  //   field
-  // row walk only (else null): the runs without a covering run of all fields first, then the
-  // others; idst[0][k] / idst[1][k] = first staged slot of field k's runs of each kind;
-  // cov = {runs without a covering run, largest |ddy|, largest |ddz| of the others}
+  // row walk only (else null): the runs without a covering run of all fields first, then
+  // those covered from another z row, then those covered within their z row; idst[j][k] =
+  // first staged slot of field k's runs of kind j; cov = {runs without a covering run,
+  // largest |ddy|, largest |ddz| of the covered runs, runs of the first two kinds, largest
+  // |ddy| of the last kind}
   int32_t (*idst)[kMaxGroupFields];
   int32_t *cov;
 };
@@ -522,7 +524,7 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
     }
     m.ioff[G.f_count] = o;
     if (m.cov) {
-      int u = 0, dy = 0, dz = 0;
+      int u = 0, dy = 0, dz = 0, dyy = 0;
       for (int k = 0; k < G.f_count; ++k)
         if (G.iv) {
           m.idst[0][k] = u;
@@ -530,17 +532,26 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
           if (m.fk[k].n_iv_unc < m.fk[k].n_iv) {
             dy = max(dy, (int)m.fk[k].cov_dy);
             dz = max(dz, (int)m.fk[k].cov_dz);
+            dyy = max(dyy, (int)m.fk[k].cov_dy_y);
           }
         }
       int c = u;
       for (int k = 0; k < G.f_count; ++k)
         if (G.iv) {
           m.idst[1][k] = c;
-          c += m.fk[k].n_iv - m.fk[k].n_iv_unc;
+          c += m.fk[k].n_iv_zc;
+        }
+      const int uz = c;
+      for (int k = 0; k < G.f_count; ++k)
+        if (G.iv) {
+          m.idst[2][k] = c;
+          c += m.fk[k].n_iv - m.fk[k].n_iv_unc - m.fk[k].n_iv_zc;
         }
       m.cov[0] = u;
       m.cov[1] = dy;
       m.cov[2] = dz;
+      m.cov[3] = uz;
+      m.cov[4] = dyy;
     }
   }
   for (int t = threadIdx.x; t < 34; t += blockDim.x) {
@@ -565,7 +576,10 @@ __device__ bool stage_group(const EnumArgs &a, int gi, int cur_cfg, const StageS
     const DField &F = m.fk[k];
     const int jj = j - m.ioff[k];
     const DIv v = a.iv[F.iv_begin + jj];
-    const int d = !m.cov ? j : jj < F.n_iv_unc ? m.idst[0][k] + jj : m.idst[1][k] + (jj - F.n_iv_unc);
+    const int d = !m.cov                          ? j
+                  : jj < F.n_iv_unc               ? m.idst[0][k] + jj
+                  : jj < F.n_iv_unc + F.n_iv_zc   ? m.idst[1][k] + (jj - F.n_iv_unc)
+                                                  : m.idst[2][k] + (jj - F.n_iv_unc - F.n_iv_zc);
     m.ibo[d] = v.boff + F.base - 32 * F.lo[1];
     m.iext[d] = v.ext;
     m.iaf[d] = (uint8_t)k;
@@ -1224,8 +1238,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int32_t s_loff[kMaxGroupFields + 1];
   __shared__ int32_t s_soff[kMaxGroupFields + 1];
   __shared__ int32_t s_ioff[kMaxGroupFields + 1];
-  __shared__ int32_t s_idst[2][kMaxGroupFields];
-  __shared__ int32_t s_cov[3];
+  __shared__ int32_t s_idst[3][kMaxGroupFields];
+  __shared__ int32_t s_cov[5];
   __shared__ uint8_t s_af[kMaxFoldedAccesses];
   __shared__ int64_t s_boff[kMaxFoldedAccesses];
   __shared__ uint8_t s_kmin[kMaxFoldedAccesses];
@@ -1295,8 +1309,11 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
     const int Mfull = s_ioff[s_g.f_count];
     // runs [0, Mu) have no covering run; at rows inside their level (row_interior) only those
     // are taken, when they are at most half of all runs (otherwise the test of each row costs
-    // more than the runs it saves: all runs are taken everywhere)
+    // more than the runs it saves: all runs are taken everywhere).  Runs [Muz, Mfull) are
+    // covered from their own z row: at rows whose rows displaced in y alone lie inside the
+    // level (a wave is often thinner in z than the z displacements) [0, Muz) are taken.
     const int Mu = 2 * s_cov[0] <= Mfull ? s_cov[0] : Mfull;
+    const int Muz = s_cov[3];
     const DField &F0 = s_fk[0];
     const int64_t es = F0.esize, sxe = es * F0.stride[0];
     const int32_t faxis = s_c.fold_axis, fold = s_c.fold;
@@ -1379,6 +1396,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       }
       const bool full = ok && r.kv == fold;
       const bool inner = full && Mu < Mfull && row_interior(s_c, r.lv, r.y, r.z, r.bxa, r.bxb, s_cov[1], s_cov[2]);
+      const bool inner_y = full && !inner && Muz < Mfull && row_interior(s_c, r.lv, r.y, r.z, r.bxa, r.bxb, s_cov[4], 0);
       const bool blk = r.lv == 3;
       const int bsel = r.lv == 0 ? BM_W : r.lv == 1 ? BM_Y : r.lv == 2 ? BM_Z : BM_BL;
       // ---- loads of a full-fold row: its merged runs, [0, Mu) when it lies inside its level.
@@ -1386,7 +1404,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       // keeps its field's bitmap pointers, merges consecutive runs that end in one 64-bit
       // unit into one red.or, and stores a page flag only when the page range moves.
       if (__any_sync(FULL, full)) {
-        const int me = !full ? 0 : inner ? Mu : Mfull;
+        const int me = !full ? 0 : inner ? Mu : inner_y ? Muz : Mfull;
         int kc = -1;
         unsigned long long *bm = nullptr;
         uint8_t *fl = nullptr;
@@ -1524,24 +1542,29 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
 __constant__ int kCountDst[12] = {C_BLK_LS, C_BLK_LL, C_BLK_SS, C_BLK_SL, C_W_LS, C_W_LL,
                                   C_Y_LINES, C_Z_LINES, C_OV_Y, C_OV_Z, C_W_SS, C_W_SL};
 
-__device__ __forceinline__ uint32_t lines_of(uint32_t x) {
-  // bit i <-> sector lo + i with lo a multiple of 32: nibbles are 128 B lines
+// Lines of four consecutive bitmap words: bit i of a word <-> sector lo + i with lo a
+// multiple of 32, so each nibble is one 128 B line; a word's nibbles are reduced to one bit
+// each (bit 4k) and the four words' bits interleaved into one word for a single popcount.
+__device__ __forceinline__ uint32_t line_bits(uint32_t x) {
   uint32_t t = x | (x >> 1);
   t |= t >> 2;
-  return __popc(t & 0x11111111u);
+  return t & 0x11111111u;
+}
+__device__ __forceinline__ uint32_t lines4(const uint4 &v) {
+  return __popc(line_bits(v.x) | (line_bits(v.y) << 1) | (line_bits(v.z) << 2) | (line_bits(v.w) << 3));
 }
 
 __device__ __forceinline__ bool nz(const uint4 &v) { return (v.x | v.y | v.z | v.w) != 0u; }
 
 __device__ __forceinline__ void tally_sectors_lines(uint32_t &sec, uint32_t &lin, const uint4 &v) {
   sec += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-  lin += lines_of(v.x) + lines_of(v.y) + lines_of(v.z) + lines_of(v.w);
+  lin += lines4(v);
 }
 
 __device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z) {
   tally_sectors_lines(acc[4], acc[5], w);
-  acc[6] += lines_of(y.x) + lines_of(y.y) + lines_of(y.z) + lines_of(y.w);
-  acc[7] += lines_of(z.x) + lines_of(z.y) + lines_of(z.z) + lines_of(z.w);
+  acc[6] += lines4(y);
+  acc[7] += lines4(z);
   acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
   acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
 }

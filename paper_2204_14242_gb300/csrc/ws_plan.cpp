@@ -320,7 +320,9 @@ struct FieldFold {
   std::vector<DAcc> da;
   std::vector<DIv> iv;     // merged load runs: those without a covering run first
   int32_t n_iv_unc = 0;     // runs without a covering run
+  int32_t n_iv_zc = 0;      // runs whose covering run lies in another z row (they come next)
   int16_t cov_dy = 0, cov_dz = 0;   // largest |row displacement| to a covering run
+  int16_t cov_dy_y = 0;     // largest |ddy| of the runs covered within their z row (they come last)
   int32_t n_load = 0, n_store = 0;
   __int128 omin = 0, omax = 0;
   int16_t cnt_load[17], cnt_store[17];
@@ -453,39 +455,67 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
     // one of the same dc whose x offsets contain its own, at a row displacement a thread row
     // can make (a multiple of the fold along the folding axis); the nearest one is taken
     const size_t nr = rr.size() <= 512 ? rr.size() : 0;   // bounded host work: no covering beyond 512 runs
-    auto rank = [&](size_t e) { return std::make_tuple(std::llabs(rr[e].dy) + std::llabs(rr[e].dz), rr[e].dz, rr[e].dy, e); };
+    // per run, in flat arrays: its rank (|dy| + |dz|, dz, dy, run) packed into one integer
+    // (|dy|, |dz| <= 65535 + 15 fit 18 bits after a 2^17 bias, their sum 18 bits, the run
+    // index (< 512) 9 bits), its row offsets and their residues along the folding axis, and
+    // its x offsets; runs of more than one row cannot cover or be covered
+    static thread_local std::vector<int64_t> rk, ry, rz, rres, rxlo, rxhi, rdc;
+    for (auto *v : {&rk, &ry, &rz, &rres, &rxlo, &rxhi, &rdc}) v->resize(nr);
+    const int64_t fm = fold_axis == 0 ? 1 : fold;
+    for (size_t e = 0; e < nr; ++e) {
+      const RunRow &r = rr[e];
+      rk[e] = r.one_row ? (int64_t)(((uint64_t)(std::llabs(r.dy) + std::llabs(r.dz)) << 45) |
+                                    ((uint64_t)(r.dz + (1 << 17)) << 27) | ((uint64_t)(r.dy + (1 << 17)) << 9) |
+                                    (uint64_t)e)
+                        : INT64_MAX;
+      ry[e] = r.dy;
+      rz[e] = r.dz;
+      const int64_t ax = fold_axis == 1 ? r.dy : fold_axis == 2 ? r.dz : 0;
+      rres[e] = ((ax % fm) + fm) % fm;
+      rxlo[e] = r.dxlo;
+      rxhi[e] = r.dxhi;
+      rdc[e] = r.dc;
+    }
+    // the covering run of e: among the runs of lower rank with the same dc whose x offsets
+    // contain its own, at a row displacement a thread row can make (a multiple of the fold
+    // along the folding axis, below 32767 in y and z), the nearest one (the first of the
+    // nearest in run order): the smallest (displacement, run) score
     for (size_t e = 0; e < nr; ++e) {
       if (!rr[e].one_row) continue;
-      int64_t best = -1, best_d = 0;
+      const int64_t ke = rk[e], ye = ry[e], ze = rz[e], re = rres[e], xlo = rxlo[e], xhi = rxhi[e], dce = rdc[e];
+      int64_t best_score = INT64_MAX;
       for (size_t f = 0; f < nr; ++f) {
-        if (f == e || !rr[f].one_row || !(rank(f) < rank(e)) || rr[f].dc != rr[e].dc) continue;
-        if (rr[f].dxlo > rr[e].dxlo || rr[f].dxhi < rr[e].dxhi) continue;
-        const int64_t ddy = rr[e].dy - rr[f].dy, ddz = rr[e].dz - rr[f].dz;
-        if ((fold_axis == 1 && ddy % fold != 0) || (fold_axis == 2 && ddz % fold != 0)) continue;
-        if (std::llabs(ddy) >= 32767 || std::llabs(ddz) >= 32767) continue;
-        const int64_t d = std::llabs(ddy) + std::llabs(ddz);
-        if (best < 0 || d < best_d) {
-          best = (int64_t)f;
-          best_d = d;
-        }
+        const int64_t ddy = ye - ry[f], ddz = ze - rz[f];
+        const int64_t ay = ddy < 0 ? -ddy : ddy, az = ddz < 0 ? -ddz : ddz;
+        const bool ok = (rk[f] < ke) & (rdc[f] == dce) & (rxlo[f] <= xlo) & (rxhi[f] >= xhi) & (rres[f] == re) &
+                        (ay < 32767) & (az < 32767);
+        const int64_t score = ok ? (((ay + az) << 9) | (int64_t)f) : INT64_MAX;
+        best_score = score < best_score ? score : best_score;
       }
-      if (best >= 0) {
-        out.iv[e].ddy = (int16_t)(rr[e].dy - rr[(size_t)best].dy);
-        out.iv[e].ddz = (int16_t)(rr[e].dz - rr[(size_t)best].dz);
+      if (best_score != INT64_MAX) {
+        const size_t best = (size_t)(best_score & 511);
+        out.iv[e].ddy = (int16_t)(rr[e].dy - rr[best].dy);
+        out.iv[e].ddz = (int16_t)(rr[e].dz - rr[best].dz);
       }
     }
-    // runs without a covering run first: the row walk takes only those at rows whose
-    // displaced rows all lie inside the level (and all runs elsewhere)
-    std::stable_partition(out.iv.begin(), out.iv.end(), [](const DIv &v) { return v.ddy == kNoCover; });
-    out.n_iv_unc = 0;
-    out.cov_dy = out.cov_dz = 0;
+    // runs without a covering run first, then those covered from another z row, then those
+    // covered within their own z row (ddz == 0): the row walk takes only the first kind at
+    // rows whose displaced rows all lie inside the level, the first two kinds at rows whose
+    // rows displaced in y alone do, and all runs elsewhere
+    auto kind = [](const DIv &v) { return v.ddy == kNoCover ? 0 : v.ddz != 0 ? 1 : 2; };
+    std::stable_sort(out.iv.begin(), out.iv.end(), [&](const DIv &p, const DIv &q) { return kind(p) < kind(q); });
+    out.n_iv_unc = out.n_iv_zc = 0;
+    out.cov_dy = out.cov_dz = out.cov_dy_y = 0;
     for (const DIv &v : out.iv) {
-      if (v.ddy == kNoCover) {
+      const int kd = kind(v);
+      if (kd == 0) {
         ++out.n_iv_unc;
-      } else {
-        out.cov_dy = std::max<int16_t>(out.cov_dy, (int16_t)std::abs(v.ddy));
-        out.cov_dz = std::max<int16_t>(out.cov_dz, (int16_t)std::abs(v.ddz));
+        continue;
       }
+      if (kd == 1) ++out.n_iv_zc;
+      else out.cov_dy_y = std::max<int16_t>(out.cov_dy_y, (int16_t)std::abs(v.ddy));
+      out.cov_dy = std::max<int16_t>(out.cov_dy, (int16_t)std::abs(v.ddy));
+      out.cov_dz = std::max<int16_t>(out.cov_dz, (int16_t)std::abs(v.ddz));
     }
   }
   // issued accesses of a thread with kv valid folded points: those with kmin < kv
@@ -884,8 +914,10 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
     df.iv_begin = 0;
     df.n_iv = (int32_t)ff->iv.size();
     df.n_iv_unc = ff->n_iv_unc;
+    df.n_iv_zc = ff->n_iv_zc;
     df.cov_dy = ff->cov_dy;
     df.cov_dz = ff->cov_dz;
+    df.cov_dy_y = ff->cov_dy_y;
     // per-instruction store sectors of the row walk add up the row segments of a warp,
     // exact when no two rows of one warp can touch a common sector: their starts lie
     // further apart than a row's byte span plus 31

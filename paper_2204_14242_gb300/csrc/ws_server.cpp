@@ -200,8 +200,9 @@ bool admit(ws_server *s, std::unique_lock<std::mutex> &lk) {
   return true;
 }
 
-// Retires finished steps.  Called with the lock held.
-void retire(ws_server *s) {
+// Retires finished steps.  Called with the lock held.  Returns the steps retired.
+int retire(ws_server *s) {
+  int n_retired = 0;
   for (size_t k = 0; k < s->inflight.size();) {
     Step *st = s->inflight[k];
     if (!st->finished) {
@@ -234,17 +235,20 @@ void retire(ws_server *s) {
     sl.busy = false;
     delete st;
     s->inflight.erase(s->inflight.begin() + k);
+    ++n_retired;
   }
   s->stats.bytes_in_use = (int64_t)s->pool->used();
   s->stats.peak_bytes = (int64_t)s->pool->peak;
+  return n_retired;
 }
 
 void worker_main(ws_server *s) {
   cudaSetDevice(s->ctx->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    retire(s);
-    if (!s->inflight.empty() || !s->queue.empty()) s->cv_done.notify_all();
+    // wake the pollers whenever requests completed, including the last step of a burst
+    // (the server then goes idle and nothing else would wake them before their deadline)
+    if (retire(s) > 0) s->cv_done.notify_all();
     bool launched = false;
     if (!s->stop && !s->paused)
       while (admit(s, lk)) launched = true;
