@@ -112,6 +112,8 @@ struct DField {
   int16_t cov_dy, cov_dz; // largest |row displacement| from an interval to its covering run
   int16_t cov_dy_y;       // largest |ddy| of the intervals covered within their z row
   int16_t pad16;
+  int32_t zshift;         // 1: the z set's sectors are the wave's moved by whole lines (loads)
+  int32_t zc_lo, zc_hi;   // zshift: sectors (from the wave origin) bounding the wave's addresses
   int16_t cnt_load[17];   // folded loads issued by a thread with kv valid points
   int16_t cnt_store[17];  // folded stores likewise
 };

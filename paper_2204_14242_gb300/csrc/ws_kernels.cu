@@ -1255,6 +1255,7 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
   __shared__ int64_t s_flim[kMaxGroupFields][2];
   __shared__ int64_t s_fblk[kMaxGroupFields];
   __shared__ int64_t s_forg[kMaxGroupFields][2];
+  __shared__ uint32_t s_fzc[kMaxGroupFields][2];                 // z-set clip window (sectors)
   __shared__ unsigned long long s_acc[kRowsThreads / 32][5];     // per warp: the item's counts
   __shared__ int s_batch;                                         // next batch of 32 slots of the item
   extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -1292,7 +1293,11 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
           s_flim[k][b] = F.words[b] << 10;
           s_forg[k][b] = F.base - 32 * F.lo[b];
         }
-        if (b == 0) s_fblk[k] = 32 * (F.lo[1] - F.lo[0]);
+        if (b == 0) {
+          s_fblk[k] = 32 * (F.lo[1] - F.lo[0]);
+          s_fzc[k][0] = F.zshift ? (uint32_t)F.zc_lo : 0u;
+          s_fzc[k][1] = F.zshift ? (uint32_t)F.zc_hi : 0xffffffffu;
+        }
       }
       __syncthreads();
     }
@@ -1402,14 +1407,16 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
       // ---- loads of a full-fold row: its merged runs, [0, Mu) when it lies inside its level.
       // The lanes walk the same run at the same time (broadcast shared-memory reads); a lane
       // keeps its field's bitmap pointers, merges consecutive runs that end in one 64-bit
-      // unit into one red.or, and stores a page flag only when the page range moves.
+      // unit into one red.or, and stores a page flag only when the page range moves.  The
+      // z-set ranges of a field whose z set is the wave moved by whole lines are clipped to
+      // the wave's address range: the counts take only their sectors that meet the wave.
       if (__any_sync(FULL, full)) {
         const int me = !full ? 0 : inner ? Mu : inner_y ? Muz : Mfull;
         int kc = -1;
         unsigned long long *bm = nullptr;
         uint8_t *fl = nullptr;
         int64_t lim = 0, fb = 0;
-        uint32_t cu = 0xffffffffu, pl0 = 1u, pl1 = 0u;
+        uint32_t cu = 0xffffffffu, pl0 = 1u, pl1 = 0u, zlo = 0u, zhi = 0xffffffffu;
         unsigned long long cb = 0ull;
         for (int e = 0; e < me; ++e) {
           const int k = s_iaf[e];
@@ -1427,6 +1434,8 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             fb = blk ? s_fblk[k] : 0;   // staged offsets are relative to the wave origin
             pl0 = 1u;
             pl1 = 0u;
+            zlo = r.lv == 2 ? s_fzc[k][0] : 0u;
+            zhi = r.lv == 2 ? s_fzc[k][1] : 0xffffffffu;
           }
           const int64_t bo = s_ibo[e] + fb;
           const int64_t a0 = r.lo + bo, a1 = r.hi + bo + (int64_t)s_iext[e];
@@ -1434,8 +1443,11 @@ __global__ void __launch_bounds__(256, 4) rows_kernel(EnumArgs a) {
             ++bad;
             continue;
           }
-          nred += put_range(bm, cu, cb, (uint32_t)(a0 >> 5), (uint32_t)(a1 >> 5));
-          const uint32_t p0 = (uint32_t)(a0 >> kPageShiftBytes), p1 = (uint32_t)(a1 >> kPageShiftBytes);
+          const uint32_t s0 = max((uint32_t)(a0 >> 5), zlo), s1 = min((uint32_t)(a1 >> 5), zhi);
+          if (s0 > s1) continue;
+          nred += put_range(bm, cu, cb, s0, s1);
+          constexpr int kPageShiftSectors = kPageShiftBytes - 5;
+          const uint32_t p0 = s0 >> kPageShiftSectors, p1 = s1 >> kPageShiftSectors;
           if (p0 < pl0 || p1 > pl1) {
             flag_pages(fl, p0, p1);
             pl0 = p0;
@@ -1561,10 +1573,12 @@ __device__ __forceinline__ void tally_sectors_lines(uint32_t &sec, uint32_t &lin
   lin += lines4(v);
 }
 
-__device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z) {
+// zs: the z set is the wave moved by whole lines (its bitmap holds only the sectors that can
+// meet the wave), so its lines are the wave's
+__device__ __forceinline__ void tally_wave(uint32_t acc[12], const uint4 &w, const uint4 &y, const uint4 &z, bool zs) {
   tally_sectors_lines(acc[4], acc[5], w);
   acc[6] += lines4(y);
-  acc[7] += lines4(z);
+  acc[7] += lines4(zs ? w : z);
   acc[8] += __popc(w.x & y.x) + __popc(w.y & y.y) + __popc(w.z & y.z) + __popc(w.w & y.w);
   acc[9] += __popc(w.x & z.x & ~y.x) + __popc(w.y & z.y & ~y.y) + __popc(w.z & z.z & ~y.z) + __popc(w.w & z.w & ~y.w);
 }
@@ -1598,6 +1612,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
   __shared__ int32_t s_uw[kCountItemUnits];        // words of the chunk
   __shared__ int32_t s_upg[kCountItemUnits + 1];   // first item page of each unit, then the end
   __shared__ uint8_t s_unb[kCountItemUnits];       // bitmaps of the part (2 block, 4 wave)
+  __shared__ uint8_t s_uzs[kCountItemUnits];       // the field's z set is its wave moved by whole lines
   __shared__ int s_cfg;
   const uint32_t lane = threadIdx.x & 31u;
   const int warp = threadIdx.x >> 5;
@@ -1640,6 +1655,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
       s_uw[t] = (int32_t)(c1 - c0);
       s_upg[t + 1] = (int32_t)((c1 - c0 + kPageWords - 1) / kPageWords);
       s_unb[t] = (uint8_t)NB;
+      s_uzs[t] = (uint8_t)(F.zshift != 0);
       if (t == 0) {
         s_cfg = F.cfg;
         s_upg[0] = 0;
@@ -1687,7 +1703,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
       const uint32_t ent = s_pl[i];
       const uint32_t m = ent & 15u;
       const int u = (int)((ent >> 4) & 255u), lp = (int)(ent >> 12);
-      const bool blk = s_unb[u] == 2;
+      const bool blk = s_unb[u] == 2, zs = s_uzs[u] != 0;
       uint4 *const *const bp = s_ubp[u];
       const int64_t q0 = s_uq0[u] + (int64_t)lp * (kPageWords / 4);           // first position of the page
       const int np = (int)min((int64_t)(kPageWords / 4), s_uq1[u] - q0);      // its positions (<= 64)
@@ -1713,7 +1729,7 @@ __global__ void __launch_bounds__(kCountThreads, 4) count_kernel(CountArgs a) {
           }
         } else {
           if (nz(v[0][h]) | nz(v[1][h]) | nz(v[2][h])) {
-            tally_wave(acc, v[0][h], v[1][h], v[2][h]);
+            tally_wave(acc, v[0][h], v[1][h], v[2][h], zs);
 #pragma unroll
             for (int b = 0; b < 3; ++b)
               if (nz(v[b][h])) bp[b][q] = zero;

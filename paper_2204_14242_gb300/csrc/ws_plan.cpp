@@ -747,6 +747,15 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       z_first = best;
     }
   }
+  // The z set is the wave moved back by one block slab (every point z - B2 * fz) when it is
+  // the whole shifted wave (the wave lies beyond the first slab, spans at most one slab and
+  // ends before the y set begins) and every point of the wave lies inside the domain in z:
+  // then the same points are valid in both and every thread issues the same accesses, so a
+  // field's z-set addresses are its wave addresses less esize * stride_z * B2 * fz bytes.
+  const int64_t slab = g[0] * g[1];
+  const bool z_is_shifted_wave = s >= slab && weff <= slab && z_lo == s - slab && z_hi == s + weff - slab &&
+                                 (y_hi <= y_lo || z_hi <= y_lo) &&
+                                 ((s + weff - 1) / slab + 1) * c.B[2] * fz <= c.N[2];
   d.y_dist = y_first >= 0 ? s - y_first : 0;
   d.z_dist = z_first >= 0 ? s - z_first : 0;
   const int64_t wpb = d.wpb;
@@ -797,6 +806,16 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
 
   // point boxes (valid points only) of the block level and of wave + y + z
   int64_t pb_lo[2][3], pb_hi[2][3];
+  int64_t pw_lo[3], pw_hi[3];   // the wave's own point box
+  {
+    int64_t bl2[3], bh2[3];
+    block_box(s, s + weff, g, bl2, bh2);
+    for (int k = 0; k < 3; ++k) {
+      const int64_t f = (k == 1 ? fy : k == 2 ? fz : 1) * c.B[k];
+      pw_lo[k] = bl2[k] * f;
+      pw_hi[k] = std::min<int64_t>(c.N[k] - 1, (bh2[k] + 1) * f - 1);
+    }
+  }
   {
     int64_t bl[3] = {rep % g[0], (rep / g[0]) % g[1], rep / (g[0] * g[1])};
     for (int k = 0; k < 3; ++k) {
@@ -901,6 +920,32 @@ static int compile_config(const ws_config &c, const ws_field *fld, int n_fld, co
       df.words[lv] = words;
     }
     const bool has_l = df.n_load > 0, has_s = df.n_store > 0;
+    // z set = wave moved by a multiple of 128 bytes: its sector set is the wave's moved by
+    // whole lines, so it has the wave's line count, and only its sectors inside the wave's
+    // address range can meet the wave (the row walk clips the z set's ranges to it)
+    df.zshift = 0;
+    df.zc_lo = 0;
+    df.zc_hi = -1;
+    if (z_is_shifted_wave && mask == 3 && has_l &&
+        ((__int128)F.elem_bytes * F.stride[2] * c.B[2] * fz) % 128 == 0) {
+      __int128 pmin = 0, pmax = 0;
+      for (int k = 0; k < 3; ++k) {
+        const __int128 a0 = (__int128)F.stride[k] * pw_lo[k], a1 = (__int128)F.stride[k] * pw_hi[k];
+        pmin += std::min(a0, a1);
+        pmax += std::max(a0, a1);
+      }
+      const __int128 wmin = (__int128)df.base + (__int128)F.elem_bytes * (pmin + omin);
+      const __int128 wmax = (__int128)df.base + (__int128)F.elem_bytes * (pmax + omax);
+      const __int128 s0 = floor_div128(wmin, 32) - df.lo[1], s1 = floor_div128(wmax, 32) - df.lo[1];
+      df.zshift = 1;
+      if (s0 >= 0 && s1 < ((__int128)1 << 31) && s0 <= s1) {
+        df.zc_lo = (int32_t)s0;
+        df.zc_hi = (int32_t)s1;
+      } else {
+        df.zc_lo = 0;   // no clipping (the row walk does not take such a field)
+        df.zc_hi = INT32_MAX;
+      }
+    }
     df.mw_block = d.lev_end[0];
     df.mw_end = !(mask & 2) ? d.lev_end[0] : has_l ? d.lev_end[3] : d.lev_end[1];
     df.first_of_cfg = first;
