@@ -288,6 +288,9 @@ struct Compiled {
   std::pmr::vector<int64_t> need_words;  // bitmap words per field
   size_t dsc_bytes = 0;             // descriptor bytes of its fields, lists and groups
   size_t need_sum = 0, need_max = 0;  // bitmap bytes of all its fields / of its largest
+  size_t items_est = 0;             // bound on its work items (owner table entries)
+  int64_t n_acc_own = 0, n_iv_own = 0;  // list entries of its fields that no other candidate shares
+  bool any_shared = false;          // some field's lists may be shared with other candidates
 };
 
 // Upstream of the compile arenas: large blocks from the host block cache.
@@ -455,45 +458,49 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
     // one of the same dc whose x offsets contain its own, at a row displacement a thread row
     // can make (a multiple of the fold along the folding axis); the nearest one is taken
     const size_t nr = rr.size() <= 512 ? rr.size() : 0;   // bounded host work: no covering beyond 512 runs
-    // per run, in flat arrays: its rank (|dy| + |dz|, dz, dy, run) packed into one integer
-    // (|dy|, |dz| <= 65535 + 15 fit 18 bits after a 2^17 bias, their sum 18 bits, the run
-    // index (< 512) 9 bits), its row offsets and their residues along the folding axis, and
-    // its x offsets; runs of more than one row cannot cover or be covered
-    static thread_local std::vector<int64_t> rk, ry, rz, rres, rxlo, rxhi, rdc;
-    for (auto *v : {&rk, &ry, &rz, &rres, &rxlo, &rxhi, &rdc}) v->resize(nr);
+    // The covering run of a run e: among the runs of lower rank (|dy| + |dz|, dz, dy, run)
+    // with the same dc whose x offsets contain its own, at a row displacement a thread row
+    // can make (a multiple of the fold along the folding axis, below 32767 in y and z), the
+    // nearest one, the first of the nearest in run order.  Only one-row runs take part.  They
+    // are visited in rank order, each scanning those before it; the smallest (displacement,
+    // run) score picks the cover.  The rank packs into one integer: |dy|, |dz| <= 65535 + 15
+    // fit 18 bits after a 2^17 bias, their sum 18 bits, the run index (< 512) 9 bits.
+    static thread_local std::vector<int64_t> rk, ry, rz, rres, rxlo, rxhi, rdc, ridx;
+    rk.clear();
+    for (size_t e = 0; e < nr; ++e)
+      if (rr[e].one_row)
+        rk.push_back((int64_t)(((uint64_t)(std::llabs(rr[e].dy) + std::llabs(rr[e].dz)) << 45) |
+                               ((uint64_t)(rr[e].dz + (1 << 17)) << 27) | ((uint64_t)(rr[e].dy + (1 << 17)) << 9) |
+                               (uint64_t)e));
+    std::sort(rk.begin(), rk.end());
+    const size_t no = rk.size();
+    for (auto *v : {&ry, &rz, &rres, &rxlo, &rxhi, &rdc, &ridx}) v->resize(no);
     const int64_t fm = fold_axis == 0 ? 1 : fold;
-    for (size_t e = 0; e < nr; ++e) {
+    for (size_t i = 0; i < no; ++i) {
+      const size_t e = (size_t)(rk[i] & 511);
       const RunRow &r = rr[e];
-      rk[e] = r.one_row ? (int64_t)(((uint64_t)(std::llabs(r.dy) + std::llabs(r.dz)) << 45) |
-                                    ((uint64_t)(r.dz + (1 << 17)) << 27) | ((uint64_t)(r.dy + (1 << 17)) << 9) |
-                                    (uint64_t)e)
-                        : INT64_MAX;
-      ry[e] = r.dy;
-      rz[e] = r.dz;
+      ridx[i] = (int64_t)e;
+      ry[i] = r.dy;
+      rz[i] = r.dz;
       const int64_t ax = fold_axis == 1 ? r.dy : fold_axis == 2 ? r.dz : 0;
-      rres[e] = ((ax % fm) + fm) % fm;
-      rxlo[e] = r.dxlo;
-      rxhi[e] = r.dxhi;
-      rdc[e] = r.dc;
+      rres[i] = ((ax % fm) + fm) % fm;
+      rxlo[i] = r.dxlo;
+      rxhi[i] = r.dxhi;
+      rdc[i] = r.dc;
     }
-    // the covering run of e: among the runs of lower rank with the same dc whose x offsets
-    // contain its own, at a row displacement a thread row can make (a multiple of the fold
-    // along the folding axis, below 32767 in y and z), the nearest one (the first of the
-    // nearest in run order): the smallest (displacement, run) score
-    for (size_t e = 0; e < nr; ++e) {
-      if (!rr[e].one_row) continue;
-      const int64_t ke = rk[e], ye = ry[e], ze = rz[e], re = rres[e], xlo = rxlo[e], xhi = rxhi[e], dce = rdc[e];
+    for (size_t i = 1; i < no; ++i) {
+      const int64_t ye = ry[i], ze = rz[i], re = rres[i], xlo = rxlo[i], xhi = rxhi[i], dce = rdc[i];
       int64_t best_score = INT64_MAX;
-      for (size_t f = 0; f < nr; ++f) {
-        const int64_t ddy = ye - ry[f], ddz = ze - rz[f];
+      for (size_t j = 0; j < i; ++j) {
+        const int64_t ddy = ye - ry[j], ddz = ze - rz[j];
         const int64_t ay = ddy < 0 ? -ddy : ddy, az = ddz < 0 ? -ddz : ddz;
-        const bool ok = (rk[f] < ke) & (rdc[f] == dce) & (rxlo[f] <= xlo) & (rxhi[f] >= xhi) & (rres[f] == re) &
-                        (ay < 32767) & (az < 32767);
-        const int64_t score = ok ? (((ay + az) << 9) | (int64_t)f) : INT64_MAX;
+        const bool ok = (rdc[j] == dce) & (rxlo[j] <= xlo) & (rxhi[j] >= xhi) & (rres[j] == re) & (ay < 32767) &
+                        (az < 32767);
+        const int64_t score = ok ? (((ay + az) << 9) | ridx[j]) : INT64_MAX;
         best_score = score < best_score ? score : best_score;
       }
       if (best_score != INT64_MAX) {
-        const size_t best = (size_t)(best_score & 511);
+        const size_t e = (size_t)ridx[i], best = (size_t)(best_score & 511);
         out.iv[e].ddy = (int16_t)(rr[e].dy - rr[best].dy);
         out.iv[e].ddz = (int16_t)(rr[e].dz - rr[best].dz);
       }
@@ -503,7 +510,14 @@ static void compile_field_fold(const ws_field &F, const ws_access *acc, int n_ac
     // rows whose displaced rows all lie inside the level, the first two kinds at rows whose
     // rows displaced in y alone do, and all runs elsewhere
     auto kind = [](const DIv &v) { return v.ddy == kNoCover ? 0 : v.ddz != 0 ? 1 : 2; };
-    std::stable_sort(out.iv.begin(), out.iv.end(), [&](const DIv &p, const DIv &q) { return kind(p) < kind(q); });
+    {
+      static thread_local std::vector<DIv> tmp;
+      tmp.clear();
+      for (int kd = 0; kd < 3; ++kd)
+        for (const DIv &v : out.iv)
+          if (kind(v) == kd) tmp.push_back(v);
+      out.iv.swap(tmp);
+    }
     out.n_iv_unc = out.n_iv_zc = 0;
     out.cov_dy = out.cov_dz = out.cov_dy_y = 0;
     for (const DIv &v : out.iv) {
@@ -1173,41 +1187,58 @@ static void default_tuning(ws_tuning &t) {
 }
 
 // Numbers work items and cuts passes for the current tuning.
+// Runs fn(lo, hi) over [0, n) in chunks on the host pool (defined with the pool below).
+static void parallel_chunks(int64_t n, int64_t chunk, const std::function<void(int64_t, int64_t)> &fn);
+
+// Counting units of field f (chunks of its block bitmaps' words, then of its wave bitmaps'
+// words; each chunk a whole number of pages of one part, larger chunks when only flagged
+// pages are read): calls unit(u, pages) for each.
+template <class F>
+static void for_count_units(const DField &f, bool paged, int count_words, F unit) {
+  const int64_t cw = paged ? kPagedChunkWords : count_words;
+  const int64_t kb = ceil_div(f.words[0], cw), kw = ceil_div(f.words[1], cw);
+  for (int64_t u = 0; u < kb + kw; ++u) {
+    const int64_t c0 = (u < kb ? u : u - kb) * cw, w = u < kb ? f.words[0] : f.words[1];
+    unit(u, ceil_div(std::min(cw, w - c0), (int64_t)kPageWords));
+  }
+}
+
 void ws_plan::layout() {
   passes.clear();
+  const int ng = (int)hgrp.size();
+  // per group (in parallel): walk flags, representative warps, bitmap words the pass holds
+  // (need_words bound them, with page flags only for the row walk) and the work items of
+  // its kernels
+  std::vector<int64_t> gneed((size_t)ng, 0), gwords((size_t)ng, 0);
+  parallel_chunks(ng, 512, [&](int64_t lo, int64_t hi) {
+    for (int64_t g = lo; g < hi; ++g) {
+      DGroup &G = hgrp[(size_t)g];
+      G.iv = grp_iv_ok[(size_t)g] && tune.walk != WS_WALK_ADDRESS;
+      G.rows = grp_rows_ok[(size_t)g] && tune.walk == WS_WALK_INTERVAL;
+      // the row walk builds the block bitmaps, so the block path counts one warp per
+      // class; otherwise it inserts every warp
+      const bool classes = G.rows && (G.levels & 1) && grp_classes[(size_t)g].n > 0;
+      const int wpb = (int)G.mw_block;
+      G.n_rep = classes ? grp_classes[(size_t)g].n : wpb;
+      for (int r = 0; r < G.n_rep; ++r) {
+        G.rep_warp[r] = classes ? grp_classes[(size_t)g].warp[r] : (uint8_t)r;
+        G.rep_mult[r] = classes ? grp_classes[(size_t)g].mult[r] : (uint8_t)1;
+      }
+      for (int k = 0; k < G.f_count; ++k) {
+        const DField &f = hfld[(size_t)(G.f_begin + k)];
+        gneed[(size_t)g] += need_words[(size_t)(G.f_begin + k)];
+        if (f.n_load > 0) gwords[(size_t)g] += f.words[0] + 3 * f.words[1];
+        if (f.n_store > 0) gwords[(size_t)g] += f.words[0] + f.words[1];
+        if (G.rows) gwords[(size_t)g] += page_flag_words(f.words[0], f.words[1]);
+      }
+    }
+  });
   // pass capacity: the tuned pass size, never below the largest field group, never
   // above the scratch the plan holds
-  std::vector<int64_t> gneed(hgrp.size(), 0);
   int64_t max_need = 0;
-  for (size_t g = 0; g < hgrp.size(); ++g) {
-    for (int k = 0; k < hgrp[g].f_count; ++k) gneed[g] += need_words[hgrp[g].f_begin + k];
-    max_need = std::max(max_need, gneed[g]);
-  }
+  for (int64_t v : gneed) max_need = std::max(max_need, v);
   int64_t cap = scratch_words;
   if (tune.pass_mb > 0) cap = std::min(cap, std::max(max_need, (int64_t)tune.pass_mb << 18));
-  int64_t items = 0, ritems = 0, used = 0;
-  // counting units (field, chunk) as pairs, and the first unit of every counting item; an
-  // item packs consecutive units of one candidate and pass (at most kCountMaxPages pages
-  // and kCountItemUnits units), so that the many small block parts of a large batch do not
-  // each pay for a whole item
-  std::vector<int32_t> cunits, citem_unit;
-  bool c_open = false;
-  int c_cfg = -1;
-  int64_t c_pages = 0, c_units = 0;
-  for (size_t g = 0; g < hgrp.size(); ++g) {
-    DGroup &G = hgrp[g];
-    G.iv = grp_iv_ok[g] && tune.walk != WS_WALK_ADDRESS;
-    G.rows = grp_rows_ok[g] && tune.walk == WS_WALK_INTERVAL;
-    // the row walk builds the block bitmaps, so the block path counts one warp per
-    // class; otherwise it inserts every warp
-    const bool classes = G.rows && (G.levels & 1) && grp_classes[g].n > 0;
-    const int wpb = (int)G.mw_block;
-    G.n_rep = classes ? grp_classes[g].n : wpb;
-    for (int r = 0; r < G.n_rep; ++r) {
-      G.rep_warp[r] = classes ? grp_classes[g].warp[r] : (uint8_t)r;
-      G.rep_mult[r] = classes ? grp_classes[g].mult[r] : (uint8_t)1;
-    }
-  }
   // row slots per row-walk item: 256 (one 32-slot batch for each of a CTA's eight warps),
   // doubled up to 1024 while every resident row-walk CTA (four per SM; a dry run without a
   // device assumes 152 SMs) still gets at least 32 items.  Larger items cost less per slot
@@ -1215,116 +1246,165 @@ void ws_plan::layout() {
   // split to balance (LBM 1.33 -> 1.51 ms at 1024)
   {
     int64_t slots = 0;
-    for (size_t g = 0; g < hgrp.size(); ++g)
-      if (hgrp[g].rows) slots += grp_slots[g];
+    for (int g = 0; g < ng; ++g)
+      if (hgrp[(size_t)g].rows) slots += grp_slots[(size_t)g];
     const int64_t ctas = 4 * (int64_t)(ctx ? ctx->sm_count : 152);
     rows_chunk = 256;
     while (!plain_layout && rows_chunk < 1024 && slots / (2 * rows_chunk) >= 32 * ctas) rows_chunk *= 2;
   }
   block_pairs = plain_layout ? kPlainBlockPairs : kBlockPairs;
   count_pack = plain_layout ? 1 : kCountItemUnits;
-  DPass cur;
-  memset(&cur, 0, sizeof(cur));
-  const int ng = (int)hgrp.size();
-  for (int g = 0; g < ng; ++g) {
-    DGroup &G = hgrp[g];
-    if (used + gneed[g] > cap && g > cur.grp_lo) {
-      cur.cf_hi = G.f_begin;
-      cur.grp_hi = g;
-      cur.item_hi = items;
-      cur.ritem_hi = ritems;
-      c_open = false;
-      cur.citem_hi = (int64_t)citem_unit.size();
-      cur.words = used;
-      passes.push_back(cur);
-      memset(&cur, 0, sizeof(cur));
-      cur.item_lo = items;
-      cur.ritem_lo = ritems;
-      cur.citem_lo = (int64_t)citem_unit.size();
-      cur.cf_lo = G.f_begin;
-      cur.grp_lo = g;
-      used = 0;
+  // passes (a group starts a new one when its words would overflow the capacity), each
+  // group's first scratch word in its pass, and the enumeration and row-walk items: the
+  // representative block (exact path) in chunks of (modelled warp, instruction) pairs; then
+  // chunks of the remaining modelled warps, or, for the row walk, chunks of row slots
+  std::vector<int64_t> gbase((size_t)ng, 0);
+  std::vector<int32_t> gpass((size_t)ng, 0);
+  int64_t items = 0, ritems = 0;
+  {
+    DPass cur;
+    memset(&cur, 0, sizeof(cur));
+    int64_t used = 0;
+    for (int g = 0; g < ng; ++g) {
+      DGroup &G = hgrp[(size_t)g];
+      if (used + gneed[(size_t)g] > cap && g > cur.grp_lo) {
+        cur.cf_hi = G.f_begin;
+        cur.grp_hi = g;
+        cur.item_hi = items;
+        cur.ritem_hi = ritems;
+        cur.words = used;
+        passes.push_back(cur);
+        memset(&cur, 0, sizeof(cur));
+        cur.item_lo = items;
+        cur.ritem_lo = ritems;
+        cur.cf_lo = G.f_begin;
+        cur.grp_lo = g;
+        used = 0;
+      }
+      gpass[(size_t)g] = (int32_t)passes.size();
+      gbase[(size_t)g] = used;
+      used += gwords[(size_t)g];
+      G.item_begin = items;
+      G.ritem_begin = ritems;
+      G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div((int64_t)G.n_rep * G.acc_count, block_pairs))
+                                  : 0;
+      items += G.n0_items;
+      if (G.rows) ritems += ceil_div(grp_slots[(size_t)g], chunk_rows());
+      else if (G.levels & 2) items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
     }
-    for (int k = 0; k < G.f_count; ++k) {
-      DField &f = hfld[G.f_begin + k];
-      int64_t o = used;
-      const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
-      for (int b = 0; b < N_BITMAPS; ++b) f.bm[b] = -1;
-      if (has_l) {
-        f.bm[BM_BL] = o; o += f.words[0];
-        f.bm[BM_W] = o; o += f.words[1];
-        f.bm[BM_Y] = o; o += f.words[1];
-        f.bm[BM_Z] = o; o += f.words[1];
-      }
-      if (has_s) {
-        f.bm[BM_BS] = o; o += f.words[0];
-        f.bm[BM_WS] = o; o += f.words[1];
-      }
-      // the row walk flags the pages it writes, so the counting reads only those
-      f.pg = -1;
-      if (G.rows) {
-        f.pg = o;
-        o += page_flag_words(f.words[0], f.words[1]);
-      }
-      used = o;
-      f.item_begin = items;
-      // counting units: chunks of the block bitmaps' words, then of the wave bitmaps' words
-      // (each chunk a whole number of pages of one part; larger chunks when only flagged
-      // pages are read)
-      const int64_t cw = f.pg >= 0 ? kPagedChunkWords : tune.count_words;
-      const int64_t kb = ceil_div(f.words[0], cw), kw = ceil_div(f.words[1], cw);
-      if (c_open && f.cfg != c_cfg) c_open = false;
-      f.citem_begin = (int64_t)citem_unit.size() - (c_open ? 1 : 0);
-      for (int64_t u = 0; u < kb + kw; ++u) {
-        const int64_t c0 = (u < kb ? u : u - kb) * cw, w = u < kb ? f.words[0] : f.words[1];
-        const int64_t pages = ceil_div(std::min(cw, w - c0), (int64_t)kPageWords);
-        if (!c_open || c_pages + pages > kCountMaxPages || c_units == count_pack) {
-          citem_unit.push_back((int32_t)(cunits.size() / 2));
-          c_open = true;
-          c_pages = c_units = 0;
-        }
-        c_cfg = f.cfg;
-        cunits.push_back(G.f_begin + k);
-        cunits.push_back((int32_t)u);
-        c_pages += pages;
-        ++c_units;
-      }
-    }
-    // enumeration items: the representative block (exact path) in chunks of (modelled
-    // warp, instruction) pairs; then chunks of the remaining modelled warps, or, for the
-    // row walk, chunks of row slots as items of the row kernel
-    G.item_begin = items;
-    G.ritem_begin = ritems;
-    G.n0_items = (G.levels & 1) ? (int32_t)std::max<int64_t>(1, ceil_div((int64_t)G.n_rep * G.acc_count, block_pairs))
-                                : 0;
-    items += G.n0_items;
-    if (G.rows) ritems += ceil_div(grp_slots[g], chunk_rows());
-    else if (G.levels & 2) items += ceil_div(G.mw_end - G.mw_block, tune.chunk_warps);
+    cur.cf_hi = (int)hfld.size();
+    cur.grp_hi = ng;
+    cur.item_hi = items;
+    cur.ritem_hi = ritems;
+    cur.words = used;
+    if (ng > 0) passes.push_back(cur);
   }
-  cur.cf_hi = (int)hfld.size();
-  cur.grp_hi = ng;
-  cur.item_hi = items;
-  cur.ritem_hi = ritems;
-  const int64_t citems = (int64_t)citem_unit.size();
-  cur.citem_hi = citems;
-  cur.words = used;
-  if (ng > 0) passes.push_back(cur);
+  // counting: units (field, chunk) packed into items of consecutive units of one candidate
+  // and pass (at most kCountMaxPages pages and count_pack units), so that the many small
+  // block parts of a large batch do not each pay for a whole item.  Packing never crosses a
+  // candidate or a pass, so each such run of groups (a segment) packs on its own: first
+  // every segment counts its items and units, then a prefix sum places them, then every
+  // segment writes its units, items and its fields' bitmap offsets.
+  std::vector<int32_t> seg_start;   // first group of each segment
+  for (int g = 0; g < ng; ++g)
+    if (g == 0 || gpass[(size_t)g] != gpass[(size_t)g - 1] || hgrp[(size_t)g].cfg != hgrp[(size_t)g - 1].cfg)
+      seg_start.push_back(g);
+  const int64_t nseg = (int64_t)seg_start.size();
+  seg_start.push_back(ng);
+  std::vector<int64_t> seg_items((size_t)nseg + 1, 0), seg_units((size_t)nseg + 1, 0);
+  std::vector<int32_t> citem_unit_, cunits_;
+  auto pack = [&](int64_t sg, bool write, int64_t item0, int64_t unit0) {
+    bool open = false;
+    int64_t n_items = 0, n_units = 0, pages_in = 0, units_in = 0;
+    for (int g = seg_start[(size_t)sg]; g < seg_start[(size_t)sg + 1]; ++g) {
+      const DGroup &G = hgrp[(size_t)g];
+      int64_t o = gbase[(size_t)g];
+      for (int k = 0; k < G.f_count; ++k) {
+        const int32_t fi = G.f_begin + k;
+        DField &f = hfld[(size_t)fi];
+        if (write) {
+          const bool has_l = f.n_load > 0, has_s = f.n_store > 0;
+          for (int b = 0; b < N_BITMAPS; ++b) f.bm[b] = -1;
+          if (has_l) {
+            f.bm[BM_BL] = o; o += f.words[0];
+            f.bm[BM_W] = o; o += f.words[1];
+            f.bm[BM_Y] = o; o += f.words[1];
+            f.bm[BM_Z] = o; o += f.words[1];
+          }
+          if (has_s) {
+            f.bm[BM_BS] = o; o += f.words[0];
+            f.bm[BM_WS] = o; o += f.words[1];
+          }
+          // the row walk flags the pages it writes, so the counting reads only those
+          f.pg = -1;
+          if (G.rows) {
+            f.pg = o;
+            o += page_flag_words(f.words[0], f.words[1]);
+          }
+          f.item_begin = G.item_begin;
+          f.citem_begin = item0 + n_items - (open ? 1 : 0);
+        }
+        for_count_units(f, G.rows != 0, tune.count_words, [&](int64_t u, int64_t pages) {
+          if (!open || pages_in + pages > kCountMaxPages || units_in == count_pack) {
+            if (write) citem_unit_[(size_t)(item0 + n_items)] = (int32_t)(unit0 + n_units);
+            ++n_items;
+            open = true;
+            pages_in = units_in = 0;
+          }
+          if (write) {
+            cunits_[(size_t)(2 * (unit0 + n_units))] = fi;
+            cunits_[(size_t)(2 * (unit0 + n_units) + 1)] = (int32_t)u;
+          }
+          ++n_units;
+          pages_in += pages;
+          ++units_in;
+        });
+      }
+    }
+    seg_items[(size_t)sg] = n_items;
+    seg_units[(size_t)sg] = n_units;
+  };
+  parallel_chunks(nseg, 64, [&](int64_t lo, int64_t hi) {
+    for (int64_t sg = lo; sg < hi; ++sg) pack(sg, false, 0, 0);
+  });
+  std::vector<int64_t> seg_item0((size_t)nseg + 1, 0), seg_unit0((size_t)nseg + 1, 0);
+  for (int64_t sg = 0; sg < nseg; ++sg) {
+    seg_item0[(size_t)sg + 1] = seg_item0[(size_t)sg] + seg_items[(size_t)sg];
+    seg_unit0[(size_t)sg + 1] = seg_unit0[(size_t)sg] + seg_units[(size_t)sg];
+  }
+  const int64_t citems = seg_item0[(size_t)nseg], units = seg_unit0[(size_t)nseg];
+  citem_unit_.assign((size_t)citems, 0);
+  cunits_.assign((size_t)(2 * units), 0);
+  parallel_chunks(nseg, 64, [&](int64_t lo, int64_t hi) {
+    for (int64_t sg = lo; sg < hi; ++sg) pack(sg, true, seg_item0[(size_t)sg], seg_unit0[(size_t)sg]);
+  });
+  // each pass's counting items: those of its segments
+  for (size_t q = 0, sg = 0; q < passes.size(); ++q) {
+    while (sg < (size_t)nseg && gpass[(size_t)seg_start[sg]] < (int32_t)q) ++sg;
+    passes[q].citem_lo = seg_item0[sg];
+    size_t e = sg;
+    while (e < (size_t)nseg && gpass[(size_t)seg_start[e]] == (int32_t)q) ++e;
+    passes[q].citem_hi = seg_item0[e];
+    sg = e;
+  }
   item_begin_end = items;
   ritem_begin_end = ritems;
   citem_begin_end = citems;
   // owners of the items: [enumeration | row walk], then the counting items' first units
   // (with an end), then the counting units as (field, chunk) pairs
-  own.resize((size_t)(items + ritems + citems + 1) + cunits.size());
-  for (int g = 0; g < ng; ++g) {
-    const DGroup &G = hgrp[g];
-    const int64_t e1 = g + 1 < ng ? hgrp[g + 1].item_begin : items;
-    const int64_t r1 = g + 1 < ng ? hgrp[g + 1].ritem_begin : ritems;
-    std::fill(own.begin() + G.item_begin, own.begin() + e1, (int32_t)g);
-    std::fill(own.begin() + items + G.ritem_begin, own.begin() + items + r1, (int32_t)g);
-  }
-  std::copy(citem_unit.begin(), citem_unit.end(), own.begin() + items + ritems);
-  own[(size_t)(items + ritems + citems)] = (int32_t)(cunits.size() / 2);
-  std::copy(cunits.begin(), cunits.end(), own.begin() + items + ritems + citems + 1);
+  own.resize((size_t)(items + ritems + citems + 1) + cunits_.size());
+  parallel_chunks(ng, 1024, [&](int64_t lo, int64_t hi) {
+    for (int64_t g = lo; g < hi; ++g) {
+      const DGroup &G = hgrp[(size_t)g];
+      const int64_t e1 = g + 1 < ng ? hgrp[(size_t)g + 1].item_begin : items;
+      const int64_t r1 = g + 1 < ng ? hgrp[(size_t)g + 1].ritem_begin : ritems;
+      std::fill(own.begin() + G.item_begin, own.begin() + e1, (int32_t)g);
+      std::fill(own.begin() + items + G.ritem_begin, own.begin() + items + r1, (int32_t)g);
+    }
+  });
+  std::copy(citem_unit_.begin(), citem_unit_.end(), own.begin() + items + ritems);
+  own[(size_t)(items + ritems + citems)] = (int32_t)units;
+  std::copy(cunits_.begin(), cunits_.end(), own.begin() + items + ritems + citems + 1);
 }
 
 int ws_plan::upload_fields(cudaStream_t st) {
@@ -1800,8 +1880,20 @@ class HostPool {
   bool stop_ = false;
 };
 
+static void parallel_chunks(int64_t n, int64_t chunk, const std::function<void(int64_t, int64_t)> &fn) {
+  const int64_t nch = (n + chunk - 1) / chunk;
+  if (nch <= 1) {
+    if (n > 0) fn(0, n);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  HostPool::get().run((int)std::min<int64_t>(nch, HostPool::get().width()), [&](int) {
+    for (int64_t c = next.fetch_add(1); c < nch; c = next.fetch_add(1)) fn(c * chunk, std::min(n, (c + 1) * chunk));
+  });
+}
+
 static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld, const ws_access *acc,
-                        int n_acc, const ws_hw &hw, CompileArena &ca, std::vector<int> &status) {
+                        int n_acc, const ws_hw &hw, int64_t chunk_warps, CompileArena &ca, std::vector<int> &status) {
   ca.comp.assign(n_cfg, nullptr);
   status.assign(n_cfg, WS_OK);
   // chunks of consecutive candidates handed out dynamically; each thread keeps its fold
@@ -1838,11 +1930,24 @@ static void compile_all(const ws_config *cfgs, int n_cfg, const ws_field *fld, i
         ca.comp[(size_t)i] = &cc;
         status[i] = compile_config(cfgs[i], fld, n_fld, acc, n_acc, hw, cc, &cache, refs.data());
         if (status[i] != WS_OK) continue;
+        const DCfg &d = cc.d;
+        const size_t cr = 256;   // the smallest row-walk item
         for (size_t k = 0; k < cc.f.size(); ++k) {
-          cc.dsc_bytes += sizeof(DField) + sizeof(DGroup) + (size_t)(cc.acc_off[k + 1] - cc.acc_off[k]) * sizeof(DAcc) +
-                          (size_t)(cc.iv_off[k + 1] - cc.iv_off[k]) * sizeof(DIv);
+          const int64_t nacc = cc.acc_off[k + 1] - cc.acc_off[k], niv = cc.iv_off[k + 1] - cc.iv_off[k];
+          cc.dsc_bytes += sizeof(DField) + sizeof(DGroup) + (size_t)nacc * sizeof(DAcc) + (size_t)niv * sizeof(DIv);
           cc.need_sum += (size_t)cc.need_words[k] * 4;
           cc.need_max = std::max(cc.need_max, (size_t)cc.need_words[k] * 4);
+          // at most one enumeration item per chunk of modelled warps and one row-walk item per
+          // chunk of row slots, plus the representative block's items
+          const DField &f = cc.f[k];
+          cc.items_est += 3 + (size_t)d.lev_end[3] / (size_t)chunk_warps + (size_t)d.rows_slot_end[3] / cr +
+                          (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kPlainBlockPairs;
+          if (cc.fkey[k] == kNoShare) {
+            cc.n_acc_own += nacc;
+            cc.n_iv_own += niv;
+          } else {
+            cc.any_shared = true;
+          }
         }
       }
   });
@@ -1976,7 +2081,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   p->cfg_cf_begin.assign(n_cfg + 1, 0);
   CompileArena ca;
   std::vector<int> status;
-  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, ca, status);
+  compile_all(cfgs, n_cfg, fld, n_fld, acc, n_acc, *hw, std::max(1, p->tune.chunk_warps), ca, status);
   const std::vector<Compiled *> &comp = ca.comp;
   // scratch capacity: what the arena can give after the descriptors (a field, its access
   // and interval lists, at most one field group each)
@@ -1989,19 +2094,12 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   }
   dsc += (size_t)n_cfg * (sizeof(DCfg) + N_COUNTERS * 8 + sizeof(ws_result) + 8 + 4 + 4 + 4);
   {
-    // owner tables of the work items (4 bytes per item): at most one enumeration item per
-    // chunk of modelled warps and one row-walk item per chunk of row slots per field
-    // group, plus the representative block's items, plus one counting item per chunk of
-    // bitmap words per field
+    // owner tables of the work items (4 bytes per item): the candidates' enumeration and
+    // row-walk items (bounded as they compiled), plus one counting item per chunk of bitmap
+    // words per field
     size_t items = total_need / ((size_t)std::max(4, p->tune.count_words) * 4) + 1;
-    const size_t cw = (size_t)std::max(1, p->tune.chunk_warps), cr = 256;   // the smallest row-walk item
-    for (int i = 0; i < n_cfg; ++i) {
-      if (status[i] != WS_OK) continue;
-      const DCfg &d = comp[i]->d;
-      for (const DField &f : comp[i]->f)
-        items += 3 + (size_t)d.lev_end[3] / cw + (size_t)d.rows_slot_end[3] / cr +
-                 (size_t)d.wpb * (size_t)(f.n_load + f.n_store) / (size_t)kPlainBlockPairs;
-    }
+    for (int i = 0; i < n_cfg; ++i)
+      if (status[i] == WS_OK) items += comp[i]->items_est;
     // an item or counting unit takes at most three table entries (a counting unit: its
     // (field, chunk) pair and its item's first unit)
     dsc += 4 * 3 * items;
@@ -2018,12 +2116,23 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
   std::vector<int64_t> cf_off(n_cfg + 1, 0);
   for (int i = 0; i < n_cfg; ++i) cf_off[i + 1] = cf_off[i] + (status[i] == WS_OK ? (int64_t)comp[i]->f.size() : 0);
   const int64_t nf = cf_off[n_cfg];
+  // access / interval list positions: a candidate none of whose fields may be shared takes
+  // its lists in one block (the fields' positions inside it are laid out in parallel below);
+  // the others go field by field, and a field whose lists an earlier field holds shares them
   std::vector<int32_t> acc_b((size_t)nf), iv_b((size_t)nf);
   std::vector<char> owner((size_t)nf, 0);
+  std::vector<int64_t> own_acc_b((size_t)n_cfg, -1), own_iv_b((size_t)n_cfg, -1);
   int64_t na = 0, ni = 0;
   {
     std::unordered_map<uint64_t, int64_t> first;   // shared fold key -> owning field
-    for (int i = 0; i < n_cfg; ++i)
+    for (int i = 0; i < n_cfg; ++i) {
+      if (cf_off[i + 1] > cf_off[i] && !comp[i]->any_shared) {
+        own_acc_b[(size_t)i] = na;
+        own_iv_b[(size_t)i] = ni;
+        na += comp[i]->n_acc_own;
+        ni += comp[i]->n_iv_own;
+        continue;
+      }
       for (int64_t j = cf_off[i]; j < cf_off[i + 1]; ++j) {
         const size_t k = (size_t)(j - cf_off[i]);
         const uint64_t key = comp[i]->fkey[k];
@@ -2042,6 +2151,7 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
         na += comp[i]->acc_off[k + 1] - comp[i]->acc_off[k];
         ni += comp[i]->iv_off[k + 1] - comp[i]->iv_off[k];
       }
+    }
   }
   hacc.resize((size_t)na);
   hiv.resize((size_t)ni);
@@ -2070,6 +2180,15 @@ static void build_host(Plan *p, const ws_config *cfgs, int n_cfg, const ws_field
           continue;
         }
         Compiled &cc = *comp[i];
+        if (own_acc_b[(size_t)i] >= 0) {
+          // the candidate's lists in one block: field k's after those of fields 0 .. k-1
+          for (size_t k = 0; k < cc.f.size(); ++k) {
+            const size_t j = (size_t)cf_off[i] + k;
+            owner[j] = 1;
+            acc_b[j] = (int32_t)(own_acc_b[(size_t)i] + cc.acc_off[k]);
+            iv_b[j] = (int32_t)(own_iv_b[(size_t)i] + cc.iv_off[k]);
+          }
+        }
         for (size_t k = 0; k < cc.f.size(); ++k) {
           const size_t j = (size_t)cf_off[i] + k;
           DField f = cc.f[k];
