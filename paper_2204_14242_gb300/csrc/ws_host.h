@@ -117,6 +117,7 @@ struct ws_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   cudaStream_t upload_stream = nullptr;   // descriptor uploads of pipelined one-shot estimates
+  cudaStream_t lane_stream = nullptr;     // second lane of a pipelined estimate's parts
   // Scratch kept between one-shot estimates (ws_estimate_batch): the counting kernel leaves
   // it zeroed, so a later estimate needs no memset.  Held while `oneshot_mu` is; given back
   // to the arena when a plan or server of the context needs the room.

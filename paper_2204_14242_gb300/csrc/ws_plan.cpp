@@ -1759,13 +1759,16 @@ extern "C" int ws_create(ws_ctx **out, int device, void *arena, size_t arena_byt
   c->arena = new Arena(base, arena_bytes);
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->upload_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&c->upload_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->lane_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    for (cudaStream_t s : {c->stream, c->capture_stream, c->upload_stream, c->lane_stream})
+      if (s) cudaStreamDestroy(s);
     if (c->owns_arena) cudaFree(base);
     delete c->arena;
     delete c;
     return WS_ECUDA;
   }
-  for (int k = 0; k < 3; ++k) count_resource(RES_STREAM);
+  for (int k = 0; k < 4; ++k) count_resource(RES_STREAM);
   *out = c;
   return WS_OK;
 }
@@ -1784,9 +1787,11 @@ extern "C" int ws_destroy(ws_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   cudaStreamSynchronize(c->upload_stream);
+  cudaStreamSynchronize(c->lane_stream);
   cudaStreamDestroy(c->stream);
   cudaStreamDestroy(c->capture_stream);
   cudaStreamDestroy(c->upload_stream);
+  cudaStreamDestroy(c->lane_stream);
   if (c->owns_arena) cudaFree(c->arena->base);
   delete c->arena;
   delete c;
@@ -2577,10 +2582,11 @@ static constexpr int kPipeMin = 2048, kPipeParts = 6;
 static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
                               const ws_access *acc, int n_acc, const ws_hw *hw, ws_result *out, int32_t *order_out,
                               cudaStream_t st) {
-  // The parts run one after another on `st`, and the counting kernel leaves the bitmaps
-  // zeroed, so they share one scratch: the context's kept one, allocated (three fifths of
-  // the free arena) and zeroed by the first estimate that needs it, reused as it is by the
-  // next ones.  When another estimate holds it, each part takes its own share.
+  // The parts run in two lanes (below), each lane's parts one after another, and the
+  // counting kernel leaves the bitmaps zeroed, so a lane's parts share one scratch: half of
+  // the context's kept one, allocated (three fifths of the free arena) and zeroed by the
+  // first estimate that needs it, reused as it is by the next ones.  When another estimate
+  // holds it, each part takes its own share.
   std::unique_lock<std::mutex> kept(ctx->oneshot_mu, std::try_to_lock);
   if (!kept.owns_lock()) ctx_reclaim(ctx);
   const int parts = std::min(kPipeParts, n_cfg / kPipeMin);
@@ -2620,29 +2626,60 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
   }
   // without the shared scratch the parts share what the arena holds
   const size_t cap = rc == WS_OK && shared < 0 ? std::max<size_t>(ar.largest_free() / (size_t)(parts + 1), 16) : 0;
+  // Two lanes: even parts run on `st`, odd ones on the context's lane stream, so that one
+  // part's kernels fill the SMs its neighbour's tails leave idle.  With the shared scratch
+  // each lane takes its own half (a lane's parts run one after another, and the counting
+  // leaves their half zeroed); without it every part has its own scratch anyway.
+  const size_t half = (shared_bytes / 2) & ~(size_t)255;
+  const int lanes = ctx->lane_stream && parts >= 2 && (shared < 0 || half >= ((size_t)512 << 20)) ? 2 : 1;
+  auto new_event = [&](cudaEvent_t *ev) {
+    cudaError_t r = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (r == cudaSuccess) {
+      count_resource(RES_EVENT);
+      evs.push_back(*ev);
+    }
+    return r;
+  };
   if (rc == WS_OK && e == cudaSuccess) {
     const int32_t seg[2] = {0, n_cfg};
     e = cudaMemcpyAsync(b + o_seg, seg, sizeof(seg), cudaMemcpyHostToDevice, ctx->upload_stream);
   }
+  if (rc == WS_OK && e == cudaSuccess && lanes == 2) {
+    // the lane stream starts after the work the caller queued on `st`
+    cudaEvent_t fork;
+    e = new_event(&fork);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->lane_stream, fork, 0);
+  }
   for (int k = 0; k < parts && rc == WS_OK && e == cudaSuccess; ++k) {
     const int lo = (int)((int64_t)n_cfg * k / parts), hi = (int)((int64_t)n_cfg * (k + 1) / parts);
+    const cudaStream_t sk = lanes == 2 && (k & 1) ? ctx->lane_stream : st;
+    const int64_t sh = shared < 0 ? shared : lanes == 2 ? shared + (int64_t)((k & 1) * half) : shared;
+    const size_t sh_bytes = shared < 0 ? 0 : lanes == 2 ? half : shared_bytes;
     ws_plan *p = nullptr;
     rc = plan_create_impl(ctx, cfgs + lo, hi - lo, fld, n_fld, acc, n_acc, hw, nullptr, 0, nullptr, cap, &p,
-                          ctx->upload_stream, shared, shared_bytes);
+                          ctx->upload_stream, sh, sh_bytes);
     if (rc != WS_OK) break;
     plans.push_back(p);
     cudaEvent_t ev;
-    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    e = new_event(&ev);
     if (e != cudaSuccess) break;
-    count_resource(RES_EVENT);
-    evs.push_back(ev);
     e = cudaEventRecord(ev, ctx->upload_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sk, ev, 0);
     if (e != cudaSuccess) break;
-    rc = p->execute(WS_MODE_DIRECT, st);
+    rc = p->execute(WS_MODE_DIRECT, sk);
     if (rc != WS_OK) break;
     e = cudaMemcpyAsync(b + o_res + (size_t)lo * sizeof(ws_result), p->dev(p->d_results),
-                        (size_t)(hi - lo) * sizeof(ws_result), cudaMemcpyDeviceToDevice, st);
+                        (size_t)(hi - lo) * sizeof(ws_result), cudaMemcpyDeviceToDevice, sk);
+  }
+  if (lanes == 2 && !evs.empty()) {
+    // `st` continues (ranking, copies back) once the lane's parts are done; joined even
+    // after a failure, so that the synchronisation below covers both lanes
+    cudaEvent_t join;
+    const cudaError_t ej = new_event(&join);
+    const cudaError_t ej2 = ej == cudaSuccess ? cudaEventRecord(join, ctx->lane_stream) : ej;
+    const cudaError_t ej3 = ej2 == cudaSuccess ? cudaStreamWaitEvent(st, join, 0) : ej2;
+    if (e == cudaSuccess) e = ej3;
   }
   if (rc == WS_OK && e == cudaSuccess) {
     e = launch_keys((const ws_result *)(b + o_res), n_cfg, (double *)(b + o_keys), st);
@@ -2662,7 +2699,8 @@ static int estimate_pipelined(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, con
   }
   // everything issued so far must finish before the plans' memory goes back to the arena
   const cudaError_t e1 = cudaStreamSynchronize(st), e2 = cudaStreamSynchronize(ctx->upload_stream);
-  if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+  const cudaError_t e3 = lanes == 2 ? cudaStreamSynchronize(ctx->lane_stream) : cudaSuccess;
+  if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
   if (rc == WS_OK && e != cudaSuccess) {
     set_error(std::string("pipelined estimate: ") + cudaGetErrorString(e));
     rc = WS_ECUDA;
