@@ -290,8 +290,8 @@ int ws_plan_dry_run(const ws_config *cfgs, int n_cfg, const ws_field *fld, int n
  * plan would be replayed only once); results are identical in every mode.  The bitmap
  * scratch stays in the context's arena between calls (kept zeroed, so later calls skip
  * the clearing); ws_plan_create and ws_server_create take that room back when they run.
- * Batches of 4096 or more candidates (not WS_MODE_PLAIN) run as up to seven parts of growing
- * size whose descriptors compile and upload while earlier parts execute, alternately on `stream` and
+ * Batches of 4096 or more candidates (not WS_MODE_PLAIN) run as up to six parts whose
+ * descriptors compile and upload while earlier parts execute, alternately on `stream` and
  * on a second stream of the context (joined back into `stream`); results and ranking are
  * those of one plan.  Blocks until the results are on the host. */
 int ws_estimate_batch(ws_ctx *ctx, const ws_config *cfgs, int n_cfg, const ws_field *fld, int n_fld,
