@@ -321,7 +321,7 @@ struct CompileArena {
 struct FieldFold {
   int status = WS_OK;
   std::vector<DAcc> da;
-  std::vector<DIv> iv;     // merged load runs: those without a covering run first
+  std::vector<DIv> iv;     // merged load runs: without a covering run, covered from another z row, from their own
   int32_t n_iv_unc = 0;     // runs without a covering run
   int32_t n_iv_zc = 0;      // runs whose covering run lies in another z row (they come next)
   int16_t cov_dy = 0, cov_dz = 0;   // largest |row displacement| to a covering run
