@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests per served run (0 = no serving)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0,
+                    help="device memory the server may hold for its steps' bitmaps (from the arena)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the 25-point and LBM sub-records")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -441,7 +443,7 @@ def serve_stream(B, srv, reqs, arrays, times):
             "configs_per_s": cfg_done / (t1 - t0), "seconds": t1 - t0, "configs": cfg_done}
 
 
-def serving(B, W, ctx, hw, n_req, rate_hz, seed=20222):
+def serving(B, W, ctx, hw, n_req, rate_hz, seed=20222, budget_gb=150.0):
     """Capacity first (every request submitted at once), then the stream at `rate_hz` and at
     the rate that offers 70 % of the measured capacity; utilisation = offered / capacity."""
     reqs = W.request_stream(n_requests=n_req, seed=seed, rate_hz=rate_hz)
@@ -450,7 +452,11 @@ def serving(B, W, ctx, hw, n_req, rate_hz, seed=20222):
     mean_k = n_cfg / len(reqs)
     out = {"stream": f"{len(reqs)} requests (seed {seed}), {n_cfg} candidates, mean {mean_k:.1f} per request, "
                      "each a mixed-style stencil with 16-512 (shape, folding) candidates"}
-    srv = B.Server(ctx, hw, mem_budget=int(24 << 30), max_inflight=8, max_step_cfgs=4096, max_queue=1 << 16)
+    # a step holds one pass of its candidates' bitmaps (about 8 MB a mixed-style candidate), so
+    # the budget decides how many steps run at once: with room for several, the worker compiles
+    # the next step while earlier ones run
+    srv = B.Server(ctx, hw, mem_budget=int(budget_gb * (1 << 30)), max_inflight=8, max_step_cfgs=4096,
+                   max_queue=1 << 16)
     try:
         cap = serve_stream(B, srv, reqs, arrays, [0.0] * len(reqs))
         capacity = cap["configs_per_s"]
@@ -537,7 +543,8 @@ def main():
 
     served = None
     if args.serve_requests > 0 and rank == 0:
-        served = serving(B, W, ctx, hw, args.serve_requests, args.serve_rate)
+        served = serving(B, W, ctx, hw, args.serve_requests, args.serve_rate,
+                         budget_gb=min(args.serve_budget_gb, 0.75 * args.arena_gb))
 
     out = None
     if rank == 0:
