@@ -106,3 +106,23 @@ def test_batch_counting_items_add_up_per_candidate():
     cfgs = W.stencil_25pt_sweep(N=(160, 128, 96))[::15]
     want = sum(packed_items(units_of(c, hw, PAGED_CHUNK)) for c in cfgs)
     assert B.ws_plan_dry_run(cfgs, hw, scratch_bytes=8 << 30)["count_items"] == want
+
+
+def test_many_passes_keep_the_work_items():
+    """Cutting a batch into many scratch passes moves no work item while every candidate's
+    fields still fit one pass: passes break between candidates, and each candidate packs its
+    own counting units alone (the layout packs each run of one candidate within one pass on
+    its own, in parallel).  A pass smaller than a candidate splits its fields into several
+    groups, each packed apart."""
+    hw = W.a100()
+    cfgs = W.stencil_25pt_sweep(N=(160, 128, 96))[::15]   # 4.7 MB of bitmaps, at most 305 KB a candidate
+    want = sum(packed_items(units_of(c, hw, PAGED_CHUNK)) for c in cfgs)
+    one = B.ws_plan_dry_run(cfgs, hw, scratch_bytes=8 << 30)
+    many = B.ws_plan_dry_run(cfgs, hw, scratch_bytes=320 << 10)
+    assert one["passes"] == 1 and many["passes"] >= 10
+    for k in ("count_items", "enum_items", "row_items", "groups", "fields", "bitmap_bytes"):
+        assert many[k] == one[k], k
+    assert many["count_items"] == want
+    split = B.ws_plan_dry_run(cfgs, hw, scratch_bytes=256 << 10)
+    extra = split["groups"] - one["groups"]
+    assert extra > 0 and split["count_items"] == want + extra
