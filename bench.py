@@ -397,14 +397,17 @@ def serve_stream(B, srv, reqs, arrays, times):
     lock = threading.Lock()
 
     def poller():
+        # one bounded wait per sweep (on the oldest request), the others are only checked: a
+        # wait per outstanding request would make a sweep over thousands of them take seconds
+        # and hold back requests that finished long ago
         while not done.is_set() or submitted:
             with lock:
                 items = list(submitted.items())
             if not items:
                 time.sleep(0.0002)
                 continue
-            for rid, t_arr in items:
-                rc, res, order = srv.poll(rid, timeout_us=200)
+            for i, (rid, t_arr) in enumerate(items):
+                rc, res, order = srv.poll(rid, timeout_us=200 if i == 0 else 0)
                 if rc == B.WS_EAGAIN:
                     continue
                 now = time.perf_counter()
