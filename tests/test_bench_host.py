@@ -56,3 +56,63 @@ def test_clock_summary():
     c = bench.summarize_clocks(lines)
     assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert bench.summarize_clocks([]) is None
+
+
+class _FakeServer:
+    """Serves requests one after another, `service` seconds each (newest first when `lifo`,
+    as a server that runs whole steps may finish later requests first); poll waits up to its
+    timeout for a request that is not done, as ws_server_poll does."""
+
+    WS_EAGAIN = -3
+
+    def __init__(self, service=20e-6, lifo=False, n=0):
+        import threading
+        import time
+        self.service, self.lifo, self.n_all = service, lifo, n
+        self.due, self.n, self.free_at, self.mu = {}, 0, 0.0, threading.Lock()
+        self.t0 = time.perf_counter()
+
+    def submit(self, arrays=None):
+        import time
+        with self.mu:
+            self.n += 1
+            if self.lifo:   # all submitted at once: request i is served (n_all - i)-th
+                self.due[self.n] = self.t0 + (self.n_all - self.n + 1) * self.service
+            else:
+                self.free_at = max(self.free_at, time.perf_counter()) + self.service
+                self.due[self.n] = self.free_at
+            return self.n
+
+    def poll(self, rid, timeout_us=0):
+        import time
+        with self.mu:
+            due = self.due[rid]
+        now = time.perf_counter()
+        if now < due:
+            if timeout_us <= 0 or now + timeout_us * 1e-6 < due:
+                time.sleep(timeout_us * 1e-6)
+                return self.WS_EAGAIN, None, None
+            time.sleep(due - now)
+        with self.mu:
+            del self.due[rid]
+        return 0, [0] * 10, None
+
+
+def test_served_requests_are_collected_as_they_finish():
+    """The serving harness (submitter and poller threads) against a server stand-in: every
+    request comes back once, with its candidates, whether the requests finish in submission
+    order or newest first, in about the time the stand-in takes to serve them."""
+    class B:
+        WS_EAGAIN = _FakeServer.WS_EAGAIN
+        WsError = RuntimeError
+    n = 5000
+    r = bench.serve_stream(B, _FakeServer(), [None] * n, [None] * n, [0.0] * n)
+    assert r["ok"] == n and r["configs"] == 10 * n
+    assert r["seconds"] < 0.5, r
+    # newest first: the oldest requests finish last
+    r = bench.serve_stream(B, _FakeServer(lifo=True, n=n), [None] * n, [None] * n, [0.0] * n)
+    assert r["ok"] == n and r["p50_ms"] < 250.0, r
+    # a paced stream below the service rate: every request back soon after its arrival
+    m = 200
+    r = bench.serve_stream(B, _FakeServer(), [None] * m, [None] * m, [i * 1e-3 for i in range(m)])
+    assert r["ok"] == m and r["p50_ms"] < 10.0, r
